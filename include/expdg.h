@@ -1,0 +1,200 @@
+/*
+ * expdg.h - C-ABI of libexpdg, the GB300 (sm_103a) exponential-DG hot path.
+ *
+ * Method: Kang & Bui-Thanh, "A scalable exponential-DG approach for
+ * nonlinear conservation laws" (arXiv 2011.01316).
+ *
+ *   dq/dt = R(q) = L q + N(q)                                  (Sec. 2.3, Eq. splitDG)
+ *   R: nodal DG right-hand side with Lax-Friedrichs fluxes      (Sec. 2.2, 3.1, 3.2)
+ *   L = L(q^n): the DG operator of the linear flux A(q^n) q,
+ *       stabilisation frozen at q^n                              (Sec. 2.2, Eq. linearflux)
+ *   phi-sums  sum_i phi_i(dt L) c_i  by Krylov on an augmented
+ *       matrix                                                   (Sec. 2.3)
+ *   EPI2 / EXPRB32 / EXPRB42 steps                               (Sec. 5 footnotes)
+ *
+ * Conventions for every call:
+ *   - State arrays are FP64 in the canonical layout q[f][e][n]: field f
+ *     (Burgers: u; Euler: rho, rho u_1..rho u_dim, rho E), element
+ *     e = ex + ne[0]*(ey + ne[1]*ez), LGL node n = i + (p+1)*(j + (p+1)*k)
+ *     with i along x.  Length expdg_num_unknowns().
+ *   - Pointers may be host or device memory (detected per call).  Host
+ *     buffers are copied through library-owned device memory; the copies
+ *     are part of the call.  The caller owns every buffer it passes; the
+ *     library owns all device memory it allocates (released by
+ *     expdg_destroy).
+ *   - Calls are synchronous with respect to the host: they return after the
+ *     work on the context's stream has finished.
+ *   - A non-zero status leaves outputs unspecified and records a message
+ *     for expdg_last_error().  A context is not thread-safe; distinct
+ *     contexts are independent.
+ */
+#ifndef EXPDG_H
+#define EXPDG_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+  EXPDG_OK = 0,
+  EXPDG_EINVAL = 1,        /* bad argument or configuration */
+  EXPDG_ENOMEM = 2,        /* device allocation failed */
+  EXPDG_EKRYLOV = 3,       /* no Krylov convergence within max_substeps halvings */
+  EXPDG_ENONPHYSICAL = 4,  /* Euler state with rho <= 0 or p <= 0 (never clipped) */
+  EXPDG_ETIMEOUT = 5,      /* a bounded device wait gave up */
+  EXPDG_ECUDA = 6          /* CUDA runtime error; see expdg_last_error() */
+} expdg_status;
+
+typedef enum { EXPDG_BURGERS = 1, EXPDG_EULER = 2 } expdg_equation;
+typedef enum { EXPDG_EPI2 = 2, EXPDG_EXPRB32 = 3, EXPDG_EXPRB42 = 4 } expdg_scheme;
+
+/* Arithmetic of the operator applies (R, Jv) and of the Arnoldi process.
+ *   EXPDG_FP64:  everything in FP64 (reference form).
+ *   EXPDG_MIXED: R and Jv in FP32 (FP32 accumulation); Arnoldi inner
+ *                products, orthogonalisation, phi(H) and the solution update
+ *                in FP64. */
+typedef enum { EXPDG_FP64 = 0, EXPDG_MIXED = 1 } expdg_precision;
+
+typedef struct {
+  int dim;              /* 1, 2 or 3 (Burgers: 1) */
+  int p;                /* polynomial order, 1..EXPDG_MAX_ORDER */
+  int ne[3];            /* elements per direction (unused entries ignored) */
+  double lo[3], hi[3];  /* periodic box [lo_d, hi_d] */
+  int eq;               /* expdg_equation */
+  double gamma;         /* ratio of specific heats (Euler) */
+  int scheme;           /* expdg_scheme */
+  int prec;             /* expdg_precision */
+  double krylov_tol;    /* accept when err <= tol * beta (see expdg_phi) */
+  int m_max;            /* Krylov dimension limit, <= EXPDG_MAX_KRYLOV */
+  int m_step;           /* error checks at m = m_step, 2 m_step, ... */
+  int max_substeps;     /* limit on rejected (halved) Krylov attempts per solve */
+} expdg_config;
+
+#define EXPDG_MAX_ORDER 8
+#define EXPDG_MAX_KRYLOV 64
+#define EXPDG_MAX_PHI 3      /* phi_0 .. phi_3 */
+
+typedef struct {
+  int krylov_iters;       /* Arnoldi iterations (operator applies), incl. rejected attempts */
+  int substeps;           /* accepted Krylov sub-steps */
+  int rejected;           /* attempts that reached m_max without acceptance */
+  int jv_applies;         /* L(q~) v applies */
+  int residual_applies;   /* R(q) applies */
+  double err_est;         /* largest error estimate of an accepted sub-step */
+} expdg_stats;
+
+/* Krylov decision trace: one record per accepted sub-step, in order, for all
+ * Krylov solves of a step (solve = 0 for the first phi-sum of the step, 1 for
+ * the second stage of EXPRB32/EXPRB42). */
+typedef struct {
+  int solve;
+  int m;          /* Krylov dimension used */
+  double sigma;   /* sub-step length (fraction of the solve's interval) */
+  double eta;     /* tail scale of the augmented matrix */
+} expdg_trace_entry;
+
+typedef struct expdg_ctx expdg_ctx;
+
+/* Default configuration: 2D Euler, p = 4, 64 x 64 on [0,10]^2, EPI2, FP64,
+ * tol 1e-10, m_max 64, m_step 5, max_substeps 32. */
+void expdg_default_config(expdg_config* cfg);
+
+/* Create a context (validates cfg, builds LGL tables, allocates the device
+ * state, Krylov basis and scratch on the current CUDA device).
+ * Returns EXPDG_EINVAL for a bad configuration, EXPDG_ENOMEM / EXPDG_ECUDA on
+ * device failures; *out is NULL then. */
+expdg_status expdg_create(const expdg_config* cfg, expdg_ctx** out);
+void expdg_destroy(expdg_ctx* ctx);
+
+/* Run the context's work on this cudaStream_t (NULL = the legacy default
+ * stream).  The stream must belong to the context's device. */
+expdg_status expdg_set_stream(expdg_ctx* ctx, void* cuda_stream);
+
+/* Sizes: fields m, elements, nodes per element (p+1)^dim, unknowns m*Ne*Np. */
+size_t expdg_num_unknowns(const expdg_ctx* ctx);
+int expdg_num_fields(const expdg_ctx* ctx);
+size_t expdg_num_elements(const expdg_ctx* ctx);
+int expdg_nodes_per_element(const expdg_ctx* ctx);
+
+/* Physical LGL node coordinates, host buffer xyz[dim][Ne][Np] (FP64):
+ * x_d = lo_d + h_d (e_d + (r_i + 1)/2), LGL nodes r of order p. */
+expdg_status expdg_node_coords(const expdg_ctx* ctx, double* xyz);
+
+/* R(q): the DG right-hand side (Sec. 2.2, Eq. EXPO-SemiDiscretizedForm_ode;
+ * strong collocated LGL form; LF flux with lambda = max(|u|) for Burgers,
+ * Sec. 3.1, and max(|u.n| + a) for Euler, Sec. 5.1).  q, r: canonical layout.
+ * In EXPDG_MIXED the arithmetic is FP32 (inputs and outputs stay FP64). */
+expdg_status expdg_residual(expdg_ctx* ctx, const double* q, double* r);
+
+/* L(qt) v: the frozen-flux linear DG operator (Sec. 2.2, Eq. linearflux, with
+ * (u~u)* of Sec. 3.1 / (A~q)* of Sec. 3.2; LF coefficient from qt).  In
+ * EXPDG_MIXED the arithmetic is FP32. */
+expdg_status expdg_jv(expdg_ctx* ctx, const double* qt, const double* v, double* out);
+
+/* out = sum_{i=0}^{P} phi_i(tau L(qt)) c_i with c = [c_0, ..., c_P] (P <= 3;
+ * c[i] may be NULL for a zero vector), Sec. 2.3 Eq.
+ * linear_combination_of_phifunctions with the dt^i folded into c_i.
+ * Augmented-matrix Arnoldi with error checks every m_step, sub-stepping on
+ * failure (see DESIGN for the exact rules).  If replay != NULL, the
+ * nreplay records (all with solve == 0) are followed instead of deciding;
+ * otherwise, if trace != NULL, up to trace_cap accepted sub-steps are written
+ * there and *ntrace is set. */
+expdg_status expdg_phi(expdg_ctx* ctx, const double* qt, double tau, const double* const* c, int P,
+                       double* out, expdg_stats* stats,
+                       const expdg_trace_entry* replay, int nreplay,
+                       expdg_trace_entry* trace, int trace_cap, int* ntrace);
+
+/* One exponential step of the configured scheme from time-independent state
+ * q (in place): EPI2 q += dt phi_1(dt L) R(q) (Sec. 5.1 footnote), EXPRB32 /
+ * EXPRB42 (Sec. 5.1 / 5.2 footnotes).  replay / trace as in expdg_phi, with
+ * the solve index distinguishing the two stages. */
+expdg_status expdg_step(expdg_ctx* ctx, double* q, double dt, expdg_stats* stats,
+                        const expdg_trace_entry* replay, int nreplay,
+                        expdg_trace_entry* trace, int trace_cap, int* ntrace);
+
+/* nsteps steps of size dt (in place); stats accumulate over the steps. */
+expdg_status expdg_advance(expdg_ctx* ctx, double* q, double dt, int nsteps, expdg_stats* stats);
+
+/* Kernel classes of the hot path, for profiling. */
+typedef enum {
+  EXPDG_K_RESIDUAL = 0,  /* R(q) */
+  EXPDG_K_JV = 1,        /* L(qt) v, incl. the augmented-matrix tail */
+  EXPDG_K_DOTS = 2,      /* Gram-Schmidt inner products */
+  EXPDG_K_UPDATE = 3,    /* Gram-Schmidt updates (+ norm) */
+  EXPDG_K_PHI = 4,       /* exp(H_m) e_1 of the projected matrix */
+  EXPDG_K_COMBINE = 5,   /* w = beta V_m y (+ state update) */
+  EXPDG_K_VECTOR = 6,    /* linear combinations, norms, conversions, start vector */
+  EXPDG_K_COUNT = 7
+} expdg_kernel_class;
+
+typedef struct {
+  long long launches;    /* kernel launches of this class */
+  double ms;             /* summed device time (CUDA events around each launch; 0 unless profiling) */
+  double bytes;          /* algorithmic bytes moved: the minimum global-memory reads + writes the
+                            launch's operation needs (neighbour traces and re-reads counted 0) */
+} expdg_kernel_prof;
+
+/* Turn per-launch CUDA-event timing on or off and clear the counters.  Launch
+ * counts and algorithmic bytes are always accumulated; durations only while
+ * profiling is on (each launch is then bracketed by two events on the
+ * context's stream). */
+expdg_status expdg_profile_enable(expdg_ctx* ctx, int on);
+
+/* Copy the per-class counters accumulated since the last enable/reset into
+ * out[EXPDG_K_COUNT] (synchronises the stream).  If reset != 0 the counters
+ * restart from zero. */
+expdg_status expdg_profile_get(expdg_ctx* ctx, expdg_kernel_prof* out, int reset);
+
+/* Message of the last failing call on this context ("" if none). */
+const char* expdg_last_error(const expdg_ctx* ctx);
+
+/* Library version string. */
+const char* expdg_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* EXPDG_H */

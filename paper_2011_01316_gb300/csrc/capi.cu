@@ -1,0 +1,783 @@
+// C-ABI of libexpdg: contexts, the Krylov phi-sum driver and the exponential
+// steps (paper Sec. 2.3 and the EPI2 / EXPRB32 / EXPRB42 footnotes of Sec. 5).
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <string>
+#include <vector>
+
+#include "common.cuh"
+#include "tables.h"
+
+using namespace expdg;
+
+struct expdg_ctx {
+  expdg_config cfg{};
+  int dev = 0;
+  cudaStream_t stream = nullptr;
+  bool ff = false;  // mixed form: FP32 operators, float-float Krylov storage
+  int M = 0, NP = 0;
+  size_t nelem = 0, N = 0, ld = 0;
+  Tab tab{};
+  DGArgs mesh{};  // mesh fields filled, pointers empty
+  double lgl_r[MAXP + 1]{}, lgl_w[MAXP + 1]{};
+  // FP64 buffers
+  double* d_q = nullptr;   // state (copy of a host state, or scratch)
+  double* d_q2 = nullptr;  // stage state
+  double* d_t2 = nullptr;  // FP64 scratch (state differences)
+  double* d_in = nullptr;  // API input scratch
+  double* d_out = nullptr; // API output scratch
+  // FP32 buffers (mixed form)
+  float* d_q32 = nullptr;
+  float* d_q32b = nullptr;
+  // vectors in the Krylov storage form
+  Vec c[EXPDG_MAX_PHI + 1]{};
+  Vec b[EXPDG_MAX_PHI + 1]{};
+  Vec w{}, rn{}, t1{}, t3{};
+  Basis U{};
+  KState* ks = nullptr;
+  void* part = nullptr;
+  KState* h_ks = nullptr;  // pinned mirror (host-visible block only is refreshed)
+  std::vector<void*> allocs;
+  std::string err;
+  // profiling
+  bool prof_on = false;
+  expdg_kernel_prof prof[EXPDG_K_COUNT]{};
+  std::vector<cudaEvent_t> ev_pool;
+  size_t ev_used = 0;
+  struct Rec {
+    int cls;
+    cudaEvent_t a, b;
+  };
+  std::vector<Rec> recs;
+};
+
+namespace {
+
+const char* kVersion = "libexpdg 0.1 (sm_103a)";
+
+expdg_status fail(expdg_ctx* ctx, expdg_status st, const std::string& msg) {
+  if (ctx) ctx->err = msg;
+  return st;
+}
+
+#define CU(ctx, call)                                                                       \
+  do {                                                                                      \
+    cudaError_t e_ = (call);                                                                \
+    if (e_ != cudaSuccess)                                                                  \
+      return fail(ctx, EXPDG_ECUDA, std::string(#call) + ": " + cudaGetErrorString(e_));   \
+  } while (0)
+
+template <typename T>
+cudaError_t dalloc(expdg_ctx* ctx, T** p, size_t n) {
+  void* q = nullptr;
+  cudaError_t e = cudaMalloc(&q, n * sizeof(T) > 0 ? n * sizeof(T) : 16);
+  if (e != cudaSuccess) return e;
+  ctx->allocs.push_back(q);
+  e = cudaMemset(q, 0, n * sizeof(T) > 0 ? n * sizeof(T) : 16);
+  *p = static_cast<T*>(q);
+  return e;
+}
+
+cudaError_t alloc_vec(expdg_ctx* ctx, Vec* v, size_t n) {
+  *v = Vec{};
+  if (ctx->ff) {
+    cudaError_t e = dalloc(ctx, &v->h, n);
+    if (e != cudaSuccess) return e;
+    return dalloc(ctx, &v->l, n);
+  }
+  return dalloc(ctx, &v->d, n);
+}
+
+bool is_device_ptr(const void* p) {
+  if (p == nullptr) return false;
+  cudaPointerAttributes at{};
+  if (cudaPointerGetAttributes(&at, p) != cudaSuccess) {
+    cudaGetLastError();
+    return false;
+  }
+  return at.type == cudaMemoryTypeDevice || at.type == cudaMemoryTypeManaged;
+}
+
+Vec null_vec() { return Vec{}; }
+Vec dvec(double* p) {
+  Vec v{};
+  v.d = p;
+  return v;
+}
+
+cudaError_t launch_dg(expdg_ctx* ctx, bool linear, const DGArgs& a) {
+  const int p = ctx->cfg.p;
+  const int eq = ctx->cfg.eq;
+  switch (ctx->cfg.dim) {
+    case 1: return launch_dg_1d(linear, ctx->ff, eq, p, a, ctx->tab, ctx->stream);
+    case 2: return launch_dg_2d(linear, ctx->ff, eq, p, a, ctx->tab, ctx->stream);
+    case 3: return launch_dg_3d(linear, ctx->ff, eq, p, a, ctx->tab, ctx->stream);
+  }
+  return cudaErrorInvalidValue;
+}
+
+cudaEvent_t pool_event(expdg_ctx* ctx) {
+  if (ctx->ev_used == ctx->ev_pool.size()) {
+    cudaEvent_t e;
+    if (cudaEventCreate(&e) != cudaSuccess) return nullptr;
+    ctx->ev_pool.push_back(e);
+  }
+  return ctx->ev_pool[ctx->ev_used++];
+}
+
+// Count (and, when profiling, time) one kernel launch of class cls.
+template <class F>
+cudaError_t run(expdg_ctx* ctx, int cls, double bytes, F&& launch) {
+  ctx->prof[cls].launches++;
+  ctx->prof[cls].bytes += bytes;
+  if (!ctx->prof_on) return launch();
+  cudaEvent_t a = pool_event(ctx), b = pool_event(ctx);
+  if (!a || !b) return cudaErrorMemoryAllocation;
+  cudaEventRecord(a, ctx->stream);
+  cudaError_t e = launch();
+  cudaEventRecord(b, ctx->stream);
+  ctx->recs.push_back(expdg_ctx::Rec{cls, a, b});
+  return e;
+}
+
+#define RUN(ctx, cls, bytes, call) CU(ctx, run(ctx, cls, (double)(bytes), [&]() { return (call); }))
+
+void set_alpha(DGArgs& a, double alpha) {
+  a.alpha = alpha;
+  a.alpha_h = (float)alpha;
+  a.alpha_l = (float)(alpha - (double)a.alpha_h);
+}
+
+// R(q) -> out.  q: FP64 state on device; mixed form converts it to FP32 first
+// (into q32).  out: Krylov storage form.
+cudaError_t residual_into(expdg_ctx* ctx, const double* q, float* q32, Vec out, double alpha) {
+  DGArgs a = ctx->mesh;
+  set_alpha(a, alpha);
+  a.status = &ctx->ks->status;
+  if (ctx->ff) {
+    cudaError_t e = run(ctx, EXPDG_K_VECTOR, 12.0 * ctx->N, [&]() { return launch_to_f32(q32, q, ctx->N, ctx->stream); });
+    if (e != cudaSuccess) return e;
+    a.q = q32;
+    a.out_h = out.h;
+    a.out_l = out.l;
+  } else {
+    a.q = q;
+    a.out = out.d;
+  }
+  return run(ctx, EXPDG_K_RESIDUAL, (ctx->ff ? 12.0 : 16.0) * ctx->N, [&]() { return launch_dg(ctx, false, a); });
+}
+
+// L(qt) v -> out (no augmentation).  qt_T: linearisation state in compute form
+// (double* or float*), v_T: input in compute form.
+cudaError_t jv_into(expdg_ctx* ctx, const void* qt_T, const void* v_T, Vec out, double alpha) {
+  DGArgs a = ctx->mesh;
+  set_alpha(a, alpha);
+  a.q = qt_T;
+  a.v = v_T;
+  if (ctx->ff) {
+    a.out_h = out.h;
+    a.out_l = out.l;
+  } else {
+    a.out = out.d;
+  }
+  return run(ctx, EXPDG_K_JV, (ctx->ff ? 16.0 : 24.0) * ctx->N, [&]() { return launch_dg(ctx, true, a); });
+}
+
+expdg_status readback(expdg_ctx* ctx) {
+  const size_t off = offsetof(KState, red);
+  CU(ctx, cudaMemcpyAsync(reinterpret_cast<char*>(ctx->h_ks) + off, reinterpret_cast<char*>(ctx->ks) + off,
+                          sizeof(KState) - off, cudaMemcpyDeviceToHost, ctx->stream));
+  CU(ctx, cudaStreamSynchronize(ctx->stream));
+  if (ctx->h_ks->status & 1) return fail(ctx, EXPDG_ENONPHYSICAL, "non-physical state (rho <= 0 or p <= 0)");
+  return EXPDG_OK;
+}
+
+double tail_scale(double nrm) {
+  if (!(nrm > 0.0) || !std::isfinite(nrm)) return 1.0;
+  return std::ldexp(1.0, -(int)std::lround(std::log2(nrm)));
+}
+
+struct Replay {
+  const expdg_trace_entry* e = nullptr;
+  int n = 0;
+};
+
+// w = sum_{i=0}^P phi_i(tau L(qt)) c_i  (c_i in ctx->c, has[i] false: zero).
+// On the final sub-step the combination writes fin_out = fin_base + w instead
+// of ctx->w (fin_out null: result left in ctx->w).
+expdg_status phi_solve(expdg_ctx* ctx, const void* qt_T, double tau, const bool* has, int P, Vec fin_base,
+                       Vec fin_out, int solve_id, const Replay& rp, expdg_stats* st,
+                       std::vector<expdg_trace_entry>* trace) {
+  const size_t N = ctx->N, n_aug = N + P;
+  const bool F = ctx->ff;
+  const cudaStream_t s = ctx->stream;
+  const expdg_config& cfg = ctx->cfg;
+  // w(0) = c_0
+  if (has[0]) {
+    Vec x[1] = {ctx->c[0]};
+    double a1[1] = {1.0};
+    RUN(ctx, EXPDG_K_VECTOR, 16.0 * N, launch_lincomb(F, ctx->w, 1, x, a1, N, s));
+  } else {
+    if (F) {
+      CU(ctx, cudaMemsetAsync(ctx->w.h, 0, N * sizeof(float), s));
+      CU(ctx, cudaMemsetAsync(ctx->w.l, 0, N * sizeof(float), s));
+    } else {
+      CU(ctx, cudaMemsetAsync(ctx->w.d, 0, N * sizeof(double), s));
+    }
+  }
+  std::vector<const expdg_trace_entry*> mine;
+  if (rp.e)
+    for (int k = 0; k < rp.n; ++k)
+      if (rp.e[k].solve == solve_id) mine.push_back(&rp.e[k]);
+  size_t krep = 0;
+  double sv = 0.0, sigma = 1.0;
+  int rejected = 0;
+  while (sv < 1.0) {
+    int m_fix = 0;
+    double eta = 1.0;
+    const bool replay = rp.e != nullptr;
+    if (replay) {
+      if (krep >= mine.size()) return fail(ctx, EXPDG_EINVAL, "replay trace ended before the solve finished");
+      sigma = mine[krep]->sigma;
+      m_fix = mine[krep]->m;
+      eta = mine[krep]->eta;
+      ++krep;
+      if (m_fix < 0 || m_fix > cfg.m_max) return fail(ctx, EXPDG_EINVAL, "replayed m out of range");
+    }
+    // b_i = sigma^i sum_{j=0}^{P-i} s^j/j! c_{i+j}
+    for (int i = 1; i <= P; ++i) {
+      Vec xs[EXPDG_MAX_PHI + 1];
+      double as[EXPDG_MAX_PHI + 1];
+      int nx = 0;
+      double fact = 1.0;
+      for (int j = 0; j <= P - i; ++j) {
+        if (j > 0) fact *= j;
+        xs[nx] = has[i + j] ? ctx->c[i + j] : null_vec();
+        as[nx] = std::pow(sigma, i) * std::pow(sv, j) / fact;
+        ++nx;
+      }
+      RUN(ctx, EXPDG_K_VECTOR, 8.0 * (nx + 1) * N, launch_lincomb(F, ctx->b[i], nx, xs, as, N, s));
+    }
+    {
+      Vec xs[EXPDG_MAX_PHI + 1];
+      xs[0] = ctx->w;
+      for (int i = 1; i <= P; ++i) xs[i] = ctx->b[i];
+      RUN(ctx, EXPDG_K_VECTOR, 8.0 * (P + 1) * N, launch_norms(F, ctx->ks, ctx->part, P + 1, xs, N, s));
+    }
+    expdg_status rs = readback(ctx);
+    if (rs != EXPDG_OK) return rs;
+    if (!replay) {
+      double mx = 0.0;
+      for (int i = 1; i <= P; ++i) mx = std::fmax(mx, std::sqrt(ctx->h_ks->red[i]));
+      eta = tail_scale(mx);
+    }
+    const double beta = std::sqrt(ctx->h_ks->red[0] + (P > 0 ? 1.0 / (eta * eta) : 0.0));
+    const bool last = (sv + sigma >= 1.0);
+    if (beta == 0.0) {  // P == 0 and c_0 == 0: the result is zero
+      sv += sigma;
+      st->substeps++;
+      if (trace) trace->push_back(expdg_trace_entry{solve_id, 0, sigma, eta});
+      continue;
+    }
+    RUN(ctx, EXPDG_K_VECTOR, 16.0 * N, launch_start(F, ctx->ks, ctx->U, ctx->w, N, P, eta, beta, s));
+    const int limit = replay ? m_fix : cfg.m_max;
+    bool accepted = false;
+    int m_acc = 0;
+    double err = 0.0;
+    for (int j = 0; j < limit; ++j) {
+      DGArgs a = ctx->mesh;
+      set_alpha(a, sigma * tau);
+      a.q = qt_T;
+      const Vec vj = ctx->U.at(j), vo = ctx->U.at(j + 1);
+      if (F) {
+        a.v = vj.h;
+        a.vs_h = &ctx->ks->sh[j];
+        a.vs_l = &ctx->ks->sl[j];
+        a.out_h = vo.h;
+        a.out_l = vo.l;
+      } else {
+        a.v = vj.d;
+        a.vs_d = &ctx->ks->s[j];
+        a.out = vo.d;
+      }
+      if (P > 0) {
+        a.paug = P;
+        a.eta = eta;
+        if (F) {
+          a.tail_h = vj.h + N;
+          a.tail_l = vj.l + N;
+          a.out_tail_h = vo.h + N;
+          a.out_tail_l = vo.l + N;
+        } else {
+          a.tail_d = vj.d + N;
+          a.out_tail_d = vo.d + N;
+        }
+        for (int i = 1; i <= P; ++i) {
+          a.W_d[i] = ctx->b[i].d;
+          a.W_h[i] = ctx->b[i].h;
+          a.W_l[i] = ctx->b[i].l;
+        }
+      }
+      RUN(ctx, EXPDG_K_JV, (F ? 16.0 : 24.0) * N, launch_dg(ctx, true, a));
+      const int J = j + 1;
+      const double vb = 8.0 * (double)n_aug;  // one vector: FP64 or float-float pair
+      RUN(ctx, EXPDG_K_DOTS, (J + 1) * vb, launch_dots(F, ctx->ks, ctx->part, ctx->U, J, n_aug, false, s));
+      RUN(ctx, EXPDG_K_UPDATE, (J + 2) * vb, launch_update(F, ctx->ks, ctx->part, ctx->U, J, n_aug, false, s));
+      RUN(ctx, EXPDG_K_DOTS, (J + 1) * vb, launch_dots(F, ctx->ks, ctx->part, ctx->U, J, n_aug, true, s));
+      RUN(ctx, EXPDG_K_UPDATE, (J + 2) * vb, launch_update(F, ctx->ks, ctx->part, ctx->U, J, n_aug, true, s));
+      st->krylov_iters++;
+      st->jv_applies++;
+      const int m = J;
+      const bool check = replay ? (m == m_fix) : (m % cfg.m_step == 0 || m == cfg.m_max);
+      if (!check) continue;
+      RUN(ctx, EXPDG_K_PHI, 8.0 * m * m, launch_phi(ctx->ks, m, beta, cfg.krylov_tol, replay ? 1 : 0, s));
+      rs = readback(ctx);
+      if (rs != EXPDG_OK) return rs;
+      if (ctx->h_ks->accept) {
+        accepted = true;
+        m_acc = ctx->h_ks->m_eff;
+        err = ctx->h_ks->err;
+        break;
+      }
+    }
+    if (!accepted) {
+      st->rejected++;
+      if (++rejected > cfg.max_substeps)
+        return fail(ctx, EXPDG_EKRYLOV, "Krylov solve did not converge within the sub-step budget");
+      sigma *= 0.5;
+      continue;
+    }
+    if (last && fin_out.d != nullptr) {
+      RUN(ctx, EXPDG_K_COMBINE, 8.0 * (m_acc + 2) * N, launch_combine(F, ctx->ks, ctx->U, fin_base, fin_out, N, s));
+    } else {
+      RUN(ctx, EXPDG_K_COMBINE, 8.0 * (m_acc + 1) * N, launch_combine(F, ctx->ks, ctx->U, null_vec(), ctx->w, N, s));
+    }
+    sv += sigma;
+    st->substeps++;
+    st->err_est = std::fmax(st->err_est, err);
+    if (trace) trace->push_back(expdg_trace_entry{solve_id, m_acc, sigma, eta});
+    if (!replay) {
+      if (m_acc <= cfg.m_max / 2) sigma *= 2.0;
+      sigma = std::fmin(sigma, 1.0 - sv);
+    }
+  }
+  return EXPDG_OK;
+}
+
+expdg_status validate(const expdg_config* c) {
+  if (!c) return EXPDG_EINVAL;
+  if (c->dim < 1 || c->dim > 3) return EXPDG_EINVAL;
+  if (c->p < 1 || c->p > EXPDG_MAX_ORDER) return EXPDG_EINVAL;
+  if (c->eq != EXPDG_BURGERS && c->eq != EXPDG_EULER) return EXPDG_EINVAL;
+  if (c->eq == EXPDG_BURGERS && c->dim != 1) return EXPDG_EINVAL;
+  for (int d = 0; d < c->dim; ++d) {
+    if (c->ne[d] < 1) return EXPDG_EINVAL;
+    if (!(c->hi[d] > c->lo[d])) return EXPDG_EINVAL;
+  }
+  if (c->eq == EXPDG_EULER && !(c->gamma > 1.0)) return EXPDG_EINVAL;
+  if (c->scheme != EXPDG_EPI2 && c->scheme != EXPDG_EXPRB32 && c->scheme != EXPDG_EXPRB42) return EXPDG_EINVAL;
+  if (c->prec != EXPDG_FP64 && c->prec != EXPDG_MIXED) return EXPDG_EINVAL;
+  if (!(c->krylov_tol > 0.0)) return EXPDG_EINVAL;
+  if (c->m_max < 1 || c->m_max > EXPDG_MAX_KRYLOV) return EXPDG_EINVAL;
+  if (c->m_step < 1) return EXPDG_EINVAL;
+  if (c->max_substeps < 0) return EXPDG_EINVAL;
+  return EXPDG_OK;
+}
+
+// Copy a caller array (host or device) of n doubles into device memory;
+// returns the device pointer to use (the caller's own if already on device).
+const double* in_dev(expdg_ctx* ctx, const double* p, double* scratch, size_t n, cudaError_t* e) {
+  *e = cudaSuccess;
+  if (p == nullptr || is_device_ptr(p)) return p;
+  *e = cudaMemcpyAsync(scratch, p, n * sizeof(double), cudaMemcpyHostToDevice, ctx->stream);
+  return scratch;
+}
+
+// One step of the configured scheme, q (device FP64) in place.
+expdg_status step_dev(expdg_ctx* ctx, double* q, double dt, const Replay& rp, expdg_stats* st,
+                      std::vector<expdg_trace_entry>* trace) {
+  const bool F = ctx->ff;
+  const size_t N = ctx->N;
+  const cudaStream_t s = ctx->stream;
+  CU(ctx, cudaMemsetAsync(&ctx->ks->status, 0, sizeof(int), s));
+  // Linearisation state in compute form (the residual below fills q32 from q).
+  const void* qt_T = F ? static_cast<const void*>(ctx->d_q32) : static_cast<const void*>(q);
+  bool has[EXPDG_MAX_PHI + 1] = {false, false, false, false};
+  const int scheme = ctx->cfg.scheme;
+  if (scheme == EXPDG_EPI2) {
+    CU(ctx, residual_into(ctx, q, ctx->d_q32, ctx->c[1], dt));
+    st->residual_applies++;
+    has[1] = true;
+    return phi_solve(ctx, qt_T, dt, has, 1, dvec(q), dvec(q), 0, rp, st, trace);
+  }
+  // EXPRB32 / EXPRB42 share: R^n, stage 1, D_{n,2} = R(q2) - R^n - L (q2 - q)
+  CU(ctx, residual_into(ctx, q, ctx->d_q32, ctx->rn, 1.0));
+  st->residual_applies++;
+  const double a1 = (scheme == EXPDG_EXPRB32) ? dt : 0.75 * dt;
+  {
+    Vec x[1] = {ctx->rn};
+    double a[1] = {a1};
+    RUN(ctx, EXPDG_K_VECTOR, 16.0 * N, launch_lincomb(F, ctx->c[1], 1, x, a, N, s));
+  }
+  has[1] = true;
+  expdg_status r = phi_solve(ctx, qt_T, a1, has, 1, dvec(q), dvec(ctx->d_q2), 0, rp, st, trace);
+  if (r != EXPDG_OK) return r;
+  // t1 = R(q2)
+  CU(ctx, residual_into(ctx, ctx->d_q2, ctx->d_q32b, ctx->t1, 1.0));
+  st->residual_applies++;
+  // t2 = q2 - q (FP64), t3 = L(q) t2
+  {
+    Vec x[2] = {dvec(ctx->d_q2), dvec(q)};
+    double a[2] = {1.0, -1.0};
+    RUN(ctx, EXPDG_K_VECTOR, 24.0 * N, launch_lincomb(false, dvec(ctx->d_t2), 2, x, a, N, s));
+  }
+  if (F) {
+    RUN(ctx, EXPDG_K_VECTOR, 12.0 * N, launch_to_f32(ctx->d_q32b, ctx->d_t2, N, s));
+    CU(ctx, jv_into(ctx, ctx->d_q32, ctx->d_q32b, ctx->t3, 1.0));
+  } else {
+    CU(ctx, jv_into(ctx, q, ctx->d_t2, ctx->t3, 1.0));
+  }
+  st->jv_applies++;
+  const double cD = (scheme == EXPDG_EXPRB32) ? 2.0 * dt : (32.0 / 9.0) * dt;
+  {
+    Vec x[3] = {ctx->t1, ctx->rn, ctx->t3};
+    double a[3] = {cD, -cD, -cD};
+    RUN(ctx, EXPDG_K_VECTOR, 32.0 * N, launch_lincomb(F, ctx->c[3], 3, x, a, N, s));
+  }
+  bool has2[EXPDG_MAX_PHI + 1] = {false, false, false, true};
+  if (scheme == EXPDG_EXPRB32) {
+    // q^{n+1} = q2 + 2 dt phi_3(dt L) D
+    return phi_solve(ctx, qt_T, dt, has2, 3, dvec(ctx->d_q2), dvec(q), 1, rp, st, trace);
+  }
+  // EXPRB42: q^{n+1} = q + dt phi_1(dt L) R^n + 32/9 dt phi_3(dt L) D
+  {
+    Vec x[1] = {ctx->rn};
+    double a[1] = {dt};
+    RUN(ctx, EXPDG_K_VECTOR, 16.0 * N, launch_lincomb(F, ctx->c[1], 1, x, a, N, s));
+  }
+  has2[1] = true;
+  return phi_solve(ctx, qt_T, dt, has2, 3, dvec(q), dvec(q), 1, rp, st, trace);
+}
+
+void write_trace(const std::vector<expdg_trace_entry>& tr, expdg_trace_entry* out, int cap, int* n) {
+  if (n) *n = (int)tr.size();
+  if (!out) return;
+  for (int k = 0; k < (int)tr.size() && k < cap; ++k) out[k] = tr[k];
+}
+
+}  // namespace
+
+extern "C" {
+
+const char* expdg_version(void) { return kVersion; }
+
+void expdg_default_config(expdg_config* c) {
+  if (!c) return;
+  std::memset(c, 0, sizeof(*c));
+  c->dim = 2;
+  c->p = 4;
+  c->ne[0] = c->ne[1] = c->ne[2] = 64;
+  for (int d = 0; d < 3; ++d) {
+    c->lo[d] = 0.0;
+    c->hi[d] = 10.0;
+  }
+  c->eq = EXPDG_EULER;
+  c->gamma = 1.4;
+  c->scheme = EXPDG_EPI2;
+  c->prec = EXPDG_FP64;
+  c->krylov_tol = 1e-10;
+  c->m_max = 64;
+  c->m_step = 5;
+  c->max_substeps = 32;
+}
+
+expdg_status expdg_create(const expdg_config* cfg, expdg_ctx** out) {
+  if (!out) return EXPDG_EINVAL;
+  *out = nullptr;
+  if (validate(cfg) != EXPDG_OK) return EXPDG_EINVAL;
+  expdg_ctx* ctx = new expdg_ctx();
+  ctx->cfg = *cfg;
+  for (int d = cfg->dim; d < 3; ++d) {
+    ctx->cfg.ne[d] = 1;
+    ctx->cfg.lo[d] = 0.0;
+    ctx->cfg.hi[d] = 1.0;
+  }
+  cudaError_t e = cudaGetDevice(&ctx->dev);
+  if (e != cudaSuccess) {
+    delete ctx;
+    return EXPDG_ECUDA;
+  }
+  ctx->ff = (cfg->prec == EXPDG_MIXED);
+  const int p = cfg->p;
+  ctx->M = (cfg->eq == EXPDG_BURGERS) ? 1 : cfg->dim + 2;
+  ctx->NP = 1;
+  for (int d = 0; d < cfg->dim; ++d) ctx->NP *= (p + 1);
+  ctx->nelem = 1;
+  for (int d = 0; d < cfg->dim; ++d) ctx->nelem *= (size_t)cfg->ne[d];
+  if (ctx->nelem > (size_t)0x7fffffff / (size_t)ctx->NP) {
+    delete ctx;
+    return EXPDG_EINVAL;
+  }
+  ctx->N = (size_t)ctx->M * ctx->nelem * ctx->NP;
+  ctx->ld = ((ctx->N + EXPDG_MAX_PHI + 63) / 64) * 64;  // 256-byte aligned vectors
+  double D[(MAXP + 1) * (MAXP + 1)];
+  build_lgl(p, ctx->lgl_r, ctx->lgl_w, D);
+  for (int k = 0; k < (p + 1) * (p + 1); ++k) ctx->tab.D[k] = D[k];
+  ctx->tab.lift = 1.0 / ctx->lgl_w[0];
+  DGArgs& m = ctx->mesh;
+  std::memset(&m, 0, sizeof(m));
+  for (int d = 0; d < 3; ++d) {
+    m.ne[d] = ctx->cfg.ne[d];
+    m.two_over_h[d] = 2.0 / ((ctx->cfg.hi[d] - ctx->cfg.lo[d]) / ctx->cfg.ne[d]);
+  }
+  m.nelem = (int)ctx->nelem;
+  m.gamma = cfg->gamma;
+  m.stride = ctx->nelem * ctx->NP;
+
+  const size_t N = ctx->N;
+#define ALLOC(call)                         \
+  do {                                      \
+    if ((e = (call)) != cudaSuccess) {      \
+      expdg_destroy(ctx);                   \
+      cudaGetLastError();                   \
+      return e == cudaErrorMemoryAllocation ? EXPDG_ENOMEM : EXPDG_ECUDA; \
+    }                                       \
+  } while (0)
+  ALLOC(dalloc(ctx, &ctx->d_q, N));
+  ALLOC(dalloc(ctx, &ctx->d_q2, N));
+  ALLOC(dalloc(ctx, &ctx->d_t2, N));
+  ALLOC(dalloc(ctx, &ctx->d_in, N));
+  ALLOC(dalloc(ctx, &ctx->d_out, N));
+  if (ctx->ff) {
+    ALLOC(dalloc(ctx, &ctx->d_q32, N));
+    ALLOC(dalloc(ctx, &ctx->d_q32b, N));
+  }
+  for (int i = 0; i <= EXPDG_MAX_PHI; ++i) {
+    ALLOC(alloc_vec(ctx, &ctx->c[i], N));
+    ALLOC(alloc_vec(ctx, &ctx->b[i], N));
+  }
+  ALLOC(alloc_vec(ctx, &ctx->w, N));
+  ALLOC(alloc_vec(ctx, &ctx->rn, N));
+  ALLOC(alloc_vec(ctx, &ctx->t1, N));
+  ALLOC(alloc_vec(ctx, &ctx->t3, N));
+  ctx->U.ld = ctx->ld;
+  const size_t nb = ctx->ld * (size_t)(cfg->m_max + 1);
+  if (ctx->ff) {
+    ALLOC(dalloc(ctx, &ctx->U.h, nb));
+    ALLOC(dalloc(ctx, &ctx->U.l, nb));
+  } else {
+    ALLOC(dalloc(ctx, &ctx->U.d, nb));
+  }
+  ALLOC(dalloc(ctx, &ctx->ks, 1));
+  double* part = nullptr;
+  ALLOC(dalloc(ctx, &part, reduction_scratch_entries()));
+  ctx->part = part;
+  void* hk = nullptr;
+  ALLOC(cudaMallocHost(&hk, sizeof(KState)));
+  ctx->h_ks = static_cast<KState*>(hk);
+  std::memset(ctx->h_ks, 0, sizeof(KState));
+#undef ALLOC
+  *out = ctx;
+  return EXPDG_OK;
+}
+
+void expdg_destroy(expdg_ctx* ctx) {
+  if (!ctx) return;
+  if (ctx->stream) cudaStreamSynchronize(ctx->stream);
+  for (void* p : ctx->allocs) cudaFree(p);
+  for (cudaEvent_t e : ctx->ev_pool) cudaEventDestroy(e);
+  if (ctx->h_ks) cudaFreeHost(ctx->h_ks);
+  delete ctx;
+}
+
+expdg_status expdg_set_stream(expdg_ctx* ctx, void* stream) {
+  if (!ctx) return EXPDG_EINVAL;
+  ctx->stream = static_cast<cudaStream_t>(stream);
+  return EXPDG_OK;
+}
+
+size_t expdg_num_unknowns(const expdg_ctx* ctx) { return ctx ? ctx->N : 0; }
+int expdg_num_fields(const expdg_ctx* ctx) { return ctx ? ctx->M : 0; }
+size_t expdg_num_elements(const expdg_ctx* ctx) { return ctx ? ctx->nelem : 0; }
+int expdg_nodes_per_element(const expdg_ctx* ctx) { return ctx ? ctx->NP : 0; }
+
+expdg_status expdg_node_coords(const expdg_ctx* ctx, double* xyz) {
+  if (!ctx || !xyz) return EXPDG_EINVAL;
+  const expdg_config& c = ctx->cfg;
+  const int p = c.p, n1 = p + 1;
+  for (int d = 0; d < c.dim; ++d) {
+    const double h = (c.hi[d] - c.lo[d]) / c.ne[d];
+    for (size_t e = 0; e < ctx->nelem; ++e) {
+      size_t t = e;
+      int ec[3] = {0, 0, 0};
+      for (int k = 0; k < c.dim; ++k) {
+        ec[k] = (int)(t % c.ne[k]);
+        t /= c.ne[k];
+      }
+      for (int n = 0; n < ctx->NP; ++n) {
+        int ii[3] = {0, 0, 0};
+        int tn = n;
+        for (int k = 0; k < c.dim; ++k) {
+          ii[k] = tn % n1;
+          tn /= n1;
+        }
+        xyz[((size_t)d * ctx->nelem + e) * ctx->NP + n] = c.lo[d] + h * (ec[d] + (ctx->lgl_r[ii[d]] + 1.0) / 2.0);
+      }
+    }
+  }
+  return EXPDG_OK;
+}
+
+expdg_status expdg_residual(expdg_ctx* ctx, const double* q, double* r) {
+  if (!ctx || !q || !r) return fail(ctx, EXPDG_EINVAL, "null argument");
+  cudaError_t e;
+  const double* qd = in_dev(ctx, q, ctx->d_in, ctx->N, &e);
+  CU(ctx, e);
+  const bool rdev = is_device_ptr(r);
+  double* rd = rdev ? r : ctx->d_out;
+  CU(ctx, cudaMemsetAsync(&ctx->ks->status, 0, sizeof(int), ctx->stream));
+  if (ctx->ff) {
+    CU(ctx, residual_into(ctx, qd, ctx->d_q32, ctx->t1, 1.0));
+    RUN(ctx, EXPDG_K_VECTOR, 16.0 * ctx->N, launch_ff_to_f64(rd, ctx->t1, ctx->N, ctx->stream));
+  } else {
+    CU(ctx, residual_into(ctx, qd, nullptr, dvec(rd), 1.0));
+  }
+  if (!rdev) CU(ctx, cudaMemcpyAsync(r, rd, ctx->N * sizeof(double), cudaMemcpyDeviceToHost, ctx->stream));
+  return readback(ctx);
+}
+
+expdg_status expdg_jv(expdg_ctx* ctx, const double* qt, const double* v, double* out) {
+  if (!ctx || !qt || !v || !out) return fail(ctx, EXPDG_EINVAL, "null argument");
+  cudaError_t e;
+  const double* qd = in_dev(ctx, qt, ctx->d_in, ctx->N, &e);
+  CU(ctx, e);
+  const double* vd = in_dev(ctx, v, ctx->d_t2, ctx->N, &e);
+  CU(ctx, e);
+  const bool odev = is_device_ptr(out);
+  double* od = odev ? out : ctx->d_out;
+  if (ctx->ff) {
+    RUN(ctx, EXPDG_K_VECTOR, 12.0 * ctx->N, launch_to_f32(ctx->d_q32, qd, ctx->N, ctx->stream));
+    RUN(ctx, EXPDG_K_VECTOR, 12.0 * ctx->N, launch_to_f32(ctx->d_q32b, vd, ctx->N, ctx->stream));
+    CU(ctx, jv_into(ctx, ctx->d_q32, ctx->d_q32b, ctx->t1, 1.0));
+    RUN(ctx, EXPDG_K_VECTOR, 16.0 * ctx->N, launch_ff_to_f64(od, ctx->t1, ctx->N, ctx->stream));
+  } else {
+    CU(ctx, jv_into(ctx, qd, vd, dvec(od), 1.0));
+  }
+  if (!odev) CU(ctx, cudaMemcpyAsync(out, od, ctx->N * sizeof(double), cudaMemcpyDeviceToHost, ctx->stream));
+  CU(ctx, cudaStreamSynchronize(ctx->stream));
+  return EXPDG_OK;
+}
+
+expdg_status expdg_phi(expdg_ctx* ctx, const double* qt, double tau, const double* const* c, int P, double* out,
+                       expdg_stats* stats, const expdg_trace_entry* replay, int nreplay, expdg_trace_entry* trace,
+                       int trace_cap, int* ntrace) {
+  if (!ctx || !qt || !out || P < 0 || P > EXPDG_MAX_PHI) return fail(ctx, EXPDG_EINVAL, "bad argument");
+  const size_t N = ctx->N;
+  const cudaStream_t s = ctx->stream;
+  cudaError_t e;
+  const double* qd = in_dev(ctx, qt, ctx->d_q, N, &e);
+  CU(ctx, e);
+  bool has[EXPDG_MAX_PHI + 1] = {false, false, false, false};
+  for (int i = 0; i <= P; ++i) {
+    if (!c || !c[i]) continue;
+    has[i] = true;
+    const double* ci = in_dev(ctx, c[i], ctx->d_in, N, &e);
+    CU(ctx, e);
+    if (ctx->ff) {
+      RUN(ctx, EXPDG_K_VECTOR, 16.0 * N, launch_f64_to_ff(ctx->c[i], ci, N, s));
+    } else {
+      CU(ctx, cudaMemcpyAsync(ctx->c[i].d, ci, N * sizeof(double), cudaMemcpyDeviceToDevice, s));
+    }
+  }
+  const void* qt_T = qd;
+  if (ctx->ff) {
+    RUN(ctx, EXPDG_K_VECTOR, 12.0 * N, launch_to_f32(ctx->d_q32, qd, N, s));
+    qt_T = ctx->d_q32;
+  }
+  const bool odev = is_device_ptr(out);
+  double* od = odev ? out : ctx->d_out;
+  expdg_stats st{};
+  std::vector<expdg_trace_entry> tr;
+  Replay rp;
+  rp.e = replay;
+  rp.n = nreplay;
+  expdg_status r = phi_solve(ctx, qt_T, tau, has, P, null_vec(), dvec(od), 0, rp, &st, &tr);
+  if (r != EXPDG_OK) return r;
+  if (!odev) CU(ctx, cudaMemcpyAsync(out, od, N * sizeof(double), cudaMemcpyDeviceToHost, s));
+  CU(ctx, cudaStreamSynchronize(s));
+  if (stats) *stats = st;
+  write_trace(tr, trace, trace_cap, ntrace);
+  return EXPDG_OK;
+}
+
+expdg_status expdg_step(expdg_ctx* ctx, double* q, double dt, expdg_stats* stats, const expdg_trace_entry* replay,
+                        int nreplay, expdg_trace_entry* trace, int trace_cap, int* ntrace) {
+  if (!ctx || !q) return fail(ctx, EXPDG_EINVAL, "null argument");
+  const size_t N = ctx->N;
+  const bool qdev = is_device_ptr(q);
+  double* qd = qdev ? q : ctx->d_q;
+  if (!qdev) CU(ctx, cudaMemcpyAsync(qd, q, N * sizeof(double), cudaMemcpyHostToDevice, ctx->stream));
+  expdg_stats st{};
+  std::vector<expdg_trace_entry> tr;
+  Replay rp;
+  rp.e = replay;
+  rp.n = nreplay;
+  expdg_status r = step_dev(ctx, qd, dt, rp, &st, &tr);
+  if (r != EXPDG_OK) return r;
+  if (!qdev) CU(ctx, cudaMemcpyAsync(q, qd, N * sizeof(double), cudaMemcpyDeviceToHost, ctx->stream));
+  r = readback(ctx);
+  if (r != EXPDG_OK) return r;
+  if (stats) *stats = st;
+  write_trace(tr, trace, trace_cap, ntrace);
+  return EXPDG_OK;
+}
+
+expdg_status expdg_advance(expdg_ctx* ctx, double* q, double dt, int nsteps, expdg_stats* stats) {
+  if (!ctx || !q || nsteps < 0) return fail(ctx, EXPDG_EINVAL, "bad argument");
+  const size_t N = ctx->N;
+  const bool qdev = is_device_ptr(q);
+  double* qd = qdev ? q : ctx->d_q;
+  if (!qdev) CU(ctx, cudaMemcpyAsync(qd, q, N * sizeof(double), cudaMemcpyHostToDevice, ctx->stream));
+  expdg_stats st{};
+  Replay rp;
+  for (int k = 0; k < nsteps; ++k) {
+    expdg_status r = step_dev(ctx, qd, dt, rp, &st, nullptr);
+    if (r != EXPDG_OK) return r;
+  }
+  if (!qdev) CU(ctx, cudaMemcpyAsync(q, qd, N * sizeof(double), cudaMemcpyDeviceToHost, ctx->stream));
+  expdg_status r = readback(ctx);
+  if (r != EXPDG_OK) return r;
+  if (stats) *stats = st;
+  return EXPDG_OK;
+}
+
+expdg_status expdg_profile_enable(expdg_ctx* ctx, int on) {
+  if (!ctx) return EXPDG_EINVAL;
+  CU(ctx, cudaStreamSynchronize(ctx->stream));
+  ctx->prof_on = on != 0;
+  for (auto& p : ctx->prof) p = expdg_kernel_prof{0, 0.0, 0.0};
+  ctx->recs.clear();
+  ctx->ev_used = 0;
+  return EXPDG_OK;
+}
+
+expdg_status expdg_profile_get(expdg_ctx* ctx, expdg_kernel_prof* out, int reset) {
+  if (!ctx || !out) return EXPDG_EINVAL;
+  CU(ctx, cudaStreamSynchronize(ctx->stream));
+  for (const auto& r : ctx->recs) {
+    float ms = 0.f;
+    CU(ctx, cudaEventElapsedTime(&ms, r.a, r.b));
+    ctx->prof[r.cls].ms += ms;
+  }
+  ctx->recs.clear();
+  ctx->ev_used = 0;
+  for (int k = 0; k < EXPDG_K_COUNT; ++k) out[k] = ctx->prof[k];
+  if (reset)
+    for (auto& p : ctx->prof) p = expdg_kernel_prof{0, 0.0, 0.0};
+  return EXPDG_OK;
+}
+
+const char* expdg_last_error(const expdg_ctx* ctx) { return ctx ? ctx->err.c_str() : "null context"; }
+
+}  // extern "C"

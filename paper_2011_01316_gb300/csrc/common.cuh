@@ -1,0 +1,144 @@
+// Internal declarations shared by the libexpdg translation units.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <cstddef>
+#include <cstdint>
+
+#include "../../include/expdg.h"
+
+namespace expdg {
+
+constexpr int MAXP = EXPDG_MAX_ORDER;
+constexpr int MMAX = EXPDG_MAX_KRYLOV;
+constexpr int RED_BLOCKS = 4 * 152;   // grid of the reduction kernels (deterministic partial order)
+constexpr int RED_THREADS = 256;
+constexpr int DOT_CHUNK = 8;          // basis vectors per block row in the multi-dot kernel
+
+// Reference-element data handed to the DG kernels by value (kernel parameter
+// space is constant memory; the kernels copy D into shared memory).
+struct Tab {
+  double D[(MAXP + 1) * (MAXP + 1)];  // row-major l_j'(r_i) for the context's order
+  double lift;                        // 1 / w_0
+};
+
+// Arguments of one DG operator apply.  T is the compute and input type
+// (double: FP64 form; float: mixed form, output as float-float pairs).
+//   residual: out = alpha * R(q)
+//   linear:   out = alpha * vs * L(q) v  +  aug,   vs = device scalar (or 1)
+//   aug (Krylov augmented matrix, only when paug > 0):
+//     out      += eta * sum_{k=1}^{paug} (vs * tail[k-1]) * W[paug+1-k]
+//     out_tail  = J (vs * tail)   (upper shift; written by block 0)
+struct DGArgs {
+  const void* q;         // T*: residual state, or linearisation state
+  const void* v;         // T*: linear input vector (top part)
+  const double* vs_d;    // FP64 form: device scalar multiplying v (nullptr: 1)
+  const float* vs_h;     // mixed form: float-float device scalar (nullptr: 1)
+  const float* vs_l;
+  double alpha;
+  float alpha_h;         // alpha as float-float (mixed form)
+  float alpha_l;
+  double* out;           // FP64 form output
+  float* out_h;          // mixed form output (float-float)
+  float* out_l;
+  int paug;
+  double eta;
+  const double* tail_d;  // tail of the input basis vector (paug entries) or nullptr
+  const float* tail_h;
+  const float* tail_l;
+  const double* W_d[EXPDG_MAX_PHI + 1];  // W[i] = b_i, i = 1..paug
+  const float* W_h[EXPDG_MAX_PHI + 1];
+  const float* W_l[EXPDG_MAX_PHI + 1];
+  double* out_tail_d;
+  float* out_tail_h;
+  float* out_tail_l;
+  int* status;           // bit 0: non-physical state met (residual)
+  int ne[3];
+  int nelem;
+  double two_over_h[3];
+  double gamma;
+  size_t stride;         // unknowns per field = nelem * Np
+};
+
+// A vector in the FP64 form (d) or the float-float form (h + l).
+struct Vec {
+  double* d;
+  float* h;
+  float* l;
+};
+
+// Krylov basis: vector i at d + i*ld (FP64 form) or h/l + i*ld (float-float).
+struct Basis {
+  double* d;
+  float* h;
+  float* l;
+  size_t ld;
+  __host__ __device__ Vec at(int i) const {
+    Vec v;
+    v.d = d ? d + (size_t)i * ld : nullptr;
+    v.h = h ? h + (size_t)i * ld : nullptr;
+    v.l = l ? l + (size_t)i * ld : nullptr;
+    return v;
+  }
+};
+
+// Device-resident scalars of one Krylov solve.  H(i, j) = H[j * (MMAX + 1) + i].
+// The fields from `red` to the end are read back by the host as one block.
+struct KState {
+  double H[(MMAX + 1) * MMAX];
+  double s[MMAX + 2];       // v_i = s_i u_i (u_i stored, unnormalised)
+  float sh[MMAX + 2];       // s_i as float-float
+  float sl[MMAX + 2];
+  double coef[MMAX + 1];    // coefficients of the running Gram-Schmidt update (multiply u_i)
+  double ycoef[MMAX + 1];   // beta * y_i * s_i for the final combination
+  unsigned int counter;     // last-block ticket of the reduction kernels
+  unsigned int pad0;
+  // ---- host-visible block ----
+  double red[8];            // results of the norms kernel
+  double wnorm0;            // ||A_hat v_j|| before orthogonalisation
+  double err;               // error estimate at the last check
+  double norm1;             // 1-norm of the last H_m
+  int accept;               // set by the phi kernel
+  int m_eff;                // Krylov dimension used by the last phi kernel
+  int breakdown_at;         // first m with a happy breakdown (0: none)
+  int squarings;            // scaling exponent used by the last phi kernel
+  int status;               // bit 0: non-physical state met by a residual
+  int pad1;
+};
+
+// ---- DG operators (dg_1d.cu, dg_2d.cu, dg_3d.cu) ----
+// fp32: mixed form (float inputs, float-float output).  Returns the launch error.
+cudaError_t launch_dg_1d(bool linear, bool fp32, int eq, int p, const DGArgs& a, const Tab& t, cudaStream_t s);
+cudaError_t launch_dg_2d(bool linear, bool fp32, int eq, int p, const DGArgs& a, const Tab& t, cudaStream_t s);
+cudaError_t launch_dg_3d(bool linear, bool fp32, int eq, int p, const DGArgs& a, const Tab& t, cudaStream_t s);
+
+// ---- Krylov and vector kernels (krylov.cu); ff selects the float-float form ----
+// partial-sum buffer entries needed by the reduction kernels
+size_t reduction_scratch_entries();
+// out = sum_k a[k] x[k] (k < nx <= 5; x[k] with null pointers counts as 0), n entries
+cudaError_t launch_lincomb(bool use_ff, Vec out, int nx, const Vec* x, const double* a, size_t n, cudaStream_t s);
+// ks->red[k] = ||x_k||^2 (k < nx <= 5; null x[k] gives 0), n entries each
+cudaError_t launch_norms(bool use_ff, KState* ks, void* part, int nx, const Vec* x, size_t n, cudaStream_t s);
+// format conversions (these use the FP64 pipe; only at API and step boundaries)
+cudaError_t launch_to_f32(float* out, const double* x, size_t n, cudaStream_t s);
+cudaError_t launch_f64_to_ff(Vec out, const double* x, size_t n, cudaStream_t s);
+cudaError_t launch_ff_to_f64(double* out, Vec x, size_t n, cudaStream_t s);
+// Arnoldi start: u_0 = [b0; e_P / eta] (b0 null: zero top), s_0 = 1/beta; clears the Krylov scalars.
+cudaError_t launch_start(bool use_ff, KState* ks, Basis U, Vec b0, size_t N, int P, double eta, double beta,
+                         cudaStream_t s);
+// Classical Gram-Schmidt building blocks; w is basis slot J, vectors have n_aug entries:
+//   dots  (second = false): h_iJ-1 = s_i <u_i, w> (i < J), coef_i = h s_i, wnorm0 = ||w||
+//   dots  (second = true) : g_i = s_i <u_i, w>, H(i, J-1) += g_i, coef_i = g_i s_i
+//   update: w -= sum_i coef_i u_i; with finish = true also H(J, J-1) = ||w||,
+//           s_J = 1/||w|| (0 on a happy breakdown, recorded in breakdown_at).
+cudaError_t launch_dots(bool use_ff, KState* ks, void* part, Basis U, int J, size_t n_aug, bool second, cudaStream_t s);
+cudaError_t launch_update(bool use_ff, KState* ks, void* part, Basis U, int J, size_t n_aug, bool finish,
+                          cudaStream_t s);
+// FP64 phi kernel: E = exp(H_m) (Taylor-18 scaling and squaring), y = E e_1, error estimate,
+// acceptance (forced when force_accept), ycoef_i = beta y_i s_i.
+cudaError_t launch_phi(KState* ks, int m, double beta, double tol, int force_accept, cudaStream_t s);
+// out = base + sum_{i < m_eff} ycoef_i u_i (first N entries; base may be null).
+// out and base may each be FP64 (d) or float-float (h, l).
+cudaError_t launch_combine(bool use_ff, const KState* ks, Basis U, Vec base, Vec out, size_t N, cudaStream_t s);
+
+}  // namespace expdg

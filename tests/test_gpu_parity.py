@@ -1,0 +1,247 @@
+"""Parity of the CUDA path (through the C-ABI) with the FP64 CPU oracle.
+
+Tolerances (relative L2 over all unknowns):
+  FP64 form, operators (R, Jv):     1e-12  (rounding order only)
+  FP64 form, phi-sums and steps:    1e-11  (decisions replayed from the oracle's trace)
+  mixed form (FP32 R/Jv, float-float Krylov, FP64 phi(H)): 1e-6 per step; the
+  FP32 operators alone: 2e-7 (p+1)^2.  Each FP32 flux value carries a relative
+  rounding error of u = 6e-8; the derivative sum_j D_ij F_j has row sums of
+  |D_ij| growing like p^2 (|D_00| = p(p+1)/4), so the error relative to the
+  result grows like u p^2 times a small constant (measured 3.9e-6 at p = 5).
+"""
+import math
+
+import numpy as np
+import pytest
+
+from oracle import dg, integrators, krylov
+from paper_2011_01316_gb300 import inputs
+
+pytestmark = pytest.mark.gpu
+
+TOL_OP64 = 1e-12
+TOL_STEP64 = 1e-11
+TOL_MIXED = 1e-6
+
+
+@pytest.fixture(scope="module")
+def E():
+    import torch
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2011_01316_gb300 import expdg
+    return expdg
+
+
+def rel(a, b):
+    a = np.asarray(a).reshape(-1)
+    b = np.asarray(b).reshape(-1)
+    return float(np.linalg.norm(a - b) / max(np.linalg.norm(b), 1e-300))
+
+
+CASES = {
+    "burgers1d_p2": dict(eq=1, dim=1, p=2, ne=(64,), lo=(0.0,), hi=(2 * math.pi,)),
+    "burgers1d_p5_ragged": dict(eq=1, dim=1, p=5, ne=(45,), lo=(0.0,), hi=(2 * math.pi,)),
+    "euler1d_p3": dict(eq=2, dim=1, p=3, ne=(37,), lo=(0.0,), hi=(2 * math.pi,)),
+    "euler2d_p4": dict(eq=2, dim=2, p=4, ne=(13, 7), lo=(0.0, 0.0), hi=(10.0, 10.0)),
+    "euler2d_p1": dict(eq=2, dim=2, p=1, ne=(17, 9), lo=(0.0, 0.0), hi=(10.0, 10.0)),
+    "euler2d_p7": dict(eq=2, dim=2, p=7, ne=(3, 4), lo=(0.0, 0.0), hi=(10.0, 10.0)),
+    "euler3d_p3": dict(eq=2, dim=3, p=3, ne=(5, 3, 4), lo=(0.0,) * 3, hi=(2 * math.pi,) * 3),
+    "euler3d_p2": dict(eq=2, dim=3, p=2, ne=(3, 3, 2), lo=(0.0,) * 3, hi=(2 * math.pi,) * 3),
+}
+
+
+def make(E, case, prec=0, scheme=2, tol=1e-10, m_max=64):
+    c = CASES[case]
+    kw = dict(eq=c["eq"], dim=c["dim"], p=c["p"], ne=list(c["ne"]) + [1] * (3 - c["dim"]),
+              lo=list(c["lo"]) + [0.0] * (3 - c["dim"]), hi=list(c["hi"]) + [1.0] * (3 - c["dim"]),
+              prec=prec, scheme=scheme, krylov_tol=tol, m_max=m_max, m_step=5, max_substeps=32, gamma=1.4)
+    ctx = E.Context(**kw)
+    mesh = dg.Mesh(dim=c["dim"], p=c["p"], ne=c["ne"], lo=c["lo"], hi=c["hi"],
+                   eq="burgers" if c["eq"] == 1 else "euler")
+    return ctx, mesh
+
+
+def state(mesh, rng, smooth=True):
+    X = dg.node_coords(mesh)
+    if mesh.eq == "burgers":
+        return inputs.fourier_modes(X[0], rng, mean=0.5)[0][None].copy()
+    if mesh.dim == 2 and smooth:
+        return inputs.isentropic_vortex(X, 0.0, center=(4.0, 6.0))
+    if smooth:
+        return inputs.density_wave(X, 0.0)
+    return inputs.random_euler_state(mesh.dim, mesh.n_elem, mesh.n_node, rng)
+
+
+@pytest.mark.parametrize("case", list(CASES))
+def test_node_coords_match(E, case):
+    ctx, mesh = make(E, case)
+    np.testing.assert_allclose(ctx.node_coords(), dg.node_coords(mesh), rtol=0, atol=1e-13)
+
+
+def tol_op32(p):
+    return 2e-7 * (p + 1) ** 2
+
+
+@pytest.mark.parametrize("prec", [0, 1])
+@pytest.mark.parametrize("case", list(CASES))
+def test_residual_and_jv_parity(E, case, prec):
+    rng = np.random.default_rng(7)
+    ctx, mesh = make(E, case, prec=prec)
+    tol = TOL_OP64 if prec == 0 else tol_op32(mesh.p)
+    for smooth in (True, False):
+        q = np.ascontiguousarray(state(mesh, rng, smooth))
+        R = ctx.residual(q)
+        assert rel(R, dg.residual(mesh, q)) <= tol
+        v = np.ascontiguousarray(rng.standard_normal(q.shape))
+        Lv = ctx.jv(q, v)
+        assert rel(Lv, dg.jv(mesh, q, v)) <= tol
+
+
+def test_device_pointers_match_host_pointers(E):
+    import torch
+    rng = np.random.default_rng(8)
+    ctx, mesh = make(E, "euler2d_p4")
+    q = np.ascontiguousarray(state(mesh, rng))
+    v = np.ascontiguousarray(rng.standard_normal(q.shape))
+    qd = torch.from_numpy(q).cuda()
+    vd = torch.from_numpy(v).cuda()
+    od = torch.empty_like(qd)
+    ctx.jv(qd, vd, od)
+    np.testing.assert_array_equal(od.cpu().numpy(), ctx.jv(q, v))
+    ctx.residual(qd, od)
+    np.testing.assert_array_equal(od.cpu().numpy(), ctx.residual(q))
+
+
+@pytest.mark.parametrize("P", [0, 1, 3])
+@pytest.mark.parametrize("case", ["burgers1d_p2", "euler2d_p4", "euler3d_p2"])
+def test_phi_parity_replayed(E, case, P):
+    rng = np.random.default_rng(9 + P)
+    ctx, mesh = make(E, case)
+    q = state(mesh, rng).reshape(-1)
+    tau = 0.05
+    c = [rng.standard_normal(q.size) * 0.1 for _ in range(P + 1)]
+    if P > 0:
+        c[0] = np.zeros_like(q)
+    ref, st = krylov.phi_sum(lambda x: tau * dg.jv(mesh, q, x).reshape(-1), c, tol=1e-10)
+    rep = [(0, m, s, e) for (s, m, e) in st.trace]
+    got, gst, gtr = ctx.phi(q, tau, [None if (i == 0 and P > 0) else np.ascontiguousarray(ci)
+                                     for i, ci in enumerate(c)], replay=rep)
+    assert rel(got, ref) <= TOL_STEP64
+    assert [(m, s) for (_, m, s, _) in gtr] == [(m, s) for (s, m, _) in st.trace]
+
+
+@pytest.mark.parametrize("case", ["burgers1d_p2", "euler2d_p4", "euler3d_p2"])
+def test_phi_adaptive_agrees(E, case):
+    """Decisions taken on the GPU (not replayed) agree with the oracle to 10 tol."""
+    rng = np.random.default_rng(11)
+    ctx, mesh = make(E, case)
+    q = state(mesh, rng).reshape(-1)
+    tau = 0.05
+    c = [np.zeros_like(q), rng.standard_normal(q.size) * 0.1]
+    ref, st = krylov.phi_sum(lambda x: tau * dg.jv(mesh, q, x).reshape(-1), c, tol=1e-10)
+    got, gst, gtr = ctx.phi(q, tau, [None, np.ascontiguousarray(c[1])])
+    assert rel(got, ref) <= 1e-9
+
+
+def test_phi_substeps_parity(E):
+    """Small m_max forces rejected attempts and sub-steps; replayed decisions
+    reproduce the oracle, and the adaptive GPU run makes the same decisions."""
+    rng = np.random.default_rng(12)
+    ctx, mesh = make(E, "burgers1d_p2", m_max=10)
+    q = state(mesh, rng).reshape(-1)
+    tau = 0.3
+    c = [rng.standard_normal(q.size) * 0.1 for _ in range(4)]
+    ref, st = krylov.phi_sum(lambda x: tau * dg.jv(mesh, q, x).reshape(-1), c, tol=1e-10, m_max=10)
+    assert st.substeps > 1
+    got, gst, gtr = ctx.phi(q, tau, [np.ascontiguousarray(x) for x in c], replay=[(0, m, s, e) for (s, m, e) in st.trace])
+    assert rel(got, ref) <= TOL_STEP64
+    got2, gst2, gtr2 = ctx.phi(q, tau, [np.ascontiguousarray(x) for x in c])
+    assert [(m, s) for (_, m, s, _) in gtr2] == [(m, s) for (s, m, _) in st.trace]
+    assert rel(got2, ref) <= 1e-9
+
+
+def _replay_from(st):
+    rep = []
+    for sid, tr in enumerate(st.traces):
+        rep += [(sid, m, s, e) for (s, m, e) in tr]
+    return rep
+
+
+@pytest.mark.parametrize("scheme", [2, 3, 4])
+@pytest.mark.parametrize("case", ["burgers1d_p2", "euler1d_p3", "euler2d_p4", "euler3d_p3"])
+def test_step_parity_fp64_replayed(E, case, scheme):
+    rng = np.random.default_rng(13)
+    ctx, mesh = make(E, case, scheme=scheme)
+    q = np.ascontiguousarray(state(mesh, rng))
+    dt = 0.05 if mesh.eq == "euler" else 0.02
+    ref, st = integrators.step(mesh, q, dt, scheme=scheme, tol=1e-10)
+    got = q.copy()
+    gst, gtr = ctx.step(got, dt, replay=_replay_from(st))
+    assert rel(got, ref) <= TOL_STEP64
+    # conservation of the quadrature totals
+    np.testing.assert_allclose(dg.totals(mesh, got), dg.totals(mesh, q), rtol=1e-13, atol=1e-13)
+
+
+@pytest.mark.parametrize("scheme", [2, 3])
+@pytest.mark.parametrize("case", ["burgers1d_p2", "euler2d_p4", "euler3d_p3"])
+def test_step_mixed_within_1e6(E, case, scheme):
+    rng = np.random.default_rng(14)
+    ctx, mesh = make(E, case, prec=1, scheme=scheme)
+    q = np.ascontiguousarray(state(mesh, rng))
+    dt = 0.05 if mesh.eq == "euler" else 0.02
+    ref, st = integrators.step(mesh, q, dt, scheme=scheme, tol=1e-10)
+    got = q.copy()
+    ctx.step(got, dt)
+    assert rel(got, ref) <= TOL_MIXED
+
+
+def test_burgers_small_workload_adaptive(E):
+    """64 elements, p = 2, u0 = 0.5 + sin x, EPI2, tol 1e-10, dt = 1e-2 to t = 0.5:
+    GPU adaptive run vs the oracle run (both adaptive) and vs characteristics."""
+    ctx, mesh = make(E, "burgers1d_p2")
+    X = dg.node_coords(mesh)
+    u0 = inputs.burgers_sine(X)
+    ref, _ = integrators.advance(mesh, u0.reshape(-1), 1e-2, 50, tol=1e-10)
+    got = np.ascontiguousarray(u0.copy())
+    st = ctx.advance(got, 1e-2, 50)
+    assert rel(got, ref) <= 1e-9
+    assert st["substeps"] == 50
+
+
+def test_euler_vortex_full_size_step(E):
+    """64 x 64 elements, p = 4 (409,600 unknowns): one EPI2 step, FP64 form with
+    the oracle's decisions, element by element."""
+    ctx, mesh = make_full(E, prec=0)
+    X = dg.node_coords(mesh)
+    q = np.ascontiguousarray(inputs.isentropic_vortex(X, 0.0))
+    ref, st = integrators.step(mesh, q, 0.05, tol=1e-10)
+    got = q.copy()
+    ctx.step(got, 0.05, replay=_replay_from(st))
+    assert rel(got, ref) <= TOL_STEP64
+    ctx2, _ = make_full(E, prec=1)
+    got2 = q.copy()
+    ctx2.step(got2, 0.05)
+    assert rel(got2, ref) <= TOL_MIXED
+
+
+def make_full(E, prec):
+    CASES["euler2d_full"] = dict(eq=2, dim=2, p=4, ne=(64, 64), lo=(0.0, 0.0), hi=(10.0, 10.0))
+    return make(E, "euler2d_full", prec=prec)
+
+
+def test_nonphysical_state_reported(E):
+    ctx, mesh = make(E, "euler2d_p1")
+    rng = np.random.default_rng(15)
+    q = np.ascontiguousarray(state(mesh, rng))
+    q[0, 3, 1] = -1.0
+    with pytest.raises(E.ExpdgError) as ei:
+        ctx.residual(q)
+    assert ei.value.status == E.EXPDG_ENONPHYSICAL
+
+
+def test_invalid_configs_rejected(E):
+    for bad in (dict(p=0), dict(p=99), dict(dim=4), dict(eq=1, dim=2), dict(m_max=65), dict(krylov_tol=0.0)):
+        with pytest.raises(E.ExpdgError) as ei:
+            E.Context(**bad)
+        assert ei.value.status == E.EXPDG_EINVAL
