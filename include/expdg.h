@@ -53,9 +53,13 @@ typedef enum { EXPDG_EPI2 = 2, EXPDG_EXPRB32 = 3, EXPDG_EXPRB42 = 4 } expdg_sche
 
 /* Arithmetic of the operator applies (R, Jv) and of the Arnoldi process.
  *   EXPDG_FP64:  everything in FP64 (reference form).
- *   EXPDG_MIXED: R and Jv in FP32 (FP32 accumulation); Arnoldi inner
- *                products, orthogonalisation, phi(H) and the solution update
- *                in FP64. */
+ *   EXPDG_MIXED: R and Jv in FP32 (FP32 accumulation); Krylov basis, inner
+ *                products and orthogonalisation in float-float (pairs of FP32
+ *                numbers, 48-bit significand, FP32 arithmetic with error-free
+ *                transformations); phi(H) and the solution update in FP64.
+ *                On this GPU the FP64 pipe (and every f32<->f64 conversion)
+ *                runs about 1/70 of the FP32 rate, so the streaming Krylov
+ *                kernels avoid it. */
 typedef enum { EXPDG_FP64 = 0, EXPDG_MIXED = 1 } expdg_precision;
 
 typedef struct {
@@ -137,11 +141,19 @@ expdg_status expdg_jv(expdg_ctx* ctx, const double* qt, const double* v, double*
 /* out = sum_{i=0}^{P} phi_i(tau L(qt)) c_i with c = [c_0, ..., c_P] (P <= 3;
  * c[i] may be NULL for a zero vector), Sec. 2.3 Eq.
  * linear_combination_of_phifunctions with the dt^i folded into c_i.
- * Augmented-matrix Arnoldi with error checks every m_step, sub-stepping on
- * failure (see DESIGN for the exact rules).  If replay != NULL, the
- * nreplay records (all with solve == 0) are followed instead of deciding;
- * otherwise, if trace != NULL, up to trace_cap accepted sub-steps are written
- * there and *ntrace is set. */
+ * Method: Arnoldi (classical Gram-Schmidt, twice) on the augmented matrix
+ *   A_hat = [[sigma tau L, eta W], [0, J]],  W = [b_P .. b_1],  J = upper shift,
+ * started from [b_0; e_P / eta], beta = its norm; the top block of
+ * beta V_m exp(H_m) e_1 approximates the sum.  The error estimate
+ * err = beta h_{m+1,m} |e_m^T exp(H_m) e_1| is checked at m = m_step,
+ * 2 m_step, ..., m_max; accepted when err <= krylov_tol * beta (or on a happy
+ * breakdown).  Reaching m_max halves the sub-step sigma; after an accepted
+ * sub-step with m <= m_max/2 sigma doubles (never past the end).  Sub-step
+ * vectors: b_0 = w(s), b_i = sigma^i sum_j s^j/j! c_{i+j}.  The tail scale
+ * eta = 2^-round(log2(max_i ||b_i||)).  If replay != NULL, the nreplay
+ * records (all with solve == 0) are followed instead of deciding; otherwise,
+ * if trace != NULL, up to trace_cap accepted sub-steps are written there and
+ * *ntrace is set. */
 expdg_status expdg_phi(expdg_ctx* ctx, const double* qt, double tau, const double* const* c, int P,
                        double* out, expdg_stats* stats,
                        const expdg_trace_entry* replay, int nreplay,

@@ -10,18 +10,21 @@
 // Reductions are deterministic: each block writes one partial per value, the
 // last block to finish (atomic ticket) sums the partials in block order, one
 // warp per value.
+#include <cooperative_groups.h>
+
 #include "common.cuh"
 #include "ff.cuh"
+
+namespace cg = cooperative_groups;
 
 namespace expdg {
 
 namespace {
 
-constexpr int RB = 2 * 152;     // blocks of the streaming reduction kernels
+constexpr int RB = 4 * 152;     // blocks of the streaming reduction kernels
 constexpr int NT = 256;         // threads per block
 constexpr int NW = NT / 32;
 constexpr int NORMS_MAX = 5;
-constexpr int PHI_THREADS = 512;
 
 template <bool FF>
 struct Acc;
@@ -82,9 +85,10 @@ __device__ __forceinline__ typename Acc<FF>::T negate(typename Acc<FF>::T x) {
     return -x;
 }
 
-// Sum K per-thread values over the block; thread k < K of warp 0 gets total k.
+// Sum K per-thread values over the block; tot[k] (shared) receives total k.
 template <bool FF, int K>
-__device__ void block_sum(typename Acc<FF>::T (&v)[K], typename Acc<FF>::T* sh /* [NW][K] */) {
+__device__ void block_sum(const typename Acc<FF>::T (&v)[K], typename Acc<FF>::T* sh /* [NW][K] */,
+                          typename Acc<FF>::T* tot /* [K] */) {
   using A = Acc<FF>;
   const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
 #pragma unroll
@@ -98,7 +102,28 @@ __device__ void block_sum(typename Acc<FF>::T (&v)[K], typename Acc<FF>::T* sh /
   if (threadIdx.x < K) {
     typename A::T x = A::zero();
     for (int ww = 0; ww < NW; ++ww) x = A::add(x, sh[ww * K + threadIdx.x]);
-    v[threadIdx.x] = x;  // dynamic index on a register array: fine for small K
+    tot[threadIdx.x] = x;
+  }
+  __syncthreads();
+}
+
+// Element i of basis vector k.
+template <bool FF>
+__device__ __forceinline__ typename Acc<FF>::T ldb(const Basis& U, int k, size_t i) {
+  const size_t o = (size_t)k * U.ld + i;
+  if constexpr (FF)
+    return ff{U.h[o], U.l[o]};
+  else
+    return U.d[o];
+}
+template <bool FF>
+__device__ __forceinline__ void stb(const Basis& U, int k, size_t i, typename Acc<FF>::T x) {
+  const size_t o = (size_t)k * U.ld + i;
+  if constexpr (FF) {
+    U.h[o] = x.h;
+    U.l[o] = x.l;
+  } else {
+    U.d[o] = x;
   }
 }
 
@@ -181,8 +206,9 @@ __global__ void __launch_bounds__(NT) k_norms(KState* ks, typename Acc<FF>::T* p
       acc[k] = fma_acc<FF>(x, x, acc[k]);
     }
   }
-  block_sum<FF, NORMS_MAX>(acc, sh);
-  if (threadIdx.x < NORMS_MAX) part[threadIdx.x * gridDim.x + blockIdx.x] = acc[threadIdx.x];
+  __shared__ typename A::T tot[NORMS_MAX];
+  block_sum<FF, NORMS_MAX>(acc, sh, tot);
+  if (threadIdx.x < NORMS_MAX) part[threadIdx.x * gridDim.x + blockIdx.x] = tot[threadIdx.x];
   if (last_block(&ks->counter, gridDim.x)) {
     __shared__ double res[NORMS_MAX];
     final_sums<FF>(part, NORMS_MAX, gridDim.x, res);
@@ -239,53 +265,115 @@ __global__ void __launch_bounds__(NT) k_start(KState* ks, Vec u0, Vec b0, size_t
   }
 }
 
-// grid: (gx, chunks); block (bx, c) handles basis vectors c*DOT_CHUNK .. +DOT_CHUNK-1.
+// Four consecutive elements of basis vector k starting at element 4g (vector
+// bases are 256-byte aligned, so these are 16-byte loads).
+template <bool FF>
+struct Quad;
+template <>
+struct Quad<true> {
+  ff v[4];
+};
+template <>
+struct Quad<false> {
+  double v[4];
+};
+
+template <bool FF>
+__device__ __forceinline__ Quad<FF> ldq(const Basis& U, int k, size_t g) {
+  Quad<FF> q;
+  const size_t o = (size_t)k * U.ld + 4 * g;
+  if constexpr (FF) {
+    const float4 h = __ldg(reinterpret_cast<const float4*>(U.h + o));
+    const float4 l = __ldg(reinterpret_cast<const float4*>(U.l + o));
+    q.v[0] = ff{h.x, l.x};
+    q.v[1] = ff{h.y, l.y};
+    q.v[2] = ff{h.z, l.z};
+    q.v[3] = ff{h.w, l.w};
+  } else {
+    const double2 a = __ldg(reinterpret_cast<const double2*>(U.d + o));
+    const double2 b = __ldg(reinterpret_cast<const double2*>(U.d + o + 2));
+    q.v[0] = a.x;
+    q.v[1] = a.y;
+    q.v[2] = b.x;
+    q.v[3] = b.y;
+  }
+  return q;
+}
+template <bool FF>
+__device__ __forceinline__ void stq(const Basis& U, int k, size_t g, const Quad<FF>& q) {
+  const size_t o = (size_t)k * U.ld + 4 * g;
+  if constexpr (FF) {
+    *reinterpret_cast<float4*>(U.h + o) = make_float4(q.v[0].h, q.v[1].h, q.v[2].h, q.v[3].h);
+    *reinterpret_cast<float4*>(U.l + o) = make_float4(q.v[0].l, q.v[1].l, q.v[2].l, q.v[3].l);
+  } else {
+    *reinterpret_cast<double2*>(U.d + o) = make_double2(q.v[0], q.v[1]);
+    *reinterpret_cast<double2*>(U.d + o + 2) = make_double2(q.v[2], q.v[3]);
+  }
+}
+
+// Multi-dot: grid (gx, chunks); block (bx, c) forms <u_k, w> for the basis
+// vectors k = c*DOT_CHUNK .. +DOT_CHUNK-1 over its share of the elements
+// (groups of four per thread, every load of a group issued before its math;
+// the ragged end of the vector is taken one element at a time).
 template <bool FF>
 __global__ void __launch_bounds__(NT) k_dots(KState* ks, typename Acc<FF>::T* part, Basis U, int J, size_t n_aug,
                                             int second) {
   using A = Acc<FF>;
   constexpr int K = DOT_CHUNK + 1;  // + ||w||^2 (first pass, chunk 0)
   __shared__ typename A::T sh[NW * K];
-  const Vec w = U.at(J);
+  __shared__ typename A::T tot[K];
   const int c0 = blockIdx.y * DOT_CHUNK;
   const int nc = min(DOT_CHUNK, J - c0);
-  Vec u[DOT_CHUNK];
-#pragma unroll
-  for (int c = 0; c < DOT_CHUNK; ++c) u[c] = U.at(c0 + (c < nc ? c : 0));
   typename A::T acc[K];
 #pragma unroll
   for (int k = 0; k < K; ++k) acc[k] = A::zero();
   const bool wnorm = (!second) && blockIdx.y == 0;
-  for (size_t i = blockIdx.x * (size_t)NT + threadIdx.x; i < n_aug; i += (size_t)gridDim.x * NT) {
-    const typename A::T wi = load<FF>(w, i);
+  const size_t ng = n_aug / 4;
+  const size_t tid = blockIdx.x * (size_t)NT + threadIdx.x, nthr = (size_t)gridDim.x * NT;
+  for (size_t g = tid; g < ng; g += nthr) {
+    const Quad<FF> w = ldq<FF>(U, J, g);
+    Quad<FF> u[DOT_CHUNK];
+#pragma unroll
+    for (int c = 0; c < DOT_CHUNK; ++c) u[c] = ldq<FF>(U, c0 + (c < nc ? c : 0), g);
 #pragma unroll
     for (int c = 0; c < DOT_CHUNK; ++c)
-      if (c < nc) acc[c] = fma_acc<FF>(load<FF>(u[c], i), wi, acc[c]);
+      if (c < nc)
+#pragma unroll
+        for (int e = 0; e < 4; ++e) acc[c] = fma_acc<FF>(u[c].v[e], w.v[e], acc[c]);
+    if (wnorm)
+#pragma unroll
+      for (int e = 0; e < 4; ++e) acc[DOT_CHUNK] = fma_acc<FF>(w.v[e], w.v[e], acc[DOT_CHUNK]);
+  }
+  for (size_t i = 4 * ng + tid; i < n_aug; i += nthr) {
+    const typename A::T wi = ldb<FF>(U, J, i);
+    for (int c = 0; c < nc; ++c) acc[c] = fma_acc<FF>(ldb<FF>(U, c0 + c, i), wi, acc[c]);
     if (wnorm) acc[DOT_CHUNK] = fma_acc<FF>(wi, wi, acc[DOT_CHUNK]);
   }
-  block_sum<FF, K>(acc, sh);
+  block_sum<FF, K>(acc, sh, tot);
   const int G = gridDim.x;
-  if (threadIdx.x < nc) part[(size_t)(c0 + threadIdx.x) * G + blockIdx.x] = acc[threadIdx.x];
-  if (wnorm && threadIdx.x == DOT_CHUNK) part[(size_t)J * G + blockIdx.x] = acc[DOT_CHUNK];
+  if (threadIdx.x < nc) part[(size_t)(c0 + threadIdx.x) * G + blockIdx.x] = tot[threadIdx.x];
+  if (wnorm && threadIdx.x == DOT_CHUNK) part[(size_t)J * G + blockIdx.x] = tot[DOT_CHUNK];
   if (last_block(&ks->counter, gridDim.x * gridDim.y)) {
     __shared__ double res[MMAX + 1];
     final_sums<FF>(part, second ? J : J + 1, G, res);
     __syncthreads();
     const int j = J - 1;  // column of H being built
     for (int i = threadIdx.x; i < J; i += NT) {
-      const double g = ks->s[i] * res[i];
+      const double gi = ks->s[i] * res[i];
       if (second) {
-        ks->H[j * (MMAX + 1) + i] += g;
+        ks->H[j * (MMAX + 1) + i] += gi;
       } else {
-        ks->H[j * (MMAX + 1) + i] = g;
+        ks->H[j * (MMAX + 1) + i] = gi;
       }
-      ks->coef[i] = g * ks->s[i];
+      ks->coef[i] = gi * ks->s[i];
     }
     if (!second && threadIdx.x == 0) ks->wnorm0 = sqrt(res[J]);
     if (threadIdx.x == 0) ks->counter = 0;
   }
 }
 
+// Update w -= sum_{k<J} coef_k u_k over groups of four elements per thread
+// (four independent accumulation chains), optionally with ||w||^2.
 template <bool FF>
 __global__ void __launch_bounds__(NT) k_update(KState* ks, typename Acc<FF>::T* part, Basis U, int J, size_t n_aug,
                                               int finish) {
@@ -294,17 +382,40 @@ __global__ void __launch_bounds__(NT) k_update(KState* ks, typename Acc<FF>::T* 
   __shared__ typename A::T sh[NW];
   for (int i = threadIdx.x; i < J; i += NT) cf[i] = negate<FF>(from_d<FF>(ks->coef[i]));
   __syncthreads();
-  const Vec w = U.at(J);
   typename A::T nrm[1] = {A::zero()};
-  for (size_t i = blockIdx.x * (size_t)NT + threadIdx.x; i < n_aug; i += (size_t)gridDim.x * NT) {
-    typename A::T x = load<FF>(w, i);
-    for (int k = 0; k < J; ++k) x = fma_acc<FF>(cf[k], load<FF>(U.at(k), i), x);
-    store<FF>(w, i, x);
+  const size_t ng = n_aug / 4;
+  const size_t tid = blockIdx.x * (size_t)NT + threadIdx.x, nthr = (size_t)gridDim.x * NT;
+  for (size_t g = tid; g < ng; g += nthr) {
+    Quad<FF> x = ldq<FF>(U, J, g);
+    int k = 0;
+    for (; k + 2 <= J; k += 2) {
+      const Quad<FF> u0 = ldq<FF>(U, k, g);
+      const Quad<FF> u1 = ldq<FF>(U, k + 1, g);
+#pragma unroll
+      for (int e = 0; e < 4; ++e) x.v[e] = fma_acc<FF>(cf[k], u0.v[e], x.v[e]);
+#pragma unroll
+      for (int e = 0; e < 4; ++e) x.v[e] = fma_acc<FF>(cf[k + 1], u1.v[e], x.v[e]);
+    }
+    if (k < J) {
+      const Quad<FF> u0 = ldq<FF>(U, k, g);
+#pragma unroll
+      for (int e = 0; e < 4; ++e) x.v[e] = fma_acc<FF>(cf[k], u0.v[e], x.v[e]);
+    }
+    stq<FF>(U, J, g, x);
+    if (finish)
+#pragma unroll
+      for (int e = 0; e < 4; ++e) nrm[0] = fma_acc<FF>(x.v[e], x.v[e], nrm[0]);
+  }
+  for (size_t i = 4 * ng + tid; i < n_aug; i += nthr) {
+    typename A::T x = ldb<FF>(U, J, i);
+    for (int k = 0; k < J; ++k) x = fma_acc<FF>(cf[k], ldb<FF>(U, k, i), x);
+    stb<FF>(U, J, i, x);
     if (finish) nrm[0] = fma_acc<FF>(x, x, nrm[0]);
   }
   if (!finish) return;
-  block_sum<FF, 1>(nrm, sh);
-  if (threadIdx.x == 0) part[blockIdx.x] = nrm[0];
+  __shared__ typename A::T tot[1];
+  block_sum<FF, 1>(nrm, sh, tot);
+  if (threadIdx.x == 0) part[blockIdx.x] = tot[0];
   if (last_block(&ks->counter, gridDim.x)) {
     __shared__ double res[1];
     final_sums<FF>(part, 1, gridDim.x, res);
@@ -313,14 +424,14 @@ __global__ void __launch_bounds__(NT) k_update(KState* ks, typename Acc<FF>::T* 
       const double h = sqrt(res[0]);
       const int j = J - 1;
       ks->H[j * (MMAX + 1) + J] = h;
-      double s = 0.0;
+      double sj = 0.0;
       if (h <= 1e-13 * ks->wnorm0 || h == 0.0) {
         if (ks->breakdown_at == 0) ks->breakdown_at = J;
       } else {
-        s = 1.0 / h;
+        sj = 1.0 / h;
       }
-      ks->s[J] = s;
-      ff t = ff_from_double(s);
+      ks->s[J] = sj;
+      ff t = ff_from_double(sj);
       ks->sh[J] = t.h;
       ks->sl[J] = t.l;
       ks->counter = 0;
@@ -328,19 +439,40 @@ __global__ void __launch_bounds__(NT) k_update(KState* ks, typename Acc<FF>::T* 
   }
 }
 
-// Dense exponential of the m x m leading block of H by scaling and squaring
-// of the degree-18 Taylor polynomial (Horner form), ||H / 2^s||_1 <= 1/2.
-// One CTA, FP64, matrices in shared memory (row-major, leading dimension m).
-__device__ void smem_matmul(const double* A, const double* B, double* C, int m) {
-  for (int idx = threadIdx.x; idx < m * m; idx += blockDim.x) {
-    const int r = idx / m, c = idx - r * m;
-    double s = 0.0;
-    for (int k = 0; k < m; ++k) s = fma(A[r * m + k], B[k * m + c], s);
-    C[idx] = s;
+// Dense exponential of the m x m leading block of H: scaling and squaring,
+// exp(H) = T(H / 2^s)^(2^s) with ||H / 2^s||_1 <= 1/2 and T the degree-18
+// Taylor polynomial, evaluated by Paterson-Stockmeyer in X^4:
+//   T(X) = B_0 + X^4 (B_1 + X^4 (B_2 + X^4 (B_3 + X^4 B_4))),
+//   B_j = sum_{i<4} X^i / (4j+i)!,  B_4 = I/16! + X/17! + X^2/18!,
+// i.e. 3 products for X^2, X^3, X^4 and 4 Horner products instead of 18.
+// FP64 on a cluster of PHI_CL CTAs: every CTA keeps full copies of the
+// matrices in shared memory; each product is split by rows across the CTAs
+// and every CTA writes its rows into all CTAs' copies (distributed shared
+// memory), followed by one cluster barrier.  Results alternate between two
+// buffers, so a CTA never overwrites a copy another CTA may still read.
+constexpr int PHI_CL = 8;
+constexpr int PHI_NT = 256;
+
+__device__ void cl_matmul(cg::cluster_group& cl, const double* A, const double* B, double* C, int m) {
+  const int rank = (int)cl.block_rank();
+  const int r0 = (m * rank) / PHI_CL, r1 = (m * (rank + 1)) / PHI_CL;
+  double* dst[PHI_CL];
+#pragma unroll
+  for (int t = 0; t < PHI_CL; ++t) dst[t] = cl.map_shared_rank(C, t);
+  const int nout = (r1 - r0) * m;
+  for (int idx = threadIdx.x; idx < nout; idx += blockDim.x) {
+    const int r = r0 + idx / m, c = idx - (idx / m) * m;
+    double acc = 0.0;
+    for (int k = 0; k < m; ++k) acc = fma(A[r * m + k], B[k * m + c], acc);
+#pragma unroll
+    for (int t = 0; t < PHI_CL; ++t) dst[t][r * m + c] = acc;
   }
+  cl.sync();
 }
 
-__global__ void __launch_bounds__(PHI_THREADS) k_phi(KState* ks, int m_req, double beta, double tol, int force) {
+__global__ void __cluster_dims__(PHI_CL, 1, 1) __launch_bounds__(PHI_NT)
+k_phi(KState* ks, int m_req, double beta, double tol, int force) {
+  cg::cluster_group cl = cg::this_cluster();
   extern __shared__ double sm[];
   __shared__ int s_m;
   __shared__ double s_norm;
@@ -349,11 +481,14 @@ __global__ void __launch_bounds__(PHI_THREADS) k_phi(KState* ks, int m_req, doub
     s_m = (b > 0 && b < m_req) ? b : m_req;
   }
   __syncthreads();
-  const int m = s_m;
+  const int m = s_m, mm = m * m;
   double* X = sm;
-  double* E = X + m * m;
-  double* T = E + m * m;
-  for (int idx = threadIdx.x; idx < m * m; idx += blockDim.x) {
+  double* X2 = X + mm;
+  double* X3 = X2 + mm;
+  double* X4 = X3 + mm;
+  double* T0 = X4 + mm;
+  double* T1 = T0 + mm;
+  for (int idx = threadIdx.x; idx < mm; idx += blockDim.x) {
     const int r = idx / m, c = idx - r * m;
     X[idx] = ks->H[c * (MMAX + 1) + r];
   }
@@ -372,40 +507,54 @@ __global__ void __launch_bounds__(PHI_THREADS) k_phi(KState* ks, int m_req, doub
   int sq = 0;
   if (s_norm > 0.5) sq = (int)ceil(log2(s_norm / 0.5));
   const double scale = ldexp(1.0, -sq);
-  for (int idx = threadIdx.x; idx < m * m; idx += blockDim.x) {
-    X[idx] *= scale;
+  for (int idx = threadIdx.x; idx < mm; idx += blockDim.x) X[idx] *= scale;
+  cl.sync();  // every CTA has its scaled copy before any remote write lands
+  cl_matmul(cl, X, X, X2, m);
+  cl_matmul(cl, X2, X, X3, m);
+  cl_matmul(cl, X2, X2, X4, m);
+  double ifact[19];
+  ifact[0] = 1.0;
+  for (int k = 1; k <= 18; ++k) ifact[k] = ifact[k - 1] / k;
+  // E = B_4
+  for (int idx = threadIdx.x; idx < mm; idx += blockDim.x) {
     const int r = idx / m, c = idx - r * m;
-    E[idx] = (r == c) ? 1.0 : 0.0;
+    T0[idx] = ((r == c) ? ifact[16] : 0.0) + ifact[17] * X[idx] + ifact[18] * X2[idx];
   }
   __syncthreads();
-  for (int k = 18; k >= 1; --k) {
-    smem_matmul(X, E, T, m);
-    __syncthreads();
-    const double inv = 1.0 / k;
-    for (int idx = threadIdx.x; idx < m * m; idx += blockDim.x) {
+  double* E = T0;
+  double* F = T1;
+  for (int j = 3; j >= 0; --j) {
+    cl_matmul(cl, X4, E, F, m);
+    for (int idx = threadIdx.x; idx < mm; idx += blockDim.x) {
       const int r = idx / m, c = idx - r * m;
-      E[idx] = ((r == c) ? 1.0 : 0.0) + T[idx] * inv;
+      F[idx] += ((r == c) ? ifact[4 * j] : 0.0) + ifact[4 * j + 1] * X[idx] + ifact[4 * j + 2] * X2[idx] +
+                ifact[4 * j + 3] * X3[idx];
     }
     __syncthreads();
+    double* t = E;
+    E = F;
+    F = t;
   }
   for (int k = 0; k < sq; ++k) {
-    smem_matmul(E, E, T, m);
-    __syncthreads();
-    for (int idx = threadIdx.x; idx < m * m; idx += blockDim.x) E[idx] = T[idx];
-    __syncthreads();
+    cl_matmul(cl, E, E, F, m);
+    double* t = E;
+    E = F;
+    F = t;
   }
-  // y = E e_1 (first column)
-  if (threadIdx.x == 0) {
-    const bool brk = ks->breakdown_at > 0 && ks->breakdown_at <= m;
-    const double hm = ks->H[(m - 1) * (MMAX + 1) + m];
-    const double err = brk ? 0.0 : beta * hm * fabs(E[(m - 1) * m]);
-    ks->err = err;
-    ks->accept = (force || brk || err <= tol * beta) ? 1 : 0;
-    ks->m_eff = m;
-    ks->norm1 = s_norm;
-    ks->squarings = sq;
+  if (cl.block_rank() == 0) {
+    if (threadIdx.x == 0) {
+      const bool brk = ks->breakdown_at > 0 && ks->breakdown_at <= m;
+      const double hm = ks->H[(m - 1) * (MMAX + 1) + m];
+      const double err = brk ? 0.0 : beta * hm * fabs(E[(m - 1) * m]);
+      ks->err = err;
+      ks->accept = (force || brk || err <= tol * beta) ? 1 : 0;
+      ks->m_eff = m;
+      ks->norm1 = s_norm;
+      ks->squarings = sq;
+    }
+    for (int i = threadIdx.x; i < m; i += blockDim.x) ks->ycoef[i] = beta * E[i * m] * ks->s[i];
   }
-  for (int i = threadIdx.x; i < m; i += blockDim.x) ks->ycoef[i] = beta * E[i * m] * ks->s[i];
+  cl.sync();  // no CTA exits while others may still write into its shared memory
 }
 
 template <bool FF>
@@ -418,7 +567,7 @@ __global__ void __launch_bounds__(NT) k_combine(const KState* ks, Basis U, Vec b
   const bool base_d = base.d != nullptr, base_ff = base.h != nullptr;
   for (size_t i = blockIdx.x * (size_t)NT + threadIdx.x; i < N; i += (size_t)gridDim.x * NT) {
     typename A::T x = A::zero();
-    for (int k = 0; k < m; ++k) x = fma_acc<FF>(cf[k], load<FF>(U.at(k), i), x);
+    for (int k = 0; k < m; ++k) x = fma_acc<FF>(cf[k], ldb<FF>(U, k, i), x);
     if (out.d != nullptr) {
       double o = A::to_d(x);
       if (base_d) o += base.d[i];
@@ -511,8 +660,8 @@ cudaError_t launch_start(bool use_ff, KState* ks, Basis U, Vec b0, size_t N, int
 cudaError_t launch_dots(bool use_ff, KState* ks, void* part, Basis U, int J, size_t n_aug, bool second, cudaStream_t s) {
   if (J < 1 || J > MMAX) return cudaErrorInvalidValue;
   const int chunks = (J + DOT_CHUNK - 1) / DOT_CHUNK;
-  int gx = RB / chunks;
-  const int need = (int)((n_aug + NT - 1) / NT);
+  int gx = (RB + chunks - 1) / chunks;
+  const int need = (int)((n_aug / 4 + NT - 1) / NT);
   if (gx > need) gx = need;
   if (gx < 1) gx = 1;
   dim3 grid(gx, chunks);
@@ -526,7 +675,7 @@ cudaError_t launch_dots(bool use_ff, KState* ks, void* part, Basis U, int J, siz
 cudaError_t launch_update(bool use_ff, KState* ks, void* part, Basis U, int J, size_t n_aug, bool finish,
                           cudaStream_t s) {
   if (J < 1 || J > MMAX) return cudaErrorInvalidValue;
-  const int g = grid_for(n_aug);
+  const int g = grid_for(n_aug / 4 + 1);
   if (use_ff)
     k_update<true><<<g, NT, 0, s>>>(ks, static_cast<ff*>(part), U, J, n_aug, finish ? 1 : 0);
   else
@@ -536,15 +685,15 @@ cudaError_t launch_update(bool use_ff, KState* ks, void* part, Basis U, int J, s
 
 cudaError_t launch_phi(KState* ks, int m, double beta, double tol, int force_accept, cudaStream_t s) {
   if (m < 1 || m > MMAX) return cudaErrorInvalidValue;
-  const size_t smem = 3 * sizeof(double) * (size_t)m * m;
+  const size_t smem = 6 * sizeof(double) * (size_t)m * m;
   static bool configured = false;
   if (!configured) {
     cudaError_t e = cudaFuncSetAttribute(k_phi, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                         (int)(3 * sizeof(double) * MMAX * MMAX));
+                                         (int)(6 * sizeof(double) * MMAX * MMAX));
     if (e != cudaSuccess) return e;
     configured = true;
   }
-  k_phi<<<1, PHI_THREADS, smem, s>>>(ks, m, beta, tol, force_accept);
+  k_phi<<<PHI_CL, PHI_NT, smem, s>>>(ks, m, beta, tol, force_accept);
   return cudaGetLastError();
 }
 

@@ -3,11 +3,14 @@
 Tolerances (relative L2 over all unknowns):
   FP64 form, operators (R, Jv):     1e-12  (rounding order only)
   FP64 form, phi-sums and steps:    1e-11  (decisions replayed from the oracle's trace)
-  mixed form (FP32 R/Jv, float-float Krylov, FP64 phi(H)): 1e-6 per step; the
-  FP32 operators alone: 2e-7 (p+1)^2.  Each FP32 flux value carries a relative
-  rounding error of u = 6e-8; the derivative sum_j D_ij F_j has row sums of
-  |D_ij| growing like p^2 (|D_00| = p(p+1)/4), so the error relative to the
-  result grows like u p^2 times a small constant (measured 3.9e-6 at p = 5).
+  mixed form (FP32 R/Jv, float-float Krylov, FP64 phi(H)): 1e-6 per step.
+  FP32 operators alone, a forward-error bound: ||R32 - R64|| <= 2e-7 (p+1)^2 S
+  with S = max_d (2/h_d) ||F_d||, the size of the terms the derivative sums
+  before they cancel (F_d = the physical flux for R, A_d(q) v for Jv).  Each
+  FP32 flux value carries a rounding error of u = 6e-8 relative to F_d; the
+  derivative sum_j D_ij F_j has row sums of |D_ij| growing like p^2
+  (|D_00| = p(p+1)/4), times (2/h_d).  Relative to ||R|| the error is not
+  bounded: for nearly uniform states R is a small difference of large terms.
 """
 import math
 
@@ -79,8 +82,14 @@ def test_node_coords_match(E, case):
     np.testing.assert_allclose(ctx.node_coords(), dg.node_coords(mesh), rtol=0, atol=1e-13)
 
 
-def tol_op32(p):
-    return 2e-7 * (p + 1) ** 2
+def flux_scale(mesh, q, v=None):
+    """max_d (2/h_d) ||F_d||: physical flux of q, or A_d(q) v when v is given."""
+    Q = mesh.to_grid(q)
+    out = 0.0
+    for d in range(mesh.dim):
+        F = dg.flux(mesh, Q, d) if v is None else dg.flux_jacobian_apply(mesh, Q, mesh.to_grid(v), d)
+        out = max(out, 2.0 / mesh.h[d] * float(np.linalg.norm(F)))
+    return out
 
 
 @pytest.mark.parametrize("prec", [0, 1])
@@ -88,14 +97,20 @@ def tol_op32(p):
 def test_residual_and_jv_parity(E, case, prec):
     rng = np.random.default_rng(7)
     ctx, mesh = make(E, case, prec=prec)
-    tol = TOL_OP64 if prec == 0 else tol_op32(mesh.p)
     for smooth in (True, False):
         q = np.ascontiguousarray(state(mesh, rng, smooth))
         R = ctx.residual(q)
-        assert rel(R, dg.residual(mesh, q)) <= tol
+        Rref = dg.residual(mesh, q)
         v = np.ascontiguousarray(rng.standard_normal(q.shape))
         Lv = ctx.jv(q, v)
-        assert rel(Lv, dg.jv(mesh, q, v)) <= tol
+        Lref = dg.jv(mesh, q, v)
+        if prec == 0:
+            assert rel(R, Rref) <= TOL_OP64
+            assert rel(Lv, Lref) <= TOL_OP64
+        else:
+            bound = 2e-7 * (mesh.p + 1) ** 2
+            assert np.linalg.norm(R - Rref) <= bound * flux_scale(mesh, q)
+            assert np.linalg.norm(Lv - Lref) <= bound * flux_scale(mesh, q, v)
 
 
 def test_device_pointers_match_host_pointers(E):
