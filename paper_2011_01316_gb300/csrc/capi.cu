@@ -280,7 +280,7 @@ expdg_status phi_solve(expdg_ctx* ctx, const void* qt_T, double tau, const bool*
       if (trace) trace->push_back(expdg_trace_entry{solve_id, 0, sigma, eta});
       continue;
     }
-    RUN(ctx, EXPDG_K_VECTOR, 16.0 * N, launch_start(F, ctx->ks, ctx->U, ctx->w, N, P, eta, beta, s));
+    RUN(ctx, EXPDG_K_VECTOR, 16.0 * N, launch_start(F, ctx->ks, ctx->U, ctx->w, N, P, eta, s));
     const int limit = replay ? m_fix : cfg.m_max;
     bool accepted = false;
     int m_acc = 0;
@@ -292,13 +292,10 @@ expdg_status phi_solve(expdg_ctx* ctx, const void* qt_T, double tau, const bool*
       const Vec vj = ctx->U.at(j), vo = ctx->U.at(j + 1);
       if (F) {
         a.v = vj.h;
-        a.vs_h = &ctx->ks->sh[j];
-        a.vs_l = &ctx->ks->sl[j];
         a.out_h = vo.h;
         a.out_l = vo.l;
       } else {
         a.v = vj.d;
-        a.vs_d = &ctx->ks->s[j];
         a.out = vo.d;
       }
       if (P > 0) {
@@ -320,12 +317,10 @@ expdg_status phi_solve(expdg_ctx* ctx, const void* qt_T, double tau, const bool*
         }
       }
       RUN(ctx, EXPDG_K_JV, (F ? 16.0 : 24.0) * N, launch_dg(ctx, true, a));
-      const int J = j + 1;
       const double vb = 8.0 * (double)n_aug;  // one vector: FP64 or float-float pair
-      RUN(ctx, EXPDG_K_DOTS, (J + 1) * vb, launch_dots(F, ctx->ks, ctx->part, ctx->U, J, n_aug, false, s));
-      RUN(ctx, EXPDG_K_UPDATE, (J + 2) * vb, launch_update(F, ctx->ks, ctx->part, ctx->U, J, n_aug, false, s));
-      RUN(ctx, EXPDG_K_DOTS, (J + 1) * vb, launch_dots(F, ctx->ks, ctx->part, ctx->U, J, n_aug, true, s));
-      RUN(ctx, EXPDG_K_UPDATE, (J + 2) * vb, launch_update(F, ctx->ks, ctx->part, ctx->U, J, n_aug, true, s));
+      RUN(ctx, EXPDG_K_DOTS, (j + 2) * vb, launch_dots(F, ctx->ks, ctx->part, ctx->U, j, n_aug, s));
+      RUN(ctx, EXPDG_K_UPDATE, (j + 4) * vb, launch_update(F, ctx->ks, ctx->part, ctx->U, j, n_aug, s));
+      const int J = j + 1;
       st->krylov_iters++;
       st->jv_applies++;
       const int m = J;

@@ -86,16 +86,16 @@ struct Basis {
 // The fields from `red` to the end are read back by the host as one block.
 struct KState {
   double H[(MMAX + 1) * MMAX];
-  double s[MMAX + 2];       // v_i = s_i u_i (u_i stored, unnormalised)
-  float sh[MMAX + 2];       // s_i as float-float
-  float sl[MMAX + 2];
-  double coef[MMAX + 1];    // coefficients of the running Gram-Schmidt update (multiply u_i)
-  double ycoef[MMAX + 1];   // beta * y_i * s_i for the final combination
+  double qcoef[MMAX + 1];   // s_k: delayed re-orthogonalisation coefficients of u_j
+  double ucoef[MMAX + 1];   // z_k - (c/r) s_k: projection coefficients of the next vector
+  double ycoef[MMAX + 1];   // beta * y_i for the final combination
+  double cu;                // c / r (coefficient of u_j in the next vector)
+  double inv_r;             // 1 / ||u_j re-orthogonalised||
+  double wnorm;             // ||A_hat q_j|| estimate (happy-breakdown scale)
   unsigned int counter;     // last-block ticket of the reduction kernels
   unsigned int pad0;
   // ---- host-visible block ----
   double red[8];            // results of the norms kernel
-  double wnorm0;            // ||A_hat v_j|| before orthogonalisation
   double err;               // error estimate at the last check
   double norm1;             // 1-norm of the last H_m
   int accept;               // set by the phi kernel
@@ -123,19 +123,23 @@ cudaError_t launch_norms(bool use_ff, KState* ks, void* part, int nx, const Vec*
 cudaError_t launch_to_f32(float* out, const double* x, size_t n, cudaStream_t s);
 cudaError_t launch_f64_to_ff(Vec out, const double* x, size_t n, cudaStream_t s);
 cudaError_t launch_ff_to_f64(double* out, Vec x, size_t n, cudaStream_t s);
-// Arnoldi start: u_0 = [b0; e_P / eta] (b0 null: zero top), s_0 = 1/beta; clears the Krylov scalars.
-cudaError_t launch_start(bool use_ff, KState* ks, Basis U, Vec b0, size_t N, int P, double eta, double beta,
-                         cudaStream_t s);
-// Classical Gram-Schmidt building blocks; w is basis slot J, vectors have n_aug entries:
-//   dots  (second = false): h_iJ-1 = s_i <u_i, w> (i < J), coef_i = h s_i, wnorm0 = ||w||
-//   dots  (second = true) : g_i = s_i <u_i, w>, H(i, J-1) += g_i, coef_i = g_i s_i
-//   update: w -= sum_i coef_i u_i; with finish = true also H(J, J-1) = ||w||,
-//           s_J = 1/||w|| (0 on a happy breakdown, recorded in breakdown_at).
-cudaError_t launch_dots(bool use_ff, KState* ks, void* part, Basis U, int J, size_t n_aug, bool second, cudaStream_t s);
-cudaError_t launch_update(bool use_ff, KState* ks, void* part, Basis U, int J, size_t n_aug, bool finish,
-                          cudaStream_t s);
+// Arnoldi start: u_0 = [b0; e_P / eta] (b0 null: zero top); clears the Krylov scalars.
+cudaError_t launch_start(bool use_ff, KState* ks, Basis U, Vec b0, size_t N, int P, double eta, cudaStream_t s);
+// Arnoldi step j by classical Gram-Schmidt with delayed re-orthogonalisation
+// (DCGS2).  On entry basis slots 0..j-1 hold the orthonormal q_i, slot j the
+// once-orthogonalised u_j, slot j+1 the operator image w = A_hat u_j.
+//   dots:   s = Q^T u_j, z = Q^T w, alpha = |u_j|^2, gamma = u_j.w, delta = |w|^2;
+//           r = sqrt(alpha - |s|^2); H(:, j-1) += s, H(j, j-1) = r;
+//           H(k, j) = (z_k - sum_i s_i H(k, i)) / r, H(j, j) = (c - s_{j-1} r) / r,
+//           c = (gamma - s.z) / r.
+//   update: q_j = (u_j - Q s) / r -> slot j;
+//           u_{j+1} = (w - Q z - c q_j) / r -> slot j+1; H(j+1, j) = |u_{j+1}|
+//           (provisional until the next step's correction); happy breakdown
+//           when |u_{j+1}| <= 1e-13 |A_hat q_j| (recorded in breakdown_at).
+cudaError_t launch_dots(bool use_ff, KState* ks, void* part, Basis U, int j, size_t n_aug, cudaStream_t s);
+cudaError_t launch_update(bool use_ff, KState* ks, void* part, Basis U, int j, size_t n_aug, cudaStream_t s);
 // FP64 phi kernel: E = exp(H_m) (Taylor-18 scaling and squaring), y = E e_1, error estimate,
-// acceptance (forced when force_accept), ycoef_i = beta y_i s_i.
+// acceptance (forced when force_accept), ycoef_i = beta y_i.
 cudaError_t launch_phi(KState* ks, int m, double beta, double tol, int force_accept, cudaStream_t s);
 // out = base + sum_{i < m_eff} ycoef_i u_i (first N entries; base may be null).
 // out and base may each be FP64 (d) or float-float (h, l).

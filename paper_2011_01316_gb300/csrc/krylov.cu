@@ -78,6 +78,13 @@ __device__ __forceinline__ typename Acc<FF>::T from_d(double x) {
     return x;
 }
 template <bool FF>
+__device__ __forceinline__ typename Acc<FF>::T mul(typename Acc<FF>::T a, typename Acc<FF>::T b) {
+  if constexpr (FF)
+    return ff_mul(a, b);
+  else
+    return a * b;
+}
+template <bool FF>
 __device__ __forceinline__ typename Acc<FF>::T negate(typename Acc<FF>::T x) {
   if constexpr (FF)
     return ff_neg(x);
@@ -235,8 +242,7 @@ __global__ void k_ff_to_f64(double* out, Vec x, size_t n) {
 }
 
 template <bool FF>
-__global__ void __launch_bounds__(NT) k_start(KState* ks, Vec u0, Vec b0, size_t N, int P, double eta,
-                                             double beta) {
+__global__ void __launch_bounds__(NT) k_start(KState* ks, Vec u0, Vec b0, size_t N, int P, double eta) {
   using A = Acc<FF>;
   const bool present = FF ? (b0.h != nullptr) : (b0.d != nullptr);
   const size_t n_aug = N + P;
@@ -251,16 +257,10 @@ __global__ void __launch_bounds__(NT) k_start(KState* ks, Vec u0, Vec b0, size_t
   if (blockIdx.x == 0) {
     for (int k = threadIdx.x; k < (MMAX + 1) * MMAX; k += NT) ks->H[k] = 0.0;
     if (threadIdx.x == 0) {
-      const double s0 = 1.0 / beta;
-      ks->s[0] = s0;
-      ff t = ff_from_double(s0);
-      ks->sh[0] = t.h;
-      ks->sl[0] = t.l;
       ks->breakdown_at = 0;
       ks->accept = 0;
       ks->m_eff = 0;
       ks->err = 0.0;
-      ks->wnorm0 = 0.0;
     }
   }
 }
@@ -311,108 +311,166 @@ __device__ __forceinline__ void stq(const Basis& U, int k, size_t g, const Quad<
   }
 }
 
-// Multi-dot: grid (gx, chunks); block (bx, c) forms <u_k, w> for the basis
-// vectors k = c*DOT_CHUNK .. +DOT_CHUNK-1 over its share of the elements
-// (groups of four per thread, every load of a group issued before its math;
-// the ragged end of the vector is taken one element at a time).
+// DCGS2 inner products of Arnoldi step j: grid (gx, chunks); block (bx, c)
+// handles the vectors x_i, i = c*DOT_CHUNK .. +DOT_CHUNK-1 of [q_0..q_{j-1}, u_j],
+// forming a_i = <x_i, u_j> and b_i = <x_i, w> (chunk 0 also <w, w>) over its
+// share of the elements, four per thread with every load issued before the
+// math.  The last block turns the sums into the Hessenberg entries and the
+// coefficients of the update pass.
 template <bool FF>
-__global__ void __launch_bounds__(NT) k_dots(KState* ks, typename Acc<FF>::T* part, Basis U, int J, size_t n_aug,
-                                            int second) {
+__global__ void __launch_bounds__(NT) k_dots(KState* ks, typename Acc<FF>::T* part, Basis U, int j, size_t n_aug) {
   using A = Acc<FF>;
-  constexpr int K = DOT_CHUNK + 1;  // + ||w||^2 (first pass, chunk 0)
+  constexpr int K = 2 * DOT_CHUNK + 1;
   __shared__ typename A::T sh[NW * K];
   __shared__ typename A::T tot[K];
+  if (ks->breakdown_at > 0 && j >= ks->breakdown_at) return;  // uniform: every block leaves
+  const int nvec = j + 1;
   const int c0 = blockIdx.y * DOT_CHUNK;
-  const int nc = min(DOT_CHUNK, J - c0);
+  const int nc = min(DOT_CHUNK, nvec - c0);
   typename A::T acc[K];
 #pragma unroll
   for (int k = 0; k < K; ++k) acc[k] = A::zero();
-  const bool wnorm = (!second) && blockIdx.y == 0;
+  const bool wnorm = blockIdx.y == 0;
   const size_t ng = n_aug / 4;
   const size_t tid = blockIdx.x * (size_t)NT + threadIdx.x, nthr = (size_t)gridDim.x * NT;
   for (size_t g = tid; g < ng; g += nthr) {
-    const Quad<FF> w = ldq<FF>(U, J, g);
-    Quad<FF> u[DOT_CHUNK];
+    const Quad<FF> uj = ldq<FF>(U, j, g);
+    const Quad<FF> w = ldq<FF>(U, j + 1, g);
+    Quad<FF> x[DOT_CHUNK];
 #pragma unroll
-    for (int c = 0; c < DOT_CHUNK; ++c) u[c] = ldq<FF>(U, c0 + (c < nc ? c : 0), g);
+    for (int c = 0; c < DOT_CHUNK; ++c) x[c] = ldq<FF>(U, c0 + (c < nc ? c : 0), g);
 #pragma unroll
     for (int c = 0; c < DOT_CHUNK; ++c)
       if (c < nc)
 #pragma unroll
-        for (int e = 0; e < 4; ++e) acc[c] = fma_acc<FF>(u[c].v[e], w.v[e], acc[c]);
+        for (int e = 0; e < 4; ++e) {
+          acc[2 * c] = fma_acc<FF>(x[c].v[e], uj.v[e], acc[2 * c]);
+          acc[2 * c + 1] = fma_acc<FF>(x[c].v[e], w.v[e], acc[2 * c + 1]);
+        }
     if (wnorm)
 #pragma unroll
-      for (int e = 0; e < 4; ++e) acc[DOT_CHUNK] = fma_acc<FF>(w.v[e], w.v[e], acc[DOT_CHUNK]);
+      for (int e = 0; e < 4; ++e) acc[2 * DOT_CHUNK] = fma_acc<FF>(w.v[e], w.v[e], acc[2 * DOT_CHUNK]);
   }
   for (size_t i = 4 * ng + tid; i < n_aug; i += nthr) {
-    const typename A::T wi = ldb<FF>(U, J, i);
-    for (int c = 0; c < nc; ++c) acc[c] = fma_acc<FF>(ldb<FF>(U, c0 + c, i), wi, acc[c]);
-    if (wnorm) acc[DOT_CHUNK] = fma_acc<FF>(wi, wi, acc[DOT_CHUNK]);
+    const typename A::T ui = ldb<FF>(U, j, i), wi = ldb<FF>(U, j + 1, i);
+    for (int c = 0; c < nc; ++c) {
+      const typename A::T xi = ldb<FF>(U, c0 + c, i);
+      acc[2 * c] = fma_acc<FF>(xi, ui, acc[2 * c]);
+      acc[2 * c + 1] = fma_acc<FF>(xi, wi, acc[2 * c + 1]);
+    }
+    if (wnorm) acc[2 * DOT_CHUNK] = fma_acc<FF>(wi, wi, acc[2 * DOT_CHUNK]);
   }
   block_sum<FF, K>(acc, sh, tot);
   const int G = gridDim.x;
-  if (threadIdx.x < nc) part[(size_t)(c0 + threadIdx.x) * G + blockIdx.x] = tot[threadIdx.x];
-  if (wnorm && threadIdx.x == DOT_CHUNK) part[(size_t)J * G + blockIdx.x] = tot[DOT_CHUNK];
+  if (threadIdx.x < 2 * nc) part[(size_t)(2 * c0 + threadIdx.x) * G + blockIdx.x] = tot[threadIdx.x];
+  if (wnorm && threadIdx.x == 2 * DOT_CHUNK) part[(size_t)(2 * nvec) * G + blockIdx.x] = tot[2 * DOT_CHUNK];
   if (last_block(&ks->counter, gridDim.x * gridDim.y)) {
-    __shared__ double res[MMAX + 1];
-    final_sums<FF>(part, second ? J : J + 1, G, res);
+    __shared__ double res[2 * MMAX + 4];
+    __shared__ double sc[4];  // r, c
+    final_sums<FF>(part, 2 * nvec + 1, G, res);
     __syncthreads();
-    const int j = J - 1;  // column of H being built
-    for (int i = threadIdx.x; i < J; i += NT) {
-      const double gi = ks->s[i] * res[i];
-      if (second) {
-        ks->H[j * (MMAX + 1) + i] += gi;
-      } else {
-        ks->H[j * (MMAX + 1) + i] = gi;
+    // res[2i] = <x_i, u_j>, res[2i+1] = <x_i, w>; x_j = u_j; res[2 nvec] = <w, w>
+    if (threadIdx.x == 0) {
+      double ss = 0.0, sz = 0.0;
+      for (int i = 0; i < j; ++i) {
+        ss += res[2 * i] * res[2 * i];
+        sz += res[2 * i] * res[2 * i + 1];
       }
-      ks->coef[i] = gi * ks->s[i];
+      const double alpha = res[2 * j], gamma = res[2 * j + 1];
+      const double r = sqrt(fmax(alpha - ss, 0.0));
+      const double c = (r > 0.0) ? (gamma - sz) / r : 0.0;
+      sc[0] = r;
+      sc[1] = c;
+      ks->inv_r = (r > 0.0) ? 1.0 / r : 0.0;
+      ks->cu = (r > 0.0) ? c / r : 0.0;
+      ks->wnorm = (r > 0.0) ? sqrt(res[2 * nvec]) / r : 0.0;
     }
-    if (!second && threadIdx.x == 0) ks->wnorm0 = sqrt(res[J]);
-    if (threadIdx.x == 0) ks->counter = 0;
+    __syncthreads();
+    const double r = sc[0], c = sc[1];
+    // column j-1: delayed re-orthogonalisation correction
+    if (j >= 1) {
+      for (int i = threadIdx.x; i < j; i += NT) ks->H[(j - 1) * (MMAX + 1) + i] += res[2 * i];
+      if (threadIdx.x == 0) ks->H[(j - 1) * (MMAX + 1) + j] = r;
+    }
+    __syncthreads();
+    // column j
+    for (int k = threadIdx.x; k < j; k += NT) {
+      double acc2 = 0.0;
+      for (int i = (k > 0 ? k - 1 : 0); i < j; ++i) acc2 += res[2 * i] * ks->H[i * (MMAX + 1) + k];
+      ks->H[j * (MMAX + 1) + k] = (r > 0.0) ? (res[2 * k + 1] - acc2) / r : 0.0;
+      ks->qcoef[k] = res[2 * k];
+      ks->ucoef[k] = res[2 * k + 1] - ((r > 0.0) ? c / r : 0.0) * res[2 * k];
+    }
+    if (threadIdx.x == 0) {
+      const double sjm1 = (j >= 1) ? res[2 * (j - 1)] : 0.0;
+      ks->H[j * (MMAX + 1) + j] = (r > 0.0) ? (c - sjm1 * r) / r : 0.0;
+      ks->counter = 0;
+    }
   }
 }
 
-// Update w -= sum_{k<J} coef_k u_k over groups of four elements per thread
-// (four independent accumulation chains), optionally with ||w||^2.
+// DCGS2 update of Arnoldi step j (coefficients from k_dots):
+//   q_j = (u_j - sum_k s_k q_k) / r                   -> slot j
+//   u_{j+1} = (w - (c/r) u_j - sum_k (z_k - (c/r) s_k) q_k) / r -> slot j+1
+// four elements per thread, two independent accumulation chains, and
+// |u_{j+1}|^2 for the provisional H(j+1, j).
 template <bool FF>
-__global__ void __launch_bounds__(NT) k_update(KState* ks, typename Acc<FF>::T* part, Basis U, int J, size_t n_aug,
-                                              int finish) {
+__global__ void __launch_bounds__(NT) k_update(KState* ks, typename Acc<FF>::T* part, Basis U, int j, size_t n_aug) {
   using A = Acc<FF>;
-  __shared__ typename A::T cf[MMAX + 1];
+  __shared__ typename A::T qc[MMAX + 1];
+  __shared__ typename A::T uc[MMAX + 1];
+  __shared__ typename A::T sc[2];
   __shared__ typename A::T sh[NW];
-  for (int i = threadIdx.x; i < J; i += NT) cf[i] = negate<FF>(from_d<FF>(ks->coef[i]));
+  if (ks->breakdown_at > 0 && j >= ks->breakdown_at) return;
+  for (int k = threadIdx.x; k < j; k += NT) {
+    qc[k] = negate<FF>(from_d<FF>(ks->qcoef[k]));
+    uc[k] = negate<FF>(from_d<FF>(ks->ucoef[k]));
+  }
+  if (threadIdx.x == 0) {
+    sc[0] = negate<FF>(from_d<FF>(ks->cu));
+    sc[1] = from_d<FF>(ks->inv_r);
+  }
   __syncthreads();
+  const typename A::T ncu = sc[0], ir = sc[1];
   typename A::T nrm[1] = {A::zero()};
   const size_t ng = n_aug / 4;
   const size_t tid = blockIdx.x * (size_t)NT + threadIdx.x, nthr = (size_t)gridDim.x * NT;
   for (size_t g = tid; g < ng; g += nthr) {
-    Quad<FF> x = ldq<FF>(U, J, g);
-    int k = 0;
-    for (; k + 2 <= J; k += 2) {
-      const Quad<FF> u0 = ldq<FF>(U, k, g);
-      const Quad<FF> u1 = ldq<FF>(U, k + 1, g);
+    Quad<FF> xq = ldq<FF>(U, j, g);
+    Quad<FF> xu = ldq<FF>(U, j + 1, g);
 #pragma unroll
-      for (int e = 0; e < 4; ++e) x.v[e] = fma_acc<FF>(cf[k], u0.v[e], x.v[e]);
+    for (int e = 0; e < 4; ++e) xu.v[e] = fma_acc<FF>(ncu, xq.v[e], xu.v[e]);
+    for (int k = 0; k < j; ++k) {
+      const Quad<FF> q = ldq<FF>(U, k, g);
 #pragma unroll
-      for (int e = 0; e < 4; ++e) x.v[e] = fma_acc<FF>(cf[k + 1], u1.v[e], x.v[e]);
+      for (int e = 0; e < 4; ++e) {
+        xq.v[e] = fma_acc<FF>(qc[k], q.v[e], xq.v[e]);
+        xu.v[e] = fma_acc<FF>(uc[k], q.v[e], xu.v[e]);
+      }
     }
-    if (k < J) {
-      const Quad<FF> u0 = ldq<FF>(U, k, g);
 #pragma unroll
-      for (int e = 0; e < 4; ++e) x.v[e] = fma_acc<FF>(cf[k], u0.v[e], x.v[e]);
+    for (int e = 0; e < 4; ++e) {
+      xq.v[e] = mul<FF>(xq.v[e], ir);
+      xu.v[e] = mul<FF>(xu.v[e], ir);
+      nrm[0] = fma_acc<FF>(xu.v[e], xu.v[e], nrm[0]);
     }
-    stq<FF>(U, J, g, x);
-    if (finish)
-#pragma unroll
-      for (int e = 0; e < 4; ++e) nrm[0] = fma_acc<FF>(x.v[e], x.v[e], nrm[0]);
+    stq<FF>(U, j, g, xq);
+    stq<FF>(U, j + 1, g, xu);
   }
   for (size_t i = 4 * ng + tid; i < n_aug; i += nthr) {
-    typename A::T x = ldb<FF>(U, J, i);
-    for (int k = 0; k < J; ++k) x = fma_acc<FF>(cf[k], ldb<FF>(U, k, i), x);
-    stb<FF>(U, J, i, x);
-    if (finish) nrm[0] = fma_acc<FF>(x, x, nrm[0]);
+    typename A::T xq = ldb<FF>(U, j, i);
+    typename A::T xu = fma_acc<FF>(ncu, xq, ldb<FF>(U, j + 1, i));
+    for (int k = 0; k < j; ++k) {
+      const typename A::T q = ldb<FF>(U, k, i);
+      xq = fma_acc<FF>(qc[k], q, xq);
+      xu = fma_acc<FF>(uc[k], q, xu);
+    }
+    xq = mul<FF>(xq, ir);
+    xu = mul<FF>(xu, ir);
+    nrm[0] = fma_acc<FF>(xu, xu, nrm[0]);
+    stb<FF>(U, j, i, xq);
+    stb<FF>(U, j + 1, i, xu);
   }
-  if (!finish) return;
   __shared__ typename A::T tot[1];
   block_sum<FF, 1>(nrm, sh, tot);
   if (threadIdx.x == 0) part[blockIdx.x] = tot[0];
@@ -422,18 +480,8 @@ __global__ void __launch_bounds__(NT) k_update(KState* ks, typename Acc<FF>::T* 
     __syncthreads();
     if (threadIdx.x == 0) {
       const double h = sqrt(res[0]);
-      const int j = J - 1;
-      ks->H[j * (MMAX + 1) + J] = h;
-      double sj = 0.0;
-      if (h <= 1e-13 * ks->wnorm0 || h == 0.0) {
-        if (ks->breakdown_at == 0) ks->breakdown_at = J;
-      } else {
-        sj = 1.0 / h;
-      }
-      ks->s[J] = sj;
-      ff t = ff_from_double(sj);
-      ks->sh[J] = t.h;
-      ks->sl[J] = t.l;
+      ks->H[j * (MMAX + 1) + j + 1] = h;
+      if ((h <= 1e-13 * ks->wnorm || h == 0.0) && ks->breakdown_at == 0) ks->breakdown_at = j + 1;
       ks->counter = 0;
     }
   }
@@ -552,7 +600,7 @@ k_phi(KState* ks, int m_req, double beta, double tol, int force) {
       ks->norm1 = s_norm;
       ks->squarings = sq;
     }
-    for (int i = threadIdx.x; i < m; i += blockDim.x) ks->ycoef[i] = beta * E[i * m] * ks->s[i];
+    for (int i = threadIdx.x; i < m; i += blockDim.x) ks->ycoef[i] = beta * E[i * m];
   }
   cl.sync();  // no CTA exits while others may still write into its shared memory
 }
@@ -596,7 +644,7 @@ int grid_for(size_t n) {
 
 }  // namespace
 
-size_t reduction_scratch_entries() { return (size_t)RB * (MMAX + 2) + 64; }
+size_t reduction_scratch_entries() { return (size_t)RB * (2 * MMAX + 4) + 64; }
 
 cudaError_t launch_lincomb(bool use_ff, Vec out, int nx, const Vec* x, const double* a, size_t n, cudaStream_t s) {
   if (nx > NORMS_MAX) return cudaErrorInvalidValue;
@@ -647,39 +695,37 @@ cudaError_t launch_ff_to_f64(double* out, Vec x, size_t n, cudaStream_t s) {
   return cudaGetLastError();
 }
 
-cudaError_t launch_start(bool use_ff, KState* ks, Basis U, Vec b0, size_t N, int P, double eta, double beta,
-                         cudaStream_t s) {
+cudaError_t launch_start(bool use_ff, KState* ks, Basis U, Vec b0, size_t N, int P, double eta, cudaStream_t s) {
   const int g = grid_for(N + P);
   if (use_ff)
-    k_start<true><<<g, NT, 0, s>>>(ks, U.at(0), b0, N, P, eta, beta);
+    k_start<true><<<g, NT, 0, s>>>(ks, U.at(0), b0, N, P, eta);
   else
-    k_start<false><<<g, NT, 0, s>>>(ks, U.at(0), b0, N, P, eta, beta);
+    k_start<false><<<g, NT, 0, s>>>(ks, U.at(0), b0, N, P, eta);
   return cudaGetLastError();
 }
 
-cudaError_t launch_dots(bool use_ff, KState* ks, void* part, Basis U, int J, size_t n_aug, bool second, cudaStream_t s) {
-  if (J < 1 || J > MMAX) return cudaErrorInvalidValue;
-  const int chunks = (J + DOT_CHUNK - 1) / DOT_CHUNK;
+cudaError_t launch_dots(bool use_ff, KState* ks, void* part, Basis U, int j, size_t n_aug, cudaStream_t s) {
+  if (j < 0 || j + 1 > MMAX) return cudaErrorInvalidValue;
+  const int chunks = (j + 1 + DOT_CHUNK - 1) / DOT_CHUNK;
   int gx = (RB + chunks - 1) / chunks;
   const int need = (int)((n_aug / 4 + NT - 1) / NT);
   if (gx > need) gx = need;
   if (gx < 1) gx = 1;
   dim3 grid(gx, chunks);
   if (use_ff)
-    k_dots<true><<<grid, NT, 0, s>>>(ks, static_cast<ff*>(part), U, J, n_aug, second ? 1 : 0);
+    k_dots<true><<<grid, NT, 0, s>>>(ks, static_cast<ff*>(part), U, j, n_aug);
   else
-    k_dots<false><<<grid, NT, 0, s>>>(ks, static_cast<double*>(part), U, J, n_aug, second ? 1 : 0);
+    k_dots<false><<<grid, NT, 0, s>>>(ks, static_cast<double*>(part), U, j, n_aug);
   return cudaGetLastError();
 }
 
-cudaError_t launch_update(bool use_ff, KState* ks, void* part, Basis U, int J, size_t n_aug, bool finish,
-                          cudaStream_t s) {
-  if (J < 1 || J > MMAX) return cudaErrorInvalidValue;
+cudaError_t launch_update(bool use_ff, KState* ks, void* part, Basis U, int j, size_t n_aug, cudaStream_t s) {
+  if (j < 0 || j + 1 > MMAX) return cudaErrorInvalidValue;
   const int g = grid_for(n_aug / 4 + 1);
   if (use_ff)
-    k_update<true><<<g, NT, 0, s>>>(ks, static_cast<ff*>(part), U, J, n_aug, finish ? 1 : 0);
+    k_update<true><<<g, NT, 0, s>>>(ks, static_cast<ff*>(part), U, j, n_aug);
   else
-    k_update<false><<<g, NT, 0, s>>>(ks, static_cast<double*>(part), U, J, n_aug, finish ? 1 : 0);
+    k_update<false><<<g, NT, 0, s>>>(ks, static_cast<double*>(part), U, j, n_aug);
   return cudaGetLastError();
 }
 
