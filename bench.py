@@ -179,41 +179,46 @@ def main():
     ctx64.step(qb, DT)
     err_vs_fp64 = float(torch.linalg.vector_norm(qa - qb) / torch.linalg.vector_norm(qb))
 
-    def timed(c, q, k, prof):
-        tot = 0.0
+    def timed(c, q, k):
         ev0 = torch.cuda.Event(enable_timing=True)
         ev1 = torch.cuda.Event(enable_timing=True)
-        per = []
+        per, iters = [], []
         for _ in range(k):
             flush.zero_()
             ev0.record(stream)
-            c.step(q, DT)
+            st, _ = c.step(q, DT)
             ev1.record(stream)
             ev1.synchronize()
             per.append(ev0.elapsed_time(ev1))
-        return per
+            iters.append(st["krylov_iters"])
+        return per, iters
 
     q = q0.clone()
     for _ in range(args.warmup):
         ctx.step(q, DT)
+    # timed region: K steps from the initial state, launch counting only
     q = q0.clone()
-    ctx.profile_enable(True)
+    ctx.profile_enable(False)
     barrier()
     with ClockSampler(local) as clk:
-        per = timed(ctx, q, args.steps, True)
+        per, iters = timed(ctx, q, args.steps)
         barrier()
-    kern = ctx.profile_get(reset=True)
-    ctx.profile_enable(False)
+    launches = sum(v["launches"] for v in ctx.profile_get(reset=True).values())
     t_local = sum(per) / 1e3
     t = torch.tensor([t_local], device="cuda", dtype=torch.float64)
     if world > 1:
         dist.all_reduce(t, op=dist.ReduceOp.MAX)
     t_max = float(t.item())
     value = world * N * args.steps / t_max
+    # the same K steps again with a CUDA event pair around every launch
+    q = q0.clone()
+    ctx.profile_enable(True)
+    per_prof, _ = timed(ctx, q, args.steps)
+    kern = ctx.profile_get(reset=True)
+    ctx.profile_enable(False)
 
     # per-kernel-class profile over the timed region
     hbm, peak_kind = peaks()
-    launches = sum(v["launches"] for v in kern.values())
     bw = {k: v for k, v in kern.items() if k in ("jv", "dots", "update", "residual", "combine")}
     dom = max(bw, key=lambda k: bw[k]["ms"])
     d = kern[dom]
@@ -225,9 +230,9 @@ def main():
     # FP64 form, same workload
     q = q0.clone()
     ctx64.step(q, DT)
-    per64 = timed(ctx64, q, args.fp64_steps, False)
+    per64, it64 = timed(ctx64, q, args.fp64_steps)
     fp64 = {"value": N * len(per64) / (sum(per64) / 1e3), "ms_per_step": sum(per64) / len(per64),
-            "steps": len(per64)}
+            "steps": len(per64), "krylov_iters_per_step": statistics.mean(it64)}
 
     # end to end through the C-ABI with pinned host buffers (copies inside the call)
     qh = torch.empty(q0.shape, dtype=torch.float64, pin_memory=True)
@@ -258,7 +263,9 @@ def main():
                            "parallelism": "replicas" if world > 1 else "single GPU"},
                 "err_vs_fp64": err_vs_fp64, "fp64_form": fp64, "e2e": e2e, "gpu_launches": launches,
                 "roofline": roofline, "kernels": kern, "cpu_baseline": cpu, "clocks": clk.summary(),
-                "ms_per_step_min": min(per), "ms_per_step_median": statistics.median(per)}
+                "ms_per_step_min": min(per), "ms_per_step_median": statistics.median(per),
+                "krylov_iters_per_step": statistics.mean(iters),
+                "ms_per_step_profiled": sum(per_prof) / len(per_prof)}
         print(json.dumps(line), flush=True)
     if world > 1:
         dist.destroy_process_group()

@@ -77,3 +77,76 @@ __device__ __forceinline__ ff ff_shfl_down(ff a, int off) {
 }
 
 }  // namespace expdg
+
+namespace expdg {
+
+// ---- two lanes at once (Blackwell packed FP32: FADD2 / FMUL2 / FFMA2) ----
+// These halve the instruction count of the error-free transformations; the
+// FP32 pipe itself runs one lane-operation per lane per clock either way.
+__device__ __forceinline__ float2 add2(float2 a, float2 b) { return __fadd2_rn(a, b); }
+__device__ __forceinline__ float2 neg2(float2 a) { return make_float2(-a.x, -a.y); }
+__device__ __forceinline__ float2 sub2(float2 a, float2 b) { return __fadd2_rn(a, neg2(b)); }
+__device__ __forceinline__ float2 mul2(float2 a, float2 b) { return __fmul2_rn(a, b); }
+__device__ __forceinline__ float2 fma2(float2 a, float2 b, float2 c) { return __ffma2_rn(a, b, c); }
+
+// Compensated dot-product accumulation (the Dot2 scheme of Ogita, Rump & Oishi,
+// with float-float operands): S carries the running sum of the rounded
+// products (TwoSum keeps it exact), C the product errors (TwoProduct), the
+// low-part cross terms and the TwoSum errors.  12 packed instructions per two
+// terms.  The value of the sum is S + C.
+__device__ __forceinline__ void dot2_acc(float2 xh, float2 xl, float2 yh, float2 yl, float2& S, float2& C) {
+  const float2 p = mul2(xh, yh);
+  float2 e = fma2(xh, yh, neg2(p));
+  e = fma2(xh, yl, e);
+  e = fma2(xl, yh, e);
+  const float2 s = add2(S, p);
+  const float2 bb = sub2(s, S);
+  const float2 err = add2(sub2(S, sub2(s, bb)), sub2(p, bb));
+  S = s;
+  C = add2(C, add2(err, e));
+}
+
+// x += c * q with x = (xh, xl) kept un-normalised: xh takes the rounded
+// products exactly (TwoSum), xl collects every error term.  Normalise with
+// ff2_norm after at most a few dozen terms.
+__device__ __forceinline__ void axpy2_acc(float2 ch, float2 cl, float2 qh, float2 ql, float2& xh, float2& xl) {
+  const float2 p = mul2(ch, qh);
+  float2 e = fma2(ch, qh, neg2(p));
+  e = fma2(ch, ql, e);
+  e = fma2(cl, qh, e);
+  const float2 s = add2(xh, p);
+  const float2 bb = sub2(s, xh);
+  const float2 err = add2(sub2(xh, sub2(s, bb)), sub2(p, bb));
+  xh = s;
+  xl = add2(xl, add2(err, e));
+}
+
+// (h, l) <- TwoSum(h, l): exact renormalisation whatever the magnitudes
+// (after cancellation |l| may exceed |h|).
+__device__ __forceinline__ void ff2_norm(float2& h, float2& l) {
+  const float2 s = add2(h, l);
+  const float2 bb = sub2(s, h);
+  const float2 e = add2(sub2(h, sub2(s, bb)), sub2(l, bb));
+  h = s;
+  l = e;
+}
+
+// (h, l) * c for a float-float scalar c, result normalised (|e| << |p|).
+__device__ __forceinline__ void ff2_scale(float2& h, float2& l, float2 ch, float2 cl) {
+  const float2 p = mul2(h, ch);
+  float2 e = fma2(h, ch, neg2(p));
+  e = fma2(h, cl, e);
+  e = fma2(l, ch, e);
+  const float2 s2 = add2(p, e);
+  l = sub2(e, sub2(s2, p));
+  h = s2;
+}
+
+// S + C of dot2_acc, both lanes summed, as one float-float value.
+__device__ __forceinline__ ff dot2_value(float2 S, float2 C) {
+  ff t = ff_two_sum(S.x, S.y);
+  const float c = __fadd_rn(__fadd_rn(C.x, C.y), t.l);
+  return ff_fast_two_sum(t.h, c);
+}
+
+}  // namespace expdg

@@ -311,6 +311,61 @@ __device__ __forceinline__ void stq(const Basis& U, int k, size_t g, const Quad<
   }
 }
 
+// Last block of a DCGS2 dots launch: partial sums -> Hessenberg column j-1
+// correction, column j, and the coefficients of the update pass.
+template <bool FF>
+__device__ void dots_last_block(KState* ks, const typename Acc<FF>::T* part, int j, int G) {
+  const int nvec = j + 1;
+    __shared__ double res[2 * MMAX + 4];
+    __shared__ double sc[4];  // r, c
+    final_sums<FF>(part, 2 * nvec + 1, G, res);
+    __syncthreads();
+    // res[2i] = <x_i, u_j>, res[2i+1] = <x_i, w>; x_j = u_j; res[2 nvec] = <w, w>
+    if (threadIdx.x == 0) {
+      double ss = 0.0, sz = 0.0;
+      for (int i = 0; i < j; ++i) {
+        ss += res[2 * i] * res[2 * i];
+        sz += res[2 * i] * res[2 * i + 1];
+      }
+      const double alpha = res[2 * j], gamma = res[2 * j + 1];
+      const double r = sqrt(fmax(alpha - ss, 0.0));
+      const double c = (r > 0.0) ? (gamma - sz) / r : 0.0;
+      sc[0] = r;
+      sc[1] = c;
+      ks->inv_r = (r > 0.0) ? 1.0 / r : 0.0;
+      ks->cu = (r > 0.0) ? c / r : 0.0;
+      ks->wnorm = (r > 0.0) ? sqrt(res[2 * nvec]) / r : 0.0;
+    }
+    // stage columns 0..j-1 of H (rows 0..j) in shared memory: one coalesced load
+    __shared__ double Hs[MMAX * (MMAX + 1)];
+    for (int idx = threadIdx.x; idx < j * (MMAX + 1); idx += NT) Hs[idx] = ks->H[idx];
+    __syncthreads();
+    const double r = sc[0], c = sc[1];
+    // column j-1: delayed re-orthogonalisation correction
+    if (j >= 1) {
+      for (int i = threadIdx.x; i < j; i += NT) {
+        const double v = Hs[(j - 1) * (MMAX + 1) + i] + res[2 * i];
+        Hs[(j - 1) * (MMAX + 1) + i] = v;
+        ks->H[(j - 1) * (MMAX + 1) + i] = v;
+      }
+      if (threadIdx.x == 0) ks->H[(j - 1) * (MMAX + 1) + j] = r;
+    }
+    __syncthreads();
+    // column j
+    for (int k = threadIdx.x; k < j; k += NT) {
+      double acc2 = 0.0;
+      for (int i = (k > 0 ? k - 1 : 0); i < j; ++i) acc2 += res[2 * i] * Hs[i * (MMAX + 1) + k];
+      ks->H[j * (MMAX + 1) + k] = (r > 0.0) ? (res[2 * k + 1] - acc2) / r : 0.0;
+      ks->qcoef[k] = res[2 * k];
+      ks->ucoef[k] = res[2 * k + 1] - ((r > 0.0) ? c / r : 0.0) * res[2 * k];
+    }
+    if (threadIdx.x == 0) {
+      const double sjm1 = (j >= 1) ? res[2 * (j - 1)] : 0.0;
+      ks->H[j * (MMAX + 1) + j] = (r > 0.0) ? (c - sjm1 * r) / r : 0.0;
+      ks->counter = 0;
+    }
+}
+
 // DCGS2 inner products of Arnoldi step j: grid (gx, chunks); block (bx, c)
 // handles the vectors x_i, i = c*DOT_CHUNK .. +DOT_CHUNK-1 of [q_0..q_{j-1}, u_j],
 // forming a_i = <x_i, u_j> and b_i = <x_i, w> (chunk 0 also <w, w>) over its
@@ -364,49 +419,7 @@ __global__ void __launch_bounds__(NT) k_dots(KState* ks, typename Acc<FF>::T* pa
   const int G = gridDim.x;
   if (threadIdx.x < 2 * nc) part[(size_t)(2 * c0 + threadIdx.x) * G + blockIdx.x] = tot[threadIdx.x];
   if (wnorm && threadIdx.x == 2 * DOT_CHUNK) part[(size_t)(2 * nvec) * G + blockIdx.x] = tot[2 * DOT_CHUNK];
-  if (last_block(&ks->counter, gridDim.x * gridDim.y)) {
-    __shared__ double res[2 * MMAX + 4];
-    __shared__ double sc[4];  // r, c
-    final_sums<FF>(part, 2 * nvec + 1, G, res);
-    __syncthreads();
-    // res[2i] = <x_i, u_j>, res[2i+1] = <x_i, w>; x_j = u_j; res[2 nvec] = <w, w>
-    if (threadIdx.x == 0) {
-      double ss = 0.0, sz = 0.0;
-      for (int i = 0; i < j; ++i) {
-        ss += res[2 * i] * res[2 * i];
-        sz += res[2 * i] * res[2 * i + 1];
-      }
-      const double alpha = res[2 * j], gamma = res[2 * j + 1];
-      const double r = sqrt(fmax(alpha - ss, 0.0));
-      const double c = (r > 0.0) ? (gamma - sz) / r : 0.0;
-      sc[0] = r;
-      sc[1] = c;
-      ks->inv_r = (r > 0.0) ? 1.0 / r : 0.0;
-      ks->cu = (r > 0.0) ? c / r : 0.0;
-      ks->wnorm = (r > 0.0) ? sqrt(res[2 * nvec]) / r : 0.0;
-    }
-    __syncthreads();
-    const double r = sc[0], c = sc[1];
-    // column j-1: delayed re-orthogonalisation correction
-    if (j >= 1) {
-      for (int i = threadIdx.x; i < j; i += NT) ks->H[(j - 1) * (MMAX + 1) + i] += res[2 * i];
-      if (threadIdx.x == 0) ks->H[(j - 1) * (MMAX + 1) + j] = r;
-    }
-    __syncthreads();
-    // column j
-    for (int k = threadIdx.x; k < j; k += NT) {
-      double acc2 = 0.0;
-      for (int i = (k > 0 ? k - 1 : 0); i < j; ++i) acc2 += res[2 * i] * ks->H[i * (MMAX + 1) + k];
-      ks->H[j * (MMAX + 1) + k] = (r > 0.0) ? (res[2 * k + 1] - acc2) / r : 0.0;
-      ks->qcoef[k] = res[2 * k];
-      ks->ucoef[k] = res[2 * k + 1] - ((r > 0.0) ? c / r : 0.0) * res[2 * k];
-    }
-    if (threadIdx.x == 0) {
-      const double sjm1 = (j >= 1) ? res[2 * (j - 1)] : 0.0;
-      ks->H[j * (MMAX + 1) + j] = (r > 0.0) ? (c - sjm1 * r) / r : 0.0;
-      ks->counter = 0;
-    }
-  }
+  if (last_block(&ks->counter, gridDim.x * gridDim.y)) dots_last_block<FF>(ks, part, j, G);
 }
 
 // DCGS2 update of Arnoldi step j (coefficients from k_dots):
@@ -477,6 +490,183 @@ __global__ void __launch_bounds__(NT) k_update(KState* ks, typename Acc<FF>::T* 
   if (last_block(&ks->counter, gridDim.x)) {
     __shared__ double res[1];
     final_sums<FF>(part, 1, gridDim.x, res);
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      const double h = sqrt(res[0]);
+      ks->H[j * (MMAX + 1) + j + 1] = h;
+      if ((h <= 1e-13 * ks->wnorm || h == 0.0) && ks->breakdown_at == 0) ks->breakdown_at = j + 1;
+      ks->counter = 0;
+    }
+  }
+}
+
+
+// ---- float-float (mixed form) Gram-Schmidt passes --------------------------
+// Same mathematics as k_dots / k_update, with the products and sums done two
+// elements at a time in packed FP32 (compensated accumulation, 12 packed
+// instructions per two terms) so that the passes stay within the FP32 issue
+// and pipe budget at HBM bandwidth.
+constexpr int FF_CH = 4;  // basis vectors per block row
+
+__device__ __forceinline__ float2 lo2(float4 v) { return make_float2(v.x, v.y); }
+__device__ __forceinline__ float2 hi2(float4 v) { return make_float2(v.z, v.w); }
+
+__global__ void __launch_bounds__(NT, 2) k_dots_ff(KState* ks, ff* part, Basis U, int j, size_t n_aug) {
+  constexpr int K = 2 * FF_CH + 1;
+  __shared__ ff sh[NW * K];
+  __shared__ ff tot[K];
+  if (ks->breakdown_at > 0 && j >= ks->breakdown_at) return;
+  const int nvec = j + 1;
+  const int c0 = blockIdx.y * FF_CH;
+  const int nc = min(FF_CH, nvec - c0);
+  const bool wnorm = blockIdx.y == 0;
+  float2 S[K], C[K];
+#pragma unroll
+  for (int k2 = 0; k2 < K; ++k2) S[k2] = C[k2] = make_float2(0.f, 0.f);
+  const size_t ld = U.ld, ng = n_aug / 4;
+  const float* __restrict__ Uh = U.h;
+  const float* __restrict__ Ul = U.l;
+  const size_t tid = blockIdx.x * (size_t)NT + threadIdx.x, nthr = (size_t)gridDim.x * NT;
+  for (size_t g = tid; g < ng; g += nthr) {
+    const size_t o = 4 * g;
+    const float4 ujh = __ldg(reinterpret_cast<const float4*>(Uh + j * ld + o));
+    const float4 ujl = __ldg(reinterpret_cast<const float4*>(Ul + j * ld + o));
+    const float4 wh = __ldg(reinterpret_cast<const float4*>(Uh + (j + 1) * ld + o));
+    const float4 wl = __ldg(reinterpret_cast<const float4*>(Ul + (j + 1) * ld + o));
+    float4 xh[FF_CH], xl[FF_CH];
+#pragma unroll
+    for (int c = 0; c < FF_CH; ++c) {
+      const size_t vo = (size_t)(c0 + (c < nc ? c : 0)) * ld + o;
+      xh[c] = __ldg(reinterpret_cast<const float4*>(Uh + vo));
+      xl[c] = __ldg(reinterpret_cast<const float4*>(Ul + vo));
+    }
+#pragma unroll
+    for (int c = 0; c < FF_CH; ++c)
+      if (c < nc) {
+        dot2_acc(lo2(xh[c]), lo2(xl[c]), lo2(ujh), lo2(ujl), S[2 * c], C[2 * c]);
+        dot2_acc(hi2(xh[c]), hi2(xl[c]), hi2(ujh), hi2(ujl), S[2 * c], C[2 * c]);
+        dot2_acc(lo2(xh[c]), lo2(xl[c]), lo2(wh), lo2(wl), S[2 * c + 1], C[2 * c + 1]);
+        dot2_acc(hi2(xh[c]), hi2(xl[c]), hi2(wh), hi2(wl), S[2 * c + 1], C[2 * c + 1]);
+      }
+    if (wnorm) {
+      dot2_acc(lo2(wh), lo2(wl), lo2(wh), lo2(wl), S[2 * FF_CH], C[2 * FF_CH]);
+      dot2_acc(hi2(wh), hi2(wl), hi2(wh), hi2(wl), S[2 * FF_CH], C[2 * FF_CH]);
+    }
+  }
+  for (size_t i = 4 * ng + tid; i < n_aug; i += nthr) {  // ragged end, one element per lane pair
+    const float2 ujh = make_float2(Uh[j * ld + i], 0.f), ujl = make_float2(Ul[j * ld + i], 0.f);
+    const float2 wh = make_float2(Uh[(j + 1) * ld + i], 0.f), wl = make_float2(Ul[(j + 1) * ld + i], 0.f);
+    for (int c = 0; c < nc; ++c) {
+      const size_t vo = (size_t)(c0 + c) * ld + i;
+      const float2 xh = make_float2(Uh[vo], 0.f), xl = make_float2(Ul[vo], 0.f);
+      dot2_acc(xh, xl, ujh, ujl, S[2 * c], C[2 * c]);
+      dot2_acc(xh, xl, wh, wl, S[2 * c + 1], C[2 * c + 1]);
+    }
+    if (wnorm) dot2_acc(wh, wl, wh, wl, S[2 * FF_CH], C[2 * FF_CH]);
+  }
+  ff v[K];
+#pragma unroll
+  for (int k2 = 0; k2 < K; ++k2) v[k2] = dot2_value(S[k2], C[k2]);
+  block_sum<true, K>(v, sh, tot);
+  const int G = gridDim.x;
+  if (threadIdx.x < 2 * nc) part[(size_t)(2 * c0 + threadIdx.x) * G + blockIdx.x] = tot[threadIdx.x];
+  if (wnorm && threadIdx.x == 2 * FF_CH) part[(size_t)(2 * nvec) * G + blockIdx.x] = tot[2 * FF_CH];
+  if (last_block(&ks->counter, gridDim.x * gridDim.y)) dots_last_block<true>(ks, part, j, G);
+}
+
+__global__ void __launch_bounds__(NT, 3) k_update_ff(KState* ks, ff* part, Basis U, int j, size_t n_aug) {
+  __shared__ float2 qc[MMAX + 1];  // (h, l) of -s_k
+  __shared__ float2 uc[MMAX + 1];  // (h, l) of -(z_k - (c/r) s_k)
+  __shared__ float2 sc[2];         // -(c/r), 1/r
+  __shared__ ff sh[NW];
+  if (ks->breakdown_at > 0 && j >= ks->breakdown_at) return;
+  for (int k2 = threadIdx.x; k2 < j; k2 += NT) {
+    const ff a = ff_from_double(-ks->qcoef[k2]);
+    const ff b = ff_from_double(-ks->ucoef[k2]);
+    qc[k2] = make_float2(a.h, a.l);
+    uc[k2] = make_float2(b.h, b.l);
+  }
+  if (threadIdx.x == 0) {
+    const ff a = ff_from_double(-ks->cu), b = ff_from_double(ks->inv_r);
+    sc[0] = make_float2(a.h, a.l);
+    sc[1] = make_float2(b.h, b.l);
+  }
+  __syncthreads();
+  const float2 ncu_h = make_float2(sc[0].x, sc[0].x), ncu_l = make_float2(sc[0].y, sc[0].y);
+  const float2 ir_h = make_float2(sc[1].x, sc[1].x), ir_l = make_float2(sc[1].y, sc[1].y);
+  float2 S = make_float2(0.f, 0.f), C = make_float2(0.f, 0.f);
+  const size_t ld = U.ld, ng = n_aug / 4;
+  float* __restrict__ Uh = U.h;
+  float* __restrict__ Ul = U.l;
+  const size_t tid = blockIdx.x * (size_t)NT + threadIdx.x, nthr = (size_t)gridDim.x * NT;
+  for (size_t g = tid; g < ng; g += nthr) {
+    const size_t o = 4 * g;
+    const float4 ujh = *reinterpret_cast<const float4*>(Uh + j * ld + o);
+    const float4 ujl = *reinterpret_cast<const float4*>(Ul + j * ld + o);
+    const float4 wh = *reinterpret_cast<const float4*>(Uh + (j + 1) * ld + o);
+    const float4 wl = *reinterpret_cast<const float4*>(Ul + (j + 1) * ld + o);
+    float2 qh0 = lo2(ujh), qh1 = hi2(ujh), ql0 = lo2(ujl), ql1 = hi2(ujl);  // q_j accumulator
+    float2 uh0 = lo2(wh), uh1 = hi2(wh), ul0 = lo2(wl), ul1 = hi2(wl);      // u_{j+1} accumulator
+    axpy2_acc(ncu_h, ncu_l, lo2(ujh), lo2(ujl), uh0, ul0);
+    axpy2_acc(ncu_h, ncu_l, hi2(ujh), hi2(ujl), uh1, ul1);
+    const float* ph = Uh + o;
+    const float* pl = Ul + o;
+    for (int k2 = 0; k2 < j; ++k2, ph += ld, pl += ld) {
+      const float4 bh = __ldg(reinterpret_cast<const float4*>(ph));
+      const float4 bl = __ldg(reinterpret_cast<const float4*>(pl));
+      const float2 a = qc[k2], b = uc[k2];
+      const float2 ah = make_float2(a.x, a.x), al = make_float2(a.y, a.y);
+      const float2 bhh = make_float2(b.x, b.x), bll = make_float2(b.y, b.y);
+      axpy2_acc(ah, al, lo2(bh), lo2(bl), qh0, ql0);
+      axpy2_acc(ah, al, hi2(bh), hi2(bl), qh1, ql1);
+      axpy2_acc(bhh, bll, lo2(bh), lo2(bl), uh0, ul0);
+      axpy2_acc(bhh, bll, hi2(bh), hi2(bl), uh1, ul1);
+      if ((k2 & 15) == 15) {
+        ff2_norm(qh0, ql0);
+        ff2_norm(qh1, ql1);
+        ff2_norm(uh0, ul0);
+        ff2_norm(uh1, ul1);
+      }
+    }
+    ff2_norm(qh0, ql0);
+    ff2_norm(qh1, ql1);
+    ff2_norm(uh0, ul0);
+    ff2_norm(uh1, ul1);
+    ff2_scale(qh0, ql0, ir_h, ir_l);
+    ff2_scale(qh1, ql1, ir_h, ir_l);
+    ff2_scale(uh0, ul0, ir_h, ir_l);
+    ff2_scale(uh1, ul1, ir_h, ir_l);
+    dot2_acc(uh0, ul0, uh0, ul0, S, C);
+    dot2_acc(uh1, ul1, uh1, ul1, S, C);
+    *reinterpret_cast<float4*>(Uh + j * ld + o) = make_float4(qh0.x, qh0.y, qh1.x, qh1.y);
+    *reinterpret_cast<float4*>(Ul + j * ld + o) = make_float4(ql0.x, ql0.y, ql1.x, ql1.y);
+    *reinterpret_cast<float4*>(Uh + (j + 1) * ld + o) = make_float4(uh0.x, uh0.y, uh1.x, uh1.y);
+    *reinterpret_cast<float4*>(Ul + (j + 1) * ld + o) = make_float4(ul0.x, ul0.y, ul1.x, ul1.y);
+  }
+  for (size_t i = 4 * ng + tid; i < n_aug; i += nthr) {  // ragged end
+    ff xq{Uh[j * ld + i], Ul[j * ld + i]};
+    ff xu = ff_fma(ff{sc[0].x, sc[0].y}, xq, ff{Uh[(j + 1) * ld + i], Ul[(j + 1) * ld + i]});
+    for (int k2 = 0; k2 < j; ++k2) {
+      const ff q{Uh[k2 * ld + i], Ul[k2 * ld + i]};
+      xq = ff_fma(ff{qc[k2].x, qc[k2].y}, q, xq);
+      xu = ff_fma(ff{uc[k2].x, uc[k2].y}, q, xu);
+    }
+    const ff ir{sc[1].x, sc[1].y};
+    xq = ff_mul(xq, ir);
+    xu = ff_mul(xu, ir);
+    dot2_acc(make_float2(xu.h, 0.f), make_float2(xu.l, 0.f), make_float2(xu.h, 0.f), make_float2(xu.l, 0.f), S, C);
+    Uh[j * ld + i] = xq.h;
+    Ul[j * ld + i] = xq.l;
+    Uh[(j + 1) * ld + i] = xu.h;
+    Ul[(j + 1) * ld + i] = xu.l;
+  }
+  ff v[1] = {dot2_value(S, C)};
+  __shared__ ff tot[1];
+  block_sum<true, 1>(v, sh, tot);
+  if (threadIdx.x == 0) part[blockIdx.x] = tot[0];
+  if (last_block(&ks->counter, gridDim.x)) {
+    __shared__ double res[1];
+    final_sums<true>(part, 1, gridDim.x, res);
     __syncthreads();
     if (threadIdx.x == 0) {
       const double h = sqrt(res[0]);
@@ -706,14 +896,15 @@ cudaError_t launch_start(bool use_ff, KState* ks, Basis U, Vec b0, size_t N, int
 
 cudaError_t launch_dots(bool use_ff, KState* ks, void* part, Basis U, int j, size_t n_aug, cudaStream_t s) {
   if (j < 0 || j + 1 > MMAX) return cudaErrorInvalidValue;
-  const int chunks = (j + 1 + DOT_CHUNK - 1) / DOT_CHUNK;
+  const int ch = use_ff ? FF_CH : DOT_CHUNK;
+  const int chunks = (j + 1 + ch - 1) / ch;
   int gx = (RB + chunks - 1) / chunks;
   const int need = (int)((n_aug / 4 + NT - 1) / NT);
   if (gx > need) gx = need;
   if (gx < 1) gx = 1;
   dim3 grid(gx, chunks);
   if (use_ff)
-    k_dots<true><<<grid, NT, 0, s>>>(ks, static_cast<ff*>(part), U, j, n_aug);
+    k_dots_ff<<<grid, NT, 0, s>>>(ks, static_cast<ff*>(part), U, j, n_aug);
   else
     k_dots<false><<<grid, NT, 0, s>>>(ks, static_cast<double*>(part), U, j, n_aug);
   return cudaGetLastError();
@@ -723,7 +914,7 @@ cudaError_t launch_update(bool use_ff, KState* ks, void* part, Basis U, int j, s
   if (j < 0 || j + 1 > MMAX) return cudaErrorInvalidValue;
   const int g = grid_for(n_aug / 4 + 1);
   if (use_ff)
-    k_update<true><<<g, NT, 0, s>>>(ks, static_cast<ff*>(part), U, j, n_aug);
+    k_update_ff<<<g, NT, 0, s>>>(ks, static_cast<ff*>(part), U, j, n_aug);
   else
     k_update<false><<<g, NT, 0, s>>>(ks, static_cast<double*>(part), U, j, n_aug);
   return cudaGetLastError();
