@@ -200,6 +200,37 @@ expdg_status expdg_profile_enable(expdg_ctx* ctx, int on);
  * restart from zero. */
 expdg_status expdg_profile_get(expdg_ctx* ctx, expdg_kernel_prof* out, int reset);
 
+/* ---- Allocation-free residual ---------------------------------------------
+ * The paper has no counterpart to this call; it is a deployment convenience.
+ *
+ * Some callers cannot let a library allocate device memory: an application
+ * whose GPU memory is entirely owned by its own pool allocator (cudaMalloc
+ * would fail or fragment that pool), code on a latency-critical path where
+ * cudaMalloc / cudaFree and their implicit device synchronisation are not
+ * acceptable, or a plug-in that may not create allocations its host cannot
+ * account for.  expdg_residual_noalloc computes exactly what expdg_residual
+ * computes for the configuration cfg, with no context and without allocating:
+ *
+ *   - q (input) and r (output) are caller-owned DEVICE arrays of
+ *     m * Ne * (p+1)^dim doubles in the canonical layout; host pointers are
+ *     rejected with EXPDG_EINVAL.  cuda_stream: the stream to run on (NULL =
+ *     legacy default stream); the call returns after that stream has finished.
+ *   - Scratch (the FP32 state copy and float-float output of EXPDG_MIXED, and
+ *     the non-physical-state flag of both forms) is a fixed static device
+ *     array of about 6 MiB that every GPU which loads the library keeps until
+ *     the process exits.  EXPDG_MIXED is limited to
+ *     EXPDG_NOALLOC_MAX_UNKNOWNS unknowns (larger sizes return EXPDG_EINVAL);
+ *     EXPDG_FP64 has no size limit.
+ *   - The first call on a device looks up the array's device address; make
+ *     that first call before any stream capture.
+ *   - All calls share the array: calls that overlap on the GPU (other streams,
+ *     other host threads) race and must be serialised by the caller.
+ *   - Returns EXPDG_ENONPHYSICAL for an Euler state with rho <= 0 or p <= 0,
+ *     EXPDG_EINVAL for a bad configuration, size or pointer, EXPDG_ECUDA on a
+ *     CUDA error.  Other fields of cfg (scheme, Krylov settings) are ignored. */
+#define EXPDG_NOALLOC_MAX_UNKNOWNS (1u << 19)
+expdg_status expdg_residual_noalloc(const expdg_config* cfg, const double* q, double* r, void* cuda_stream);
+
 /* Message of the last failing call on this context ("" if none). */
 const char* expdg_last_error(const expdg_ctx* ctx);
 

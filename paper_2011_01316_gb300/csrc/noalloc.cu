@@ -1,0 +1,143 @@
+// expdg_residual_noalloc: the residual R(q) without a context and without any
+// device allocation, for callers that cannot allocate device memory.
+//
+// Its scratch - the FP32 copy of the state and the float-float output of the
+// mixed form, and the non-physical-state flag of both forms - lives in the
+// file-scope arrays below.  Every GPU that loads this library holds them
+// (about 6 MiB) until the process exits.
+#include <cstring>
+
+#include "common.cuh"
+#include "tables.h"
+
+namespace {
+
+constexpr size_t kMaxUnknowns = (size_t)1 << 19;  // EXPDG_NOALLOC_MAX_UNKNOWNS
+constexpr int kMaxDevices = 64;
+
+// [0, kMax): FP32 state; [kMax, 2 kMax): residual hi; [2 kMax, 3 kMax): residual lo
+static __device__ __align__(256) float g_scratch[3 * kMaxUnknowns];
+static __device__ __align__(256) int g_status[64];
+
+// Device addresses of the arrays, per device ordinal (the host-side names of
+// g_scratch / g_status are stand-ins, not device addresses).
+struct Addr {
+  float* scratch;
+  int* status;
+  bool ready;
+};
+Addr g_addr[kMaxDevices];
+
+cudaError_t device_addresses(int dev, Addr** out) {
+  if (dev < 0 || dev >= kMaxDevices) return cudaErrorInvalidDevice;
+  Addr& a = g_addr[dev];
+  if (!a.ready) {
+    void* p = nullptr;
+    cudaError_t e = cudaGetSymbolAddress(&p, g_scratch);
+    if (e != cudaSuccess) return e;
+    a.scratch = static_cast<float*>(p);
+    e = cudaGetSymbolAddress(&p, g_status);
+    if (e != cudaSuccess) return e;
+    a.status = static_cast<int*>(p);
+    a.ready = true;
+  }
+  *out = &a;
+  return cudaSuccess;
+}
+
+bool on_device(const void* p) {
+  cudaPointerAttributes at{};
+  if (p == nullptr || cudaPointerGetAttributes(&at, p) != cudaSuccess) {
+    cudaGetLastError();
+    return false;
+  }
+  return at.type == cudaMemoryTypeDevice || at.type == cudaMemoryTypeManaged;
+}
+
+}  // namespace
+
+extern "C" expdg_status expdg_residual_noalloc(const expdg_config* cfg, const double* q, double* r,
+                                               void* cuda_stream) {
+  using namespace expdg;
+  if (!cfg || !q || !r) return EXPDG_EINVAL;
+  const int dim = cfg->dim, p = cfg->p;
+  if (dim < 1 || dim > 3 || p < 1 || p > EXPDG_MAX_ORDER) return EXPDG_EINVAL;
+  if (cfg->eq != EXPDG_BURGERS && cfg->eq != EXPDG_EULER) return EXPDG_EINVAL;
+  if (cfg->eq == EXPDG_BURGERS && dim != 1) return EXPDG_EINVAL;
+  if (cfg->eq == EXPDG_EULER && !(cfg->gamma > 1.0)) return EXPDG_EINVAL;
+  if (cfg->prec != EXPDG_FP64 && cfg->prec != EXPDG_MIXED) return EXPDG_EINVAL;
+  size_t nelem = 1;
+  int np = 1;
+  for (int d = 0; d < dim; ++d) {
+    if (cfg->ne[d] < 1 || !(cfg->hi[d] > cfg->lo[d])) return EXPDG_EINVAL;
+    nelem *= (size_t)cfg->ne[d];
+    np *= p + 1;
+  }
+  const int m = (cfg->eq == EXPDG_BURGERS) ? 1 : dim + 2;
+  if (nelem > (size_t)0x7fffffff / (size_t)np) return EXPDG_EINVAL;
+  const size_t N = (size_t)m * nelem * np;
+  const bool mixed = cfg->prec == EXPDG_MIXED;
+  if (mixed && N > kMaxUnknowns) return EXPDG_EINVAL;  // beyond the static scratch
+  if (!on_device(q) || !on_device(r)) return EXPDG_EINVAL;
+
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess) return EXPDG_ECUDA;
+  Addr* ad = nullptr;
+  if (device_addresses(dev, &ad) != cudaSuccess) return EXPDG_ECUDA;
+  const cudaStream_t s = static_cast<cudaStream_t>(cuda_stream);
+
+  Tab tab{};
+  double rr[MAXP + 1], ww[MAXP + 1], D[(MAXP + 1) * (MAXP + 1)];
+  build_lgl(p, rr, ww, D);
+  for (int k = 0; k < (p + 1) * (p + 1); ++k) tab.D[k] = D[k];
+  tab.lift = 1.0 / ww[0];
+  DGArgs a;
+  std::memset(&a, 0, sizeof(a));
+  for (int d = 0; d < 3; ++d) {
+    const bool used = d < dim;
+    a.ne[d] = used ? cfg->ne[d] : 1;
+    a.two_over_h[d] = used ? 2.0 / ((cfg->hi[d] - cfg->lo[d]) / cfg->ne[d]) : 2.0;
+  }
+  a.nelem = (int)nelem;
+  a.gamma = cfg->gamma;
+  a.stride = nelem * np;
+  a.alpha = 1.0;
+  a.alpha_h = 1.0f;
+  a.alpha_l = 0.0f;
+  a.status = ad->status;
+
+  // the status word keeps the previous call's value: clear it first
+  if (cudaMemsetAsync(ad->status, 0, sizeof(int), s) != cudaSuccess) return EXPDG_ECUDA;
+  float* q32 = ad->scratch;
+  float* rh = ad->scratch + kMaxUnknowns;
+  float* rl = ad->scratch + 2 * kMaxUnknowns;
+  cudaError_t e = cudaSuccess;
+  if (mixed) {
+    e = launch_to_f32(q32, q, N, s);
+    a.q = q32;
+    a.out_h = rh;
+    a.out_l = rl;
+  } else {
+    a.q = q;
+    a.out = r;
+  }
+  if (e == cudaSuccess) {
+    if (dim == 1)
+      e = launch_dg_1d(false, mixed, cfg->eq, p, a, tab, s);
+    else if (dim == 2)
+      e = launch_dg_2d(false, mixed, cfg->eq, p, a, tab, s);
+    else
+      e = launch_dg_3d(false, mixed, cfg->eq, p, a, tab, s);
+  }
+  if (e == cudaSuccess && mixed) {
+    Vec v{};
+    v.h = rh;
+    v.l = rl;
+    e = launch_ff_to_f64(r, v, N, s);
+  }
+  if (e != cudaSuccess) return EXPDG_ECUDA;
+  int flag = 0;
+  if (cudaMemcpyAsync(&flag, ad->status, sizeof(int), cudaMemcpyDeviceToHost, s) != cudaSuccess) return EXPDG_ECUDA;
+  if (cudaStreamSynchronize(s) != cudaSuccess) return EXPDG_ECUDA;
+  return (flag & 1) ? EXPDG_ENONPHYSICAL : EXPDG_OK;
+}

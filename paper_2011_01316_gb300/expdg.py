@@ -84,6 +84,7 @@ def _load():
         "expdg_last_error": (ctypes.c_char_p, [P]),
         "expdg_profile_enable": (ctypes.c_int, [P, ctypes.c_int]),
         "expdg_profile_get": (ctypes.c_int, [P, P, ctypes.c_int]),
+        "expdg_residual_noalloc": (ctypes.c_int, [vp(expdg_config), P, P, P]),
     }
     for name, (res, args) in sig.items():
         f = getattr(lib, name)
