@@ -4,7 +4,8 @@
 Workload (N = 1): 2D compressible Euler (gamma = 1.4) isentropic vortex
 (strength 5, decay 1, free stream (1, 1), centre (5, 5)) on the periodic
 [0,10]^2, 64 x 64 quadrilaterals, p = 4 LGL (409,600 unknowns), Lax-Friedrichs
-flux, EPI2 steps of dt = 0.05 with Krylov tolerance 1e-10.  One step = one
+flux, EPI2 steps of dt = 0.05 with Krylov tolerance 1e-8 (the tolerance the
+survey gives for the FP32-Jv configurations).  One step = one
 residual, one adaptive augmented-Krylov phi_1 solve (Jv applies, Gram-Schmidt,
 phi(H) checks) and the state update.
 
@@ -42,9 +43,9 @@ sys.path.insert(0, ROOT)
 METRIC = "DOF-steps/s"
 UNIT = "DOF-steps/s"
 WORKLOAD = ("2D Euler isentropic vortex, periodic [0,10]^2, 64x64 quads, p=4 LGL, 409,600 unknowns, "
-            "LF flux, EPI2, dt=0.05, Krylov tol 1e-10")
+            "LF flux, EPI2, dt=0.05, Krylov tol 1e-8")
 CFG = dict(dim=2, p=4, ne=[64, 64, 1], lo=[0.0, 0.0, 0.0], hi=[10.0, 10.0, 1.0], eq=2, gamma=1.4,
-           scheme=2, krylov_tol=1e-10, m_max=64, m_step=5, max_substeps=32)
+           scheme=2, krylov_tol=1e-8, m_max=64, m_step=5, max_substeps=32)
 DT = 0.05
 CLASSES = ["residual", "jv", "dots", "update", "phi", "combine", "vector"]
 
@@ -113,6 +114,89 @@ def oracle_step_rate(steps=1):
     return mesh.n_unknowns * steps / dt, dt
 
 
+def serving_workload(n, seed=1, rate=200.0, workers=8):
+    """Poisson stream (mean `rate`/s) of n 2D Euler vortex solves (side 8..128,
+    p 2..5, strength U[1,5], centre U(domain), 50 EPI2 steps at Courant 5, tol
+    1e-8).  The served form: mixed precision, `workers` solves in flight.  The
+    plain form: FP64, one solve at a time, same requests.  Reports solves/s,
+    p50/p99 arrival-to-completion latency and the largest relative error of a
+    served result against the FP64 result of the same request."""
+    from paper_2011_01316_gb300 import serve
+    rng = np.random.default_rng(seed)
+    reqs_m, reqs_d = [], []
+    for _ in range(n):
+        state = rng.bit_generator.state
+        reqs_m.append(serve.vortex_request(rng, 1))
+        rng.bit_generator.state = state
+        reqs_d.append(serve.vortex_request(rng, 0))
+    # warm the kernels of every order once (outside the measured streams)
+    warm = serve.Server(workers=1)
+    seen = set()
+    for r in reqs_m + reqs_d:
+        key = (r[0].p, r[0].prec)
+        if key not in seen:
+            seen.add(key)
+            serve.run_stream(warm, [(r[0], r[1], r[2], 1)], 0.0, rng)
+    warm.close()
+    srv = serve.Server(workers=workers)
+    res_m, wall_m = serve.run_stream(srv, reqs_m, rate, np.random.default_rng(seed + 1))
+    srv.close()
+    srv = serve.Server(workers=1)
+    res_d, wall_d = serve.run_stream(srv, reqs_d, rate, np.random.default_rng(seed + 1))
+    srv.close()
+    err = max(float(np.linalg.norm(a[0] - b[0]) / np.linalg.norm(b[0])) for a, b in zip(res_m, res_d))
+    dofs = sum(r[1].size * r[3] for r in reqs_m)
+    out = {"workload": f"{n} 2D Euler vortex solves, Poisson {rate:g}/s, side 8..128, p 2..5, 50 EPI2 steps, Cr 5",
+           "served_mixed": dict(serve.latency_summary(res_m, wall_m), workers=workers,
+                                dof_steps_per_s=dofs / wall_m),
+           "plain_fp64": dict(serve.latency_summary(res_d, wall_d), workers=1, dof_steps_per_s=dofs / wall_d),
+           "max_rel_err_vs_fp64": err}
+    out["speedup_solves_per_s"] = out["served_mixed"]["solves_per_s"] / out["plain_fp64"]["solves_per_s"]
+    return out
+
+
+def batched_workload(n, seed=0, workers=16, steps=20):
+    """n independent periodic instances (half 1D Burgers with Ne log-uniform in
+    [16, 4096], half 2D Euler density waves with side in {8..96}; p uniform in
+    {1..5}; initial data 1 + 4 seeded Fourier modes, a_k ~ U[0, 0.3]; dt from
+    Courant 5; 20 EPI2 steps; mixed precision) run concurrently through the solve
+    server, against the same instances run one after another."""
+    from paper_2011_01316_gb300 import expdg, inputs, serve
+    rng = np.random.default_rng(seed)
+    reqs = []
+    for i in range(n):
+        p = int(rng.integers(1, 6))
+        if i % 2 == 0:
+            ne = int(round(math.exp(rng.uniform(math.log(16), math.log(4096)))))
+            cfg = expdg.default_config(dim=1, p=p, ne=[ne, 1, 1], lo=[0, 0, 0], hi=[2 * math.pi, 1, 1],
+                                       eq=expdg.EXPDG_BURGERS, prec=1, krylov_tol=1e-8)
+            X = expdg.config_node_coords(cfg)
+            u0 = inputs.fourier_modes(X[0], rng)[0][None]
+            umax = float(np.max(np.abs(u0)))
+            dx = float(np.min(np.diff(X[0, 0, : p + 1])))
+            reqs.append((cfg, np.ascontiguousarray(u0), 5.0 * dx / umax, steps))
+        else:
+            side = int(rng.integers(8, 97))
+            cfg = expdg.default_config(dim=2, p=p, ne=[side, side, 1], lo=[0, 0, 0], hi=[2 * math.pi] * 2 + [1],
+                                       eq=expdg.EXPDG_EULER, prec=1, krylov_tol=1e-8)
+            X = expdg.config_node_coords(cfg)
+            rho = inputs.fourier_modes(X[0] + X[1], rng)[0]
+            q0 = inputs.conservative(rho, [1.0, 1.0], np.ones_like(rho), 1.4)
+            reqs.append((cfg, np.ascontiguousarray(q0), serve.courant_dt(cfg, q0, 5.0), steps))
+    dofs = sum(r[1].size * r[3] for r in reqs)
+    srv = serve.Server(workers=1)
+    res1, wall1 = serve.run_stream(srv, reqs, 0.0, rng)
+    srv.close()
+    srv = serve.Server(workers=workers)
+    resn, walln = serve.run_stream(srv, reqs, 0.0, rng)
+    srv.close()
+    same = all(np.array_equal(a[0], b[0]) for a, b in zip(res1, resn))
+    return {"workload": f"{n} instances (1D Burgers / 2D Euler, p 1..5, uneven sizes), {steps} EPI2 steps each",
+            "concurrent": {"workers": workers, "wall_s": walln, "dof_steps_per_s": dofs / walln},
+            "sequential": {"wall_s": wall1, "dof_steps_per_s": dofs / wall1},
+            "speedup": wall1 / walln, "identical_results": same}
+
+
 def run_reference(args, rank, world):
     if rank != 0:
         return
@@ -142,6 +226,9 @@ def main():
     ap.add_argument("--impl", default="expdg", choices=["expdg", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--fp64-steps", type=int, default=3)
+    ap.add_argument("--tol", type=float, default=None, help="Krylov tolerance (default: the workload's)")
+    ap.add_argument("--serve-requests", type=int, default=48, help="requests of the serving workload (0: skip)")
+    ap.add_argument("--batch-instances", type=int, default=64, help="instances of the batched workload (0: skip)")
     args = ap.parse_args()
 
     world = int(os.environ.get("WORLD_SIZE", "1"))
@@ -151,6 +238,8 @@ def main():
         run_reference(args, rank, world)
         return
 
+    if args.tol is not None:
+        CFG["krylov_tol"] = args.tol
     import torch
     import torch.distributed as dist
     if world > 1:
@@ -247,6 +336,9 @@ def main():
     e2e = {"value": world * N * args.steps / te, "unit": UNIT, "h2d_bytes_per_step": 8 * N,
            "d2h_bytes_per_step": 8 * N}
 
+    serving = serving_workload(args.serve_requests) if args.serve_requests > 0 else None
+    batched = batched_workload(args.batch_instances) if args.batch_instances > 0 else None
+
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         r, tt = oracle_step_rate(1)
@@ -262,6 +354,7 @@ def main():
                            "l2": "flushed between timed steps (512 MiB write)",
                            "parallelism": "replicas" if world > 1 else "single GPU"},
                 "err_vs_fp64": err_vs_fp64, "fp64_form": fp64, "e2e": e2e, "gpu_launches": launches,
+                "serving": serving, "batched": batched,
                 "roofline": roofline, "kernels": kern, "cpu_baseline": cpu, "clocks": clk.summary(),
                 "ms_per_step_min": min(per), "ms_per_step_median": statistics.median(per),
                 "krylov_iters_per_step": statistics.mean(iters),

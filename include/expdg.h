@@ -53,10 +53,13 @@ typedef enum { EXPDG_EPI2 = 2, EXPDG_EXPRB32 = 3, EXPDG_EXPRB42 = 4 } expdg_sche
 
 /* Arithmetic of the operator applies (R, Jv) and of the Arnoldi process.
  *   EXPDG_FP64:  everything in FP64 (reference form).
- *   EXPDG_MIXED: R and Jv in FP32 (FP32 accumulation); Krylov basis, inner
- *                products and orthogonalisation in float-float (pairs of FP32
- *                numbers, 48-bit significand, FP32 arithmetic with error-free
- *                transformations); phi(H) and the solution update in FP64.
+ *   EXPDG_MIXED: Jv in FP32 (FP32 accumulation); expdg_residual in FP32;
+ *                Krylov basis, inner products and orthogonalisation in
+ *                float-float (pairs of FP32 numbers, 48-bit significand, FP32
+ *                arithmetic with error-free transformations); phi(H) and the
+ *                solution update in FP64.  Inside expdg_step / expdg_advance
+ *                the stage residuals R(q^n), R(q2) are computed in FP64: their
+ *                FP32 rounding noise would cost extra Arnoldi steps.
  *                On this GPU the FP64 pipe (and every f32<->f64 conversion)
  *                runs about 1/70 of the FP32 rate, so the streaming Krylov
  *                kernels avoid it. */
@@ -126,6 +129,8 @@ int expdg_nodes_per_element(const expdg_ctx* ctx);
 /* Physical LGL node coordinates, host buffer xyz[dim][Ne][Np] (FP64):
  * x_d = lo_d + h_d (e_d + (r_i + 1)/2), LGL nodes r of order p. */
 expdg_status expdg_node_coords(const expdg_ctx* ctx, double* xyz);
+/* The same without a context (host computation only). */
+expdg_status expdg_config_node_coords(const expdg_config* cfg, double* xyz);
 
 /* R(q): the DG right-hand side (Sec. 2.2, Eq. EXPO-SemiDiscretizedForm_ode;
  * strong collocated LGL form; LF flux with lambda = max(|u|) for Burgers,
@@ -147,7 +152,10 @@ expdg_status expdg_jv(expdg_ctx* ctx, const double* qt, const double* v, double*
  * beta V_m exp(H_m) e_1 approximates the sum.  The error estimate
  * err = beta h_{m+1,m} |e_m^T exp(H_m) e_1| is checked at m = m_step,
  * 2 m_step, ..., m_max; accepted when err <= krylov_tol * beta (or on a happy
- * breakdown).  Reaching m_max halves the sub-step sigma; after an accepted
+ * breakdown).  In EXPDG_MIXED a check is also accepted when the approximation
+ * changed by at most krylov_tol * beta since the previous check
+ * (beta |y_m - [y_prev; 0]|): the FP32 operator's rounding noise inflates
+ * Saad's estimate there without slowing the convergence of the approximation.  Reaching m_max halves the sub-step sigma; after an accepted
  * sub-step with m <= m_max/2 sigma doubles (never past the end).  Sub-step
  * vectors: b_0 = w(s), b_i = sigma^i sum_j s^j/j! c_{i+j}.  The tail scale
  * eta = 2^-round(log2(max_i ||b_i||)).  If replay != NULL, the nreplay
@@ -199,6 +207,45 @@ expdg_status expdg_profile_enable(expdg_ctx* ctx, int on);
  * out[EXPDG_K_COUNT] (synchronises the stream).  If reset != 0 the counters
  * restart from zero. */
 expdg_status expdg_profile_get(expdg_ctx* ctx, expdg_kernel_prof* out, int reset);
+
+/* Device memory one context of this configuration holds (state, scratch,
+ * Krylov basis of m_max + 1 vectors, reduction buffers), each allocation
+ * rounded up to 2 MiB; 0 if cfg is invalid. */
+size_t expdg_context_bytes(const expdg_config* cfg);
+
+/* ---- Solve server: continuous batching of independent solves --------------
+ * Serving pattern (not in the paper, which runs one solve per MPI job):
+ * requests are queued and taken in arrival order by worker threads, each with
+ * its own CUDA stream, as soon as the device-memory budget admits the
+ * request's context (expdg_context_bytes); solves arriving while others run
+ * start as soon as a worker and memory free up, and their kernels overlap on
+ * the GPU.  Each solve's state and Krylov basis stay resident on the device
+ * for the whole solve.  Finished contexts are cached and reused by requests of
+ * the same configuration (no device allocation per request); idle cached
+ * contexts are released when a request needs their memory.  Results are
+ * deterministic: a solve gives the same result alone or among others. */
+typedef struct expdg_server expdg_server;
+typedef struct {
+  size_t hbm_budget;  /* bytes of device memory the server's contexts may hold (0: 90% of free memory) */
+  int workers;        /* solves in flight at once, 1..64 (one host thread and CUDA stream each) */
+} expdg_server_config;
+
+expdg_status expdg_server_create(const expdg_server_config* cfg, expdg_server** out);
+/* Waits for running solves, releases all contexts. */
+void expdg_server_destroy(expdg_server* s);
+/* Queue nsteps steps of size dt of configuration cfg from host state q0 (copied
+ * before returning).  Non-blocking.  EXPDG_ENOMEM if the context can never fit
+ * the budget, EXPDG_EINVAL for a bad configuration. */
+expdg_status expdg_server_submit(expdg_server* s, const expdg_config* cfg, const double* q0, double dt, int nsteps,
+                                 int64_t* id);
+/* Non-blocking: ids (up to cap) of solves finished since the last poll. */
+expdg_status expdg_server_poll(expdg_server* s, int64_t* ids, int cap, int* n);
+/* Result of a finished solve (host q_out, stats, times[3] = queueing, service and
+ * total latency in seconds; any may be NULL); releases the request.  Returns the
+ * solve's own status (EXPDG_EINVAL if id is unknown or not finished). */
+expdg_status expdg_server_fetch(expdg_server* s, int64_t id, double* q_out, expdg_stats* stats, double* times);
+/* Bytes held by contexts, queued and running solve counts. */
+expdg_status expdg_server_info(expdg_server* s, size_t* used_bytes, int* pending, int* running);
 
 /* ---- Allocation-free residual ---------------------------------------------
  * The paper has no counterpart to this call; it is a deployment convenience.

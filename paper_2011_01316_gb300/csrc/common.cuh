@@ -89,6 +89,9 @@ struct KState {
   double qcoef[MMAX + 1];   // s_k: delayed re-orthogonalisation coefficients of u_j
   double ucoef[MMAX + 1];   // z_k - (c/r) s_k: projection coefficients of the next vector
   double ycoef[MMAX + 1];   // beta * y_i for the final combination
+  double yprev[MMAX + 1];   // y = exp(H_m) e_1 of the previous check (mixed-form rule)
+  int mprev;                // m of the previous check (0: none)
+  int pad2;
   double cu;                // c / r (coefficient of u_j in the next vector)
   double inv_r;             // 1 / ||u_j re-orthogonalised||
   double wnorm;             // ||A_hat q_j|| estimate (happy-breakdown scale)
@@ -139,8 +142,11 @@ cudaError_t launch_start(bool use_ff, KState* ks, Basis U, Vec b0, size_t N, int
 cudaError_t launch_dots(bool use_ff, KState* ks, void* part, Basis U, int j, size_t n_aug, cudaStream_t s);
 cudaError_t launch_update(bool use_ff, KState* ks, void* part, Basis U, int j, size_t n_aug, cudaStream_t s);
 // FP64 phi kernel: E = exp(H_m) (Taylor-18 scaling and squaring), y = E e_1, error estimate,
-// acceptance (forced when force_accept), ycoef_i = beta y_i.
-cudaError_t launch_phi(KState* ks, int m, double beta, double tol, int force_accept, cudaStream_t s);
+// acceptance (forced when force_accept), ycoef_i = beta y_i.  Acceptance: Saad's
+// estimate beta h_{m+1,m} |y_m| <= tol beta; with diff_rule also when the change
+// from the previous check, beta |y - [y_prev; 0]|, is <= tol beta.
+cudaError_t launch_phi(KState* ks, int m, double beta, double tol, int force_accept, int diff_rule,
+                       cudaStream_t s);
 // out = base + sum_{i < m_eff} ycoef_i u_i (first N entries; base may be null).
 // out and base may each be FP64 (d) or float-float (h, l).
 cudaError_t launch_combine(bool use_ff, const KState* ks, Basis U, Vec base, Vec out, size_t N, cudaStream_t s);

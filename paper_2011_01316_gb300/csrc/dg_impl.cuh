@@ -309,12 +309,10 @@ cudaError_t launch_dg_t(const DGArgs& a, const Tab& t, cudaStream_t s) {
   const size_t smem = sizeof(T) * ((size_t)DIM * M * EPB * NP + (P + 1) * (P + 1));
   const int blocks = (a.nelem + EPB - 1) / EPB;
   auto kern = k_dg<DIM, P, EQ, T, LINEAR>;
-  static bool configured = false;  // per instantiation; attribute is per function
-  if (!configured) {
-    cudaError_t err = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    if (err != cudaSuccess) return err;
-    configured = true;
-  }
+  // once per instantiation, thread-safe (function-local static initialisation)
+  static const cudaError_t configured =
+      cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (configured != cudaSuccess) return configured;
   if (blocks == 0) return cudaSuccess;
   kern<<<blocks, threads, smem, s>>>(a, t);
   return cudaGetLastError();

@@ -144,28 +144,40 @@ __device__ bool last_block(unsigned int* counter, unsigned int total) {
   return am_last;
 }
 
-// In the last block: total_k = sum over g < G of part[k*G + g], k < K, one warp per k.
-// Results to out[k] (double) by lane 0 of the owning warp.
+// In the last block: total_k = sum over g < G of part[k*G + g], k < K.
+// All K*G partials are first staged in shared memory `stage` (one coalesced
+// load by every thread, so the L2 latency is paid once), then each warp sums
+// its values from shared memory.  Results to out[k] (double).
 template <bool FF>
-__device__ void final_sums(const typename Acc<FF>::T* part, int K, int G, double* out) {
+__device__ void final_sums(const typename Acc<FF>::T* part, int K, int G, double* out,
+                           typename Acc<FF>::T* stage) {
   using A = Acc<FF>;
+  const int total = K * G;
+  for (int i = threadIdx.x; i < total; i += blockDim.x) {
+    if constexpr (FF) {
+      const float2 t = __ldcg(reinterpret_cast<const float2*>(part) + i);
+      stage[i] = ff{t.x, t.y};
+    } else {
+      stage[i] = __ldcg(part + i);
+    }
+  }
+  __syncthreads();
   const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
   for (int k = w; k < K; k += NW) {
     typename A::T x = A::zero();
-    for (int g = lane; g < G; g += 32) {
-      typename A::T pv;
-      if constexpr (FF) {
-        const float2 t = __ldcg(reinterpret_cast<const float2*>(part) + (size_t)k * G + g);
-        pv = ff{t.x, t.y};
-      } else {
-        pv = __ldcg(part + (size_t)k * G + g);
-      }
-      x = A::add(x, pv);
-    }
+    for (int g = lane; g < G; g += 32) x = A::add(x, stage[k * G + g]);
 #pragma unroll
     for (int off = 16; off > 0; off >>= 1) x = A::add(x, A::shfl(x, off));
     if (lane == 0) out[k] = A::to_d(x);
   }
+  __syncthreads();
+}
+
+// Dynamic shared memory of the reduction kernels (partial-sum staging).
+template <bool FF>
+__device__ __forceinline__ typename Acc<FF>::T* red_stage() {
+  extern __shared__ __align__(16) unsigned char dyn_smem[];
+  return reinterpret_cast<typename Acc<FF>::T*>(dyn_smem);
 }
 
 struct LinArgs {
@@ -218,7 +230,7 @@ __global__ void __launch_bounds__(NT) k_norms(KState* ks, typename Acc<FF>::T* p
   if (threadIdx.x < NORMS_MAX) part[threadIdx.x * gridDim.x + blockIdx.x] = tot[threadIdx.x];
   if (last_block(&ks->counter, gridDim.x)) {
     __shared__ double res[NORMS_MAX];
-    final_sums<FF>(part, NORMS_MAX, gridDim.x, res);
+    final_sums<FF>(part, NORMS_MAX, gridDim.x, res, red_stage<FF>());
     __syncthreads();
     if (threadIdx.x < NORMS_MAX) ks->red[threadIdx.x] = (threadIdx.x < a.nx) ? res[threadIdx.x] : 0.0;
     if (threadIdx.x == 0) ks->counter = 0;
@@ -258,6 +270,7 @@ __global__ void __launch_bounds__(NT) k_start(KState* ks, Vec u0, Vec b0, size_t
     for (int k = threadIdx.x; k < (MMAX + 1) * MMAX; k += NT) ks->H[k] = 0.0;
     if (threadIdx.x == 0) {
       ks->breakdown_at = 0;
+      ks->mprev = 0;
       ks->accept = 0;
       ks->m_eff = 0;
       ks->err = 0.0;
@@ -318,7 +331,7 @@ __device__ void dots_last_block(KState* ks, const typename Acc<FF>::T* part, int
   const int nvec = j + 1;
     __shared__ double res[2 * MMAX + 4];
     __shared__ double sc[4];  // r, c
-    final_sums<FF>(part, 2 * nvec + 1, G, res);
+    final_sums<FF>(part, 2 * nvec + 1, G, res, red_stage<FF>());
     __syncthreads();
     // res[2i] = <x_i, u_j>, res[2i+1] = <x_i, w>; x_j = u_j; res[2 nvec] = <w, w>
     if (threadIdx.x == 0) {
@@ -489,7 +502,7 @@ __global__ void __launch_bounds__(NT) k_update(KState* ks, typename Acc<FF>::T* 
   if (threadIdx.x == 0) part[blockIdx.x] = tot[0];
   if (last_block(&ks->counter, gridDim.x)) {
     __shared__ double res[1];
-    final_sums<FF>(part, 1, gridDim.x, res);
+    final_sums<FF>(part, 1, gridDim.x, res, red_stage<FF>());
     __syncthreads();
     if (threadIdx.x == 0) {
       const double h = sqrt(res[0]);
@@ -506,12 +519,12 @@ __global__ void __launch_bounds__(NT) k_update(KState* ks, typename Acc<FF>::T* 
 // elements at a time in packed FP32 (compensated accumulation, 12 packed
 // instructions per two terms) so that the passes stay within the FP32 issue
 // and pipe budget at HBM bandwidth.
-constexpr int FF_CH = 4;  // basis vectors per block row
+constexpr int FF_CH = 2;  // basis vectors per block row
 
 __device__ __forceinline__ float2 lo2(float4 v) { return make_float2(v.x, v.y); }
 __device__ __forceinline__ float2 hi2(float4 v) { return make_float2(v.z, v.w); }
 
-__global__ void __launch_bounds__(NT, 2) k_dots_ff(KState* ks, ff* part, Basis U, int j, size_t n_aug) {
+__global__ void __launch_bounds__(NT, 3) k_dots_ff(KState* ks, ff* part, Basis U, int j, size_t n_aug) {
   constexpr int K = 2 * FF_CH + 1;
   __shared__ ff sh[NW * K];
   __shared__ ff tot[K];
@@ -574,10 +587,28 @@ __global__ void __launch_bounds__(NT, 2) k_dots_ff(KState* ks, ff* part, Basis U
   if (last_block(&ks->counter, gridDim.x * gridDim.y)) dots_last_block<true>(ks, part, j, G);
 }
 
+// (h, l) += (bh, bl) for float-float pairs, left un-normalised.
+__device__ __forceinline__ void ff2_add_acc(float2& h, float2& l, float2 bh, float2 bl) {
+  const float2 s = add2(h, bh);
+  const float2 bb = sub2(s, h);
+  const float2 e = add2(sub2(h, sub2(s, bb)), sub2(bh, bb));
+  h = s;
+  l = add2(l, add2(e, bl));
+}
+
+constexpr int UKG = 4;         // thread groups sharing one quad's basis loop
+constexpr int UQB = NT / UKG;  // quads per block tile
+
+// Update pass, float-float form.  A block tile is UQB quads (four elements
+// each); the UKG thread groups of the block split the basis vectors of every
+// quad (k = group, group + UKG, ...) so each quad has UKG independent load
+// chains, and group 0 adds the other groups' partial sums from shared memory,
+// scales, stores q_j and u_{j+1} and accumulates |u_{j+1}|^2.
 __global__ void __launch_bounds__(NT, 3) k_update_ff(KState* ks, ff* part, Basis U, int j, size_t n_aug) {
   __shared__ float2 qc[MMAX + 1];  // (h, l) of -s_k
   __shared__ float2 uc[MMAX + 1];  // (h, l) of -(z_k - (c/r) s_k)
   __shared__ float2 sc[2];         // -(c/r), 1/r
+  __shared__ float4 xs[UKG - 1][4][UQB];
   __shared__ ff sh[NW];
   if (ks->breakdown_at > 0 && j >= ks->breakdown_at) return;
   for (int k2 = threadIdx.x; k2 < j; k2 += NT) {
@@ -594,55 +625,94 @@ __global__ void __launch_bounds__(NT, 3) k_update_ff(KState* ks, ff* part, Basis
   __syncthreads();
   const float2 ncu_h = make_float2(sc[0].x, sc[0].x), ncu_l = make_float2(sc[0].y, sc[0].y);
   const float2 ir_h = make_float2(sc[1].x, sc[1].x), ir_l = make_float2(sc[1].y, sc[1].y);
+  const int qi = threadIdx.x % UQB, grp = threadIdx.x / UQB;
   float2 S = make_float2(0.f, 0.f), C = make_float2(0.f, 0.f);
   const size_t ld = U.ld, ng = n_aug / 4;
   float* __restrict__ Uh = U.h;
   float* __restrict__ Ul = U.l;
-  const size_t tid = blockIdx.x * (size_t)NT + threadIdx.x, nthr = (size_t)gridDim.x * NT;
-  for (size_t g = tid; g < ng; g += nthr) {
+  const float2 z2 = make_float2(0.f, 0.f);
+  for (size_t tile = blockIdx.x; tile * UQB < ng; tile += gridDim.x) {
+    const size_t g = tile * UQB + qi;
+    const bool valid = g < ng;
     const size_t o = 4 * g;
-    const float4 ujh = *reinterpret_cast<const float4*>(Uh + j * ld + o);
-    const float4 ujl = *reinterpret_cast<const float4*>(Ul + j * ld + o);
-    const float4 wh = *reinterpret_cast<const float4*>(Uh + (j + 1) * ld + o);
-    const float4 wl = *reinterpret_cast<const float4*>(Ul + (j + 1) * ld + o);
-    float2 qh0 = lo2(ujh), qh1 = hi2(ujh), ql0 = lo2(ujl), ql1 = hi2(ujl);  // q_j accumulator
-    float2 uh0 = lo2(wh), uh1 = hi2(wh), ul0 = lo2(wl), ul1 = hi2(wl);      // u_{j+1} accumulator
-    axpy2_acc(ncu_h, ncu_l, lo2(ujh), lo2(ujl), uh0, ul0);
-    axpy2_acc(ncu_h, ncu_l, hi2(ujh), hi2(ujl), uh1, ul1);
-    const float* ph = Uh + o;
-    const float* pl = Ul + o;
-    for (int k2 = 0; k2 < j; ++k2, ph += ld, pl += ld) {
-      const float4 bh = __ldg(reinterpret_cast<const float4*>(ph));
-      const float4 bl = __ldg(reinterpret_cast<const float4*>(pl));
-      const float2 a = qc[k2], b = uc[k2];
-      const float2 ah = make_float2(a.x, a.x), al = make_float2(a.y, a.y);
-      const float2 bhh = make_float2(b.x, b.x), bll = make_float2(b.y, b.y);
-      axpy2_acc(ah, al, lo2(bh), lo2(bl), qh0, ql0);
-      axpy2_acc(ah, al, hi2(bh), hi2(bl), qh1, ql1);
-      axpy2_acc(bhh, bll, lo2(bh), lo2(bl), uh0, ul0);
-      axpy2_acc(bhh, bll, hi2(bh), hi2(bl), uh1, ul1);
-      if ((k2 & 15) == 15) {
-        ff2_norm(qh0, ql0);
-        ff2_norm(qh1, ql1);
-        ff2_norm(uh0, ul0);
-        ff2_norm(uh1, ul1);
+    float2 qh0 = z2, qh1 = z2, ql0 = z2, ql1 = z2, uh0 = z2, uh1 = z2, ul0 = z2, ul1 = z2;
+    if (valid) {
+      if (grp == 0) {
+        const float4 ujh = *reinterpret_cast<const float4*>(Uh + j * ld + o);
+        const float4 ujl = *reinterpret_cast<const float4*>(Ul + j * ld + o);
+        const float4 wh = *reinterpret_cast<const float4*>(Uh + (j + 1) * ld + o);
+        const float4 wl = *reinterpret_cast<const float4*>(Ul + (j + 1) * ld + o);
+        qh0 = lo2(ujh), qh1 = hi2(ujh), ql0 = lo2(ujl), ql1 = hi2(ujl);
+        uh0 = lo2(wh), uh1 = hi2(wh), ul0 = lo2(wl), ul1 = hi2(wl);
+        axpy2_acc(ncu_h, ncu_l, lo2(ujh), lo2(ujl), uh0, ul0);
+        axpy2_acc(ncu_h, ncu_l, hi2(ujh), hi2(ujl), uh1, ul1);
       }
+      int cnt = 0;
+      // one basis quad in flight ahead of the arithmetic
+      float4 nh = make_float4(0.f, 0.f, 0.f, 0.f), nl = nh;
+      if (grp < j) {
+        nh = __ldg(reinterpret_cast<const float4*>(Uh + (size_t)grp * ld + o));
+        nl = __ldg(reinterpret_cast<const float4*>(Ul + (size_t)grp * ld + o));
+      }
+      for (int k2 = grp; k2 < j; k2 += UKG, ++cnt) {
+        const float4 bh = nh, bl = nl;
+        if (k2 + UKG < j) {
+          nh = __ldg(reinterpret_cast<const float4*>(Uh + (size_t)(k2 + UKG) * ld + o));
+          nl = __ldg(reinterpret_cast<const float4*>(Ul + (size_t)(k2 + UKG) * ld + o));
+        }
+        const float2 a = qc[k2], b = uc[k2];
+        const float2 ah = make_float2(a.x, a.x), al = make_float2(a.y, a.y);
+        const float2 bhh = make_float2(b.x, b.x), bll = make_float2(b.y, b.y);
+        axpy2_acc(ah, al, lo2(bh), lo2(bl), qh0, ql0);
+        axpy2_acc(ah, al, hi2(bh), hi2(bl), qh1, ql1);
+        axpy2_acc(bhh, bll, lo2(bh), lo2(bl), uh0, ul0);
+        axpy2_acc(bhh, bll, hi2(bh), hi2(bl), uh1, ul1);
+        if ((cnt & 15) == 15) {
+          ff2_norm(qh0, ql0);
+          ff2_norm(qh1, ql1);
+          ff2_norm(uh0, ul0);
+          ff2_norm(uh1, ul1);
+        }
+      }
+      ff2_norm(qh0, ql0);
+      ff2_norm(qh1, ql1);
+      ff2_norm(uh0, ul0);
+      ff2_norm(uh1, ul1);
     }
-    ff2_norm(qh0, ql0);
-    ff2_norm(qh1, ql1);
-    ff2_norm(uh0, ul0);
-    ff2_norm(uh1, ul1);
-    ff2_scale(qh0, ql0, ir_h, ir_l);
-    ff2_scale(qh1, ql1, ir_h, ir_l);
-    ff2_scale(uh0, ul0, ir_h, ir_l);
-    ff2_scale(uh1, ul1, ir_h, ir_l);
-    dot2_acc(uh0, ul0, uh0, ul0, S, C);
-    dot2_acc(uh1, ul1, uh1, ul1, S, C);
-    *reinterpret_cast<float4*>(Uh + j * ld + o) = make_float4(qh0.x, qh0.y, qh1.x, qh1.y);
-    *reinterpret_cast<float4*>(Ul + j * ld + o) = make_float4(ql0.x, ql0.y, ql1.x, ql1.y);
-    *reinterpret_cast<float4*>(Uh + (j + 1) * ld + o) = make_float4(uh0.x, uh0.y, uh1.x, uh1.y);
-    *reinterpret_cast<float4*>(Ul + (j + 1) * ld + o) = make_float4(ul0.x, ul0.y, ul1.x, ul1.y);
+    if (grp > 0) {
+      xs[grp - 1][0][qi] = make_float4(qh0.x, qh0.y, qh1.x, qh1.y);
+      xs[grp - 1][1][qi] = make_float4(ql0.x, ql0.y, ql1.x, ql1.y);
+      xs[grp - 1][2][qi] = make_float4(uh0.x, uh0.y, uh1.x, uh1.y);
+      xs[grp - 1][3][qi] = make_float4(ul0.x, ul0.y, ul1.x, ul1.y);
+    }
+    __syncthreads();
+    if (grp == 0 && valid) {
+#pragma unroll
+      for (int gg = 0; gg < UKG - 1; ++gg) {
+        const float4 a0 = xs[gg][0][qi], a1 = xs[gg][1][qi], a2 = xs[gg][2][qi], a3 = xs[gg][3][qi];
+        ff2_add_acc(qh0, ql0, lo2(a0), lo2(a1));
+        ff2_add_acc(qh1, ql1, hi2(a0), hi2(a1));
+        ff2_add_acc(uh0, ul0, lo2(a2), lo2(a3));
+        ff2_add_acc(uh1, ul1, hi2(a2), hi2(a3));
+      }
+      ff2_norm(qh0, ql0);
+      ff2_norm(qh1, ql1);
+      ff2_norm(uh0, ul0);
+      ff2_norm(uh1, ul1);
+      ff2_scale(qh0, ql0, ir_h, ir_l);
+      ff2_scale(qh1, ql1, ir_h, ir_l);
+      ff2_scale(uh0, ul0, ir_h, ir_l);
+      ff2_scale(uh1, ul1, ir_h, ir_l);
+      dot2_acc(uh0, ul0, uh0, ul0, S, C);
+      dot2_acc(uh1, ul1, uh1, ul1, S, C);
+      *reinterpret_cast<float4*>(Uh + j * ld + o) = make_float4(qh0.x, qh0.y, qh1.x, qh1.y);
+      *reinterpret_cast<float4*>(Ul + j * ld + o) = make_float4(ql0.x, ql0.y, ql1.x, ql1.y);
+      *reinterpret_cast<float4*>(Uh + (j + 1) * ld + o) = make_float4(uh0.x, uh0.y, uh1.x, uh1.y);
+      *reinterpret_cast<float4*>(Ul + (j + 1) * ld + o) = make_float4(ul0.x, ul0.y, ul1.x, ul1.y);
+    }
+    __syncthreads();  // xs is reused by the next tile
   }
+  const size_t tid = blockIdx.x * (size_t)NT + threadIdx.x, nthr = (size_t)gridDim.x * NT;
   for (size_t i = 4 * ng + tid; i < n_aug; i += nthr) {  // ragged end
     ff xq{Uh[j * ld + i], Ul[j * ld + i]};
     ff xu = ff_fma(ff{sc[0].x, sc[0].y}, xq, ff{Uh[(j + 1) * ld + i], Ul[(j + 1) * ld + i]});
@@ -666,7 +736,7 @@ __global__ void __launch_bounds__(NT, 3) k_update_ff(KState* ks, ff* part, Basis
   if (threadIdx.x == 0) part[blockIdx.x] = tot[0];
   if (last_block(&ks->counter, gridDim.x)) {
     __shared__ double res[1];
-    final_sums<true>(part, 1, gridDim.x, res);
+    final_sums<true>(part, 1, gridDim.x, res, red_stage<true>());
     __syncthreads();
     if (threadIdx.x == 0) {
       const double h = sqrt(res[0]);
@@ -709,7 +779,7 @@ __device__ void cl_matmul(cg::cluster_group& cl, const double* A, const double* 
 }
 
 __global__ void __cluster_dims__(PHI_CL, 1, 1) __launch_bounds__(PHI_NT)
-k_phi(KState* ks, int m_req, double beta, double tol, int force) {
+k_phi(KState* ks, int m_req, double beta, double tol, int force, int diff_rule) {
   cg::cluster_group cl = cg::this_cluster();
   extern __shared__ double sm[];
   __shared__ int s_m;
@@ -780,17 +850,37 @@ k_phi(KState* ks, int m_req, double beta, double tol, int force) {
     F = t;
   }
   if (cl.block_rank() == 0) {
+    __shared__ double s_d2[PHI_NT / 32];
+    // squared change of y from the previous check (entries beyond m_prev count fully)
+    double d2 = 0.0;
+    const int mp = ks->mprev;
+    for (int i = threadIdx.x; i < m; i += blockDim.x) {
+      const double di = E[i * m] - ((i < mp) ? ks->yprev[i] : 0.0);
+      d2 += di * di;
+    }
+    for (int off = 16; off > 0; off >>= 1) d2 += __shfl_down_sync(0xffffffffu, d2, off);
+    if ((threadIdx.x & 31) == 0) s_d2[threadIdx.x >> 5] = d2;
+    __syncthreads();
     if (threadIdx.x == 0) {
+      double dsum = 0.0;
+      for (int w = 0; w < PHI_NT / 32; ++w) dsum += s_d2[w];
       const bool brk = ks->breakdown_at > 0 && ks->breakdown_at <= m;
       const double hm = ks->H[(m - 1) * (MMAX + 1) + m];
       const double err = brk ? 0.0 : beta * hm * fabs(E[(m - 1) * m]);
-      ks->err = err;
-      ks->accept = (force || brk || err <= tol * beta) ? 1 : 0;
+      const double dif = (mp > 0) ? beta * sqrt(dsum) : 1.0 / 0.0;
+      const bool ok = brk || err <= tol * beta || (diff_rule && dif <= tol * beta);
+      ks->err = diff_rule ? fmin(err, dif) : err;
+      ks->accept = (force || ok) ? 1 : 0;
       ks->m_eff = m;
       ks->norm1 = s_norm;
       ks->squarings = sq;
     }
-    for (int i = threadIdx.x; i < m; i += blockDim.x) ks->ycoef[i] = beta * E[i * m];
+    __syncthreads();
+    for (int i = threadIdx.x; i < m; i += blockDim.x) {
+      ks->ycoef[i] = beta * E[i * m];
+      ks->yprev[i] = E[i * m];
+    }
+    if (threadIdx.x == 0) ks->mprev = m;
   }
   cl.sync();  // no CTA exits while others may still write into its shared memory
 }
@@ -862,10 +952,12 @@ cudaError_t launch_norms(bool use_ff, KState* ks, void* part, int nx, const Vec*
   la.nx = nx;
   la.n = n;
   for (int k = 0; k < nx; ++k) la.x[k] = x[k];
+  const int g = grid_for(n);
+  const size_t smem = (size_t)NORMS_MAX * g * 8;
   if (use_ff)
-    k_norms<true><<<grid_for(n), NT, 0, s>>>(ks, static_cast<ff*>(part), la);
+    k_norms<true><<<g, NT, smem, s>>>(ks, static_cast<ff*>(part), la);
   else
-    k_norms<false><<<grid_for(n), NT, 0, s>>>(ks, static_cast<double*>(part), la);
+    k_norms<false><<<g, NT, smem, s>>>(ks, static_cast<double*>(part), la);
   return cudaGetLastError();
 }
 
@@ -903,34 +995,43 @@ cudaError_t launch_dots(bool use_ff, KState* ks, void* part, Basis U, int j, siz
   if (gx > need) gx = need;
   if (gx < 1) gx = 1;
   dim3 grid(gx, chunks);
+  const size_t smem = (size_t)(2 * (j + 1) + 1) * gx * 8;
+  // thread-safe one-time set-up (function-local static initialisation)
+  static const cudaError_t configured = [] {
+    cudaError_t e = cudaFuncSetAttribute(k_dots_ff, cudaFuncAttributeMaxDynamicSharedMemorySize, 128 * 1024);
+    if (e == cudaSuccess)
+      e = cudaFuncSetAttribute(k_dots<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, 128 * 1024);
+    return e;
+  }();
+  if (configured != cudaSuccess) return configured;
   if (use_ff)
-    k_dots_ff<<<grid, NT, 0, s>>>(ks, static_cast<ff*>(part), U, j, n_aug);
+    k_dots_ff<<<grid, NT, smem, s>>>(ks, static_cast<ff*>(part), U, j, n_aug);
   else
-    k_dots<false><<<grid, NT, 0, s>>>(ks, static_cast<double*>(part), U, j, n_aug);
+    k_dots<false><<<grid, NT, smem, s>>>(ks, static_cast<double*>(part), U, j, n_aug);
   return cudaGetLastError();
 }
 
 cudaError_t launch_update(bool use_ff, KState* ks, void* part, Basis U, int j, size_t n_aug, cudaStream_t s) {
   if (j < 0 || j + 1 > MMAX) return cudaErrorInvalidValue;
-  const int g = grid_for(n_aug / 4 + 1);
-  if (use_ff)
-    k_update_ff<<<g, NT, 0, s>>>(ks, static_cast<ff*>(part), U, j, n_aug);
-  else
-    k_update<false><<<g, NT, 0, s>>>(ks, static_cast<double*>(part), U, j, n_aug);
+  if (use_ff) {
+    const size_t tiles = (n_aug / 4 + UQB - 1) / UQB;
+    const int g = (int)(tiles < (size_t)(3 * 152) ? (tiles > 0 ? tiles : 1) : 3 * 152);
+    k_update_ff<<<g, NT, (size_t)g * 8, s>>>(ks, static_cast<ff*>(part), U, j, n_aug);
+  } else {
+    const int g = grid_for(n_aug / 4 + 1);
+    k_update<false><<<g, NT, (size_t)g * 8, s>>>(ks, static_cast<double*>(part), U, j, n_aug);
+  }
   return cudaGetLastError();
 }
 
-cudaError_t launch_phi(KState* ks, int m, double beta, double tol, int force_accept, cudaStream_t s) {
+cudaError_t launch_phi(KState* ks, int m, double beta, double tol, int force_accept, int diff_rule,
+                       cudaStream_t s) {
   if (m < 1 || m > MMAX) return cudaErrorInvalidValue;
   const size_t smem = 6 * sizeof(double) * (size_t)m * m;
-  static bool configured = false;
-  if (!configured) {
-    cudaError_t e = cudaFuncSetAttribute(k_phi, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                         (int)(6 * sizeof(double) * MMAX * MMAX));
-    if (e != cudaSuccess) return e;
-    configured = true;
-  }
-  k_phi<<<PHI_CL, PHI_NT, smem, s>>>(ks, m, beta, tol, force_accept);
+  static const cudaError_t configured =
+      cudaFuncSetAttribute(k_phi, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)(6 * sizeof(double) * MMAX * MMAX));
+  if (configured != cudaSuccess) return configured;
+  k_phi<<<PHI_CL, PHI_NT, smem, s>>>(ks, m, beta, tol, force_accept, diff_rule);
   return cudaGetLastError();
 }
 

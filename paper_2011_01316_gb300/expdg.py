@@ -50,6 +50,10 @@ class expdg_kernel_prof(ctypes.Structure):
 KERNEL_CLASSES = ["residual", "jv", "dots", "update", "phi", "combine", "vector"]
 
 
+class expdg_server_config(ctypes.Structure):
+    _fields_ = [("hbm_budget", ctypes.c_size_t), ("workers", ctypes.c_int)]
+
+
 class ExpdgError(RuntimeError):
     def __init__(self, status, msg):
         super().__init__(f"{STATUS_NAMES.get(status, status)}: {msg}")
@@ -85,6 +89,15 @@ def _load():
         "expdg_profile_enable": (ctypes.c_int, [P, ctypes.c_int]),
         "expdg_profile_get": (ctypes.c_int, [P, P, ctypes.c_int]),
         "expdg_residual_noalloc": (ctypes.c_int, [vp(expdg_config), P, P, P]),
+        "expdg_config_node_coords": (ctypes.c_int, [vp(expdg_config), P]),
+        "expdg_context_bytes": (ctypes.c_size_t, [vp(expdg_config)]),
+        "expdg_server_create": (ctypes.c_int, [vp(expdg_server_config), vp(P)]),
+        "expdg_server_destroy": (None, [P]),
+        "expdg_server_submit": (ctypes.c_int, [P, vp(expdg_config), P, ctypes.c_double, ctypes.c_int,
+                                               vp(ctypes.c_int64)]),
+        "expdg_server_poll": (ctypes.c_int, [P, vp(ctypes.c_int64), ctypes.c_int, vp(ctypes.c_int)]),
+        "expdg_server_fetch": (ctypes.c_int, [P, ctypes.c_int64, P, vp(expdg_stats), vp(ctypes.c_double)]),
+        "expdg_server_info": (ctypes.c_int, [P, vp(ctypes.c_size_t), vp(ctypes.c_int), vp(ctypes.c_int)]),
     }
     for name, (res, args) in sig.items():
         f = getattr(lib, name)
@@ -128,6 +141,22 @@ def default_config(**kw):
         else:
             setattr(c, k, v)
     return c
+
+
+def config_node_coords(cfg):
+    """Node coordinates [dim, Ne, Np] of a configuration, without a context."""
+    nelem = 1
+    for d in range(cfg.dim):
+        nelem *= cfg.ne[d]
+    out = np.zeros((cfg.dim, nelem, (cfg.p + 1) ** cfg.dim))
+    st = _lib.expdg_config_node_coords(ctypes.byref(cfg), _ptr(out))
+    if st != EXPDG_OK:
+        raise ExpdgError(st, "expdg_config_node_coords failed")
+    return out
+
+
+def context_bytes(cfg):
+    return int(_lib.expdg_context_bytes(ctypes.byref(cfg)))
 
 
 def _trace_array(trace):
