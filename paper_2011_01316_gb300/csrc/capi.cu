@@ -1,5 +1,6 @@
 // C-ABI of libexpdg: contexts, the Krylov phi-sum driver and the exponential
 // steps (paper Sec. 2.3 and the EPI2 / EXPRB32 / EXPRB42 footnotes of Sec. 5).
+#include <algorithm>
 #include <cmath>
 #include <cstdio>
 #include <cstring>
@@ -38,6 +39,7 @@ struct expdg_ctx {
   KState* ks = nullptr;
   void* part = nullptr;
   KState* h_ks = nullptr;  // pinned mirror (host-visible block only is refreshed)
+  int m_hint[2] = {0, 0};  // m accepted by each stage's first sub-step in the previous step
   std::vector<void*> allocs;
   std::string err;
   // profiling
@@ -74,7 +76,10 @@ cudaError_t dalloc(expdg_ctx* ctx, T** p, size_t n) {
   cudaError_t e = cudaMalloc(&q, n * sizeof(T) > 0 ? n * sizeof(T) : 16);
   if (e != cudaSuccess) return e;
   ctx->allocs.push_back(q);
-  e = cudaMemset(q, 0, n * sizeof(T) > 0 ? n * sizeof(T) : 16);
+  // zero-fill on the legacy default stream; expdg_create synchronises that
+  // stream before returning, so work the caller later queues on any stream
+  // (including non-blocking ones, which never wait for it) sees zeros
+  e = cudaMemsetAsync(q, 0, n * sizeof(T) > 0 ? n * sizeof(T) : 16, 0);
   *p = static_cast<T*>(q);
   return e;
 }
@@ -228,9 +233,12 @@ struct Replay {
 // w = sum_{i=0}^P phi_i(tau L(qt)) c_i  (c_i in ctx->c, has[i] false: zero).
 // On the final sub-step the combination writes fin_out = fin_base + w instead
 // of ctx->w (fin_out null: result left in ctx->w).
+// use_hint: start the error checks of the first sub-step at
+// max(m_step, m_prev - m_step), m_prev the m this stage accepted in the previous
+// step (consecutive steps need similar m; a later acceptance is only more exact).
 expdg_status phi_solve(expdg_ctx* ctx, const void* qt_T, double tau, const bool* has, int P, Vec fin_base,
                        Vec fin_out, int solve_id, const Replay& rp, expdg_stats* st,
-                       std::vector<expdg_trace_entry>* trace) {
+                       std::vector<expdg_trace_entry>* trace, bool use_hint = false) {
   const size_t N = ctx->N, n_aug = N + P;
   const bool F = ctx->ff;
   const cudaStream_t s = ctx->stream;
@@ -304,6 +312,10 @@ expdg_status phi_solve(expdg_ctx* ctx, const void* qt_T, double tau, const bool*
     }
     RUN(ctx, EXPDG_K_VECTOR, 16.0 * N, launch_start(F, ctx->ks, ctx->U, ctx->w, N, P, eta, s));
     const int limit = replay ? m_fix : cfg.m_max;
+    int m_first = cfg.m_step;
+    const bool first_sub = (sv == 0.0 && rejected == 0);
+    if (use_hint && first_sub && !replay && ctx->m_hint[solve_id & 1] > 0)
+      m_first = std::max(cfg.m_step, ctx->m_hint[solve_id & 1] - cfg.m_step);
     bool accepted = false;
     int m_acc = 0;
     double err = 0.0;
@@ -346,7 +358,7 @@ expdg_status phi_solve(expdg_ctx* ctx, const void* qt_T, double tau, const bool*
       st->krylov_iters++;
       st->jv_applies++;
       const int m = J;
-      const bool check = replay ? (m == m_fix) : (m % cfg.m_step == 0 || m == cfg.m_max);
+      const bool check = replay ? (m == m_fix) : (m == cfg.m_max || (m >= m_first && m % cfg.m_step == 0));
       if (!check) continue;
       // mixed form: the FP32 operator's rounding noise inflates Saad's estimate, so a
       // converged change between consecutive checks also accepts
@@ -372,6 +384,7 @@ expdg_status phi_solve(expdg_ctx* ctx, const void* qt_T, double tau, const bool*
     } else {
       RUN(ctx, EXPDG_K_COMBINE, 8.0 * (m_acc + 1) * N, launch_combine(F, ctx->ks, ctx->U, null_vec(), ctx->w, N, s));
     }
+    if (use_hint && first_sub && !replay) ctx->m_hint[solve_id & 1] = m_acc;
     sv += sigma;
     st->substeps++;
     st->err_est = std::fmax(st->err_est, err);
@@ -428,7 +441,7 @@ expdg_status step_dev(expdg_ctx* ctx, double* q, double dt, const Replay& rp, ex
     CU(ctx, residual_for_step(ctx, q, ctx->d_q32, ctx->c[1], dt));
     st->residual_applies++;
     has[1] = true;
-    return phi_solve(ctx, qt_T, dt, has, 1, dvec(q), dvec(q), 0, rp, st, trace);
+    return phi_solve(ctx, qt_T, dt, has, 1, dvec(q), dvec(q), 0, rp, st, trace, true);
   }
   // EXPRB32 / EXPRB42 share: R^n, stage 1, D_{n,2} = R(q2) - R^n - L (q2 - q)
   CU(ctx, residual_for_step(ctx, q, ctx->d_q32, ctx->rn, 1.0));
@@ -440,7 +453,7 @@ expdg_status step_dev(expdg_ctx* ctx, double* q, double dt, const Replay& rp, ex
     RUN(ctx, EXPDG_K_VECTOR, 16.0 * N, launch_lincomb(F, ctx->c[1], 1, x, a, N, s));
   }
   has[1] = true;
-  expdg_status r = phi_solve(ctx, qt_T, a1, has, 1, dvec(q), dvec(ctx->d_q2), 0, rp, st, trace);
+  expdg_status r = phi_solve(ctx, qt_T, a1, has, 1, dvec(q), dvec(ctx->d_q2), 0, rp, st, trace, true);
   if (r != EXPDG_OK) return r;
   // t1 = R(q2)
   CU(ctx, residual_for_step(ctx, ctx->d_q2, ctx->d_q32b, ctx->t1, 1.0));
@@ -467,7 +480,7 @@ expdg_status step_dev(expdg_ctx* ctx, double* q, double dt, const Replay& rp, ex
   bool has2[EXPDG_MAX_PHI + 1] = {false, false, false, true};
   if (scheme == EXPDG_EXPRB32) {
     // q^{n+1} = q2 + 2 dt phi_3(dt L) D
-    return phi_solve(ctx, qt_T, dt, has2, 3, dvec(ctx->d_q2), dvec(q), 1, rp, st, trace);
+    return phi_solve(ctx, qt_T, dt, has2, 3, dvec(ctx->d_q2), dvec(q), 1, rp, st, trace, true);
   }
   // EXPRB42: q^{n+1} = q + dt phi_1(dt L) R^n + 32/9 dt phi_3(dt L) D
   {
@@ -476,7 +489,7 @@ expdg_status step_dev(expdg_ctx* ctx, double* q, double dt, const Replay& rp, ex
     RUN(ctx, EXPDG_K_VECTOR, 16.0 * N, launch_lincomb(F, ctx->c[1], 1, x, a, N, s));
   }
   has2[1] = true;
-  return phi_solve(ctx, qt_T, dt, has2, 3, dvec(q), dvec(q), 1, rp, st, trace);
+  return phi_solve(ctx, qt_T, dt, has2, 3, dvec(q), dvec(q), 1, rp, st, trace, true);
 }
 
 void write_trace(const std::vector<expdg_trace_entry>& tr, expdg_trace_entry* out, int cap, int* n) {
@@ -619,6 +632,7 @@ expdg_status expdg_create(const expdg_config* cfg, expdg_ctx** out) {
   ALLOC(cudaMallocHost(&hk, sizeof(KState)));
   ctx->h_ks = static_cast<KState*>(hk);
   std::memset(ctx->h_ks, 0, sizeof(KState));
+  ALLOC(cudaStreamSynchronize(0));  // the zero-fills above are complete
 #undef ALLOC
   *out = ctx;
   return EXPDG_OK;
@@ -802,6 +816,8 @@ expdg_status expdg_advance(expdg_ctx* ctx, double* q, double dt, int nsteps, exp
   if (!qdev) CU(ctx, cudaMemcpyAsync(qd, q, N * sizeof(double), cudaMemcpyHostToDevice, ctx->stream));
   expdg_stats st{};
   Replay rp;
+  // a solve's decisions depend only on its own inputs, not on earlier calls
+  ctx->m_hint[0] = ctx->m_hint[1] = 0;
   for (int k = 0; k < nsteps; ++k) {
     expdg_status r = step_dev(ctx, qd, dt, rp, &st, nullptr);
     if (r != EXPDG_OK) return r;

@@ -9,6 +9,30 @@
 
 namespace expdg {
 
+// Programmatic dependent launch: a kernel launched with pdl_launch may start
+// while the previous kernel in its stream is finishing; it must execute
+// griddep_wait() before touching any memory that kernel reads or writes.
+__device__ __forceinline__ void griddep_wait() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
+// Signal that this block's share of the work is done, so the dependent grid may
+// be scheduled (it still waits in griddep_wait for this grid's completion).
+__device__ __forceinline__ void griddep_launch() { asm volatile("griddepcontrol.launch_dependents;" ::: "memory"); }
+
+template <typename... KArgs, typename... Args>
+cudaError_t pdl_launch(void (*kern)(KArgs...), dim3 grid, dim3 block, size_t smem, cudaStream_t s,
+                       Args... args) {
+  cudaLaunchConfig_t lc = {};
+  lc.gridDim = grid;
+  lc.blockDim = block;
+  lc.dynamicSmemBytes = smem;
+  lc.stream = s;
+  cudaLaunchAttribute at[1];
+  at[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+  at[0].val.programmaticStreamSerializationAllowed = 1;
+  lc.attrs = at;
+  lc.numAttrs = 1;
+  return cudaLaunchKernelEx(&lc, kern, static_cast<KArgs>(args)...);
+}
+
 constexpr int MAXP = EXPDG_MAX_ORDER;
 constexpr int MMAX = EXPDG_MAX_KRYLOV;
 constexpr int RED_BLOCKS = 4 * 152;   // grid of the reduction kernels (deterministic partial order)

@@ -120,6 +120,7 @@ k_dg(const DGArgs a, const Tab tab) {
   constexpr bool FF = !std::is_same<T, double>::value;
   using PH = Phys<DIM, EQ, T>;
 
+  griddep_wait();
   extern __shared__ __align__(16) unsigned char smem_raw[];
   T* sF = reinterpret_cast<T*>(smem_raw);  // [DIM][M][SLOT]
   T* sD = sF + DIM * M * SLOT;             // [NP1][NP1]
@@ -160,6 +161,7 @@ k_dg(const DGArgs a, const Tab tab) {
     }
   }
   __syncthreads();
+  griddep_launch();
   if (!active) return;
 
   int ii[DIM];
@@ -314,8 +316,7 @@ cudaError_t launch_dg_t(const DGArgs& a, const Tab& t, cudaStream_t s) {
       cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (configured != cudaSuccess) return configured;
   if (blocks == 0) return cudaSuccess;
-  kern<<<blocks, threads, smem, s>>>(a, t);
-  return cudaGetLastError();
+  return pdl_launch(kern, dim3(blocks), dim3(threads), smem, s, a, t);
 }
 
 template <int DIM, int EQ, typename T, bool LINEAR>

@@ -387,6 +387,7 @@ __device__ void dots_last_block(KState* ks, const typename Acc<FF>::T* part, int
 // coefficients of the update pass.
 template <bool FF>
 __global__ void __launch_bounds__(NT) k_dots(KState* ks, typename Acc<FF>::T* part, Basis U, int j, size_t n_aug) {
+  griddep_wait();
   using A = Acc<FF>;
   constexpr int K = 2 * DOT_CHUNK + 1;
   __shared__ typename A::T sh[NW * K];
@@ -432,6 +433,7 @@ __global__ void __launch_bounds__(NT) k_dots(KState* ks, typename Acc<FF>::T* pa
   const int G = gridDim.x;
   if (threadIdx.x < 2 * nc) part[(size_t)(2 * c0 + threadIdx.x) * G + blockIdx.x] = tot[threadIdx.x];
   if (wnorm && threadIdx.x == 2 * DOT_CHUNK) part[(size_t)(2 * nvec) * G + blockIdx.x] = tot[2 * DOT_CHUNK];
+  griddep_launch();
   if (last_block(&ks->counter, gridDim.x * gridDim.y)) dots_last_block<FF>(ks, part, j, G);
 }
 
@@ -442,6 +444,7 @@ __global__ void __launch_bounds__(NT) k_dots(KState* ks, typename Acc<FF>::T* pa
 // |u_{j+1}|^2 for the provisional H(j+1, j).
 template <bool FF>
 __global__ void __launch_bounds__(NT) k_update(KState* ks, typename Acc<FF>::T* part, Basis U, int j, size_t n_aug) {
+  griddep_wait();
   using A = Acc<FF>;
   __shared__ typename A::T qc[MMAX + 1];
   __shared__ typename A::T uc[MMAX + 1];
@@ -500,6 +503,7 @@ __global__ void __launch_bounds__(NT) k_update(KState* ks, typename Acc<FF>::T* 
   __shared__ typename A::T tot[1];
   block_sum<FF, 1>(nrm, sh, tot);
   if (threadIdx.x == 0) part[blockIdx.x] = tot[0];
+  griddep_launch();
   if (last_block(&ks->counter, gridDim.x)) {
     __shared__ double res[1];
     final_sums<FF>(part, 1, gridDim.x, res, red_stage<FF>());
@@ -525,6 +529,7 @@ __device__ __forceinline__ float2 lo2(float4 v) { return make_float2(v.x, v.y); 
 __device__ __forceinline__ float2 hi2(float4 v) { return make_float2(v.z, v.w); }
 
 __global__ void __launch_bounds__(NT, 3) k_dots_ff(KState* ks, ff* part, Basis U, int j, size_t n_aug) {
+  griddep_wait();
   constexpr int K = 2 * FF_CH + 1;
   __shared__ ff sh[NW * K];
   __shared__ ff tot[K];
@@ -584,6 +589,7 @@ __global__ void __launch_bounds__(NT, 3) k_dots_ff(KState* ks, ff* part, Basis U
   const int G = gridDim.x;
   if (threadIdx.x < 2 * nc) part[(size_t)(2 * c0 + threadIdx.x) * G + blockIdx.x] = tot[threadIdx.x];
   if (wnorm && threadIdx.x == 2 * FF_CH) part[(size_t)(2 * nvec) * G + blockIdx.x] = tot[2 * FF_CH];
+  griddep_launch();
   if (last_block(&ks->counter, gridDim.x * gridDim.y)) dots_last_block<true>(ks, part, j, G);
 }
 
@@ -605,6 +611,7 @@ constexpr int UQB = NT / UKG;  // quads per block tile
 // chains, and group 0 adds the other groups' partial sums from shared memory,
 // scales, stores q_j and u_{j+1} and accumulates |u_{j+1}|^2.
 __global__ void __launch_bounds__(NT, 3) k_update_ff(KState* ks, ff* part, Basis U, int j, size_t n_aug) {
+  griddep_wait();
   __shared__ float2 qc[MMAX + 1];  // (h, l) of -s_k
   __shared__ float2 uc[MMAX + 1];  // (h, l) of -(z_k - (c/r) s_k)
   __shared__ float2 sc[2];         // -(c/r), 1/r
@@ -734,6 +741,7 @@ __global__ void __launch_bounds__(NT, 3) k_update_ff(KState* ks, ff* part, Basis
   __shared__ ff tot[1];
   block_sum<true, 1>(v, sh, tot);
   if (threadIdx.x == 0) part[blockIdx.x] = tot[0];
+  griddep_launch();
   if (last_block(&ks->counter, gridDim.x)) {
     __shared__ double res[1];
     final_sums<true>(part, 1, gridDim.x, res, red_stage<true>());
@@ -1004,11 +1012,8 @@ cudaError_t launch_dots(bool use_ff, KState* ks, void* part, Basis U, int j, siz
     return e;
   }();
   if (configured != cudaSuccess) return configured;
-  if (use_ff)
-    k_dots_ff<<<grid, NT, smem, s>>>(ks, static_cast<ff*>(part), U, j, n_aug);
-  else
-    k_dots<false><<<grid, NT, smem, s>>>(ks, static_cast<double*>(part), U, j, n_aug);
-  return cudaGetLastError();
+  if (use_ff) return pdl_launch(k_dots_ff, grid, dim3(NT), smem, s, ks, static_cast<ff*>(part), U, j, n_aug);
+  return pdl_launch(k_dots<false>, grid, dim3(NT), smem, s, ks, static_cast<double*>(part), U, j, n_aug);
 }
 
 cudaError_t launch_update(bool use_ff, KState* ks, void* part, Basis U, int j, size_t n_aug, cudaStream_t s) {
@@ -1016,12 +1021,10 @@ cudaError_t launch_update(bool use_ff, KState* ks, void* part, Basis U, int j, s
   if (use_ff) {
     const size_t tiles = (n_aug / 4 + UQB - 1) / UQB;
     const int g = (int)(tiles < (size_t)(3 * 152) ? (tiles > 0 ? tiles : 1) : 3 * 152);
-    k_update_ff<<<g, NT, (size_t)g * 8, s>>>(ks, static_cast<ff*>(part), U, j, n_aug);
-  } else {
-    const int g = grid_for(n_aug / 4 + 1);
-    k_update<false><<<g, NT, (size_t)g * 8, s>>>(ks, static_cast<double*>(part), U, j, n_aug);
+    return pdl_launch(k_update_ff, dim3(g), dim3(NT), (size_t)g * 8, s, ks, static_cast<ff*>(part), U, j, n_aug);
   }
-  return cudaGetLastError();
+  const int g = grid_for(n_aug / 4 + 1);
+  return pdl_launch(k_update<false>, dim3(g), dim3(NT), (size_t)g * 8, s, ks, static_cast<double*>(part), U, j, n_aug);
 }
 
 cudaError_t launch_phi(KState* ks, int m, double beta, double tol, int force_accept, int diff_rule,

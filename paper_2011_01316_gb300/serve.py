@@ -53,15 +53,16 @@ class Server:
         expdg.lib.expdg_server_poll(self.h, ids, cap, ctypes.byref(n))
         return [ids[i] for i in range(n.value)]
 
-    def fetch(self, rid):
-        """(final state, stats dict, (queueing, service, latency) seconds)."""
+    def fetch(self, rid, check=True):
+        """(final state, stats dict, (queueing, service, latency) seconds, status).
+        With check=True a failed solve raises ExpdgError."""
         q = np.empty(self._shapes.pop(rid))
         stt = expdg.expdg_stats()
         times = (ctypes.c_double * 3)()
         st = expdg.lib.expdg_server_fetch(self.h, rid, q.ctypes.data, ctypes.byref(stt), times)
-        if st != expdg.EXPDG_OK:
+        if check and st != expdg.EXPDG_OK:
             raise expdg.ExpdgError(st, f"solve {rid} failed")
-        return q, stt.as_dict(), tuple(times)
+        return q, stt.as_dict(), tuple(times), st
 
     def info(self):
         used = ctypes.c_size_t(0)
@@ -104,10 +105,11 @@ def vortex_request(rng, prec, courant=5.0, sides=(8, 128), orders=(2, 5), steps=
     return cfg, np.ascontiguousarray(q0), dt, steps
 
 
-def run_stream(server, requests, rate, rng, poll_interval=2e-4):
+def run_stream(server, requests, rate, rng, poll_interval=2e-4, check=True):
     """Submit `requests` [(cfg, q0, dt, nsteps)] with Poisson arrivals of mean
-    `rate` per second (rate <= 0: all at once); return per-request results in
-    submission order and the wall time from first arrival to last completion."""
+    `rate` per second (rate <= 0: all at once); return per-request results
+    (q, stats, times, status) in submission order and the wall time from first
+    arrival to last completion.  check=False keeps failed solves as results."""
     n = len(requests)
     gaps = rng.exponential(1.0 / rate, n) if rate > 0 else np.zeros(n)
     arrivals = np.cumsum(gaps) - gaps[0]
@@ -126,7 +128,7 @@ def run_stream(server, requests, rate, rng, poll_interval=2e-4):
             k += 1
         for rid in server.poll():
             i = where.pop(rid)
-            out[i] = server.fetch(rid)
+            out[i] = server.fetch(rid, check=check)
             done += 1
         if done < n:
             time.sleep(poll_interval)
@@ -135,8 +137,10 @@ def run_stream(server, requests, rate, rng, poll_interval=2e-4):
 
 
 def latency_summary(results, wall):
-    lat = np.array([r[2][2] for r in results])
-    return {"solves": len(results), "wall_s": wall, "solves_per_s": len(results) / wall,
+    """Throughput and latency over the successful solves (failures counted)."""
+    ok = [r for r in results if r[3] == expdg.EXPDG_OK]
+    lat = np.array([r[2][2] for r in ok]) if ok else np.array([float("nan")])
+    return {"solves": len(ok), "failed": len(results) - len(ok), "wall_s": wall, "solves_per_s": len(ok) / wall,
             "p50_ms": 1e3 * float(np.percentile(lat, 50)), "p99_ms": 1e3 * float(np.percentile(lat, 99)),
-            "mean_queue_ms": 1e3 * float(np.mean([r[2][0] for r in results])),
-            "mean_service_ms": 1e3 * float(np.mean([r[2][1] for r in results]))}
+            "mean_queue_ms": 1e3 * float(np.mean([r[2][0] for r in ok])) if ok else None,
+            "mean_service_ms": 1e3 * float(np.mean([r[2][1] for r in ok])) if ok else None}

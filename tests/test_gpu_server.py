@@ -51,11 +51,28 @@ def test_same_result_alone_and_in_the_mix(mods, prec):
     mix, wall = serve.run_stream(s8, reqs, 0.0, np.random.default_rng(0))
     info = s8.info()
     s8.close()
-    for (q_mix, st, times), q_alone in zip(mix, alone):
+    for (q_mix, st, times, status), q_alone in zip(mix, alone):
         # deterministic kernels and reductions: identical bits alone and in the mix
         np.testing.assert_array_equal(q_mix, q_alone)
         assert times[2] >= times[1] > 0.0
     assert info["pending"] == 0 and info["running"] == 0
+
+
+def test_fresh_contexts_under_concurrency(mods):
+    """Many fresh contexts created and run at once on non-blocking worker
+    streams (as under load): every result equals its single-stream result."""
+    expdg, inputs, serve = mods
+    rng = np.random.default_rng(5)
+    reqs = [serve.vortex_request(rng, 1, sides=(20, 90), orders=(2, 5), steps=3) for _ in range(16)]
+    s = serve.Server(workers=8)
+    mix, _ = serve.run_stream(s, reqs, 0.0, rng)
+    s.close()
+    for (cfg, q0, dt, n), (q_mix, st, times, status) in zip(reqs, mix):
+        ctx = expdg.Context(cfg)
+        q = q0.copy()
+        ctx.advance(q, dt, n)
+        ctx.close()
+        np.testing.assert_array_equal(q_mix, q)
 
 
 def test_budget_admission_and_refusal(mods):
