@@ -299,6 +299,10 @@ def main():
     ap.add_argument("--serve-requests", type=int, default=48, help="requests of the serving workload (0: skip)")
     ap.add_argument("--batch-instances", type=int, default=64, help="instances of the batched workload (0: skip)")
     ap.add_argument("--no-3d", action="store_true", help="skip the 3D HBM-roofline workload")
+    ap.add_argument("--legs", default="main,wave3d,serving,batched",
+                    help="comma list of legs to run (main = the timed workload; profiling runs pick one)")
+    ap.add_argument("--wave3d-ne", type=int, default=32, help="elements per direction of the 3D leg")
+    ap.add_argument("--wave3d-steps", type=int, default=2)
     args = ap.parse_args()
 
     world = int(os.environ.get("WORLD_SIZE", "1"))
@@ -322,6 +326,18 @@ def main():
             dist.barrier()
         torch.cuda.synchronize()
 
+    if "main" not in set(args.legs.split(",")):
+        hbm, _ = peaks()
+        out = {}
+        if "wave3d" in args.legs:
+            out["wave3d"] = wave3d_workload(steps=args.wave3d_steps, hbm=hbm, ne=args.wave3d_ne)
+        if "serving" in args.legs:
+            out["serving"] = serving_workload(args.serve_requests)
+        if "batched" in args.legs:
+            out["batched"] = batched_workload(args.batch_instances)
+        if rank == 0:
+            print(json.dumps({"legs": args.legs, **out}), flush=True)
+        return
     stream = torch.cuda.current_stream()
     ctx = expdg.Context(**CFG, prec=expdg.EXPDG_MIXED)
     ctx.set_stream(stream)
@@ -404,9 +420,12 @@ def main():
            "d2h_bytes_per_step": 8 * N}
 
     hbm, _ = peaks()
-    wave3d = None if args.no_3d else wave3d_workload(hbm=hbm)
-    serving = serving_workload(args.serve_requests) if args.serve_requests > 0 else None
-    batched = batched_workload(args.batch_instances) if args.batch_instances > 0 else None
+    legs = set(args.legs.split(","))
+    wave3d = None
+    if "wave3d" in legs and not args.no_3d:
+        wave3d = wave3d_workload(steps=args.wave3d_steps, hbm=hbm, ne=args.wave3d_ne)
+    serving = serving_workload(args.serve_requests) if args.serve_requests > 0 and "serving" in legs else None
+    batched = batched_workload(args.batch_instances) if args.batch_instances > 0 and "batched" in legs else None
 
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:

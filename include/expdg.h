@@ -252,6 +252,19 @@ expdg_status expdg_server_fetch(expdg_server* s, int64_t id, double* q_out, expd
 /* Bytes held by contexts, queued and running solve counts. */
 expdg_status expdg_server_info(expdg_server* s, size_t* used_bytes, int* pending, int* running);
 
+/* Arithmetic-unit throughput of the current device, measured by short
+ * dependent-chain-free loops (allocates and frees a small buffer): FP64 FMA,
+ * FP32 FMA, packed FP32 FMA (lane FMAs) and f64 -> f32 conversions per second. */
+typedef struct {
+  double fp64_fma_per_s;
+  double fp32_fma_per_s;
+  double fp32x2_fma_per_s;
+  double f64_to_f32_per_s;
+  int sms;
+  double clock_mhz;
+} expdg_rates;
+expdg_status expdg_probe_rates(expdg_rates* out);
+
 /* ---- Allocation-free residual ---------------------------------------------
  * The paper has no counterpart to this call; it is a deployment convenience.
  *

@@ -535,16 +535,20 @@ __global__ void __launch_bounds__(NT, 3) k_dots_ff(KState* ks, ff* part, Basis U
   __shared__ ff tot[K];
   if (ks->breakdown_at > 0 && j >= ks->breakdown_at) return;
   const int nvec = j + 1;
-  const int c0 = blockIdx.y * FF_CH;
+  const int nch = (nvec + FF_CH - 1) / FF_CH;
+  // consecutive blocks take the chunks of one element range, so u_j and w of
+  // that range are read from HBM once and from L2 by the other chunks
+  const int cy = blockIdx.x % nch, bx = blockIdx.x / nch, G = gridDim.x / nch;
+  const int c0 = cy * FF_CH;
   const int nc = min(FF_CH, nvec - c0);
-  const bool wnorm = blockIdx.y == 0;
+  const bool wnorm = cy == 0;
   float2 S[K], C[K];
 #pragma unroll
   for (int k2 = 0; k2 < K; ++k2) S[k2] = C[k2] = make_float2(0.f, 0.f);
   const size_t ld = U.ld, ng = n_aug / 4;
   const float* __restrict__ Uh = U.h;
   const float* __restrict__ Ul = U.l;
-  const size_t tid = blockIdx.x * (size_t)NT + threadIdx.x, nthr = (size_t)gridDim.x * NT;
+  const size_t tid = bx * (size_t)NT + threadIdx.x, nthr = (size_t)G * NT;
   for (size_t g = tid; g < ng; g += nthr) {
     const size_t o = 4 * g;
     const float4 ujh = __ldg(reinterpret_cast<const float4*>(Uh + j * ld + o));
@@ -586,11 +590,10 @@ __global__ void __launch_bounds__(NT, 3) k_dots_ff(KState* ks, ff* part, Basis U
 #pragma unroll
   for (int k2 = 0; k2 < K; ++k2) v[k2] = dot2_value(S[k2], C[k2]);
   block_sum<true, K>(v, sh, tot);
-  const int G = gridDim.x;
-  if (threadIdx.x < 2 * nc) part[(size_t)(2 * c0 + threadIdx.x) * G + blockIdx.x] = tot[threadIdx.x];
-  if (wnorm && threadIdx.x == 2 * FF_CH) part[(size_t)(2 * nvec) * G + blockIdx.x] = tot[2 * FF_CH];
+  if (threadIdx.x < 2 * nc) part[(size_t)(2 * c0 + threadIdx.x) * G + bx] = tot[threadIdx.x];
+  if (wnorm && threadIdx.x == 2 * FF_CH) part[(size_t)(2 * nvec) * G + bx] = tot[2 * FF_CH];
   griddep_launch();
-  if (last_block(&ks->counter, gridDim.x * gridDim.y)) dots_last_block<true>(ks, part, j, G);
+  if (last_block(&ks->counter, gridDim.x)) dots_last_block<true>(ks, part, j, G);
 }
 
 // (h, l) += (bh, bl) for float-float pairs, left un-normalised.
@@ -615,7 +618,7 @@ __global__ void __launch_bounds__(NT, 3) k_update_ff(KState* ks, ff* part, Basis
   __shared__ float2 qc[MMAX + 1];  // (h, l) of -s_k
   __shared__ float2 uc[MMAX + 1];  // (h, l) of -(z_k - (c/r) s_k)
   __shared__ float2 sc[2];         // -(c/r), 1/r
-  __shared__ float4 xs[UKG - 1][4][UQB];
+  __shared__ float4 xs[UKG][4][UQB];  // every group's partial sums of the tile
   __shared__ ff sh[NW];
   if (ks->breakdown_at > 0 && j >= ks->breakdown_at) return;
   for (int k2 = threadIdx.x; k2 < j; k2 += NT) {
@@ -686,36 +689,33 @@ __global__ void __launch_bounds__(NT, 3) k_update_ff(KState* ks, ff* part, Basis
       ff2_norm(uh0, ul0);
       ff2_norm(uh1, ul1);
     }
-    if (grp > 0) {
-      xs[grp - 1][0][qi] = make_float4(qh0.x, qh0.y, qh1.x, qh1.y);
-      xs[grp - 1][1][qi] = make_float4(ql0.x, ql0.y, ql1.x, ql1.y);
-      xs[grp - 1][2][qi] = make_float4(uh0.x, uh0.y, uh1.x, uh1.y);
-      xs[grp - 1][3][qi] = make_float4(ul0.x, ul0.y, ul1.x, ul1.y);
-    }
+    xs[grp][0][qi] = make_float4(qh0.x, qh0.y, qh1.x, qh1.y);
+    xs[grp][1][qi] = make_float4(ql0.x, ql0.y, ql1.x, ql1.y);
+    xs[grp][2][qi] = make_float4(uh0.x, uh0.y, uh1.x, uh1.y);
+    xs[grp][3][qi] = make_float4(ul0.x, ul0.y, ul1.x, ul1.y);
     __syncthreads();
-    if (grp == 0 && valid) {
+    {
+      // thread t finalises element t of the tile: quad t/4, lane t%4
+      const int eq = threadIdx.x >> 2, el = threadIdx.x & 3;
+      const size_t ge = tile * UQB + eq;
+      if (ge < ng) {
+        auto pick = [&](const float4& v) { return el == 0 ? v.x : el == 1 ? v.y : el == 2 ? v.z : v.w; };
+        ff xq{0.f, 0.f}, xu{0.f, 0.f};
 #pragma unroll
-      for (int gg = 0; gg < UKG - 1; ++gg) {
-        const float4 a0 = xs[gg][0][qi], a1 = xs[gg][1][qi], a2 = xs[gg][2][qi], a3 = xs[gg][3][qi];
-        ff2_add_acc(qh0, ql0, lo2(a0), lo2(a1));
-        ff2_add_acc(qh1, ql1, hi2(a0), hi2(a1));
-        ff2_add_acc(uh0, ul0, lo2(a2), lo2(a3));
-        ff2_add_acc(uh1, ul1, hi2(a2), hi2(a3));
+        for (int gg = 0; gg < UKG; ++gg) {
+          xq = ff_add(xq, ff{pick(xs[gg][0][eq]), pick(xs[gg][1][eq])});
+          xu = ff_add(xu, ff{pick(xs[gg][2][eq]), pick(xs[gg][3][eq])});
+        }
+        const ff ir{sc[1].x, sc[1].y};
+        xq = ff_mul(xq, ir);
+        xu = ff_mul(xu, ir);
+        dot2_acc(make_float2(xu.h, 0.f), make_float2(xu.l, 0.f), make_float2(xu.h, 0.f), make_float2(xu.l, 0.f), S, C);
+        const size_t i = 4 * ge + el;
+        Uh[j * ld + i] = xq.h;
+        Ul[j * ld + i] = xq.l;
+        Uh[(j + 1) * ld + i] = xu.h;
+        Ul[(j + 1) * ld + i] = xu.l;
       }
-      ff2_norm(qh0, ql0);
-      ff2_norm(qh1, ql1);
-      ff2_norm(uh0, ul0);
-      ff2_norm(uh1, ul1);
-      ff2_scale(qh0, ql0, ir_h, ir_l);
-      ff2_scale(qh1, ql1, ir_h, ir_l);
-      ff2_scale(uh0, ul0, ir_h, ir_l);
-      ff2_scale(uh1, ul1, ir_h, ir_l);
-      dot2_acc(uh0, ul0, uh0, ul0, S, C);
-      dot2_acc(uh1, ul1, uh1, ul1, S, C);
-      *reinterpret_cast<float4*>(Uh + j * ld + o) = make_float4(qh0.x, qh0.y, qh1.x, qh1.y);
-      *reinterpret_cast<float4*>(Ul + j * ld + o) = make_float4(ql0.x, ql0.y, ql1.x, ql1.y);
-      *reinterpret_cast<float4*>(Uh + (j + 1) * ld + o) = make_float4(uh0.x, uh0.y, uh1.x, uh1.y);
-      *reinterpret_cast<float4*>(Ul + (j + 1) * ld + o) = make_float4(ul0.x, ul0.y, ul1.x, ul1.y);
     }
     __syncthreads();  // xs is reused by the next tile
   }
@@ -1004,6 +1004,7 @@ cudaError_t launch_dots(bool use_ff, KState* ks, void* part, Basis U, int j, siz
   if (gx < 1) gx = 1;
   dim3 grid(gx, chunks);
   const size_t smem = (size_t)(2 * (j + 1) + 1) * gx * 8;
+  const dim3 grid1((unsigned)(gx * chunks));  // float-float kernel: chunk-fastest 1D grid
   // thread-safe one-time set-up (function-local static initialisation)
   static const cudaError_t configured = [] {
     cudaError_t e = cudaFuncSetAttribute(k_dots_ff, cudaFuncAttributeMaxDynamicSharedMemorySize, 128 * 1024);
@@ -1012,7 +1013,7 @@ cudaError_t launch_dots(bool use_ff, KState* ks, void* part, Basis U, int j, siz
     return e;
   }();
   if (configured != cudaSuccess) return configured;
-  if (use_ff) return pdl_launch(k_dots_ff, grid, dim3(NT), smem, s, ks, static_cast<ff*>(part), U, j, n_aug);
+  if (use_ff) return pdl_launch(k_dots_ff, grid1, dim3(NT), smem, s, ks, static_cast<ff*>(part), U, j, n_aug);
   return pdl_launch(k_dots<false>, grid, dim3(NT), smem, s, ks, static_cast<double*>(part), U, j, n_aug);
 }
 

@@ -54,6 +54,12 @@ class expdg_server_config(ctypes.Structure):
     _fields_ = [("hbm_budget", ctypes.c_size_t), ("workers", ctypes.c_int)]
 
 
+class expdg_rates(ctypes.Structure):
+    _fields_ = [("fp64_fma_per_s", ctypes.c_double), ("fp32_fma_per_s", ctypes.c_double),
+                ("fp32x2_fma_per_s", ctypes.c_double), ("f64_to_f32_per_s", ctypes.c_double),
+                ("sms", ctypes.c_int), ("clock_mhz", ctypes.c_double)]
+
+
 class ExpdgError(RuntimeError):
     def __init__(self, status, msg):
         super().__init__(f"{STATUS_NAMES.get(status, status)}: {msg}")
@@ -90,6 +96,7 @@ def _load():
         "expdg_profile_get": (ctypes.c_int, [P, P, ctypes.c_int]),
         "expdg_residual_noalloc": (ctypes.c_int, [vp(expdg_config), P, P, P]),
         "expdg_config_node_coords": (ctypes.c_int, [vp(expdg_config), P]),
+        "expdg_probe_rates": (ctypes.c_int, [vp(expdg_rates)]),
         "expdg_context_bytes": (ctypes.c_size_t, [vp(expdg_config)]),
         "expdg_server_create": (ctypes.c_int, [vp(expdg_server_config), vp(P)]),
         "expdg_server_destroy": (None, [P]),
@@ -153,6 +160,15 @@ def config_node_coords(cfg):
     if st != EXPDG_OK:
         raise ExpdgError(st, "expdg_config_node_coords failed")
     return out
+
+
+def probe_rates():
+    """Measured FP64 / FP32 / packed-FP32 FMA and f64->f32 conversion rates (per second)."""
+    r = expdg_rates()
+    st = _lib.expdg_probe_rates(ctypes.byref(r))
+    if st != EXPDG_OK:
+        raise ExpdgError(st, "expdg_probe_rates failed")
+    return {k: getattr(r, k) for k, _ in r._fields_}
 
 
 def context_bytes(cfg):
