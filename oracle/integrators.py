@@ -40,10 +40,11 @@ class StepStats:
     traces: list = field(default_factory=list)   # one (sigma, m, eta) list per Krylov solve
 
 
-def step(mesh, q, dt, scheme=EPI2, tol=1e-10, m_max=64, m_step=5, max_substeps=64, replay=None):
+def step(mesh, q, dt, scheme=EPI2, tol=1e-10, m_max=64, m_step=5, max_substeps=64, replay=None, iop=None):
     """One exponential step from q^n; returns (q^{n+1}, StepStats).
     ``replay`` is an optional list (one entry per Krylov solve of the step)
-    of (sigma, m, eta) traces to follow."""
+    of (sigma, m, eta) traces to follow; ``iop`` the incomplete
+    orthogonalisation window of the Krylov solves (None: full Arnoldi)."""
     q = np.asarray(q, dtype=np.float64).reshape(-1)
     st = StepStats()
     Rn = dg.residual(mesh, q).reshape(-1)
@@ -60,7 +61,7 @@ def step(mesh, q, dt, scheme=EPI2, tol=1e-10, m_max=64, m_step=5, max_substeps=6
         rp = None if replay is None else replay[solve_id[0]]
         solve_id[0] += 1
         w, ks = phi_sum(A, c, tol=tol, m_max=m_max, m_step=m_step,
-                        max_substeps=max_substeps, replay=rp)
+                        max_substeps=max_substeps, replay=rp, iop=iop)
         st.krylov_iters += ks.iterations
         st.substeps += ks.substeps
         st.rejected += ks.rejected

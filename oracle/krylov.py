@@ -18,6 +18,12 @@ reading (shared, decision for decision, with the GPU path):
 
 * Arnoldi with modified Gram-Schmidt on A_hat, Euclidean inner product over
   all N + P entries, start vector b = [c_0; e_P/eta], beta = ||b||.
+* Or, with a window iop >= 1, the incomplete orthogonalisation procedure that
+  KIOPS puts in place of Arnoldi (Sec. 1): step j orthogonalises A_hat v_j
+  (modified Gram-Schmidt) against v_{j-iop+1}, ..., v_j only, so H_m is
+  banded upper Hessenberg and V_m is orthonormal only within each window.
+  The projected approximation and the error estimate below are used
+  unchanged.  iop >= m_max is full Arnoldi.
 * Projected approximation exp(A_hat) b ~ beta V_m exp(H_m) e_1, checked at
   m = m_step, 2 m_step, ..., m_max with Saad's estimate
   err = beta h_{m+1,m} |e_m^T exp(H_m) e_1|; accepted when err <= tol beta.
@@ -69,10 +75,11 @@ def tail_scale(vecs):
     return 2.0 ** (-round(math.log2(nrm)))
 
 
-def _arnoldi_expm(apply_A, b, sigma, eta, m_max, m_step, tol, fixed_m=None):
+def _arnoldi_expm(apply_A, b, sigma, eta, m_max, m_step, tol, fixed_m=None, iop=None):
     """One Krylov attempt for exp(A_hat) [b_0; e_P/eta] with A_hat built on
     sigma*A and W = [b_P, ..., b_1] (b = [b_0, b_1, ..., b_P], b_i already
-    carrying sigma^i).  Returns (accepted, m, top, err, iterations)."""
+    carrying sigma^i); iop: orthogonalisation window (None: full Arnoldi).
+    Returns (accepted, m, top, err, iterations)."""
     P = len(b) - 1
     N = b[0].shape[0]
     n_aug = N + P
@@ -99,7 +106,8 @@ def _arnoldi_expm(apply_A, b, sigma, eta, m_max, m_step, tol, fixed_m=None):
             w[N:N + P - 1] = y[1:]
         iters += 1
         wnorm0 = float(np.linalg.norm(w))
-        for i in range(j + 1):               # modified Gram-Schmidt
+        lo = 0 if iop is None else max(0, j - iop + 1)
+        for i in range(lo, j + 1):           # modified Gram-Schmidt
             H[i, j] = float(np.dot(V[i], w))
             w = w - H[i, j] * V[i]
         H[j + 1, j] = float(np.linalg.norm(w))
@@ -127,13 +135,16 @@ def _arnoldi_expm(apply_A, b, sigma, eta, m_max, m_step, tol, fixed_m=None):
     return False, m_max, None, float("inf"), iters
 
 
-def phi_sum(apply_A, c, tol=1e-10, m_max=64, m_step=5, max_substeps=64, replay=None):
+def phi_sum(apply_A, c, tol=1e-10, m_max=64, m_step=5, max_substeps=64, replay=None, iop=None):
     """w = sum_{i=0}^{P} phi_i(A) c_i by the augmented Krylov method above.
 
     apply_A : x -> A x (FP64 vectors of length N)
     c       : [c_0, ..., c_P]; c_0 may be all zeros
     replay  : optional list of (sigma, m, eta) to follow instead of deciding
+    iop     : incomplete-orthogonalisation window (None or 0: full Arnoldi)
     Returns (w, KrylovStats)."""
+    if iop is not None and iop <= 0:
+        iop = None
     c = [np.asarray(ci, dtype=np.float64) for ci in c]
     P = len(c) - 1
     stats = KrylovStats()
@@ -152,10 +163,10 @@ def phi_sum(apply_A, c, tol=1e-10, m_max=64, m_step=5, max_substeps=64, replay=N
         b = [chat[0]] + [(sigma ** i) * chat[i] for i in range(1, P + 1)]
         if replay is None:
             eta = tail_scale(b[1:])
-            ok, m, top, err, iters = _arnoldi_expm(apply_A, b, sigma, eta, m_max, m_step, tol)
+            ok, m, top, err, iters = _arnoldi_expm(apply_A, b, sigma, eta, m_max, m_step, tol, iop=iop)
         else:
             ok, m, top, err, iters = _arnoldi_expm(apply_A, b, sigma, eta, m_max, m_step, tol,
-                                                   fixed_m=m_fix)
+                                                   fixed_m=m_fix, iop=iop)
         stats.iterations += iters
         if not ok:
             stats.rejected += 1

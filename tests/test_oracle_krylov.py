@@ -166,3 +166,83 @@ def test_linear_advection_exponential_full_size(c, p, ne, dt):
     ref = _bloch_exp_advection(c, p, ne, length, dt, v)
     w, st = krylov.phi_sum(lambda y: dt * dg.jv(mesh, ut, y).reshape(-1), [v], tol=1e-12, m_max=64)
     assert np.max(np.abs(w - ref)) <= 1e-9 * np.max(np.abs(ref))
+
+
+# ---- incomplete orthogonalisation (KIOPS's replacement for Arnoldi, Sec. 1) ----
+
+def _recorded_basis(A, c0, iop, m):
+    """Vectors v_0..v_{m-1} the solver feeds to the operator (P = 0, so they
+    are the whole basis vectors), with a fixed m and no acceptance test."""
+    seen = []
+
+    def apply(x):
+        seen.append(np.array(x))
+        return A @ x
+    krylov.phi_sum(apply, [c0], replay=[(1.0, m, 1.0)], iop=iop)
+    return np.array(seen)
+
+
+@pytest.mark.parametrize("iop", [1, 2, 3, 5])
+def test_iom_orthogonality_pattern(iop):
+    """v_{j+1} is orthogonalised against v_{j-iop+1..j}: each basis vector is
+    orthogonal to exactly the iop vectors before it.  Inner products inside
+    that window vanish to rounding, those outside it do not (non-symmetric
+    operator)."""
+    rng = np.random.default_rng(50)
+    n, m = 80, 14
+    A = rng.standard_normal((n, n)) / math.sqrt(n) - 0.3 * np.eye(n)
+    V = _recorded_basis(A, rng.standard_normal(n), iop, m)
+    G = V @ V.T
+    np.testing.assert_allclose(np.diag(G), 1.0, rtol=1e-13)
+    for j in range(m):
+        for i in range(max(0, j - iop), j):
+            assert abs(G[i, j]) < 1e-12
+        if j - iop - 1 >= 0:
+            assert abs(G[j - iop - 1, j]) > 1e-6
+
+
+def test_iom_window_covering_m_is_full_arnoldi():
+    rng = np.random.default_rng(51)
+    n = 50
+    A = rng.standard_normal((n, n)) / math.sqrt(n) - np.eye(n)
+    c = [rng.standard_normal(n), rng.standard_normal(n)]
+    w0, s0 = krylov.phi_sum(lambda x: A @ x, c, tol=1e-12, m_max=40)
+    w1, s1 = krylov.phi_sum(lambda x: A @ x, c, tol=1e-12, m_max=40, iop=40)
+    np.testing.assert_array_equal(w0, w1)
+    assert s0.trace == s1.trace
+
+
+def test_iom_symmetric_operator_is_lanczos():
+    """Symmetric A (P = 0): Arnoldi reduces to the three-term Lanczos
+    recurrence, so a window of 2 spans the same space with the same H as
+    full orthogonalisation; the phi-sums agree to rounding and with the
+    dense exponential."""
+    rng = np.random.default_rng(52)
+    n = 120
+    Q, _ = np.linalg.qr(rng.standard_normal((n, n)))
+    A = (Q * rng.uniform(-8.0, 0.0, n)) @ Q.T
+    A = 0.5 * (A + A.T)
+    c0 = rng.standard_normal(n)
+    ref = scipy.linalg.expm(A) @ c0
+    wf, _ = krylov.phi_sum(lambda x: A @ x, [c0], tol=1e-13, m_max=40, m_step=5)
+    wl, _ = krylov.phi_sum(lambda x: A @ x, [c0], tol=1e-13, m_max=40, m_step=5, iop=2)
+    assert np.max(np.abs(wl - ref)) <= 1e-11 * np.max(np.abs(ref))
+    assert np.max(np.abs(wl - wf)) <= 1e-11 * np.max(np.abs(ref))
+
+
+@pytest.mark.parametrize("iop", [2, 4])
+@pytest.mark.parametrize("P", [1, 3])
+def test_iom_tiny_mesh_dense_expm(iop, P):
+    """With incomplete orthogonalisation the accepted result still meets the
+    tolerance against the dense augmented exponential (Euler, 2x2, p = 2)."""
+    from tests.test_oracle_dg import make_mesh, random_state
+    rng = np.random.default_rng(53 + P)
+    mesh = make_mesh("euler", 2, 2, (2, 2))
+    qt = random_state(mesh, rng).reshape(-1)
+    A = 0.05 * _assembled(mesh, qt)
+    c = [np.zeros(qt.size)] + [rng.standard_normal(qt.size) for _ in range(P)]
+    ref = _augmented_dense(A, c)
+    tol = 1e-10
+    w, st = krylov.phi_sum(lambda x: A @ x, c, tol=tol, m_max=64, iop=iop)
+    assert st.substeps >= 1
+    assert np.max(np.abs(w - ref)) <= 10 * tol * np.linalg.norm(ref)
