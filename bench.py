@@ -4,15 +4,17 @@
 Workload (N = 1): 2D compressible Euler (gamma = 1.4) isentropic vortex
 (strength 5, decay 1, free stream (1, 1), centre (5, 5)) on the periodic
 [0,10]^2, 64 x 64 quadrilaterals, p = 4 LGL (409,600 unknowns), Lax-Friedrichs
-flux, EPI2 steps of dt = 0.05 with Krylov tolerance 1e-8 (the tolerance the
-survey gives for the FP32-Jv configurations).  One step = one
-residual, one adaptive augmented-Krylov phi_1 solve (Jv applies, Gram-Schmidt,
-phi(H) checks) and the state update.
+flux, EPI2 steps of dt = 0.05 with Krylov tolerance 1e-8.  One step = one
+residual, one adaptive augmented-Krylov phi_1 solve (Jv applies,
+orthogonalisation, phi(H) checks) and the state update.
 
 `value` times the mixed form (FP32 R/Jv, float-float Krylov basis and
-orthogonalisation, FP64 phi(H) and FP64 state update), the production form;
-its relative L2 error against the FP64 form after one step from the same state
-is reported as `err_vs_fp64`.  The FP64 form is timed too (`fp64_form`).
+orthogonalisation, FP64 phi(H) and FP64 state update) with incomplete
+orthogonalisation over the last 4 basis vectors (the procedure of KIOPS, the
+Krylov solver of the paper, Sec. 1 and 2.3), the production form; its relative
+L2 error against the FP64 form with full orthogonalisation after one step from
+the same state is reported as `err_vs_fp64`.  That FP64 form is timed too
+(`fp64_form`).
 L2 is flushed (a 512 MiB write) between timed steps, outside the timed region.
 
 `python bench.py --gpus N --steps K --warmup W [--impl reference]`; for N > 1
@@ -45,7 +47,7 @@ UNIT = "DOF-steps/s"
 WORKLOAD = ("2D Euler isentropic vortex, periodic [0,10]^2, 64x64 quads, p=4 LGL, 409,600 unknowns, "
             "LF flux, EPI2, dt=0.05, Krylov tol 1e-8")
 CFG = dict(dim=2, p=4, ne=[64, 64, 1], lo=[0.0, 0.0, 0.0], hi=[10.0, 10.0, 1.0], eq=2, gamma=1.4,
-           scheme=2, krylov_tol=1e-8, m_max=64, m_step=5, max_substeps=32)
+           scheme=2, krylov_tol=1e-8, m_max=64, m_step=5, max_substeps=32, iop=4)
 DT = 0.05
 CLASSES = ["residual", "jv", "dots", "update", "phi", "combine", "vector"]
 
@@ -77,7 +79,10 @@ def peaks():
 
 
 class ClockSampler:
-    """nvidia-smi clock / throttle sampling during the timed region."""
+    """nvidia-smi clock / throttle sampling (every 200 ms) around the timed
+    region.  __enter__ returns once the first sample has arrived, so sampling
+    is running when the region starts; `extend` keeps the same work running
+    after the region until enough samples have been taken."""
 
     Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
          "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
@@ -86,27 +91,48 @@ class ClockSampler:
     def __init__(self, index):
         self.index = index
         self.proc = None
+        self.rows = []
+        self.thread = None
+
+    def _read(self):
+        for line in self.proc.stdout:
+            if line.count(",") >= 8:
+                self.rows.append(line.strip().split(","))
 
     def __enter__(self):
+        import threading
         try:
             self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.index), f"--query-gpu={self.Q}",
                                           "--format=csv,noheader,nounits", "-lms", "200"],
                                          stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
         except Exception:
             self.proc = None
+            return self
+        self.thread = threading.Thread(target=self._read, daemon=True)
+        self.thread.start()
+        t0 = time.time()
+        while not self.rows and time.time() - t0 < 10.0 and self.proc.poll() is None:
+            time.sleep(0.01)
         return self
 
+    def extend(self, work, min_samples=6, max_s=3.0):
+        """Run work() (the timed step, untimed) until min_samples samples exist."""
+        t0 = time.time()
+        while self.proc is not None and len(self.rows) < min_samples and time.time() - t0 < max_s:
+            work()
+
     def __exit__(self, *a):
-        self.out = ""
         if self.proc is not None:
             self.proc.terminate()
             try:
-                self.out, _ = self.proc.communicate(timeout=5)
+                self.proc.wait(timeout=5)
             except Exception:
                 self.proc.kill()
+            if self.thread is not None:
+                self.thread.join(timeout=5)
 
     def summary(self):
-        rows = [r.split(",") for r in (self.out or "").strip().splitlines() if r.count(",") >= 8]
+        rows = list(self.rows)
         if not rows:
             return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unsampled"]}
         sm = [float(r[1]) for r in rows if r[1].strip().replace(".", "").isdigit()]
@@ -114,7 +140,8 @@ class ClockSampler:
         names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
         reasons = sorted({names[k] for r in rows for k in range(4) if r[5 + k].strip() == "Active"})
         return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(smax) if smax else None,
-                "reasons": reasons, "samples": len(rows)}
+                "reasons": reasons, "samples": len(rows),
+                "window": "timed region, then the same steps untimed until 6 samples"}
 
 
 def oracle_step_rate(steps=1):
@@ -125,12 +152,13 @@ def oracle_step_rate(steps=1):
     q = inputs.isentropic_vortex(dg.node_coords(mesh), 0.0).reshape(-1)
     t0 = time.perf_counter()
     for _ in range(steps):
-        q, _ = integrators.step(mesh, q, DT, tol=CFG["krylov_tol"], m_max=CFG["m_max"], m_step=CFG["m_step"])
+        q, _ = integrators.step(mesh, q, DT, tol=CFG["krylov_tol"], m_max=CFG["m_max"], m_step=CFG["m_step"],
+                                iop=CFG["iop"] or None)
     dt = time.perf_counter() - t0
     return mesh.n_unknowns * steps / dt, dt
 
 
-def wave3d_workload(steps=2, hbm=6788.6, ne=32):
+def wave3d_workload(steps=2, hbm=6788.6, ne=32, iop=0):
     """3D Euler density wave rho = 1 + 0.2 sin(x+y+z), u = (1,1,1), pressure 1 on
     the periodic [0, 2 pi]^3, ne^3 hexahedra, p = 3 (10,485,760 unknowns at
     ne = 32), EPI2 dt = 0.1, Krylov tol 1e-8, mixed form: vectors of 84 MB (far
@@ -140,7 +168,7 @@ def wave3d_workload(steps=2, hbm=6788.6, ne=32):
     import torch
     from paper_2011_01316_gb300 import expdg, inputs
     cfg = dict(dim=3, p=3, ne=[ne, ne, ne], lo=[0.0] * 3, hi=[2 * math.pi] * 3, eq=2, gamma=1.4, scheme=2,
-               krylov_tol=1e-8, m_max=64, m_step=5, max_substeps=32)
+               krylov_tol=1e-8, m_max=64, m_step=5, max_substeps=32, iop=iop)
     ctx = expdg.Context(**cfg, prec=expdg.EXPDG_MIXED)
     stream = torch.cuda.current_stream()
     ctx.set_stream(stream)
@@ -185,7 +213,7 @@ def serving_workload(n, seed=1, rate=200.0, workers=8):
     reqs_m, reqs_d = [], []
     for _ in range(n):
         state = rng.bit_generator.state
-        reqs_m.append(serve.vortex_request(rng, 1))
+        reqs_m.append(serve.vortex_request(rng, 1, iop=CFG["iop"]))
         rng.bit_generator.state = state
         reqs_d.append(serve.vortex_request(rng, 0))
     # warm the kernels of every order once (outside the measured streams)
@@ -231,7 +259,7 @@ def batched_workload(n, seed=0, workers=16, steps=20):
         if i % 2 == 0:
             ne = int(round(math.exp(rng.uniform(math.log(16), math.log(4096)))))
             cfg = expdg.default_config(dim=1, p=p, ne=[ne, 1, 1], lo=[0, 0, 0], hi=[2 * math.pi, 1, 1],
-                                       eq=expdg.EXPDG_BURGERS, prec=1, krylov_tol=1e-8)
+                                       eq=expdg.EXPDG_BURGERS, prec=1, krylov_tol=1e-8, iop=CFG["iop"])
             X = expdg.config_node_coords(cfg)
             u0, (amp, _) = inputs.fourier_modes(X[0], rng)
             u0 = u0[None]
@@ -244,7 +272,7 @@ def batched_workload(n, seed=0, workers=16, steps=20):
         else:
             side = int(rng.integers(8, 97))
             cfg = expdg.default_config(dim=2, p=p, ne=[side, side, 1], lo=[0, 0, 0], hi=[2 * math.pi] * 2 + [1],
-                                       eq=expdg.EXPDG_EULER, prec=1, krylov_tol=1e-8)
+                                       eq=expdg.EXPDG_EULER, prec=1, krylov_tol=1e-8, iop=CFG["iop"])
             X = expdg.config_node_coords(cfg)
             rho, (amp, _) = inputs.fourier_modes(X[0] + X[1], rng)
             if amp.sum() > 0.8:  # keep rho >= 0.2: 1 - sum a_k must stay positive
@@ -303,6 +331,8 @@ def main():
                     help="comma list of legs to run (main = the timed workload; profiling runs pick one)")
     ap.add_argument("--wave3d-ne", type=int, default=32, help="elements per direction of the 3D leg")
     ap.add_argument("--wave3d-steps", type=int, default=2)
+    ap.add_argument("--iop", type=int, default=CFG["iop"],
+                    help="Krylov orthogonalisation window (0: full Arnoldi; k: incomplete, last k vectors)")
     args = ap.parse_args()
 
     world = int(os.environ.get("WORLD_SIZE", "1"))
@@ -314,6 +344,7 @@ def main():
 
     if args.tol is not None:
         CFG["krylov_tol"] = args.tol
+    CFG["iop"] = args.iop
     import torch
     import torch.distributed as dist
     if world > 1:
@@ -330,7 +361,7 @@ def main():
         hbm, _ = peaks()
         out = {}
         if "wave3d" in args.legs:
-            out["wave3d"] = wave3d_workload(steps=args.wave3d_steps, hbm=hbm, ne=args.wave3d_ne)
+            out["wave3d"] = wave3d_workload(steps=args.wave3d_steps, hbm=hbm, ne=args.wave3d_ne, iop=args.iop)
         if "serving" in args.legs:
             out["serving"] = serving_workload(args.serve_requests)
         if "batched" in args.legs:
@@ -341,7 +372,8 @@ def main():
     stream = torch.cuda.current_stream()
     ctx = expdg.Context(**CFG, prec=expdg.EXPDG_MIXED)
     ctx.set_stream(stream)
-    ctx64 = expdg.Context(**CFG, prec=expdg.EXPDG_FP64)
+    # reference form: FP64 with full orthogonalisation
+    ctx64 = expdg.Context(**{**CFG, "iop": 0}, prec=expdg.EXPDG_FP64)
     ctx64.set_stream(stream)
     q0 = torch.from_numpy(np.ascontiguousarray(inputs.isentropic_vortex(ctx.node_coords(), 0.0))).cuda()
     N = ctx.n
@@ -378,7 +410,9 @@ def main():
     with ClockSampler(local) as clk:
         per, iters = timed(ctx, q, args.steps)
         barrier()
-    launches = sum(v["launches"] for v in ctx.profile_get(reset=True).values())
+        launches = sum(v["launches"] for v in ctx.profile_get(reset=True).values())
+        qx = q0.clone()
+        clk.extend(lambda: (ctx.step(qx, DT), torch.cuda.synchronize()))
     t_local = sum(per) / 1e3
     t_max = max_over_ranks(t_local, world, "cuda")
     value = replica_value(N, args.steps, t_max, world)
@@ -423,7 +457,7 @@ def main():
     legs = set(args.legs.split(","))
     wave3d = None
     if "wave3d" in legs and not args.no_3d:
-        wave3d = wave3d_workload(steps=args.wave3d_steps, hbm=hbm, ne=args.wave3d_ne)
+        wave3d = wave3d_workload(steps=args.wave3d_steps, hbm=hbm, ne=args.wave3d_ne, iop=args.iop)
     serving = serving_workload(args.serve_requests) if args.serve_requests > 0 and "serving" in legs else None
     batched = batched_workload(args.batch_instances) if args.batch_instances > 0 and "batched" in legs else None
 
@@ -439,6 +473,8 @@ def main():
                 "scaling": "weak", "vs_baseline": None, "dtype": "f32+ff(48-bit)+f64",
                 "data": "synthetic",
                 "config": {"workload": WORKLOAD, "precision": "mixed: FP32 R/Jv, float-float Krylov, FP64 phi(H)",
+                           "krylov": (f"incomplete orthogonalisation, window {CFG['iop']} (KIOPS)" if CFG["iop"]
+                                      else "full Arnoldi (DCGS2)"),
                            "l2": "flushed between timed steps (512 MiB write)",
                            "parallelism": "replicas" if world > 1 else "single GPU"},
                 "err_vs_fp64": err_vs_fp64, "fp64_form": fp64, "e2e": e2e, "gpu_launches": launches,

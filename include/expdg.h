@@ -78,11 +78,16 @@ typedef struct {
   int m_max;            /* Krylov dimension limit, <= EXPDG_MAX_KRYLOV */
   int m_step;           /* error checks at m = m_step, 2 m_step, ... */
   int max_substeps;     /* limit on rejected (halved) Krylov attempts per solve */
+  int iop;              /* Krylov orthogonalisation: 0 = full (Arnoldi by two-pass classical
+                           Gram-Schmidt with delayed re-orthogonalisation); k = 1..EXPDG_MAX_IOP =
+                           incomplete orthogonalisation against the last k basis vectors, the
+                           procedure KIOPS uses in place of Arnoldi (Sec. 1, Sec. 2.3) */
 } expdg_config;
 
 #define EXPDG_MAX_ORDER 8
 #define EXPDG_MAX_KRYLOV 64
 #define EXPDG_MAX_PHI 3      /* phi_0 .. phi_3 */
+#define EXPDG_MAX_IOP 8      /* largest incomplete-orthogonalisation window */
 
 typedef struct {
   int krylov_iters;       /* Arnoldi iterations (operator applies), incl. rejected attempts */
@@ -106,7 +111,7 @@ typedef struct {
 typedef struct expdg_ctx expdg_ctx;
 
 /* Default configuration: 2D Euler, p = 4, 64 x 64 on [0,10]^2, EPI2, FP64,
- * tol 1e-10, m_max 64, m_step 5, max_substeps 32. */
+ * tol 1e-10, m_max 64, m_step 5, max_substeps 32, iop 0 (full orthogonalisation). */
 void expdg_default_config(expdg_config* cfg);
 
 /* Create a context (validates cfg, builds LGL tables, allocates the device
@@ -149,7 +154,10 @@ expdg_status expdg_jv(expdg_ctx* ctx, const double* qt, const double* v, double*
  * Method: Arnoldi (classical Gram-Schmidt, twice) on the augmented matrix
  *   A_hat = [[sigma tau L, eta W], [0, J]],  W = [b_P .. b_1],  J = upper shift,
  * started from [b_0; e_P / eta], beta = its norm; the top block of
- * beta V_m exp(H_m) e_1 approximates the sum.  The error estimate
+ * beta V_m exp(H_m) e_1 approximates the sum.  With cfg.iop = k > 0 the
+ * Arnoldi process is replaced by incomplete orthogonalisation: step j
+ * orthogonalises A_hat v_j against v_{j-k+1}, ..., v_j only (H_m banded);
+ * the approximation and the error estimate are unchanged.  The error estimate
  * err = beta h_{m+1,m} |e_m^T exp(H_m) e_1| is checked at m = m_step,
  * 2 m_step, ..., m_max; accepted when err <= krylov_tol * beta (or on a happy
  * breakdown).  In EXPDG_MIXED a check is also accepted when the approximation

@@ -31,6 +31,8 @@ struct expdg_ctx {
   // FP32 buffers (mixed form)
   float* d_q32 = nullptr;
   float* d_q32b = nullptr;
+  // linearisation state of the linear operator (compute form: float or double)
+  void* d_z = nullptr;
   // vectors in the Krylov storage form
   Vec c[EXPDG_MAX_PHI + 1]{};
   Vec b[EXPDG_MAX_PHI + 1]{};
@@ -179,12 +181,10 @@ cudaError_t residual_into(expdg_ctx* ctx, const double* q, float* q32, Vec out, 
 // in FP64 and stored as float-float: R of a smooth state is a small difference
 // of large fluxes, and its FP32 rounding (relative error 6e-5 on the 64^2
 // p = 4 vortex) puts broadband noise into the Krylov start vector that costs
-// about five extra Arnoldi steps; one FP64 residual per stage is cheaper.  The
-// FP32 copy of q for the Jv is made here as well.
-cudaError_t residual_for_step(expdg_ctx* ctx, const double* q, float* q32, Vec out, double alpha) {
-  if (!ctx->ff) return residual_into(ctx, q, q32, out, alpha);
-  cudaError_t e = run(ctx, EXPDG_K_VECTOR, 12.0 * ctx->N, [&]() { return launch_to_f32(q32, q, ctx->N, ctx->stream); });
-  if (e != cudaSuccess) return e;
+// about five extra Arnoldi steps; one FP64 residual per stage is cheaper.
+cudaError_t residual_for_step(expdg_ctx* ctx, const double* q, Vec out, double alpha) {
+  if (!ctx->ff) return residual_into(ctx, q, nullptr, out, alpha);
+  cudaError_t e;
   DGArgs a = ctx->mesh;
   set_alpha(a, alpha);
   a.status = &ctx->ks->status;
@@ -195,8 +195,22 @@ cudaError_t residual_for_step(expdg_ctx* ctx, const double* q, float* q32, Vec o
   return run(ctx, EXPDG_K_VECTOR, 16.0 * ctx->N, [&]() { return launch_f64_to_ff(out, ctx->d_t2, ctx->N, ctx->stream); });
 }
 
-// L(qt) v -> out (no augmentation).  qt_T: linearisation state in compute form
-// (double* or float*), v_T: input in compute form.
+// Linearisation state of qt (FP64, device) -> ctx->d_z, in compute form.
+cudaError_t linstate_into(expdg_ctx* ctx, const double* qt) {
+  const double bytes = (8.0 + (ctx->ff ? 4.0 : 8.0)) * ctx->N;
+  return run(ctx, EXPDG_K_VECTOR, bytes, [&]() {
+    const size_t stride = ctx->mesh.stride;
+    switch (ctx->cfg.dim) {
+      case 1: return launch_linstate_1d(ctx->cfg.eq, ctx->ff, qt, ctx->d_z, stride, ctx->cfg.gamma, ctx->stream);
+      case 2: return launch_linstate_2d(ctx->cfg.eq, ctx->ff, qt, ctx->d_z, stride, ctx->cfg.gamma, ctx->stream);
+      case 3: return launch_linstate_3d(ctx->cfg.eq, ctx->ff, qt, ctx->d_z, stride, ctx->cfg.gamma, ctx->stream);
+    }
+    return cudaErrorInvalidValue;
+  });
+}
+
+// L(qt) v -> out (no augmentation).  qt_T: linearisation state of qt in compute
+// form (ctx->d_z, from linstate_into), v_T: input in compute form.
 cudaError_t jv_into(expdg_ctx* ctx, const void* qt_T, const void* v_T, Vec out, double alpha) {
   DGArgs a = ctx->mesh;
   set_alpha(a, alpha);
@@ -310,7 +324,9 @@ expdg_status phi_solve(expdg_ctx* ctx, const void* qt_T, double tau, const bool*
       if (trace) trace->push_back(expdg_trace_entry{solve_id, 0, sigma, eta});
       continue;
     }
-    RUN(ctx, EXPDG_K_VECTOR, 16.0 * N, launch_start(F, ctx->ks, ctx->U, ctx->w, N, P, eta, s));
+    const int iop = cfg.iop;
+    const double s0 = iop ? 1.0 / beta : 1.0;  // incomplete orthogonalisation: slot 0 holds beta v_0
+    RUN(ctx, EXPDG_K_VECTOR, 16.0 * N, launch_start(F, ctx->ks, ctx->U, ctx->w, N, P, eta, s0, s));
     const int limit = replay ? m_fix : cfg.m_max;
     int m_first = cfg.m_step;
     const bool first_sub = (sv == 0.0 && rejected == 0);
@@ -332,6 +348,11 @@ expdg_status phi_solve(expdg_ctx* ctx, const void* qt_T, double tau, const bool*
         a.v = vj.d;
         a.out = vo.d;
       }
+      if (iop) {  // slot j holds v_j / vscale_j
+        a.vs_d = &ctx->ks->vscale[j];
+        a.vs_h = &ctx->ks->vs_h[j];
+        a.vs_l = &ctx->ks->vs_l[j];
+      }
       if (P > 0) {
         a.paug = P;
         a.eta = eta;
@@ -352,8 +373,15 @@ expdg_status phi_solve(expdg_ctx* ctx, const void* qt_T, double tau, const bool*
       }
       RUN(ctx, EXPDG_K_JV, (F ? 16.0 : 24.0) * N, launch_dg(ctx, true, a));
       const double vb = 8.0 * (double)n_aug;  // one vector: FP64 or float-float pair
-      RUN(ctx, EXPDG_K_DOTS, (j + 2) * vb, launch_dots(F, ctx->ks, ctx->part, ctx->U, j, n_aug, s));
-      RUN(ctx, EXPDG_K_UPDATE, (j + 4) * vb, launch_update(F, ctx->ks, ctx->part, ctx->U, j, n_aug, s));
+      if (iop) {
+        const int nwin = std::min(iop, j + 1);
+        RUN(ctx, EXPDG_K_DOTS, (nwin + 1) * vb, launch_iom_dots(F, iop, ctx->ks, ctx->part, ctx->U, j, n_aug, s));
+        RUN(ctx, EXPDG_K_UPDATE, (nwin + 2) * vb,
+            launch_iom_update(F, iop, ctx->ks, ctx->part, ctx->U, j, n_aug, s));
+      } else {
+        RUN(ctx, EXPDG_K_DOTS, (j + 2) * vb, launch_dots(F, ctx->ks, ctx->part, ctx->U, j, n_aug, s));
+        RUN(ctx, EXPDG_K_UPDATE, (j + 4) * vb, launch_update(F, ctx->ks, ctx->part, ctx->U, j, n_aug, s));
+      }
       const int J = j + 1;
       st->krylov_iters++;
       st->jv_applies++;
@@ -414,6 +442,7 @@ expdg_status validate(const expdg_config* c) {
   if (c->m_max < 1 || c->m_max > EXPDG_MAX_KRYLOV) return EXPDG_EINVAL;
   if (c->m_step < 1) return EXPDG_EINVAL;
   if (c->max_substeps < 0) return EXPDG_EINVAL;
+  if (c->iop < 0 || c->iop > EXPDG_MAX_IOP) return EXPDG_EINVAL;
   return EXPDG_OK;
 }
 
@@ -433,18 +462,19 @@ expdg_status step_dev(expdg_ctx* ctx, double* q, double dt, const Replay& rp, ex
   const size_t N = ctx->N;
   const cudaStream_t s = ctx->stream;
   CU(ctx, cudaMemsetAsync(&ctx->ks->status, 0, sizeof(int), s));
-  // Linearisation state in compute form (the residual below fills q32 from q).
-  const void* qt_T = F ? static_cast<const void*>(ctx->d_q32) : static_cast<const void*>(q);
+  // Linearisation state of the Jacobian point q, shared by every stage.
+  CU(ctx, linstate_into(ctx, q));
+  const void* qt_T = ctx->d_z;
   bool has[EXPDG_MAX_PHI + 1] = {false, false, false, false};
   const int scheme = ctx->cfg.scheme;
   if (scheme == EXPDG_EPI2) {
-    CU(ctx, residual_for_step(ctx, q, ctx->d_q32, ctx->c[1], dt));
+    CU(ctx, residual_for_step(ctx, q, ctx->c[1], dt));
     st->residual_applies++;
     has[1] = true;
     return phi_solve(ctx, qt_T, dt, has, 1, dvec(q), dvec(q), 0, rp, st, trace, true);
   }
   // EXPRB32 / EXPRB42 share: R^n, stage 1, D_{n,2} = R(q2) - R^n - L (q2 - q)
-  CU(ctx, residual_for_step(ctx, q, ctx->d_q32, ctx->rn, 1.0));
+  CU(ctx, residual_for_step(ctx, q, ctx->rn, 1.0));
   st->residual_applies++;
   const double a1 = (scheme == EXPDG_EXPRB32) ? dt : 0.75 * dt;
   {
@@ -456,7 +486,7 @@ expdg_status step_dev(expdg_ctx* ctx, double* q, double dt, const Replay& rp, ex
   expdg_status r = phi_solve(ctx, qt_T, a1, has, 1, dvec(q), dvec(ctx->d_q2), 0, rp, st, trace, true);
   if (r != EXPDG_OK) return r;
   // t1 = R(q2)
-  CU(ctx, residual_for_step(ctx, ctx->d_q2, ctx->d_q32b, ctx->t1, 1.0));
+  CU(ctx, residual_for_step(ctx, ctx->d_q2, ctx->t1, 1.0));
   st->residual_applies++;
   // t2 = q2 - q (FP64), t3 = L(q) t2
   {
@@ -466,9 +496,9 @@ expdg_status step_dev(expdg_ctx* ctx, double* q, double dt, const Replay& rp, ex
   }
   if (F) {
     RUN(ctx, EXPDG_K_VECTOR, 12.0 * N, launch_to_f32(ctx->d_q32b, ctx->d_t2, N, s));
-    CU(ctx, jv_into(ctx, ctx->d_q32, ctx->d_q32b, ctx->t3, 1.0));
+    CU(ctx, jv_into(ctx, qt_T, ctx->d_q32b, ctx->t3, 1.0));
   } else {
-    CU(ctx, jv_into(ctx, q, ctx->d_t2, ctx->t3, 1.0));
+    CU(ctx, jv_into(ctx, qt_T, ctx->d_t2, ctx->t3, 1.0));
   }
   st->jv_applies++;
   const double cD = (scheme == EXPDG_EXPRB32) ? 2.0 * dt : (32.0 / 9.0) * dt;
@@ -539,6 +569,7 @@ size_t expdg_context_bytes(const expdg_config* cfg) {
   auto r = [&](size_t b) { return ((b + gran - 1) / gran) * gran; };
   size_t total = 5 * r(N * sizeof(double));                 // q, q2, t2, in, out
   if (ff) total += 2 * r(N * sizeof(float));                // FP32 state copies
+  total += r(N * (ff ? sizeof(float) : sizeof(double)));     // linearisation state
   const size_t nvec = 2 * (EXPDG_MAX_PHI + 1) + 4;          // c, b, w, rn, t1, t3
   total += nvec * (ff ? 2 * r(N * sizeof(float)) : r(N * sizeof(double)));
   const size_t nb = ld * (size_t)(cfg->m_max + 1);
@@ -607,6 +638,13 @@ expdg_status expdg_create(const expdg_config* cfg, expdg_ctx** out) {
   if (ctx->ff) {
     ALLOC(dalloc(ctx, &ctx->d_q32, N));
     ALLOC(dalloc(ctx, &ctx->d_q32b, N));
+    float* z = nullptr;
+    ALLOC(dalloc(ctx, &z, N));
+    ctx->d_z = z;
+  } else {
+    double* z = nullptr;
+    ALLOC(dalloc(ctx, &z, N));
+    ctx->d_z = z;
   }
   for (int i = 0; i <= EXPDG_MAX_PHI; ++i) {
     ALLOC(alloc_vec(ctx, &ctx->c[i], N));
@@ -731,13 +769,13 @@ expdg_status expdg_jv(expdg_ctx* ctx, const double* qt, const double* v, double*
   CU(ctx, e);
   const bool odev = is_device_ptr(out);
   double* od = odev ? out : ctx->d_out;
+  CU(ctx, linstate_into(ctx, qd));
   if (ctx->ff) {
-    RUN(ctx, EXPDG_K_VECTOR, 12.0 * ctx->N, launch_to_f32(ctx->d_q32, qd, ctx->N, ctx->stream));
     RUN(ctx, EXPDG_K_VECTOR, 12.0 * ctx->N, launch_to_f32(ctx->d_q32b, vd, ctx->N, ctx->stream));
-    CU(ctx, jv_into(ctx, ctx->d_q32, ctx->d_q32b, ctx->t1, 1.0));
+    CU(ctx, jv_into(ctx, ctx->d_z, ctx->d_q32b, ctx->t1, 1.0));
     RUN(ctx, EXPDG_K_VECTOR, 16.0 * ctx->N, launch_ff_to_f64(od, ctx->t1, ctx->N, ctx->stream));
   } else {
-    CU(ctx, jv_into(ctx, qd, vd, dvec(od), 1.0));
+    CU(ctx, jv_into(ctx, ctx->d_z, vd, dvec(od), 1.0));
   }
   if (!odev) CU(ctx, cudaMemcpyAsync(out, od, ctx->N * sizeof(double), cudaMemcpyDeviceToHost, ctx->stream));
   CU(ctx, cudaStreamSynchronize(ctx->stream));
@@ -765,11 +803,8 @@ expdg_status expdg_phi(expdg_ctx* ctx, const double* qt, double tau, const doubl
       CU(ctx, cudaMemcpyAsync(ctx->c[i].d, ci, N * sizeof(double), cudaMemcpyDeviceToDevice, s));
     }
   }
-  const void* qt_T = qd;
-  if (ctx->ff) {
-    RUN(ctx, EXPDG_K_VECTOR, 12.0 * N, launch_to_f32(ctx->d_q32, qd, N, s));
-    qt_T = ctx->d_q32;
-  }
+  CU(ctx, linstate_into(ctx, qd));
+  const void* qt_T = ctx->d_z;
   const bool odev = is_device_ptr(out);
   double* od = odev ? out : ctx->d_out;
   expdg_stats st{};

@@ -54,7 +54,7 @@ struct Tab {
 //     out      += eta * sum_{k=1}^{paug} (vs * tail[k-1]) * W[paug+1-k]
 //     out_tail  = J (vs * tail)   (upper shift; written by block 0)
 struct DGArgs {
-  const void* q;         // T*: residual state, or linearisation state
+  const void* q;         // T*: residual state q, or linearisation state z of qt
   const void* v;         // T*: linear input vector (top part)
   const double* vs_d;    // FP64 form: device scalar multiplying v (nullptr: 1)
   const float* vs_h;     // mixed form: float-float device scalar (nullptr: 1)
@@ -114,6 +114,9 @@ struct KState {
   double ucoef[MMAX + 1];   // z_k - (c/r) s_k: projection coefficients of the next vector
   double ycoef[MMAX + 1];   // beta * y_i for the final combination
   double yprev[MMAX + 1];   // y = exp(H_m) e_1 of the previous check (mixed-form rule)
+  double vscale[MMAX + 1];  // basis vector i = vscale_i * slot i (incomplete orthogonalisation; 1 otherwise)
+  float vs_h[MMAX + 1];     // vscale as float-float pairs (mixed-form operator applies)
+  float vs_l[MMAX + 1];
   int mprev;                // m of the previous check (0: none)
   int pad2;
   double cu;                // c / r (coefficient of u_j in the next vector)
@@ -138,6 +141,11 @@ struct KState {
 cudaError_t launch_dg_1d(bool linear, bool fp32, int eq, int p, const DGArgs& a, const Tab& t, cudaStream_t s);
 cudaError_t launch_dg_2d(bool linear, bool fp32, int eq, int p, const DGArgs& a, const Tab& t, cudaStream_t s);
 cudaError_t launch_dg_3d(bool linear, bool fp32, int eq, int p, const DGArgs& a, const Tab& t, cudaStream_t s);
+// Linearisation state z of the FP64 state q for the linear operator (FP32 when
+// fp32, else FP64; same layout and size as q).  stride = unknowns per field.
+cudaError_t launch_linstate_1d(int eq, bool fp32, const double* q, void* z, size_t stride, double gamma, cudaStream_t s);
+cudaError_t launch_linstate_2d(int eq, bool fp32, const double* q, void* z, size_t stride, double gamma, cudaStream_t s);
+cudaError_t launch_linstate_3d(int eq, bool fp32, const double* q, void* z, size_t stride, double gamma, cudaStream_t s);
 
 // ---- Krylov and vector kernels (krylov.cu); ff selects the float-float form ----
 // partial-sum buffer entries needed by the reduction kernels
@@ -150,8 +158,10 @@ cudaError_t launch_norms(bool use_ff, KState* ks, void* part, int nx, const Vec*
 cudaError_t launch_to_f32(float* out, const double* x, size_t n, cudaStream_t s);
 cudaError_t launch_f64_to_ff(Vec out, const double* x, size_t n, cudaStream_t s);
 cudaError_t launch_ff_to_f64(double* out, Vec x, size_t n, cudaStream_t s);
-// Arnoldi start: u_0 = [b0; e_P / eta] (b0 null: zero top); clears the Krylov scalars.
-cudaError_t launch_start(bool use_ff, KState* ks, Basis U, Vec b0, size_t N, int P, double eta, cudaStream_t s);
+// Arnoldi start: u_0 = [b0; e_P / eta] (b0 null: zero top); clears the Krylov scalars;
+// vscale_0 = s0 (1 / beta for incomplete orthogonalisation, else 1), vscale_i = 1 for i > 0.
+cudaError_t launch_start(bool use_ff, KState* ks, Basis U, Vec b0, size_t N, int P, double eta, double s0,
+                         cudaStream_t s);
 // Arnoldi step j by classical Gram-Schmidt with delayed re-orthogonalisation
 // (DCGS2).  On entry basis slots 0..j-1 hold the orthonormal q_i, slot j the
 // once-orthogonalised u_j, slot j+1 the operator image w = A_hat u_j.
@@ -165,8 +175,20 @@ cudaError_t launch_start(bool use_ff, KState* ks, Basis U, Vec b0, size_t N, int
 //           when |u_{j+1}| <= 1e-13 |A_hat q_j| (recorded in breakdown_at).
 cudaError_t launch_dots(bool use_ff, KState* ks, void* part, Basis U, int j, size_t n_aug, cudaStream_t s);
 cudaError_t launch_update(bool use_ff, KState* ks, void* part, Basis U, int j, size_t n_aug, cudaStream_t s);
+// Arnoldi step j by incomplete orthogonalisation over the window of the last
+// iop basis vectors, i = lo..j, lo = max(0, j - iop + 1) (1 <= iop <= EXPDG_MAX_IOP).
+// Slot i holds an unnormalised vector, v_i = vscale_i slot_i; on entry slot
+// j+1 holds w = A_hat v_j.
+//   iom_dots:   h_i = vscale_i <slot_i, w> -> H(i, j); |w| (breakdown scale).
+//   iom_update: slot j+1 = w - sum_i h_i v_i (in place); h = |slot j+1| ->
+//               H(j+1, j), vscale_{j+1} = 1 / h; happy breakdown when
+//               h <= 1e-13 |w|.
+cudaError_t launch_iom_dots(bool use_ff, int iop, KState* ks, void* part, Basis U, int j, size_t n_aug,
+                            cudaStream_t s);
+cudaError_t launch_iom_update(bool use_ff, int iop, KState* ks, void* part, Basis U, int j, size_t n_aug,
+                              cudaStream_t s);
 // FP64 phi kernel: E = exp(H_m) (Taylor-18 scaling and squaring), y = E e_1, error estimate,
-// acceptance (forced when force_accept), ycoef_i = beta y_i.  Acceptance: Saad's
+// acceptance (forced when force_accept), ycoef_i = beta y_i vscale_i.  Acceptance: Saad's
 // estimate beta h_{m+1,m} |y_m| <= tol beta; with diff_rule also when the change
 // from the previous check, beta |y - [y_prev; 0]|, is <= tol beta.
 cudaError_t launch_phi(KState* ks, int m, double beta, double tol, int force_accept, int diff_rule,

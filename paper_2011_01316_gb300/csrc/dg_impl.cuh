@@ -41,74 +41,143 @@ __host__ __device__ constexpr int elems_per_block() {
 }
 
 // ---------------------------------------------------------------- physics ---
+// Residual: fluxes from the primitive variables, computed once per state.
+// Linear operator: A_d(qt) v from the linearisation state z of qt, computed
+// once per step by k_linstate (Euler: z = (u_1..u_DIM, H, a) with the total
+// enthalpy H = (E + p) / rho and the sound speed a; Burgers: z = qt), so the
+// operator applies take no division and no square root.  With u_d and
+// du_d = (v_{m_d} - u_d v_rho) / rho,
+//   A_d v = ( v_{m_d},  v_{m_k} u_d + rho u_k du_d + delta_kd dp,
+//             (v_E + dp) u_d + (E + p) du_d ),
+//   dp = (gamma - 1) (v_E - u.v_m + |u|^2 v_rho / 2),
+// and rho u_k du_d = u_k (v_{m_d} - u_d v_rho), (E + p) du_d = H (v_{m_d} - u_d v_rho).
 template <int DIM, int EQ, typename T>
 struct Phys {
   static constexpr int M = NFields<DIM, EQ>::value;
+  static constexpr bool EULER = EQ == EXPDG_EULER;
 
-  __device__ __forceinline__ static T pressure(const T* q, T gm1) {
-    T inv = T(1) / q[0];
+  struct Prim {
+    T u[DIM];  // velocity (Burgers: the state)
+    T p;       // pressure
+    T a;       // sound speed
+  };
+
+  __device__ __forceinline__ static Prim prim(const T* q, T gamma) {
+    Prim w;
+    if (!EULER) {
+      w.u[0] = q[0];
+      w.p = T(0);
+      w.a = T(0);
+      return w;
+    }
+    const T inv = T(1) / q[0];
     T ke = T(0);
 #pragma unroll
-    for (int k = 0; k < DIM; ++k) ke += q[1 + k] * q[1 + k];
-    return gm1 * (q[DIM + 1] - T(0.5) * ke * inv);
+    for (int k = 0; k < DIM; ++k) {
+      w.u[k] = q[1 + k] * inv;
+      ke += q[1 + k] * w.u[k];
+    }
+    w.p = (gamma - T(1)) * (q[DIM + 1] - T(0.5) * ke);
+    w.a = sqrt(gamma * w.p * inv);
+    return w;
+  }
+
+  __device__ __forceinline__ static bool physical(const T* q, const Prim& w) {
+    return !EULER || (q[0] > T(0) && w.p > T(0));
   }
 
   // physical flux F_d(q)
-  __device__ __forceinline__ static void flux(const T* q, int d, T gm1, T* F) {
-    if (EQ == EXPDG_BURGERS) {
+  __device__ __forceinline__ static void flux(const T* q, const Prim& w, int d, T* F) {
+    if (!EULER) {
       F[0] = T(0.5) * q[0] * q[0];
       return;
     }
-    T inv = T(1) / q[0];
-    T ud = q[1 + d] * inv;
-    T p = pressure(q, gm1);
+    const T ud = w.u[d];
     F[0] = q[1 + d];
 #pragma unroll
-    for (int k = 0; k < DIM; ++k) F[1 + k] = q[1 + k] * ud + (k == d ? p : T(0));
-    F[DIM + 1] = (q[DIM + 1] + p) * ud;
-  }
-
-  // A_d(qt) v: directional derivative of F_d at qt along v
-  __device__ __forceinline__ static void jac(const T* qt, const T* v, int d, T gm1, T* F) {
-    if (EQ == EXPDG_BURGERS) {
-      F[0] = qt[0] * v[0];
-      return;
-    }
-    T inv = T(1) / qt[0];
-    T u[DIM];
-#pragma unroll
-    for (int k = 0; k < DIM; ++k) u[k] = qt[1 + k] * inv;
-    T uu = T(0), udm = T(0);
-#pragma unroll
-    for (int k = 0; k < DIM; ++k) {
-      uu += u[k] * u[k];
-      udm += u[k] * v[1 + k];
-    }
-    T p = gm1 * (qt[DIM + 1] - T(0.5) * qt[0] * uu);
-    T dp = gm1 * (v[DIM + 1] - udm + T(0.5) * uu * v[0]);
-    T dud = (v[1 + d] - u[d] * v[0]) * inv;  // delta u_d
-    F[0] = v[1 + d];
-#pragma unroll
-    for (int k = 0; k < DIM; ++k) F[1 + k] = v[1 + k] * u[d] + qt[1 + k] * dud + (k == d ? dp : T(0));
-    F[DIM + 1] = (v[DIM + 1] + dp) * u[d] + (qt[DIM + 1] + p) * dud;
+    for (int k = 0; k < DIM; ++k) F[1 + k] = q[1 + k] * ud + (k == d ? w.p : T(0));
+    F[DIM + 1] = (q[DIM + 1] + w.p) * ud;
   }
 
   // |u.e_d| + a  (Euler), |u| (Burgers)
-  __device__ __forceinline__ static T wave(const T* q, int d, T gamma) {
-    if (EQ == EXPDG_BURGERS) return fabs(q[0]);
-    T inv = T(1) / q[0];
-    T p = pressure(q, gamma - T(1));
-    return fabs(q[1 + d] * inv) + sqrt(gamma * p * inv);
+  __device__ __forceinline__ static T wave(const Prim& w, int d) {
+    return EULER ? fabs(w.u[d]) + w.a : fabs(w.u[0]);
   }
 
-  __device__ __forceinline__ static bool physical(const T* q, T gamma) {
-    if (EQ == EXPDG_BURGERS) return true;
-    return q[0] > T(0) && pressure(q, gamma - T(1)) > T(0);
+  // pressure perturbation dp of v at the linearisation state z (0 for Burgers)
+  __device__ __forceinline__ static T lin_dp(const T* z, const T* v, T gm1) {
+    if (!EULER) return T(0);
+    T uu = T(0), uv = T(0);
+#pragma unroll
+    for (int k = 0; k < DIM; ++k) {
+      uu += z[k] * z[k];
+      uv += z[k] * v[1 + k];
+    }
+    return gm1 * (v[DIM + 1] - uv + T(0.5) * uu * v[0]);
+  }
+
+  // A_d(qt) v
+  __device__ __forceinline__ static void lin_flux(const T* z, const T* v, T dp, int d, T* F) {
+    if (!EULER) {
+      F[0] = z[0] * v[0];
+      return;
+    }
+    const T ud = z[d];
+    const T du = v[1 + d] - ud * v[0];  // rho du_d
+    F[0] = v[1 + d];
+#pragma unroll
+    for (int k = 0; k < DIM; ++k) F[1 + k] = v[1 + k] * ud + z[k] * du + (k == d ? dp : T(0));
+    F[DIM + 1] = (v[DIM + 1] + dp) * ud + z[DIM] * du;
+  }
+
+  __device__ __forceinline__ static T lin_wave(const T* z, int d) {
+    return EULER ? fabs(z[d]) + z[DIM + 1] : fabs(z[0]);
   }
 };
 
-// LINEAR = false: residual; true: linear operator.  T = double: FP64 form
-// (double in, double out); T = float: mixed form (float in, float-float out).
+// Linearisation state z of q (FP64 in, T out), node by node; stride =
+// unknowns per field.  Computed in FP64 and rounded once.
+template <int DIM, int EQ, typename T>
+__global__ void __launch_bounds__(256) k_linstate(const double* __restrict__ q, T* __restrict__ z, size_t stride,
+                                                  double gamma) {
+  constexpr int M = NFields<DIM, EQ>::value;
+  griddep_wait();
+  const size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < stride) {
+    double qv[M];
+#pragma unroll
+    for (int f = 0; f < M; ++f) qv[f] = q[f * stride + i];
+    if (EQ != EXPDG_EULER) {
+      z[i] = (T)qv[0];
+    } else {
+      const double inv = 1.0 / qv[0];
+      double ke = 0.0;
+#pragma unroll
+      for (int k = 0; k < DIM; ++k) {
+        const double u = qv[1 + k] * inv;
+        z[k * stride + i] = (T)u;
+        ke += qv[1 + k] * u;
+      }
+      const double p = (gamma - 1.0) * (qv[DIM + 1] - 0.5 * ke);
+      z[DIM * stride + i] = (T)((qv[DIM + 1] + p) * inv);
+      z[(DIM + 1) * stride + i] = (T)sqrt(gamma * p * inv);
+    }
+  }
+  griddep_launch();
+}
+
+template <int DIM, int EQ>
+cudaError_t launch_linstate_dim(bool fp32, const double* q, void* z, size_t stride, double gamma, cudaStream_t s) {
+  if (stride == 0) return cudaSuccess;
+  const dim3 grid((unsigned)((stride + 255) / 256));
+  if (fp32) return pdl_launch(k_linstate<DIM, EQ, float>, grid, dim3(256), 0, s, q, static_cast<float*>(z), stride, gamma);
+  return pdl_launch(k_linstate<DIM, EQ, double>, grid, dim3(256), 0, s, q, static_cast<double*>(z), stride, gamma);
+}
+
+// LINEAR = false: residual R(q), a.q = q.  LINEAR = true: linear operator,
+// a.q = the linearisation state z of qt (k_linstate), a.v = v.
+// T = double: FP64 form (double in, double out); T = float: mixed form (float
+// in, float-float out).
 template <int DIM, int P, int EQ, typename T, bool LINEAR>
 __global__ void __launch_bounds__(ipow(P + 1, DIM) * elems_per_block<DIM, P>() <= 256 ? 256 : 1024)
 k_dg(const DGArgs a, const Tab tab) {
@@ -117,18 +186,34 @@ k_dg(const DGArgs a, const Tab tab) {
   constexpr int M = NFields<DIM, EQ>::value;
   constexpr int EPB = elems_per_block<DIM, P>();
   constexpr int SLOT = EPB * NP;  // nodes held by the CTA
+  constexpr int NF = 2 * DIM;     // faces per element
   constexpr bool FF = !std::is_same<T, double>::value;
   using PH = Phys<DIM, EQ, T>;
 
   griddep_wait();
   extern __shared__ __align__(16) unsigned char smem_raw[];
-  T* sF = reinterpret_cast<T*>(smem_raw);  // [DIM][M][SLOT]
-  T* sD = sF + DIM * M * SLOT;             // [NP1][NP1]
+  T* sF = reinterpret_cast<T*>(smem_raw);          // [DIM][M][SLOT]
+  T* sD = sF + DIM * M * SLOT;                     // [NP1][NP1]
+  int* sNb = reinterpret_cast<int*>(sD + NP1 * NP1);  // [EPB][NF]: neighbour element across face (d, side)
 
   const int tid = threadIdx.x;
   for (int k = tid; k < NP1 * NP1; k += blockDim.x) sD[k] = (T)tab.D[k];
-
   const int e0 = blockIdx.x * EPB;
+  for (int k = tid; k < EPB * NF; k += blockDim.x) {
+    const int el = k / NF, d = (k - el * NF) >> 1, hi = k & 1;
+    int t = e0 + el, ec[3] = {0, 0, 0};
+#pragma unroll
+    for (int dd = 0; dd < DIM; ++dd) {
+      ec[dd] = t % a.ne[dd];
+      t /= a.ne[dd];
+    }
+    int c = ec[d] + (hi ? 1 : -1);  // periodic
+    if (c < 0) c += a.ne[d];
+    if (c >= a.ne[d]) c -= a.ne[d];
+    ec[d] = c;
+    sNb[k] = ec[0] + (DIM > 1 ? a.ne[0] * (ec[1] + (DIM > 2 ? a.ne[1] * ec[2] : 0)) : 0);
+  }
+
   const int le = tid / NP;
   const int n = tid - le * NP;
   const int e = e0 + le;
@@ -139,8 +224,10 @@ k_dg(const DGArgs a, const Tab tab) {
   const T* __restrict__ qin = static_cast<const T*>(a.q);
   const T* __restrict__ vin = static_cast<const T*>(a.v);
 
-  T qv[M];  // residual: q at the node; linear: qt at the node
+  T qv[M];  // residual: q at the node; linear: z at the node
   T vv[M];  // linear: v at the node
+  typename PH::Prim w{};
+  T dp = T(0);
   if (active) {
     const size_t base = (size_t)e * NP + n;
 #pragma unroll
@@ -148,14 +235,19 @@ k_dg(const DGArgs a, const Tab tab) {
       qv[f] = qin[f * stride + base];
       if (LINEAR) vv[f] = vin[f * stride + base];
     }
-    if (!LINEAR && !PH::physical(qv, gamma)) atomicOr(a.status, 1);
+    if (LINEAR) {
+      dp = PH::lin_dp(qv, vv, gm1);
+    } else {
+      w = PH::prim(qv, gamma);
+      if (!PH::physical(qv, w)) atomicOr(a.status, 1);
+    }
 #pragma unroll
     for (int d = 0; d < DIM; ++d) {
       T F[M];
       if (LINEAR)
-        PH::jac(qv, vv, d, gm1, F);
+        PH::lin_flux(qv, vv, dp, d, F);
       else
-        PH::flux(qv, d, gm1, F);
+        PH::flux(qv, w, d, F);
 #pragma unroll
       for (int f = 0; f < M; ++f) sF[(d * M + f) * SLOT + tid] = F[f];
     }
@@ -171,15 +263,6 @@ k_dg(const DGArgs a, const Tab tab) {
     for (int d = 0; d < DIM; ++d) {
       ii[d] = t % NP1;
       t /= NP1;
-    }
-  }
-  int ec[3] = {0, 0, 0};
-  {
-    int t = e;
-#pragma unroll
-    for (int d = 0; d < DIM; ++d) {
-      ec[d] = t % a.ne[d];
-      t /= a.ne[d];
     }
   }
 
@@ -203,14 +286,9 @@ k_dg(const DGArgs a, const Tab tab) {
       acc[f] -= c2h * sum;
     }
     if (ii[d] == 0 || ii[d] == P) {
-      const int side = (ii[d] == 0) ? -1 : 1;
-      int nc[3] = {ec[0], ec[1], ec[2]};
-      nc[d] = nc[d] + side;
-      if (nc[d] < 0) nc[d] += a.ne[d];
-      if (nc[d] >= a.ne[d]) nc[d] -= a.ne[d];
-      int en = nc[0];
-      if (DIM > 1) en += a.ne[0] * (nc[1] + (DIM > 2 ? a.ne[1] * nc[2] : 0));
-      const int nn = n + (side < 0 ? P : -P) * sd;
+      const bool hi = ii[d] == P;
+      const int en = sNb[le * NF + 2 * d + (hi ? 1 : 0)];
+      const int nn = n + (hi ? -P : P) * sd;
       const size_t nb = (size_t)en * NP + nn;
       T qn[M], vn[M], Fp[M], Fm[M];
 #pragma unroll
@@ -219,12 +297,16 @@ k_dg(const DGArgs a, const Tab tab) {
         if (LINEAR) vn[f] = vin[f * stride + nb];
         Fm[f] = sF[(d * M + f) * SLOT + tid];
       }
-      if (LINEAR)
-        PH::jac(qn, vn, d, gm1, Fp);
-      else
-        PH::flux(qn, d, gm1, Fp);
-      const T lam = fmax(PH::wave(qv, d, gamma), PH::wave(qn, d, gamma));
-      const T sgn = (T)side;
+      T lam;
+      if (LINEAR) {
+        PH::lin_flux(qn, vn, PH::lin_dp(qn, vn, gm1), d, Fp);
+        lam = fmax(PH::lin_wave(qv, d), PH::lin_wave(qn, d));
+      } else {
+        const typename PH::Prim wn = PH::prim(qn, gamma);
+        PH::flux(qn, wn, d, Fp);
+        lam = fmax(PH::wave(w, d), PH::wave(wn, d));
+      }
+      const T sgn = hi ? T(1) : T(-1);
 #pragma unroll
       for (int f = 0; f < M; ++f) {
         const T jump = LINEAR ? (vv[f] - vn[f]) : (qv[f] - qn[f]);
@@ -308,7 +390,7 @@ cudaError_t launch_dg_t(const DGArgs& a, const Tab& t, cudaStream_t s) {
   constexpr int M = NFields<DIM, EQ>::value;
   constexpr int EPB = elems_per_block<DIM, P>();
   const int threads = ((EPB * NP + 31) / 32) * 32;
-  const size_t smem = sizeof(T) * ((size_t)DIM * M * EPB * NP + (P + 1) * (P + 1));
+  const size_t smem = sizeof(T) * ((size_t)DIM * M * EPB * NP + (P + 1) * (P + 1)) + sizeof(int) * EPB * 2 * DIM;
   const int blocks = (a.nelem + EPB - 1) / EPB;
   auto kern = k_dg<DIM, P, EQ, T, LINEAR>;
   // once per instantiation, thread-safe (function-local static initialisation)

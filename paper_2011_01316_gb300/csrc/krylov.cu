@@ -10,6 +10,7 @@
 // Reductions are deterministic: each block writes one partial per value, the
 // last block to finish (atomic ticket) sums the partials in block order, one
 // warp per value.
+#include <algorithm>
 #include <cooperative_groups.h>
 
 #include "common.cuh"
@@ -254,7 +255,7 @@ __global__ void k_ff_to_f64(double* out, Vec x, size_t n) {
 }
 
 template <bool FF>
-__global__ void __launch_bounds__(NT) k_start(KState* ks, Vec u0, Vec b0, size_t N, int P, double eta) {
+__global__ void __launch_bounds__(NT) k_start(KState* ks, Vec u0, Vec b0, size_t N, int P, double eta, double s0) {
   using A = Acc<FF>;
   const bool present = FF ? (b0.h != nullptr) : (b0.d != nullptr);
   const size_t n_aug = N + P;
@@ -268,6 +269,13 @@ __global__ void __launch_bounds__(NT) k_start(KState* ks, Vec u0, Vec b0, size_t
   }
   if (blockIdx.x == 0) {
     for (int k = threadIdx.x; k < (MMAX + 1) * MMAX; k += NT) ks->H[k] = 0.0;
+    for (int k = threadIdx.x; k <= MMAX; k += NT) {
+      const double v = (k == 0) ? s0 : 1.0;
+      const ff f = ff_from_double(v);
+      ks->vscale[k] = v;
+      ks->vs_h[k] = f.h;
+      ks->vs_l[k] = f.l;
+    }
     if (threadIdx.x == 0) {
       ks->breakdown_at = 0;
       ks->mprev = 0;
@@ -755,6 +763,251 @@ __global__ void __launch_bounds__(NT, 3) k_update_ff(KState* ks, ff* part, Basis
   }
 }
 
+// ---- incomplete orthogonalisation (KIOPS's replacement for Arnoldi, Sec. 1) ----
+// Window of the last KW basis vectors.  Slot i holds an unnormalised vector,
+// v_i = vscale_i slot_i, so the normalisation costs no extra pass: the
+// operator apply of the next step takes vscale_{j+1} as its input scale and
+// the final combination folds it into its coefficients.  The window vectors
+// are mutually orthogonal in exact arithmetic, so one classical pass (all
+// window products at once, then one update) equals the modified sweep.
+constexpr int IOP_MAX = EXPDG_MAX_IOP;
+
+// Last block of an incomplete-orthogonalisation dots launch.
+template <bool FF>
+__device__ void iom_dots_last_block(KState* ks, const typename Acc<FF>::T* part, int j, int lo, int nwin, int K,
+                                    int G) {
+  __shared__ double res[IOP_MAX + 1];
+  final_sums<FF>(part, K, G, res, red_stage<FF>());  // res[c] = <slot_{lo+c}, w>, res[K-1] = |w|^2
+  if ((int)threadIdx.x < nwin) {
+    const int i = lo + threadIdx.x;
+    const double sc = ks->vscale[i];
+    const double h = sc * res[threadIdx.x];
+    ks->H[j * (MMAX + 1) + i] = h;
+    ks->ucoef[threadIdx.x] = -h * sc;  // coefficient of slot_i in the update
+  }
+  if (threadIdx.x == 0) {
+    ks->wnorm = sqrt(res[K - 1]);
+    ks->counter = 0;
+  }
+}
+
+// Last block of an incomplete-orthogonalisation update launch.
+template <bool FF>
+__device__ void iom_update_last_block(KState* ks, const typename Acc<FF>::T* part, int j, int G) {
+  __shared__ double res[1];
+  final_sums<FF>(part, 1, G, res, red_stage<FF>());
+  if (threadIdx.x == 0) {
+    const double h = sqrt(res[0]);
+    const bool brk = h <= 1e-13 * ks->wnorm || h == 0.0;
+    ks->H[j * (MMAX + 1) + j + 1] = h;
+    const double v = (h > 0.0) ? 1.0 / h : 0.0;
+    const ff f = ff_from_double(v);
+    ks->vscale[j + 1] = v;
+    ks->vs_h[j + 1] = f.h;
+    ks->vs_l[j + 1] = f.l;
+    if (brk && ks->breakdown_at == 0) ks->breakdown_at = j + 1;
+    ks->counter = 0;
+  }
+}
+
+// Float-float form: packed compensated products, four elements per thread
+// per trip, every load of a trip issued before the arithmetic.
+template <int KW>
+__global__ void __launch_bounds__(NT) k_iom_dots_ff(KState* ks, ff* part, Basis U, int j, size_t n_aug) {
+  griddep_wait();
+  constexpr int K = KW + 1;
+  __shared__ ff sh[NW * K];
+  __shared__ ff tot[K];
+  if (ks->breakdown_at > 0 && j >= ks->breakdown_at) return;
+  const int lo = max(0, j - KW + 1), nwin = j - lo + 1;
+  float2 S[K], C[K];
+#pragma unroll
+  for (int k = 0; k < K; ++k) S[k] = C[k] = make_float2(0.f, 0.f);
+  const size_t ld = U.ld, ng = n_aug / 4;
+  const float* __restrict__ Uh = U.h;
+  const float* __restrict__ Ul = U.l;
+  const size_t tid = blockIdx.x * (size_t)NT + threadIdx.x, nthr = (size_t)gridDim.x * NT;
+  for (size_t g = tid; g < ng; g += nthr) {
+    const size_t o = 4 * g;
+    const float4 wh = __ldg(reinterpret_cast<const float4*>(Uh + (j + 1) * ld + o));
+    const float4 wl = __ldg(reinterpret_cast<const float4*>(Ul + (j + 1) * ld + o));
+    float4 xh[KW], xl[KW];
+#pragma unroll
+    for (int c = 0; c < KW; ++c) {
+      const size_t vo = (size_t)(lo + (c < nwin ? c : 0)) * ld + o;
+      xh[c] = __ldg(reinterpret_cast<const float4*>(Uh + vo));
+      xl[c] = __ldg(reinterpret_cast<const float4*>(Ul + vo));
+    }
+#pragma unroll
+    for (int c = 0; c < KW; ++c)
+      if (c < nwin) {
+        dot2_acc(lo2(xh[c]), lo2(xl[c]), lo2(wh), lo2(wl), S[c], C[c]);
+        dot2_acc(hi2(xh[c]), hi2(xl[c]), hi2(wh), hi2(wl), S[c], C[c]);
+      }
+    dot2_acc(lo2(wh), lo2(wl), lo2(wh), lo2(wl), S[KW], C[KW]);
+    dot2_acc(hi2(wh), hi2(wl), hi2(wh), hi2(wl), S[KW], C[KW]);
+  }
+  for (size_t i = 4 * ng + tid; i < n_aug; i += nthr) {  // ragged end
+    const float2 wh = make_float2(Uh[(j + 1) * ld + i], 0.f), wl = make_float2(Ul[(j + 1) * ld + i], 0.f);
+#pragma unroll
+    for (int c = 0; c < KW; ++c)  // constant indices keep S, C in registers
+      if (c < nwin) {
+        const size_t vo = (size_t)(lo + c) * ld + i;
+        dot2_acc(make_float2(Uh[vo], 0.f), make_float2(Ul[vo], 0.f), wh, wl, S[c], C[c]);
+      }
+    dot2_acc(wh, wl, wh, wl, S[KW], C[KW]);
+  }
+  ff v[K];
+#pragma unroll
+  for (int k = 0; k < K; ++k) v[k] = dot2_value(S[k], C[k]);
+  block_sum<true, K>(v, sh, tot);
+  const int G = gridDim.x;
+  if (threadIdx.x < K) part[(size_t)threadIdx.x * G + blockIdx.x] = tot[threadIdx.x];
+  griddep_launch();
+  if (last_block(&ks->counter, gridDim.x)) iom_dots_last_block<true>(ks, part, j, lo, nwin, K, G);
+}
+
+template <int KW>
+__global__ void __launch_bounds__(NT) k_iom_update_ff(KState* ks, ff* part, Basis U, int j, size_t n_aug) {
+  griddep_wait();
+  __shared__ float2 cf[KW];
+  __shared__ ff sh[NW];
+  __shared__ ff tot[1];
+  if (ks->breakdown_at > 0 && j >= ks->breakdown_at) return;
+  const int lo = max(0, j - KW + 1), nwin = j - lo + 1;
+  if ((int)threadIdx.x < nwin) {
+    const ff a = ff_from_double(ks->ucoef[threadIdx.x]);
+    cf[threadIdx.x] = make_float2(a.h, a.l);
+  }
+  __syncthreads();
+  float2 S = make_float2(0.f, 0.f), C = make_float2(0.f, 0.f);
+  const size_t ld = U.ld, ng = n_aug / 4;
+  float* __restrict__ Uh = U.h;
+  float* __restrict__ Ul = U.l;
+  const size_t tid = blockIdx.x * (size_t)NT + threadIdx.x, nthr = (size_t)gridDim.x * NT;
+  for (size_t g = tid; g < ng; g += nthr) {
+    const size_t o = 4 * g;
+    const float4 wh = *reinterpret_cast<const float4*>(Uh + (j + 1) * ld + o);
+    const float4 wl = *reinterpret_cast<const float4*>(Ul + (j + 1) * ld + o);
+    float4 xh[KW], xl[KW];
+#pragma unroll
+    for (int c = 0; c < KW; ++c) {
+      const size_t vo = (size_t)(lo + (c < nwin ? c : 0)) * ld + o;
+      xh[c] = __ldg(reinterpret_cast<const float4*>(Uh + vo));
+      xl[c] = __ldg(reinterpret_cast<const float4*>(Ul + vo));
+    }
+    float2 uh0 = lo2(wh), uh1 = hi2(wh), ul0 = lo2(wl), ul1 = hi2(wl);
+#pragma unroll
+    for (int c = 0; c < KW; ++c)
+      if (c < nwin) {
+        const float2 ah = make_float2(cf[c].x, cf[c].x), al = make_float2(cf[c].y, cf[c].y);
+        axpy2_acc(ah, al, lo2(xh[c]), lo2(xl[c]), uh0, ul0);
+        axpy2_acc(ah, al, hi2(xh[c]), hi2(xl[c]), uh1, ul1);
+      }
+    ff2_norm(uh0, ul0);
+    ff2_norm(uh1, ul1);
+    *reinterpret_cast<float4*>(Uh + (j + 1) * ld + o) = make_float4(uh0.x, uh0.y, uh1.x, uh1.y);
+    *reinterpret_cast<float4*>(Ul + (j + 1) * ld + o) = make_float4(ul0.x, ul0.y, ul1.x, ul1.y);
+    dot2_acc(uh0, ul0, uh0, ul0, S, C);
+    dot2_acc(uh1, ul1, uh1, ul1, S, C);
+  }
+  for (size_t i = 4 * ng + tid; i < n_aug; i += nthr) {  // ragged end
+    ff x{Uh[(j + 1) * ld + i], Ul[(j + 1) * ld + i]};
+    for (int c = 0; c < nwin; ++c) {
+      const size_t vo = (size_t)(lo + c) * ld + i;
+      x = ff_fma(ff{cf[c].x, cf[c].y}, ff{Uh[vo], Ul[vo]}, x);
+    }
+    Uh[(j + 1) * ld + i] = x.h;
+    Ul[(j + 1) * ld + i] = x.l;
+    dot2_acc(make_float2(x.h, 0.f), make_float2(x.l, 0.f), make_float2(x.h, 0.f), make_float2(x.l, 0.f), S, C);
+  }
+  ff v[1] = {dot2_value(S, C)};
+  block_sum<true, 1>(v, sh, tot);
+  if (threadIdx.x == 0) part[blockIdx.x] = tot[0];
+  griddep_launch();
+  if (last_block(&ks->counter, gridDim.x)) iom_update_last_block<true>(ks, part, j, gridDim.x);
+}
+
+// FP64 form: four elements per thread per trip, loads first.
+template <int KW>
+__global__ void __launch_bounds__(NT) k_iom_dots(KState* ks, double* part, Basis U, int j, size_t n_aug) {
+  griddep_wait();
+  constexpr int K = KW + 1;
+  __shared__ double sh[NW * K];
+  __shared__ double tot[K];
+  if (ks->breakdown_at > 0 && j >= ks->breakdown_at) return;
+  const int lo = max(0, j - KW + 1), nwin = j - lo + 1;
+  double acc[K];
+#pragma unroll
+  for (int k = 0; k < K; ++k) acc[k] = 0.0;
+  const size_t ng = n_aug / 4;
+  const size_t tid = blockIdx.x * (size_t)NT + threadIdx.x, nthr = (size_t)gridDim.x * NT;
+  for (size_t g = tid; g < ng; g += nthr) {
+    const Quad<false> w = ldq<false>(U, j + 1, g);
+    Quad<false> x[KW];
+#pragma unroll
+    for (int c = 0; c < KW; ++c) x[c] = ldq<false>(U, lo + (c < nwin ? c : 0), g);
+#pragma unroll
+    for (int c = 0; c < KW; ++c)
+      if (c < nwin)
+#pragma unroll
+        for (int e = 0; e < 4; ++e) acc[c] = fma(x[c].v[e], w.v[e], acc[c]);
+#pragma unroll
+    for (int e = 0; e < 4; ++e) acc[KW] = fma(w.v[e], w.v[e], acc[KW]);
+  }
+  for (size_t i = 4 * ng + tid; i < n_aug; i += nthr) {
+    const double wi = ldb<false>(U, j + 1, i);
+#pragma unroll
+    for (int c = 0; c < KW; ++c)
+      if (c < nwin) acc[c] = fma(ldb<false>(U, lo + c, i), wi, acc[c]);
+    acc[KW] = fma(wi, wi, acc[KW]);
+  }
+  block_sum<false, K>(acc, sh, tot);
+  const int G = gridDim.x;
+  if (threadIdx.x < K) part[(size_t)threadIdx.x * G + blockIdx.x] = tot[threadIdx.x];
+  griddep_launch();
+  if (last_block(&ks->counter, gridDim.x)) iom_dots_last_block<false>(ks, part, j, lo, nwin, K, G);
+}
+
+template <int KW>
+__global__ void __launch_bounds__(NT) k_iom_update(KState* ks, double* part, Basis U, int j, size_t n_aug) {
+  griddep_wait();
+  __shared__ double cf[KW];
+  __shared__ double sh[NW];
+  __shared__ double tot[1];
+  if (ks->breakdown_at > 0 && j >= ks->breakdown_at) return;
+  const int lo = max(0, j - KW + 1), nwin = j - lo + 1;
+  if ((int)threadIdx.x < nwin) cf[threadIdx.x] = ks->ucoef[threadIdx.x];
+  __syncthreads();
+  double nrm[1] = {0.0};
+  const size_t ng = n_aug / 4;
+  const size_t tid = blockIdx.x * (size_t)NT + threadIdx.x, nthr = (size_t)gridDim.x * NT;
+  for (size_t g = tid; g < ng; g += nthr) {
+    Quad<false> w = ldq<false>(U, j + 1, g);
+    Quad<false> x[KW];
+#pragma unroll
+    for (int c = 0; c < KW; ++c) x[c] = ldq<false>(U, lo + (c < nwin ? c : 0), g);
+#pragma unroll
+    for (int c = 0; c < KW; ++c)
+      if (c < nwin)
+#pragma unroll
+        for (int e = 0; e < 4; ++e) w.v[e] = fma(cf[c], x[c].v[e], w.v[e]);
+#pragma unroll
+    for (int e = 0; e < 4; ++e) nrm[0] = fma(w.v[e], w.v[e], nrm[0]);
+    stq<false>(U, j + 1, g, w);
+  }
+  for (size_t i = 4 * ng + tid; i < n_aug; i += nthr) {
+    double w = ldb<false>(U, j + 1, i);
+    for (int c = 0; c < nwin; ++c) w = fma(cf[c], ldb<false>(U, lo + c, i), w);
+    stb<false>(U, j + 1, i, w);
+    nrm[0] = fma(w, w, nrm[0]);
+  }
+  block_sum<false, 1>(nrm, sh, tot);
+  if (threadIdx.x == 0) part[blockIdx.x] = tot[0];
+  griddep_launch();
+  if (last_block(&ks->counter, gridDim.x)) iom_update_last_block<false>(ks, part, j, gridDim.x);
+}
+
 // Dense exponential of the m x m leading block of H: scaling and squaring,
 // exp(H) = T(H / 2^s)^(2^s) with ||H / 2^s||_1 <= 1/2 and T the degree-18
 // Taylor polynomial, evaluated by Paterson-Stockmeyer in X^4:
@@ -885,7 +1138,7 @@ k_phi(KState* ks, int m_req, double beta, double tol, int force, int diff_rule) 
     }
     __syncthreads();
     for (int i = threadIdx.x; i < m; i += blockDim.x) {
-      ks->ycoef[i] = beta * E[i * m];
+      ks->ycoef[i] = beta * E[i * m] * ks->vscale[i];
       ks->yprev[i] = E[i * m];
     }
     if (threadIdx.x == 0) ks->mprev = m;
@@ -985,12 +1238,13 @@ cudaError_t launch_ff_to_f64(double* out, Vec x, size_t n, cudaStream_t s) {
   return cudaGetLastError();
 }
 
-cudaError_t launch_start(bool use_ff, KState* ks, Basis U, Vec b0, size_t N, int P, double eta, cudaStream_t s) {
+cudaError_t launch_start(bool use_ff, KState* ks, Basis U, Vec b0, size_t N, int P, double eta, double s0,
+                         cudaStream_t s) {
   const int g = grid_for(N + P);
   if (use_ff)
-    k_start<true><<<g, NT, 0, s>>>(ks, U.at(0), b0, N, P, eta);
+    k_start<true><<<g, NT, 0, s>>>(ks, U.at(0), b0, N, P, eta, s0);
   else
-    k_start<false><<<g, NT, 0, s>>>(ks, U.at(0), b0, N, P, eta);
+    k_start<false><<<g, NT, 0, s>>>(ks, U.at(0), b0, N, P, eta, s0);
   return cudaGetLastError();
 }
 
@@ -1026,6 +1280,84 @@ cudaError_t launch_update(bool use_ff, KState* ks, void* part, Basis U, int j, s
   }
   const int g = grid_for(n_aug / 4 + 1);
   return pdl_launch(k_update<false>, dim3(g), dim3(NT), (size_t)g * 8, s, ks, static_cast<double*>(part), U, j, n_aug);
+}
+
+namespace {
+
+// One full wave of kernel Kern (its resident blocks on every SM with
+// smem_max bytes of dynamic shared memory each), capped at RB blocks (the
+// partial-sum scratch) and at `need`.  Measured once per kernel (thread-safe
+// static initialisation; smem_max is a constant of the kernel).
+template <auto Kern>
+int one_wave(size_t need, size_t smem_max) {
+  static const int wave = [smem_max] {
+    int dev = 0, nsm = 0, occ = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, Kern, NT, smem_max);
+    return std::min(RB, std::max(1, nsm) * std::max(1, occ));
+  }();
+  return (int)std::max<size_t>(std::min(need, (size_t)wave), 1);
+}
+
+template <int KW>
+cudaError_t iom_dots_kw(bool use_ff, KState* ks, void* part, Basis U, int j, size_t n_aug, cudaStream_t s) {
+  const size_t need = (n_aug / 4 + NT - 1) / NT;
+  if (use_ff) {
+    const int g = one_wave<k_iom_dots_ff<KW>>(need, (size_t)(KW + 1) * RB * sizeof(ff));
+    return pdl_launch(k_iom_dots_ff<KW>, dim3(g), dim3(NT), (size_t)(KW + 1) * g * sizeof(ff), s, ks,
+                      static_cast<ff*>(part), U, j, n_aug);
+  }
+  const int g = one_wave<k_iom_dots<KW>>(need, (size_t)(KW + 1) * RB * sizeof(double));
+  return pdl_launch(k_iom_dots<KW>, dim3(g), dim3(NT), (size_t)(KW + 1) * g * sizeof(double), s, ks,
+                    static_cast<double*>(part), U, j, n_aug);
+}
+
+template <int KW>
+cudaError_t iom_update_kw(bool use_ff, KState* ks, void* part, Basis U, int j, size_t n_aug, cudaStream_t s) {
+  const size_t need = (n_aug / 4 + NT - 1) / NT;
+  if (use_ff) {
+    const int g = one_wave<k_iom_update_ff<KW>>(need, (size_t)RB * sizeof(ff));
+    return pdl_launch(k_iom_update_ff<KW>, dim3(g), dim3(NT), (size_t)g * sizeof(ff), s, ks, static_cast<ff*>(part),
+                      U, j, n_aug);
+  }
+  const int g = one_wave<k_iom_update<KW>>(need, (size_t)RB * sizeof(double));
+  return pdl_launch(k_iom_update<KW>, dim3(g), dim3(NT), (size_t)g * sizeof(double), s, ks,
+                    static_cast<double*>(part), U, j, n_aug);
+}
+
+}  // namespace
+
+cudaError_t launch_iom_dots(bool use_ff, int iop, KState* ks, void* part, Basis U, int j, size_t n_aug,
+                            cudaStream_t s) {
+  if (j < 0 || j + 1 > MMAX) return cudaErrorInvalidValue;
+  switch (iop) {
+    case 1: return iom_dots_kw<1>(use_ff, ks, part, U, j, n_aug, s);
+    case 2: return iom_dots_kw<2>(use_ff, ks, part, U, j, n_aug, s);
+    case 3: return iom_dots_kw<3>(use_ff, ks, part, U, j, n_aug, s);
+    case 4: return iom_dots_kw<4>(use_ff, ks, part, U, j, n_aug, s);
+    case 5: return iom_dots_kw<5>(use_ff, ks, part, U, j, n_aug, s);
+    case 6: return iom_dots_kw<6>(use_ff, ks, part, U, j, n_aug, s);
+    case 7: return iom_dots_kw<7>(use_ff, ks, part, U, j, n_aug, s);
+    case 8: return iom_dots_kw<8>(use_ff, ks, part, U, j, n_aug, s);
+    default: return cudaErrorInvalidValue;
+  }
+}
+
+cudaError_t launch_iom_update(bool use_ff, int iop, KState* ks, void* part, Basis U, int j, size_t n_aug,
+                              cudaStream_t s) {
+  if (j < 0 || j + 1 > MMAX) return cudaErrorInvalidValue;
+  switch (iop) {
+    case 1: return iom_update_kw<1>(use_ff, ks, part, U, j, n_aug, s);
+    case 2: return iom_update_kw<2>(use_ff, ks, part, U, j, n_aug, s);
+    case 3: return iom_update_kw<3>(use_ff, ks, part, U, j, n_aug, s);
+    case 4: return iom_update_kw<4>(use_ff, ks, part, U, j, n_aug, s);
+    case 5: return iom_update_kw<5>(use_ff, ks, part, U, j, n_aug, s);
+    case 6: return iom_update_kw<6>(use_ff, ks, part, U, j, n_aug, s);
+    case 7: return iom_update_kw<7>(use_ff, ks, part, U, j, n_aug, s);
+    case 8: return iom_update_kw<8>(use_ff, ks, part, U, j, n_aug, s);
+    default: return cudaErrorInvalidValue;
+  }
 }
 
 cudaError_t launch_phi(KState* ks, int m, double beta, double tol, int force_accept, int diff_rule,

@@ -89,16 +89,17 @@ def courant_dt(cfg, q, courant):
     return courant * dx / c
 
 
-def vortex_request(rng, prec, courant=5.0, sides=(8, 128), orders=(2, 5), steps=50):
+def vortex_request(rng, prec, courant=5.0, sides=(8, 128), orders=(2, 5), steps=50, iop=0):
     """One request of the serving workload: 2D Euler isentropic vortex on the
     periodic [0,10]^2, side ~ U{8..128} elements, p ~ U{2..5}, strength
-    ~ U[1, 5], centre ~ U(domain), free stream (1, 1), EPI2 at Courant 5."""
+    ~ U[1, 5], centre ~ U(domain), free stream (1, 1), EPI2 at Courant 5;
+    iop = Krylov orthogonalisation window (0: full)."""
     side = int(rng.integers(sides[0], sides[1] + 1))
     p = int(rng.integers(orders[0], orders[1] + 1))
     strength = float(rng.uniform(1.0, 5.0))
     center = (float(rng.uniform(0, 10)), float(rng.uniform(0, 10)))
     cfg = expdg.default_config(dim=2, p=p, ne=[side, side, 1], lo=[0, 0, 0], hi=[10, 10, 1], eq=expdg.EXPDG_EULER,
-                               prec=prec, krylov_tol=1e-8)
+                               prec=prec, krylov_tol=1e-8, iop=iop)
     X = expdg.config_node_coords(cfg)
     q0 = inputs.isentropic_vortex(X, 0.0, strength=strength, center=center)
     dt = courant_dt(cfg, q0, courant)

@@ -1,0 +1,153 @@
+"""Incomplete orthogonalisation (the procedure KIOPS uses in place of Arnoldi,
+Sec. 1) on the CUDA path, against the oracle run with the same window.
+
+FP64 form with the oracle's decisions replayed: 1e-11 relative (rounding
+order only: the GPU forms the window's inner products in one classical pass,
+the oracle sweeps them in modified Gram-Schmidt order; the window vectors are
+mutually orthogonal, so both are the same projection).  Mixed form: 1e-6
+against the oracle's full-Arnoldi step, the bar of the mixed form."""
+import numpy as np
+import pytest
+
+from oracle import dg, integrators, krylov
+from paper_2011_01316_gb300 import inputs
+from tests.test_gpu_parity import CASES, TOL_MIXED, TOL_STEP64, _replay_from, rel, state
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def E():
+    import torch
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2011_01316_gb300 import expdg
+    return expdg
+
+
+def make(E, case, iop, prec=0, scheme=2, tol=1e-10, m_max=64):
+    c = CASES[case]
+    kw = dict(eq=c["eq"], dim=c["dim"], p=c["p"], ne=list(c["ne"]) + [1] * (3 - c["dim"]),
+              lo=list(c["lo"]) + [0.0] * (3 - c["dim"]), hi=list(c["hi"]) + [1.0] * (3 - c["dim"]),
+              prec=prec, scheme=scheme, krylov_tol=tol, m_max=m_max, m_step=5, max_substeps=32, gamma=1.4,
+              iop=iop)
+    ctx = E.Context(**kw)
+    mesh = dg.Mesh(dim=c["dim"], p=c["p"], ne=c["ne"], lo=c["lo"], hi=c["hi"],
+                   eq="burgers" if c["eq"] == 1 else "euler")
+    return ctx, mesh
+
+
+@pytest.mark.parametrize("iop", [1, 2, 4, 8])
+@pytest.mark.parametrize("P", [0, 1, 3])
+@pytest.mark.parametrize("case", ["burgers1d_p2", "euler2d_p4", "euler3d_p2"])
+def test_phi_iom_replayed(E, case, P, iop):
+    rng = np.random.default_rng(60 + P)
+    ctx, mesh = make(E, case, iop)
+    q = state(mesh, rng).reshape(-1)
+    tau = 0.05
+    c = [rng.standard_normal(q.size) * 0.1 for _ in range(P + 1)]
+    if P > 0:
+        c[0] = np.zeros_like(q)
+    ref, st = krylov.phi_sum(lambda x: tau * dg.jv(mesh, q, x).reshape(-1), c, tol=1e-10, iop=iop)
+    rep = [(0, m, s, e) for (s, m, e) in st.trace]
+    got, gst, gtr = ctx.phi(q, tau, [None if (i == 0 and P > 0) else np.ascontiguousarray(ci)
+                                     for i, ci in enumerate(c)], replay=rep)
+    assert rel(got, ref) <= TOL_STEP64
+    assert [(m, s) for (_, m, s, _) in gtr] == [(m, s) for (s, m, _) in st.trace]
+
+
+@pytest.mark.parametrize("iop", [2, 4])
+@pytest.mark.parametrize("case", ["burgers1d_p2", "euler2d_p4", "euler3d_p2"])
+def test_phi_iom_adaptive_agrees(E, case, iop):
+    """Decisions taken on the GPU agree with the oracle's (same window) to 10 tol."""
+    rng = np.random.default_rng(61)
+    ctx, mesh = make(E, case, iop)
+    q = state(mesh, rng).reshape(-1)
+    tau = 0.05
+    c = [np.zeros_like(q), rng.standard_normal(q.size) * 0.1]
+    ref, st = krylov.phi_sum(lambda x: tau * dg.jv(mesh, q, x).reshape(-1), c, tol=1e-10, iop=iop)
+    got, gst, gtr = ctx.phi(q, tau, [None, np.ascontiguousarray(c[1])])
+    assert rel(got, ref) <= 1e-9
+
+
+def test_phi_iom_substeps_parity(E):
+    """Small m_max forces rejected attempts and sub-steps with a window of 2."""
+    rng = np.random.default_rng(62)
+    ctx, mesh = make(E, "burgers1d_p2", 2, m_max=10)
+    q = state(mesh, rng).reshape(-1)
+    tau = 0.3
+    c = [rng.standard_normal(q.size) * 0.1 for _ in range(4)]
+    ref, st = krylov.phi_sum(lambda x: tau * dg.jv(mesh, q, x).reshape(-1), c, tol=1e-10, m_max=10, iop=2)
+    assert st.substeps > 1
+    got, _, _ = ctx.phi(q, tau, [np.ascontiguousarray(x) for x in c],
+                        replay=[(0, m, s, e) for (s, m, e) in st.trace])
+    assert rel(got, ref) <= TOL_STEP64
+
+
+def test_iom_window_covering_m_matches_full_orthogonalisation(E):
+    """A window at least as long as the Krylov dimension orthogonalises against
+    every previous vector: the same result as the full (DCGS2) path."""
+    rng = np.random.default_rng(63)
+    case = "euler2d_p4"
+    ctx_f, mesh = make(E, case, 0)
+    ctx_w, _ = make(E, case, 8)
+    q = state(mesh, rng).reshape(-1)
+    c = [None, np.ascontiguousarray(rng.standard_normal(q.size) * 0.1)]
+    rep = [(0, 5, 1.0, 1.0)]
+    a, _, _ = ctx_f.phi(q, 0.02, c, replay=rep)
+    b, _, _ = ctx_w.phi(q, 0.02, c, replay=rep)
+    assert rel(b, a) <= 1e-12
+
+
+@pytest.mark.parametrize("scheme", [2, 3, 4])
+@pytest.mark.parametrize("case", ["burgers1d_p2", "euler1d_p3", "euler2d_p4", "euler3d_p3"])
+def test_step_iom_fp64_replayed(E, case, scheme):
+    rng = np.random.default_rng(64)
+    iop = 4
+    ctx, mesh = make(E, case, iop, scheme=scheme)
+    q = np.ascontiguousarray(state(mesh, rng))
+    dt = 0.05 if mesh.eq == "euler" else 0.02
+    ref, st = integrators.step(mesh, q, dt, scheme=scheme, tol=1e-10, iop=iop)
+    got = q.copy()
+    ctx.step(got, dt, replay=_replay_from(st))
+    assert rel(got, ref) <= TOL_STEP64
+    np.testing.assert_allclose(dg.totals(mesh, got), dg.totals(mesh, q), rtol=1e-13, atol=1e-13)
+
+
+@pytest.mark.parametrize("iop", [2, 4])
+@pytest.mark.parametrize("scheme", [2, 3])
+@pytest.mark.parametrize("case", ["burgers1d_p2", "euler2d_p4", "euler3d_p3"])
+def test_step_iom_mixed_within_1e6(E, case, scheme, iop):
+    rng = np.random.default_rng(65)
+    ctx, mesh = make(E, case, iop, prec=1, scheme=scheme)
+    q = np.ascontiguousarray(state(mesh, rng))
+    dt = 0.05 if mesh.eq == "euler" else 0.02
+    ref, _ = integrators.step(mesh, q, dt, scheme=scheme, tol=1e-10)
+    got = q.copy()
+    ctx.step(got, dt)
+    assert rel(got, ref) <= TOL_MIXED
+
+
+def test_iom_vortex_full_size(E):
+    """64 x 64 elements, p = 4 (409,600 unknowns), window 4: one EPI2 step, FP64
+    form with the oracle's decisions, and the adaptive mixed form at tol 1e-8
+    against the oracle's full-Arnoldi step at 1e-10."""
+    CASES["euler2d_full"] = dict(eq=2, dim=2, p=4, ne=(64, 64), lo=(0.0, 0.0), hi=(10.0, 10.0))
+    ctx, mesh = make(E, "euler2d_full", 4)
+    q = np.ascontiguousarray(inputs.isentropic_vortex(dg.node_coords(mesh), 0.0))
+    ref, st = integrators.step(mesh, q, 0.05, tol=1e-10, iop=4)
+    got = q.copy()
+    ctx.step(got, 0.05, replay=_replay_from(st))
+    assert rel(got, ref) <= TOL_STEP64
+    full, _ = integrators.step(mesh, q, 0.05, tol=1e-10)
+    ctx2, _ = make(E, "euler2d_full", 4, prec=1, tol=1e-8)
+    got2 = q.copy()
+    ctx2.step(got2, 0.05)
+    assert rel(got2, full) <= TOL_MIXED
+
+
+def test_invalid_window_rejected(E):
+    for bad in (-1, E.EXPDG_MAX_IOP + 1):
+        with pytest.raises(E.ExpdgError) as ei:
+            E.Context(iop=bad)
+        assert ei.value.status == E.EXPDG_EINVAL
