@@ -33,6 +33,17 @@ Discretisation (Sec. 2.2, Eq. EXPO-SemiDiscretizedForm_ode; Sec. 3):
   the stabilisation parameter).  Equivalently L(q~) v is the derivative of R
   at q~ with lambda frozen; ``residual(..., lam=face_lambda(q~))`` is that
   frozen-lambda residual, used by the complex-step pin.
+* Viscous Burgers (Sec. 3.1, Eq. pde-burgers-eq with kappa > 0; weak forms
+  Eq. gov-burgers1d / Burger): the auxiliary q = du/dx with the central flux
+  u** = {u} (Eq. gov-burgers1d-gradu), and the total flux u^2/2 - kappa q with
+  the central flux q** = {q} for the diffusion part.  In strong collocated form
+    q = (2/h) D u + (2/h)(1/w_0) n (u** - u^-)            at face nodes,
+    R = R_convective + kappa [ (2/h) D q + (2/h)(1/w_0) n (q** - q^-) ].
+  The diffusion part is linear, so L(u~) v carries the same term with q(v).
+  Zero Dirichlet boundaries (the paper's footnote to Sec. 4): u^+ = u_D = 0 in
+  the convective fluxes (u~u)* and (u^2/2)*, u** = u_D = 0, q** = q^-.
+* A time-independent forcing (``Mesh.source``, canonical layout) is added to R,
+  as the manufactured-solution experiment of Sec. 5.1 adds its source term.
 """
 
 from dataclasses import dataclass, field
@@ -50,6 +61,9 @@ class Mesh:
     hi: tuple
     eq: str = "euler"          # "burgers" (dim 1) or "euler"
     gamma: float = 1.4
+    kappa: float = 0.0         # viscosity (Burgers only)
+    bc: str = "periodic"       # "periodic" or "dirichlet" (u_D = 0 at both ends; Burgers only)
+    source: object = None      # optional forcing added to R (canonical layout)
     r: np.ndarray = field(init=False, repr=False)
     w: np.ndarray = field(init=False, repr=False)
     D: np.ndarray = field(init=False, repr=False)
@@ -61,6 +75,10 @@ class Mesh:
         assert len(self.ne) == self.dim == len(self.lo) == len(self.hi)
         if self.eq == "burgers" and self.dim != 1:
             raise ValueError("Burgers is one-dimensional (Sec. 3.1)")
+        if self.bc not in ("periodic", "dirichlet"):
+            raise ValueError("bc must be 'periodic' or 'dirichlet'")
+        if (self.kappa != 0.0 or self.bc != "periodic") and self.eq != "burgers":
+            raise ValueError("viscosity and Dirichlet boundaries are defined for Burgers (Sec. 3.1)")
         self.r = lgl.nodes(self.p)
         self.w = lgl.weights(self.p)
         self.D = lgl.diff_matrix(self.p)
@@ -193,14 +211,63 @@ def face_traces(mesh, Q, d):
     """Traces on the two faces normal to x_d of every element:
     returns (own_left, nbr_left, own_right, nbr_right); 'nbr_left' is the
     right-end trace of element e-1 (periodic), 'nbr_right' the left-end trace
-    of element e+1."""
+    of element e+1.  With zero Dirichlet boundaries the outside trace of the
+    first and last element is u_D = 0."""
     nd = Q.ndim
     eax, nax, p = mesh.elem_axis(d), mesh.node_axis(d), mesh.p
     own_left = Q[_at(nd, nax, 0)]
     own_right = Q[_at(nd, nax, p)]
     nbr_left = np.roll(Q, 1, axis=eax)[_at(nd, nax, p)]
     nbr_right = np.roll(Q, -1, axis=eax)[_at(nd, nax, 0)]
+    if mesh.bc == "dirichlet":
+        nbr_left = nbr_left.copy()
+        nbr_right = nbr_right.copy()
+        nbr_left[_at(nd - 1, eax, 0)] = 0.0
+        nbr_right[_at(nd - 1, eax, mesh.ne[d] - 1)] = 0.0
     return own_left, nbr_left, own_right, nbr_right
+
+
+def _boundary_mask(mesh, trace, d, side):
+    """True on the traces of the domain boundary face (side 0: left end of
+    element 0, side 1: right end of the last element) of a Dirichlet mesh."""
+    mask = np.zeros(trace.shape, dtype=bool)
+    if mesh.bc == "dirichlet":
+        mask[_at(trace.ndim, mesh.elem_axis(d), 0 if side == 0 else mesh.ne[d] - 1)] = True
+    return mask
+
+
+def gradient(mesh, U):
+    """Auxiliary variable q = du/dx of the viscous Burgers equation (grid
+    form in, grid form out): Eq. gov-burgers1d-gradu in strong collocated form,
+    q = (2/h) D u + (2/h)(1/w_0) n (u** - u^-) at face nodes, with the central
+    flux u** = {u} and u** = u_D = 0 on a Dirichlet boundary."""
+    d, hd = 0, mesh.h[0]
+    nd, nax = U.ndim, mesh.node_axis(0)
+    lift = 1.0 / lgl.endpoint_weight(mesh.p)
+    G = (2.0 / hd) * _apply_D(mesh, U, d)
+    ol, nl, orr, nr = face_traces(mesh, U, d)
+    us_l = np.where(_boundary_mask(mesh, ol, d, 0), 0.0, 0.5 * (ol + nl))
+    us_r = np.where(_boundary_mask(mesh, orr, d, 1), 0.0, 0.5 * (orr + nr))
+    G[_at(nd, nax, 0)] += (2.0 / hd) * lift * (-1.0) * (us_l - ol)
+    G[_at(nd, nax, mesh.p)] += (2.0 / hd) * lift * (+1.0) * (us_r - orr)
+    return G
+
+
+def _viscous(mesh, U):
+    """kappa [ (2/h) D q + (2/h)(1/w_0) n (q** - q^-) ] with q = gradient(u)
+    and the central flux q** = {q} (q** = q^- on a Dirichlet boundary): the
+    diffusion part of R (Sec. 3.1, Eq. Burger), linear in u."""
+    d, hd = 0, mesh.h[0]
+    nd, nax = U.ndim, mesh.node_axis(0)
+    lift = 1.0 / lgl.endpoint_weight(mesh.p)
+    Qg = gradient(mesh, U)
+    R = (2.0 / hd) * _apply_D(mesh, Qg, d)
+    ol, nl, orr, nr = face_traces(mesh, Qg, d)
+    qs_l = np.where(_boundary_mask(mesh, ol, d, 0), ol, 0.5 * (ol + nl))
+    qs_r = np.where(_boundary_mask(mesh, orr, d, 1), orr, 0.5 * (orr + nr))
+    R[_at(nd, nax, 0)] += (2.0 / hd) * lift * (-1.0) * (qs_l - ol)
+    R[_at(nd, nax, mesh.p)] += (2.0 / hd) * lift * (+1.0) * (qs_r - orr)
+    return mesh.kappa * R
 
 
 def face_lambda(mesh, q):
@@ -260,7 +327,12 @@ def residual(mesh, q, lam=None):
     if lam is None:
         lam = face_lambda(mesh, q)
     R = _operator(mesh, Q, lambda S, d: flux(mesh, S, d), lam)
-    return mesh.from_grid(R)
+    if mesh.kappa != 0.0:
+        R = R + _viscous(mesh, Q)
+    R = mesh.from_grid(R)
+    if mesh.source is not None:
+        R = R + np.asarray(mesh.source).reshape(R.shape)
+    return R
 
 
 def jv(mesh, qt, v):
@@ -297,6 +369,8 @@ def jv(mesh, qt, v):
         fstar_n = 0.5 * (Fm + Fp) * (+1.0) + 0.5 * lam_r * (orr[m:] - nr[m:])
         R[_at(nd, nax, mesh.p)] -= (2.0 / hd) * lift * (fstar_n - Fm * (+1.0))
     del lin_flux
+    if mesh.kappa != 0.0:
+        R = R + _viscous(mesh, V)
     return mesh.from_grid(R)
 
 
