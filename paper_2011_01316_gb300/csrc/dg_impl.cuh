@@ -39,6 +39,11 @@ template <int DIM, int P>
 __host__ __device__ constexpr int elems_per_block() {
   return (256 / ipow(P + 1, DIM)) > 0 ? (256 / ipow(P + 1, DIM)) : 1;
 }
+// Threads per CTA: one per node of its elements, whole warps.
+template <int DIM, int P>
+__host__ __device__ constexpr int dg_threads() {
+  return ((elems_per_block<DIM, P>() * ipow(P + 1, DIM) + 31) / 32) * 32;
+}
 
 // ---------------------------------------------------------------- physics ---
 // Residual: fluxes from the primitive variables, computed once per state.
@@ -174,32 +179,12 @@ cudaError_t launch_linstate_dim(bool fp32, const double* q, void* z, size_t stri
   return pdl_launch(k_linstate<DIM, EQ, double>, grid, dim3(256), 0, s, q, static_cast<double*>(z), stride, gamma);
 }
 
-// LINEAR = false: residual R(q), a.q = q.  LINEAR = true: linear operator,
-// a.q = the linearisation state z of qt (k_linstate), a.v = v.
-// T = double: FP64 form (double in, double out); T = float: mixed form (float
-// in, float-float out).
-template <int DIM, int P, int EQ, typename T, bool LINEAR>
-__global__ void __launch_bounds__(ipow(P + 1, DIM) * elems_per_block<DIM, P>() <= 256 ? 256 : 1024)
-k_dg(const DGArgs a, const Tab tab) {
-  constexpr int NP1 = P + 1;
-  constexpr int NP = ipow(NP1, DIM);
-  constexpr int M = NFields<DIM, EQ>::value;
-  constexpr int EPB = elems_per_block<DIM, P>();
-  constexpr int SLOT = EPB * NP;  // nodes held by the CTA
-  constexpr int NF = 2 * DIM;     // faces per element
-  constexpr bool FF = !std::is_same<T, double>::value;
-  using PH = Phys<DIM, EQ, T>;
-
-  griddep_wait();
-  extern __shared__ __align__(16) unsigned char smem_raw[];
-  T* sF = reinterpret_cast<T*>(smem_raw);          // [DIM][M][SLOT]
-  T* sD = sF + DIM * M * SLOT;                     // [NP1][NP1]
-  int* sNb = reinterpret_cast<int*>(sD + NP1 * NP1);  // [EPB][NF]: neighbour element across face (d, side)
-
-  const int tid = threadIdx.x;
-  for (int k = tid; k < NP1 * NP1; k += blockDim.x) sD[k] = (T)tab.D[k];
-  const int e0 = blockIdx.x * EPB;
-  for (int k = tid; k < EPB * NF; k += blockDim.x) {
+// Neighbour element across each face of the CTA's EPB elements e0, e0+1, ...
+// (periodic box) into sNb[EPB][2 DIM], face (d, side) at 2 d + (side > 0).
+template <int DIM, int P>
+__device__ __forceinline__ void build_neighbours(const DGArgs& a, int e0, int* sNb) {
+  constexpr int EPB = elems_per_block<DIM, P>(), NF = 2 * DIM;
+  for (int k = threadIdx.x; k < EPB * NF; k += blockDim.x) {
     const int el = k / NF, d = (k - el * NF) >> 1, hi = k & 1;
     int t = e0 + el, ec[3] = {0, 0, 0};
 #pragma unroll
@@ -207,55 +192,32 @@ k_dg(const DGArgs a, const Tab tab) {
       ec[dd] = t % a.ne[dd];
       t /= a.ne[dd];
     }
-    int c = ec[d] + (hi ? 1 : -1);  // periodic
+    int c = ec[d] + (hi ? 1 : -1);
     if (c < 0) c += a.ne[d];
     if (c >= a.ne[d]) c -= a.ne[d];
     ec[d] = c;
     sNb[k] = ec[0] + (DIM > 1 ? a.ne[0] * (ec[1] + (DIM > 2 ? a.ne[1] * ec[2] : 0)) : 0);
   }
+}
 
-  const int le = tid / NP;
-  const int n = tid - le * NP;
-  const int e = e0 + le;
-  const bool active = (tid < SLOT) && (e < a.nelem);
-  const T gamma = (T)a.gamma;
-  const T gm1 = gamma - T(1);
+// Derivative and face terms at node n of the CTA's element le (thread tid):
+//   acc = - sum_d (2/h_d) ( [D^(d) F_d]_n + (1/w_0) (F*.n - F^-.n) at face nodes ),
+// from the fluxes of the CTA's nodes in sF.  qv: own state (residual) or
+// linearisation state z (linear); vv: own linear input; w: own primitive
+// variables (residual); nb_v(f, gi): the linear input of field f at node gi
+// (index within the field plane) of a neighbour element.
+template <int DIM, int P, int EQ, typename T, bool LINEAR, class NbV>
+__device__ __forceinline__ void node_terms(const DGArgs& a, T lift, const T* __restrict__ qin, const T* sF,
+                                           const T* sD, const int* sNb, int tid, int le, int n,
+                                           const T (&qv)[NFields<DIM, EQ>::value],
+                                           const T (&vv)[NFields<DIM, EQ>::value],
+                                           const typename Phys<DIM, EQ, T>::Prim& w, NbV nb_v,
+                                           T (&acc)[NFields<DIM, EQ>::value]) {
+  constexpr int NP1 = P + 1, NP = ipow(NP1, DIM), M = NFields<DIM, EQ>::value;
+  constexpr int SLOT = elems_per_block<DIM, P>() * NP, NF = 2 * DIM;
+  using PH = Phys<DIM, EQ, T>;
+  const T gamma = (T)a.gamma, gm1 = gamma - T(1);
   const size_t stride = a.stride;
-  const T* __restrict__ qin = static_cast<const T*>(a.q);
-  const T* __restrict__ vin = static_cast<const T*>(a.v);
-
-  T qv[M];  // residual: q at the node; linear: z at the node
-  T vv[M];  // linear: v at the node
-  typename PH::Prim w{};
-  T dp = T(0);
-  if (active) {
-    const size_t base = (size_t)e * NP + n;
-#pragma unroll
-    for (int f = 0; f < M; ++f) {
-      qv[f] = qin[f * stride + base];
-      if (LINEAR) vv[f] = vin[f * stride + base];
-    }
-    if (LINEAR) {
-      dp = PH::lin_dp(qv, vv, gm1);
-    } else {
-      w = PH::prim(qv, gamma);
-      if (!PH::physical(qv, w)) atomicOr(a.status, 1);
-    }
-#pragma unroll
-    for (int d = 0; d < DIM; ++d) {
-      T F[M];
-      if (LINEAR)
-        PH::lin_flux(qv, vv, dp, d, F);
-      else
-        PH::flux(qv, w, d, F);
-#pragma unroll
-      for (int f = 0; f < M; ++f) sF[(d * M + f) * SLOT + tid] = F[f];
-    }
-  }
-  __syncthreads();
-  griddep_launch();
-  if (!active) return;
-
   int ii[DIM];
   {
     int t = n;
@@ -265,12 +227,8 @@ k_dg(const DGArgs a, const Tab tab) {
       t /= NP1;
     }
   }
-
-  T acc[M];
 #pragma unroll
   for (int f = 0; f < M; ++f) acc[f] = T(0);
-  const T lift = (T)tab.lift;
-
 #pragma unroll
   for (int d = 0; d < DIM; ++d) {
     const int sd = (d == 0) ? 1 : (d == 1 ? NP1 : NP1 * NP1);
@@ -294,7 +252,7 @@ k_dg(const DGArgs a, const Tab tab) {
 #pragma unroll
       for (int f = 0; f < M; ++f) {
         qn[f] = qin[f * stride + nb];
-        if (LINEAR) vn[f] = vin[f * stride + nb];
+        if (LINEAR) vn[f] = nb_v(f, nb);
         Fm[f] = sF[(d * M + f) * SLOT + tid];
       }
       T lam;
@@ -315,6 +273,79 @@ k_dg(const DGArgs a, const Tab tab) {
       }
     }
   }
+}
+
+// LINEAR = false: residual R(q), a.q = q.  LINEAR = true: linear operator,
+// a.q = the linearisation state z of qt (k_linstate), a.v = v.
+// T = double: FP64 form (double in, double out); T = float: mixed form (float
+// in, float-float out).
+template <int DIM, int P, int EQ, typename T, bool LINEAR>
+__global__ void __launch_bounds__(dg_threads<DIM, P>())
+k_dg(const DGArgs a, const Tab tab) {
+  constexpr int NP1 = P + 1;
+  constexpr int NP = ipow(NP1, DIM);
+  constexpr int M = NFields<DIM, EQ>::value;
+  constexpr int EPB = elems_per_block<DIM, P>();
+  constexpr int SLOT = EPB * NP;  // nodes held by the CTA
+  constexpr bool FF = !std::is_same<T, double>::value;
+  using PH = Phys<DIM, EQ, T>;
+
+  griddep_wait();
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  T* sF = reinterpret_cast<T*>(smem_raw);             // [DIM][M][SLOT]
+  T* sD = sF + DIM * M * SLOT;                        // [NP1][NP1]
+  int* sNb = reinterpret_cast<int*>(sD + NP1 * NP1);  // [EPB][2 DIM]
+
+  const int tid = threadIdx.x;
+  for (int k = tid; k < NP1 * NP1; k += blockDim.x) sD[k] = (T)tab.D[k];
+  const int e0 = blockIdx.x * EPB;
+  build_neighbours<DIM, P>(a, e0, sNb);
+
+  const int le = tid / NP;
+  const int n = tid - le * NP;
+  const int e = e0 + le;
+  const bool active = (tid < SLOT) && (e < a.nelem);
+  const T gamma = (T)a.gamma;
+  const T gm1 = gamma - T(1);
+  const size_t stride = a.stride;
+  const T* __restrict__ qin = static_cast<const T*>(a.q);
+  const T* __restrict__ vin = static_cast<const T*>(a.v);
+
+  T qv[M];  // residual: q at the node; linear: z at the node
+  T vv[M];  // linear: v at the node
+  typename PH::Prim w{};
+  T dp = T(0);
+  if (active) {
+    const size_t base = (size_t)e * NP + n;
+#pragma unroll
+    for (int f = 0; f < M; ++f) {
+      qv[f] = qin[f * stride + base];
+      vv[f] = LINEAR ? vin[f * stride + base] : qv[f];
+    }
+    if (LINEAR) {
+      dp = PH::lin_dp(qv, vv, gm1);
+    } else {
+      w = PH::prim(qv, gamma);
+      if (!PH::physical(qv, w)) atomicOr(a.status, 1);
+    }
+#pragma unroll
+    for (int d = 0; d < DIM; ++d) {
+      T F[M];
+      if (LINEAR)
+        PH::lin_flux(qv, vv, dp, d, F);
+      else
+        PH::flux(qv, w, d, F);
+#pragma unroll
+      for (int f = 0; f < M; ++f) sF[(d * M + f) * SLOT + tid] = F[f];
+    }
+  }
+  __syncthreads();
+  griddep_launch();
+  if (!active) return;
+
+  T acc[M];
+  node_terms<DIM, P, EQ, T, LINEAR>(a, (T)tab.lift, qin, sF, sD, sNb, tid, le, n, qv, vv, w,
+                                    [&](int f, size_t gi) { return vin[f * stride + gi]; }, acc);
 
   const size_t base = (size_t)e * NP + n;
   const bool aug = LINEAR && a.paug > 0 && (FF ? a.tail_h != nullptr : a.tail_d != nullptr);
@@ -389,7 +420,7 @@ cudaError_t launch_dg_t(const DGArgs& a, const Tab& t, cudaStream_t s) {
   constexpr int NP = ipow(P + 1, DIM);
   constexpr int M = NFields<DIM, EQ>::value;
   constexpr int EPB = elems_per_block<DIM, P>();
-  const int threads = ((EPB * NP + 31) / 32) * 32;
+  const int threads = dg_threads<DIM, P>();
   const size_t smem = sizeof(T) * ((size_t)DIM * M * EPB * NP + (P + 1) * (P + 1)) + sizeof(int) * EPB * 2 * DIM;
   const int blocks = (a.nelem + EPB - 1) / EPB;
   auto kern = k_dg<DIM, P, EQ, T, LINEAR>;

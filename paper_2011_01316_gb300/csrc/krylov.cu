@@ -1176,6 +1176,74 @@ __global__ void __launch_bounds__(NT) k_combine(const KState* ks, Basis U, Vec b
   }
 }
 
+// Float-float combination: x = sum_{k < m} ycoef_k slot_k for a quad of
+// elements per thread (two float4 loads per vector, the next vector's loads
+// issued before this one's arithmetic; packed compensated accumulation), then
+// out = base + x, out FP64 (d) or float-float (h, l), base FP64, float-float or
+// absent.
+__global__ void __launch_bounds__(NT) k_combine_ff(const KState* ks, Basis U, Vec base, Vec out, size_t N) {
+  __shared__ float2 cf[MMAX + 1];
+  const int m = ks->m_eff;
+  for (int i = threadIdx.x; i < m; i += NT) {
+    const ff c = ff_from_double(ks->ycoef[i]);
+    cf[i] = make_float2(c.h, c.l);
+  }
+  __syncthreads();
+  const size_t ld = U.ld, ng = N / 4;
+  const float* __restrict__ Uh = U.h;
+  const float* __restrict__ Ul = U.l;
+  const bool base_d = base.d != nullptr, base_ff = base.h != nullptr;
+  auto emit = [&](size_t i, ff x) {
+    if (out.d != nullptr) {
+      double o = ff_to_double(x);
+      if (base_d) o += base.d[i];
+      if (base_ff) o += ff_to_double(ff{base.h[i], base.l[i]});
+      out.d[i] = o;
+    } else {
+      if (base_ff) x = ff_add(x, ff{base.h[i], base.l[i]});
+      if (base_d) x = ff_add(x, ff_from_double(base.d[i]));
+      out.h[i] = x.h;
+      out.l[i] = x.l;
+    }
+  };
+  const float2 z2 = make_float2(0.f, 0.f);
+  const size_t tid = blockIdx.x * (size_t)NT + threadIdx.x, nthr = (size_t)gridDim.x * NT;
+  for (size_t g = tid; g < ng; g += nthr) {
+    const size_t o = 4 * g;
+    float2 xh0 = z2, xh1 = z2, xl0 = z2, xl1 = z2;
+    float4 nh = make_float4(0.f, 0.f, 0.f, 0.f), nl = nh;
+    if (m > 0) {
+      nh = __ldg(reinterpret_cast<const float4*>(Uh + o));
+      nl = __ldg(reinterpret_cast<const float4*>(Ul + o));
+    }
+    for (int k = 0; k < m; ++k) {
+      const float4 bh = nh, bl = nl;
+      if (k + 1 < m) {
+        nh = __ldg(reinterpret_cast<const float4*>(Uh + (size_t)(k + 1) * ld + o));
+        nl = __ldg(reinterpret_cast<const float4*>(Ul + (size_t)(k + 1) * ld + o));
+      }
+      const float2 ah = make_float2(cf[k].x, cf[k].x), al = make_float2(cf[k].y, cf[k].y);
+      axpy2_acc(ah, al, lo2(bh), lo2(bl), xh0, xl0);
+      axpy2_acc(ah, al, hi2(bh), hi2(bl), xh1, xl1);
+      if ((k & 15) == 15) {
+        ff2_norm(xh0, xl0);
+        ff2_norm(xh1, xl1);
+      }
+    }
+    ff2_norm(xh0, xl0);
+    ff2_norm(xh1, xl1);
+    emit(o, ff{xh0.x, xl0.x});
+    emit(o + 1, ff{xh0.y, xl0.y});
+    emit(o + 2, ff{xh1.x, xl1.x});
+    emit(o + 3, ff{xh1.y, xl1.y});
+  }
+  for (size_t i = 4 * ng + tid; i < N; i += nthr) {  // ragged end
+    ff x{0.f, 0.f};
+    for (int k = 0; k < m; ++k) x = ff_fma(ff{cf[k].x, cf[k].y}, ff{Uh[(size_t)k * ld + i], Ul[(size_t)k * ld + i]}, x);
+    emit(i, x);
+  }
+}
+
 int grid_for(size_t n) {
   size_t b = (n + NT - 1) / NT;
   if (b > (size_t)RB) b = RB;
@@ -1374,7 +1442,7 @@ cudaError_t launch_phi(KState* ks, int m, double beta, double tol, int force_acc
 cudaError_t launch_combine(bool use_ff, const KState* ks, Basis U, Vec base, Vec out, size_t N, cudaStream_t s) {
   if (N == 0) return cudaSuccess;
   if (use_ff)
-    k_combine<true><<<grid_for(N), NT, 0, s>>>(ks, U, base, out, N);
+    k_combine_ff<<<grid_for(N / 4 + 1), NT, 0, s>>>(ks, U, base, out, N);
   else
     k_combine<false><<<grid_for(N), NT, 0, s>>>(ks, U, base, out, N);
   return cudaGetLastError();
