@@ -50,6 +50,10 @@ CFG = dict(dim=2, p=4, ne=[64, 64, 1], lo=[0.0, 0.0, 0.0], hi=[10.0, 10.0, 1.0],
            scheme=2, krylov_tol=1e-8, m_max=64, m_step=5, max_substeps=32, iop=4)
 DT = 0.05
 CLASSES = ["residual", "jv", "dots", "update", "phi", "combine", "vector"]
+# DRAM bytes per algorithmic byte of a kernel class on this workload, from one ncu
+# capture (profiles/ncu_vortex64_p4_kernels.md: k_iom_dots_ff<4>, 16.411648 MB read for
+# 16.384 MB algorithmic); used for roofline.traffic.  Refresh when the kernel changes.
+NCU_TRAFFIC_RATIO = {"dots": 16.411648 / 16.384}
 
 
 def max_over_ranks(x, world, device="cpu"):
@@ -429,8 +433,10 @@ def main():
     dom = max(bw, key=lambda k: bw[k]["ms"])
     d = kern[dom]
     achieved = (d["bytes"] / d["launches"]) / (d["ms"] / d["launches"] * 1e-3) / 1e9 if d["ms"] > 0 else 0.0
+    traffic = NCU_TRAFFIC_RATIO[dom] * d["bytes"] / d["launches"] if dom in NCU_TRAFFIC_RATIO else None
     roofline = {"kernel": dom, "bound": "hbm", "achieved": achieved, "peak": hbm, "unit": "GB/s",
-                "frac": achieved / hbm, "traffic": None, "peak_kind": peak_kind,
+                "frac": achieved / hbm, "traffic": traffic, "traffic_unit": "bytes per launch",
+                "peak_kind": peak_kind,
                 "kernel_share": d["ms"] / max(1e-9, sum(v["ms"] for v in kern.values()))}
 
     # FP64 form, same workload

@@ -50,6 +50,10 @@ typedef enum {
 
 typedef enum { EXPDG_BURGERS = 1, EXPDG_EULER = 2 } expdg_equation;
 typedef enum { EXPDG_EPI2 = 2, EXPDG_EXPRB32 = 3, EXPDG_EXPRB42 = 4 } expdg_scheme;
+/* Boundary conditions: periodic box, or zero Dirichlet data at both ends
+ * (1D Burgers only; the paper's footnote to Sec. 4: u+ = u_D = 0 in the
+ * convective numerical fluxes, u** = u_D = 0, q** = q-). */
+typedef enum { EXPDG_BC_PERIODIC = 0, EXPDG_BC_DIRICHLET = 1 } expdg_bc;
 
 /* Arithmetic of the operator applies (R, Jv) and of the Arnoldi process.
  *   EXPDG_FP64:  everything in FP64 (reference form).
@@ -82,6 +86,10 @@ typedef struct {
                            Gram-Schmidt with delayed re-orthogonalisation); k = 1..EXPDG_MAX_IOP =
                            incomplete orthogonalisation against the last k basis vectors, the
                            procedure KIOPS uses in place of Arnoldi (Sec. 1, Sec. 2.3) */
+  double kappa;         /* viscosity of the Burgers equation (Sec. 3.1, Eq. pde-burgers-eq), >= 0;
+                           > 0 adds kappa d/dx(q) with q = du/dx, central fluxes u** = {u},
+                           q** = {q} (Eq. gov-burgers1d); Burgers only */
+  int bc;               /* expdg_bc */
 } expdg_config;
 
 #define EXPDG_MAX_ORDER 8
@@ -136,6 +144,13 @@ int expdg_nodes_per_element(const expdg_ctx* ctx);
 expdg_status expdg_node_coords(const expdg_ctx* ctx, double* xyz);
 /* The same without a context (host computation only). */
 expdg_status expdg_config_node_coords(const expdg_config* cfg, double* xyz);
+
+/* Time-independent forcing s added to R (N values in the canonical layout,
+ * host or device memory; NULL removes it), e.g. the source of a manufactured
+ * solution (Sec. 5.1).  The first call allocates N doubles on the device
+ * (not counted by expdg_context_bytes).  Used by expdg_residual and the
+ * exponential steps (R = L q + N(q) + s); not by expdg_jv. */
+expdg_status expdg_set_source(expdg_ctx* ctx, const double* s);
 
 /* R(q): the DG right-hand side (Sec. 2.2, Eq. EXPO-SemiDiscretizedForm_ode;
  * strong collocated LGL form; LF flux with lambda = max(|u|) for Burgers,

@@ -31,6 +31,8 @@ struct expdg_ctx {
   // FP32 buffers (mixed form)
   float* d_q32 = nullptr;
   float* d_q32b = nullptr;
+  double* d_src = nullptr;  // forcing added to R (expdg_set_source), allocated on first use
+  bool has_src = false;
   // linearisation state of the linear operator (compute form: float or double)
   void* d_z = nullptr;
   // vectors in the Krylov storage form
@@ -163,6 +165,7 @@ void set_alpha(DGArgs& a, double alpha) {
 cudaError_t residual_into(expdg_ctx* ctx, const double* q, float* q32, Vec out, double alpha) {
   DGArgs a = ctx->mesh;
   set_alpha(a, alpha);
+  a.src = ctx->has_src ? ctx->d_src : nullptr;
   a.status = &ctx->ks->status;
   if (ctx->ff) {
     cudaError_t e = run(ctx, EXPDG_K_VECTOR, 12.0 * ctx->N, [&]() { return launch_to_f32(q32, q, ctx->N, ctx->stream); });
@@ -187,6 +190,7 @@ cudaError_t residual_for_step(expdg_ctx* ctx, const double* q, Vec out, double a
   cudaError_t e;
   DGArgs a = ctx->mesh;
   set_alpha(a, alpha);
+  a.src = ctx->has_src ? ctx->d_src : nullptr;
   a.status = &ctx->ks->status;
   a.q = q;
   a.out = ctx->d_t2;
@@ -443,6 +447,9 @@ expdg_status validate(const expdg_config* c) {
   if (c->m_step < 1) return EXPDG_EINVAL;
   if (c->max_substeps < 0) return EXPDG_EINVAL;
   if (c->iop < 0 || c->iop > EXPDG_MAX_IOP) return EXPDG_EINVAL;
+  if (!(c->kappa >= 0.0) || !std::isfinite(c->kappa)) return EXPDG_EINVAL;
+  if (c->bc != EXPDG_BC_PERIODIC && c->bc != EXPDG_BC_DIRICHLET) return EXPDG_EINVAL;
+  if ((c->kappa > 0.0 || c->bc != EXPDG_BC_PERIODIC) && c->eq != EXPDG_BURGERS) return EXPDG_EINVAL;
   return EXPDG_OK;
 }
 
@@ -620,6 +627,8 @@ expdg_status expdg_create(const expdg_config* cfg, expdg_ctx** out) {
   m.nelem = (int)ctx->nelem;
   m.gamma = cfg->gamma;
   m.stride = ctx->nelem * ctx->NP;
+  m.kappa = cfg->kappa;
+  m.dirichlet = (cfg->bc == EXPDG_BC_DIRICHLET) ? 1 : 0;
 
   const size_t N = ctx->N;
 #define ALLOC(call)                         \
@@ -739,6 +748,26 @@ expdg_status expdg_config_node_coords(const expdg_config* cfg, double* xyz) {
   double r[MAXP + 1], w[MAXP + 1], D[(MAXP + 1) * (MAXP + 1)];
   build_lgl(cfg->p, r, w, D);
   fill_node_coords(*cfg, r, xyz);
+  return EXPDG_OK;
+}
+
+expdg_status expdg_set_source(expdg_ctx* ctx, const double* s) {
+  if (!ctx) return EXPDG_EINVAL;
+  if (!s) {
+    ctx->has_src = false;
+    return EXPDG_OK;
+  }
+  if (!ctx->d_src) {
+    cudaError_t e = dalloc(ctx, &ctx->d_src, ctx->N);
+    if (e != cudaSuccess) {
+      cudaGetLastError();
+      return fail(ctx, e == cudaErrorMemoryAllocation ? EXPDG_ENOMEM : EXPDG_ECUDA, "source allocation");
+    }
+  }
+  const cudaMemcpyKind kind = is_device_ptr(s) ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice;
+  CU(ctx, cudaMemcpyAsync(ctx->d_src, s, ctx->N * sizeof(double), kind, ctx->stream));
+  CU(ctx, cudaStreamSynchronize(ctx->stream));
+  ctx->has_src = true;
   return EXPDG_OK;
 }
 

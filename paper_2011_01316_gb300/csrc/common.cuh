@@ -82,6 +82,9 @@ struct DGArgs {
   double two_over_h[3];
   double gamma;
   size_t stride;         // unknowns per field = nelem * Np
+  double kappa;          // viscosity (1D Burgers; 0: inviscid)
+  int dirichlet;         // zero Dirichlet data at both ends (1D Burgers)
+  const double* src;     // residual: forcing added to R (FP64, N values) or nullptr
 };
 
 // A vector in the FP64 form (d) or the float-float form (h + l).

@@ -180,7 +180,8 @@ cudaError_t launch_linstate_dim(bool fp32, const double* q, void* z, size_t stri
 }
 
 // Neighbour element across each face of the CTA's EPB elements e0, e0+1, ...
-// (periodic box) into sNb[EPB][2 DIM], face (d, side) at 2 d + (side > 0).
+// into sNb[EPB][2 DIM], face (d, side) at 2 d + (side > 0): periodic box, or
+// -1 outside a Dirichlet end.
 template <int DIM, int P>
 __device__ __forceinline__ void build_neighbours(const DGArgs& a, int e0, int* sNb) {
   constexpr int EPB = elems_per_block<DIM, P>(), NF = 2 * DIM;
@@ -193,10 +194,11 @@ __device__ __forceinline__ void build_neighbours(const DGArgs& a, int e0, int* s
       t /= a.ne[dd];
     }
     int c = ec[d] + (hi ? 1 : -1);
+    const bool outside = c < 0 || c >= a.ne[d];
     if (c < 0) c += a.ne[d];
     if (c >= a.ne[d]) c -= a.ne[d];
     ec[d] = c;
-    sNb[k] = ec[0] + (DIM > 1 ? a.ne[0] * (ec[1] + (DIM > 2 ? a.ne[1] * ec[2] : 0)) : 0);
+    sNb[k] = (outside && a.dirichlet) ? -1 : ec[0] + (DIM > 1 ? a.ne[0] * (ec[1] + (DIM > 2 ? a.ne[1] * ec[2] : 0)) : 0);
   }
 }
 
@@ -205,7 +207,8 @@ __device__ __forceinline__ void build_neighbours(const DGArgs& a, int e0, int* s
 // from the fluxes of the CTA's nodes in sF.  qv: own state (residual) or
 // linearisation state z (linear); vv: own linear input; w: own primitive
 // variables (residual); nb_v(f, gi): the linear input of field f at node gi
-// (index within the field plane) of a neighbour element.
+// (index within the field plane) of a neighbour element.  Outside a Dirichlet
+// end the neighbour's state and input are the boundary data 0.
 template <int DIM, int P, int EQ, typename T, bool LINEAR, class NbV>
 __device__ __forceinline__ void node_terms(const DGArgs& a, T lift, const T* __restrict__ qin, const T* sF,
                                            const T* sD, const int* sNb, int tid, int le, int n,
@@ -247,12 +250,12 @@ __device__ __forceinline__ void node_terms(const DGArgs& a, T lift, const T* __r
       const bool hi = ii[d] == P;
       const int en = sNb[le * NF + 2 * d + (hi ? 1 : 0)];
       const int nn = n + (hi ? -P : P) * sd;
-      const size_t nb = (size_t)en * NP + nn;
+      const size_t nb = (size_t)(en < 0 ? 0 : en) * NP + nn;
       T qn[M], vn[M], Fp[M], Fm[M];
 #pragma unroll
       for (int f = 0; f < M; ++f) {
-        qn[f] = qin[f * stride + nb];
-        if (LINEAR) vn[f] = nb_v(f, nb);
+        qn[f] = (en < 0) ? T(0) : qin[f * stride + nb];
+        if (LINEAR) vn[f] = (en < 0) ? T(0) : nb_v(f, nb);
         Fm[f] = sF[(d * M + f) * SLOT + tid];
       }
       T lam;
@@ -275,6 +278,77 @@ __device__ __forceinline__ void node_terms(const DGArgs& a, T lift, const T* __r
   }
 }
 
+// Diffusion part of the 1D viscous Burgers operator (Sec. 3.1, Eq. gov-burgers1d,
+// central fluxes) at the thread's node:
+//   kappa [ (2/h) D q + (2/h)(1/w_0) n (q** - q^-) ],
+//   q = (2/h) D u + (2/h)(1/w_0) n (u** - u^-),   u** = {u},  q** = {q},
+// at a Dirichlet end u** = 0 and q** = q^-.  uin: the operand (the state for
+// R, the input vector for L) in the compute type.  The CTA forms q on its
+// elements and one halo element on each side (sU, sQ: (EPB + 2)(P + 1) + 2
+// entries each); every thread of the CTA must call it.
+template <int P, typename T>
+__device__ T visc_term(const DGArgs& a, const T* __restrict__ uin, const T* sD, T lift, T* sU, T* sQ, int e0,
+                       int tid, int le, int n, bool active) {
+  constexpr int NP1 = P + 1;
+  constexpr int EPB = elems_per_block<1, P>();
+  constexpr int NH = (EPB + 2) * NP1;  // halo slots: elements e0 - 1 .. e0 + EPB
+  const int ne = a.ne[0];
+  const T c2h = (T)a.two_over_h[0];
+  auto elem_val = [&](int ge, int i) -> T {  // u at node i of element ge (periodic / zero outside)
+    if (ge < 0 || ge >= ne) {
+      if (a.dirichlet) return T(0);
+      ge = ((ge % ne) + ne) % ne;
+    }
+    return uin[(size_t)ge * NP1 + i];
+  };
+  for (int k = tid; k < NH; k += blockDim.x) sU[k] = elem_val(e0 - 1 + k / NP1, k % NP1);
+  if (tid == 0) sU[NH] = elem_val(e0 - 2, P);             // right end of element e0 - 2
+  if (tid == 1) sU[NH + 1] = elem_val(e0 + EPB + 1, 0);  // left end of element e0 + EPB + 1
+  __syncthreads();
+  for (int k = tid; k < NH; k += blockDim.x) {
+    const int kk = k / NP1, i = k - kk * NP1, ge = e0 - 1 + kk;
+    T q = T(0);
+#pragma unroll
+    for (int jn = 0; jn < NP1; ++jn) q += sD[i * NP1 + jn] * sU[kk * NP1 + jn];
+    q *= c2h;
+    if (i == 0) {
+      const T u0 = sU[kk * NP1], uo = (kk == 0) ? sU[NH] : sU[(kk - 1) * NP1 + P];
+      const T us = (a.dirichlet && ge == 0) ? T(0) : T(0.5) * (u0 + uo);
+      q -= c2h * lift * (us - u0);
+    }
+    if (i == P) {
+      const T uP = sU[kk * NP1 + P], uo = (kk == EPB + 1) ? sU[NH + 1] : sU[(kk + 1) * NP1];
+      const T us = (a.dirichlet && ge == ne - 1) ? T(0) : T(0.5) * (uP + uo);
+      q += c2h * lift * (us - uP);
+    }
+    sQ[k] = q;
+  }
+  __syncthreads();
+  if (!active) return T(0);
+  const int kk = le + 1, e = e0 + le;
+  T r = T(0);
+#pragma unroll
+  for (int jn = 0; jn < NP1; ++jn) r += sD[n * NP1 + jn] * sQ[kk * NP1 + jn];
+  r *= c2h;
+  if (n == 0) {
+    const T q0 = sQ[kk * NP1], qo = sQ[(kk - 1) * NP1 + P];
+    const T qs = (a.dirichlet && e == 0) ? q0 : T(0.5) * (q0 + qo);
+    r -= c2h * lift * (qs - q0);
+  }
+  if (n == P) {
+    const T qP = sQ[kk * NP1 + P], qo = sQ[(kk + 1) * NP1];
+    const T qs = (a.dirichlet && e == ne - 1) ? qP : T(0.5) * (qP + qo);
+    r += c2h * lift * (qs - qP);
+  }
+  return (T)a.kappa * r;
+}
+
+// Extra shared memory of the 1D Burgers kernels (the viscous halo), in T units.
+template <int DIM, int P, int EQ>
+__host__ __device__ constexpr int visc_smem_entries() {
+  return (DIM == 1 && EQ == EXPDG_BURGERS) ? 2 * ((elems_per_block<1, P>() + 2) * (P + 1) + 2) : 0;
+}
+
 // LINEAR = false: residual R(q), a.q = q.  LINEAR = true: linear operator,
 // a.q = the linearisation state z of qt (k_linstate), a.v = v.
 // T = double: FP64 form (double in, double out); T = float: mixed form (float
@@ -294,7 +368,8 @@ k_dg(const DGArgs a, const Tab tab) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   T* sF = reinterpret_cast<T*>(smem_raw);             // [DIM][M][SLOT]
   T* sD = sF + DIM * M * SLOT;                        // [NP1][NP1]
-  int* sNb = reinterpret_cast<int*>(sD + NP1 * NP1);  // [EPB][2 DIM]
+  T* sV = sD + NP1 * NP1;                             // viscous halo (1D Burgers)
+  int* sNb = reinterpret_cast<int*>(sV + visc_smem_entries<DIM, P, EQ>());  // [EPB][2 DIM]
 
   const int tid = threadIdx.x;
   for (int k = tid; k < NP1 * NP1; k += blockDim.x) sD[k] = (T)tab.D[k];
@@ -341,11 +416,18 @@ k_dg(const DGArgs a, const Tab tab) {
   }
   __syncthreads();
   griddep_launch();
+  T visc = T(0);
+  if constexpr (DIM == 1 && EQ == EXPDG_BURGERS) {
+    constexpr int NH2 = visc_smem_entries<DIM, P, EQ>() / 2;
+    if (a.kappa != 0.0)  // uniform
+      visc = visc_term<P, T>(a, LINEAR ? vin : qin, sD, (T)tab.lift, sV, sV + NH2, e0, tid, le, n, active);
+  }
   if (!active) return;
 
   T acc[M];
   node_terms<DIM, P, EQ, T, LINEAR>(a, (T)tab.lift, qin, sF, sD, sNb, tid, le, n, qv, vv, w,
                                     [&](int f, size_t gi) { return vin[f * stride + gi]; }, acc);
+  acc[0] += visc;
 
   const size_t base = (size_t)e * NP + n;
   const bool aug = LINEAR && a.paug > 0 && (FF ? a.tail_h != nullptr : a.tail_d != nullptr);
@@ -362,6 +444,7 @@ k_dg(const DGArgs a, const Tab tab) {
 #pragma unroll
     for (int f = 0; f < M; ++f) {
       double o = scale * (double)acc[f];
+      if (!LINEAR && a.src != nullptr) o += a.alpha * a.src[f * stride + base];
       if (any) {
         const size_t gi = f * stride + base;
 #pragma unroll
@@ -394,6 +477,7 @@ k_dg(const DGArgs a, const Tab tab) {
       float pe = __fmaf_rn((float)acc[f], scale.h, -p);
       pe = __fmaf_rn((float)acc[f], scale.l, pe);
       ff o = ff_fast_two_sum(p, pe);
+      if (!LINEAR && a.src != nullptr) o = ff_add(o, ff_from_double(a.alpha * a.src[f * stride + base]));
       if (any) {
         const size_t gi = f * stride + base;
 #pragma unroll
@@ -421,7 +505,8 @@ cudaError_t launch_dg_t(const DGArgs& a, const Tab& t, cudaStream_t s) {
   constexpr int M = NFields<DIM, EQ>::value;
   constexpr int EPB = elems_per_block<DIM, P>();
   const int threads = dg_threads<DIM, P>();
-  const size_t smem = sizeof(T) * ((size_t)DIM * M * EPB * NP + (P + 1) * (P + 1)) + sizeof(int) * EPB * 2 * DIM;
+  const size_t smem = sizeof(T) * ((size_t)DIM * M * EPB * NP + (P + 1) * (P + 1) + visc_smem_entries<DIM, P, EQ>()) +
+                      sizeof(int) * EPB * 2 * DIM;
   const int blocks = (a.nelem + EPB - 1) / EPB;
   auto kern = k_dg<DIM, P, EQ, T, LINEAR>;
   // once per instantiation, thread-safe (function-local static initialisation)

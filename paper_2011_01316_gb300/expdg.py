@@ -19,6 +19,7 @@ EXPDG_OK, EXPDG_EINVAL, EXPDG_ENOMEM, EXPDG_EKRYLOV, EXPDG_ENONPHYSICAL, EXPDG_E
 EXPDG_BURGERS, EXPDG_EULER = 1, 2
 EXPDG_EPI2, EXPDG_EXPRB32, EXPDG_EXPRB42 = 2, 3, 4
 EXPDG_FP64, EXPDG_MIXED = 0, 1
+EXPDG_BC_PERIODIC, EXPDG_BC_DIRICHLET = 0, 1
 EXPDG_MAX_ORDER, EXPDG_MAX_KRYLOV, EXPDG_MAX_PHI, EXPDG_MAX_IOP = 8, 64, 3, 8
 STATUS_NAMES = {0: "EXPDG_OK", 1: "EXPDG_EINVAL", 2: "EXPDG_ENOMEM", 3: "EXPDG_EKRYLOV",
                 4: "EXPDG_ENONPHYSICAL", 5: "EXPDG_ETIMEOUT", 6: "EXPDG_ECUDA"}
@@ -29,7 +30,8 @@ class expdg_config(ctypes.Structure):
                 ("lo", ctypes.c_double * 3), ("hi", ctypes.c_double * 3), ("eq", ctypes.c_int),
                 ("gamma", ctypes.c_double), ("scheme", ctypes.c_int), ("prec", ctypes.c_int),
                 ("krylov_tol", ctypes.c_double), ("m_max", ctypes.c_int), ("m_step", ctypes.c_int),
-                ("max_substeps", ctypes.c_int), ("iop", ctypes.c_int)]
+                ("max_substeps", ctypes.c_int), ("iop", ctypes.c_int), ("kappa", ctypes.c_double),
+                ("bc", ctypes.c_int)]
 
 
 class expdg_stats(ctypes.Structure):
@@ -86,6 +88,7 @@ def _load():
         "expdg_nodes_per_element": (ctypes.c_int, [P]),
         "expdg_node_coords": (ctypes.c_int, [P, P]),
         "expdg_residual": (ctypes.c_int, [P, P, P]),
+        "expdg_set_source": (ctypes.c_int, [P, P]),
         "expdg_jv": (ctypes.c_int, [P, P, P, P]),
         "expdg_phi": (ctypes.c_int, [P, P, ctypes.c_double, P, ctypes.c_int, P, vp(expdg_stats),
                                      P, ctypes.c_int, P, ctypes.c_int, vp(ctypes.c_int)]),
@@ -230,6 +233,10 @@ class Context:
         out = np.zeros((self.cfg.dim, self.nelem, self.np))
         self._check(_lib.expdg_node_coords(self.h, _ptr(out)))
         return out
+
+    def set_source(self, s):
+        """Forcing added to R (canonical layout, N values); None removes it."""
+        self._check(_lib.expdg_set_source(self.h, None if s is None else _ptr(s)))
 
     def residual(self, q, out=None):
         out = np.empty_like(q) if out is None else out
