@@ -44,6 +44,12 @@ Discretisation (Sec. 2.2, Eq. EXPO-SemiDiscretizedForm_ode; Sec. 3):
   the convective fluxes (u~u)* and (u^2/2)*, u** = u_D = 0, q** = q^-.
 * A time-independent forcing (``Mesh.source``, canonical layout) is added to R,
   as the manufactured-solution experiment of Sec. 5.1 adds its source term.
+* Roe flux for Euler (Sec. 3.2, ``Mesh.flux = "roe"``): the LF term
+  1/2 lambda (q^- - q^+) becomes 1/2 |A(q*_Roe)| (q^- - q^+), |A| = R |Lambda| R^-1
+  of the flux Jacobian in the face normal at the Roe average of the two
+  traces (rho* = sqrt(rho^- rho^+), u* and H* weighted by sqrt(rho), a* from
+  H* and u*).  The linear operator uses the Roe average of the linearisation
+  state's traces, frozen like lambda.
 """
 
 from dataclasses import dataclass, field
@@ -64,6 +70,7 @@ class Mesh:
     kappa: float = 0.0         # viscosity (Burgers only)
     bc: str = "periodic"       # "periodic" or "dirichlet" (u_D = 0 at both ends; Burgers only)
     source: object = None      # optional forcing added to R (canonical layout)
+    flux: str = "lf"           # numerical flux: "lf" (Lax-Friedrichs) or "roe" (Euler)
     r: np.ndarray = field(init=False, repr=False)
     w: np.ndarray = field(init=False, repr=False)
     D: np.ndarray = field(init=False, repr=False)
@@ -79,6 +86,8 @@ class Mesh:
             raise ValueError("bc must be 'periodic' or 'dirichlet'")
         if (self.kappa != 0.0 or self.bc != "periodic") and self.eq != "burgers":
             raise ValueError("viscosity and Dirichlet boundaries are defined for Burgers (Sec. 3.1)")
+        if self.flux not in ("lf", "roe") or (self.flux == "roe" and self.eq != "euler"):
+            raise ValueError("flux must be 'lf', or 'roe' for Euler (Sec. 3.2)")
         self.r = lgl.nodes(self.p)
         self.w = lgl.weights(self.p)
         self.D = lgl.diff_matrix(self.p)
@@ -270,6 +279,66 @@ def _viscous(mesh, U):
     return mesh.kappa * R
 
 
+def roe_dissipation(mesh, QL, QR, dQ, d):
+    """|A(q*_Roe)| dQ for the flux Jacobian in direction e_d (Sec. 3.2 and its
+    footnote): the Roe average of the states QL, QR (traces, field-major), then
+    the eigen-decomposition of A at (u*, H*) written as waves: acoustic
+    u_n -+ a with strengths (dp -+ a (dm_n - u_n drho)) / (2 a^2), entropy u_n
+    with drho - dp / a^2, shear u_n with dm_t - u_t drho, where
+    dp = (gamma - 1)(dE - u.dm + |u|^2 drho / 2) and the right eigenvectors
+    (1, u -+ a e_d, H -+ u_n a), (1, u, |u|^2/2), (0, e_t, u_t)."""
+    dim, g1 = mesh.dim, mesh.gamma - 1.0
+    rl, rr = QL[0], QR[0]
+    sl, sr = np.sqrt(rl), np.sqrt(rr)
+    ul, ur = QL[1:1 + dim] / rl, QR[1:1 + dim] / rr
+    Hl = (QL[dim + 1] + pressure(mesh, QL)) / rl
+    Hr = (QR[dim + 1] + pressure(mesh, QR)) / rr
+    u = (sl * ul + sr * ur) / (sl + sr)
+    H = (sl * Hl + sr * Hr) / (sl + sr)
+    uu = np.sum(u * u, axis=0)
+    a2 = g1 * (H - 0.5 * uu)
+    a = np.sqrt(a2)
+    un = u[d]
+    dr, dm, dE = dQ[0], dQ[1:1 + dim], dQ[dim + 1]
+    dp = g1 * (dE - np.sum(u * dm, axis=0) + 0.5 * uu * dr)
+    dun = dm[d] - un * dr
+    am = (dp - a * dun) / (2.0 * a2)
+    ap = (dp + a * dun) / (2.0 * a2)
+    a0 = dr - dp / a2
+    lm, l0, lp = np.abs(un - a), np.abs(un), np.abs(un + a)
+    out = np.empty_like(dQ)
+    out[0] = lm * am + l0 * a0 + lp * ap
+    shear_E = 0.0
+    for k in range(dim):
+        if k == d:
+            out[1 + k] = lm * am * (u[k] - a) + l0 * a0 * u[k] + lp * ap * (u[k] + a)
+        else:
+            st = dm[k] - u[k] * dr
+            out[1 + k] = lm * am * u[k] + l0 * (a0 * u[k] + st) + lp * ap * u[k]
+            shear_E = shear_E + u[k] * st
+    out[dim + 1] = lm * am * (H - un * a) + l0 * (a0 * 0.5 * uu + shear_E) + lp * ap * (H + un * a)
+    return out
+
+
+def face_dissipation(mesh, q):
+    """Frozen data of the face dissipation, per direction: the LF coefficients
+    (lam_left, lam_right) of ``face_lambda``, or for the Roe flux the state
+    traces (own_left, nbr_left, own_right, nbr_right) that define |A|."""
+    if mesh.flux == "roe":
+        Q = mesh.to_grid(q)
+        return [("roe",) + face_traces(mesh, Q, d) for d in range(mesh.dim)]
+    return face_lambda(mesh, q)
+
+
+def _dissipate(mesh, data, side, dq, d):
+    """The dissipation term of a face: lambda dq (LF) or |A(q*_Roe)| dq (Roe)."""
+    if len(data) == 5:
+        _, ol, nl, orr, nr = data
+        ql, qr = (ol, nl) if side == 0 else (orr, nr)
+        return roe_dissipation(mesh, ql, qr, dq, d)
+    return (data[0] if side == 0 else data[1]) * dq
+
+
 def face_lambda(mesh, q):
     """LF dissipation coefficient lambda per face-node pair, for each
     direction: [(lam_left, lam_right) for d] (Sec. 3.1 max|u^+-|;
@@ -305,15 +374,14 @@ def _operator(mesh, Q, fluxfn, lam):
         # volume term  -(2/h_d) D^(d) F_d
         R -= (2.0 / hd) * _apply_D(mesh, fluxfn(Q, d), d)
         ol, nl, orr, nr = face_traces(mesh, Q, d)
-        lam_l, lam_r = lam[d]
         # left face, outward normal n = -e_d:
-        #   F*.n = 1/2 (F(q-) + F(q+)).n + 1/2 lam (q- - q+)
+        #   F*.n = 1/2 (F(q-) + F(q+)).n + 1/2 D (q- - q+),  D = lam (LF) or |A| (Roe)
         Fm, Fp = fluxfn(ol, d), fluxfn(nl, d)
-        fstar_n = 0.5 * (Fm + Fp) * (-1.0) + 0.5 * lam_l * (ol - nl)
+        fstar_n = 0.5 * (Fm + Fp) * (-1.0) + 0.5 * _dissipate(mesh, lam[d], 0, ol - nl, d)
         R[_at(nd, nax, 0)] -= (2.0 / hd) * lift * (fstar_n - Fm * (-1.0))
         # right face, outward normal n = +e_d
         Fm, Fp = fluxfn(orr, d), fluxfn(nr, d)
-        fstar_n = 0.5 * (Fm + Fp) * (+1.0) + 0.5 * lam_r * (orr - nr)
+        fstar_n = 0.5 * (Fm + Fp) * (+1.0) + 0.5 * _dissipate(mesh, lam[d], 1, orr - nr, d)
         R[_at(nd, nax, mesh.p)] -= (2.0 / hd) * lift * (fstar_n - Fm * (+1.0))
     return R
 
@@ -325,7 +393,7 @@ def residual(mesh, q, lam=None):
     computed from q itself.  Works for complex q when ``lam`` is given."""
     Q = mesh.to_grid(q)
     if lam is None:
-        lam = face_lambda(mesh, q)
+        lam = face_dissipation(mesh, q)
     R = _operator(mesh, Q, lambda S, d: flux(mesh, S, d), lam)
     if mesh.kappa != 0.0:
         R = R + _viscous(mesh, Q)
@@ -342,7 +410,7 @@ def jv(mesh, qt, v):
     Sec. 3.2 (A~q)*)."""
     Qt = mesh.to_grid(qt)
     V = mesh.to_grid(v)
-    lam = face_lambda(mesh, qt)
+    lam = face_dissipation(mesh, qt)
     # the face traces of the linearisation point travel with those of v:
     # apply the operator to the stacked pair and use only the v half.
     m = mesh.m
@@ -359,14 +427,13 @@ def jv(mesh, qt, v):
         nax = mesh.node_axis(d)
         R -= (2.0 / hd) * _apply_D(mesh, flux_jacobian_apply(mesh, Qt, V, d), d)
         ol, nl, orr, nr = face_traces(mesh, S, d)
-        lam_l, lam_r = lam[d]
         Fm = flux_jacobian_apply(mesh, ol[:m], ol[m:], d)
         Fp = flux_jacobian_apply(mesh, nl[:m], nl[m:], d)
-        fstar_n = 0.5 * (Fm + Fp) * (-1.0) + 0.5 * lam_l * (ol[m:] - nl[m:])
+        fstar_n = 0.5 * (Fm + Fp) * (-1.0) + 0.5 * _dissipate(mesh, lam[d], 0, ol[m:] - nl[m:], d)
         R[_at(nd, nax, 0)] -= (2.0 / hd) * lift * (fstar_n - Fm * (-1.0))
         Fm = flux_jacobian_apply(mesh, orr[:m], orr[m:], d)
         Fp = flux_jacobian_apply(mesh, nr[:m], nr[m:], d)
-        fstar_n = 0.5 * (Fm + Fp) * (+1.0) + 0.5 * lam_r * (orr[m:] - nr[m:])
+        fstar_n = 0.5 * (Fm + Fp) * (+1.0) + 0.5 * _dissipate(mesh, lam[d], 1, orr[m:] - nr[m:], d)
         R[_at(nd, nax, mesh.p)] -= (2.0 / hd) * lift * (fstar_n - Fm * (+1.0))
     del lin_flux
     if mesh.kappa != 0.0:
