@@ -162,6 +162,35 @@ def oracle_step_rate(steps=1):
     return mesh.n_unknowns * steps / dt, dt
 
 
+def burgers_workload(steps=50):
+    """1D Burgers, 64 elements, p = 2 on the periodic [0, 2 pi] (192
+    unknowns), u0 = 0.5 + sin x, LF flux, EPI2 steps of dt = 1e-2 with Krylov
+    tol 1e-10, FP64 form: a launch-latency-bound solve.  Reports us per step
+    (CUDA events around one expdg_advance of `steps` steps, after 3 warm-up
+    steps) and DOF-steps/s."""
+    import torch
+    from paper_2011_01316_gb300 import expdg, inputs
+    ctx = expdg.Context(dim=1, p=2, ne=[64, 1, 1], lo=[0.0, 0.0, 0.0], hi=[2 * math.pi, 1.0, 1.0],
+                        eq=expdg.EXPDG_BURGERS, scheme=expdg.EXPDG_EPI2, prec=expdg.EXPDG_FP64, krylov_tol=1e-10,
+                        m_max=64, m_step=5, max_substeps=32)
+    stream = torch.cuda.current_stream()
+    ctx.set_stream(stream)
+    q0 = torch.from_numpy(np.ascontiguousarray(inputs.burgers_sine(ctx.node_coords()))).cuda()
+    q = q0.clone()
+    ctx.advance(q, 1e-2, 3)
+    q = q0.clone()
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize()
+    ev0.record(stream)
+    st = ctx.advance(q, 1e-2, steps)
+    ev1.record(stream)
+    ev1.synchronize()
+    ms = ev0.elapsed_time(ev1)
+    return {"workload": "1D Burgers, 64 elements, p=2, 192 unknowns, u0 = 0.5 + sin x, EPI2 dt=1e-2, tol 1e-10, FP64",
+            "steps": steps, "us_per_step": 1e3 * ms / steps, "dof_steps_per_s": ctx.n * steps / (ms * 1e-3),
+            "krylov_iters_per_step": st["krylov_iters"] / steps}
+
+
 def wave3d_workload(steps=2, hbm=6788.6, ne=32, iop=0):
     """3D Euler density wave rho = 1 + 0.2 sin(x+y+z), u = (1,1,1), pressure 1 on
     the periodic [0, 2 pi]^3, ne^3 hexahedra, p = 3 (10,485,760 unknowns at
@@ -331,7 +360,7 @@ def main():
     ap.add_argument("--serve-requests", type=int, default=48, help="requests of the serving workload (0: skip)")
     ap.add_argument("--batch-instances", type=int, default=64, help="instances of the batched workload (0: skip)")
     ap.add_argument("--no-3d", action="store_true", help="skip the 3D HBM-roofline workload")
-    ap.add_argument("--legs", default="main,wave3d,serving,batched",
+    ap.add_argument("--legs", default="main,wave3d,burgers,serving,batched",
                     help="comma list of legs to run (main = the timed workload; profiling runs pick one)")
     ap.add_argument("--wave3d-ne", type=int, default=32, help="elements per direction of the 3D leg")
     ap.add_argument("--wave3d-steps", type=int, default=2)
@@ -370,6 +399,8 @@ def main():
             out["serving"] = serving_workload(args.serve_requests)
         if "batched" in args.legs:
             out["batched"] = batched_workload(args.batch_instances)
+        if "burgers" in args.legs:
+            out["burgers"] = burgers_workload()
         if rank == 0:
             print(json.dumps({"legs": args.legs, **out}), flush=True)
         return
@@ -466,6 +497,7 @@ def main():
         wave3d = wave3d_workload(steps=args.wave3d_steps, hbm=hbm, ne=args.wave3d_ne, iop=args.iop)
     serving = serving_workload(args.serve_requests) if args.serve_requests > 0 and "serving" in legs else None
     batched = batched_workload(args.batch_instances) if args.batch_instances > 0 and "batched" in legs else None
+    burgers = burgers_workload() if "burgers" in legs else None
 
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
@@ -484,7 +516,7 @@ def main():
                            "l2": "flushed between timed steps (512 MiB write)",
                            "parallelism": "replicas" if world > 1 else "single GPU"},
                 "err_vs_fp64": err_vs_fp64, "fp64_form": fp64, "e2e": e2e, "gpu_launches": launches,
-                "serving": serving, "batched": batched, "wave3d": wave3d,
+                "serving": serving, "batched": batched, "wave3d": wave3d, "burgers": burgers,
                 "roofline": roofline, "kernels": kern, "cpu_baseline": cpu, "clocks": clk.summary(),
                 "ms_per_step_min": min(per), "ms_per_step_median": statistics.median(per),
                 "krylov_iters_per_step": statistics.mean(iters),

@@ -54,6 +54,10 @@ typedef enum { EXPDG_EPI2 = 2, EXPDG_EXPRB32 = 3, EXPDG_EXPRB42 = 4 } expdg_sche
  * (1D Burgers only; the paper's footnote to Sec. 4: u+ = u_D = 0 in the
  * convective numerical fluxes, u** = u_D = 0, q** = q-). */
 typedef enum { EXPDG_BC_PERIODIC = 0, EXPDG_BC_DIRICHLET = 1 } expdg_bc;
+/* Numerical flux of the Euler equations: Lax-Friedrichs (Sec. 5.1, the
+ * paper's Euler experiments) or Roe (Sec. 3.2: {F} + 1/2 |A(q*_Roe)| [q] for
+ * both the nonlinear and the linear flux, q*_Roe the Roe average). */
+typedef enum { EXPDG_FLUX_LF = 0, EXPDG_FLUX_ROE = 1 } expdg_flux;
 
 /* Arithmetic of the operator applies (R, Jv) and of the Arnoldi process.
  *   EXPDG_FP64:  everything in FP64 (reference form).
@@ -90,6 +94,7 @@ typedef struct {
                            > 0 adds kappa d/dx(q) with q = du/dx, central fluxes u** = {u},
                            q** = {q} (Eq. gov-burgers1d); Burgers only */
   int bc;               /* expdg_bc */
+  int flux;             /* expdg_flux (Euler; Burgers uses Lax-Friedrichs) */
 } expdg_config;
 
 #define EXPDG_MAX_ORDER 8

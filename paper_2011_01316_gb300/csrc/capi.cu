@@ -128,6 +128,7 @@ cudaError_t launch_dg(expdg_ctx* ctx, bool linear, const DGArgs& a, bool fp32) {
 
 cudaError_t launch_dg(expdg_ctx* ctx, bool linear, const DGArgs& a) { return launch_dg(ctx, linear, a, ctx->ff); }
 
+
 cudaEvent_t pool_event(expdg_ctx* ctx) {
   if (ctx->ev_used == ctx->ev_pool.size()) {
     cudaEvent_t e;
@@ -205,9 +206,12 @@ cudaError_t linstate_into(expdg_ctx* ctx, const double* qt) {
   return run(ctx, EXPDG_K_VECTOR, bytes, [&]() {
     const size_t stride = ctx->mesh.stride;
     switch (ctx->cfg.dim) {
-      case 1: return launch_linstate_1d(ctx->cfg.eq, ctx->ff, qt, ctx->d_z, stride, ctx->cfg.gamma, ctx->stream);
-      case 2: return launch_linstate_2d(ctx->cfg.eq, ctx->ff, qt, ctx->d_z, stride, ctx->cfg.gamma, ctx->stream);
-      case 3: return launch_linstate_3d(ctx->cfg.eq, ctx->ff, qt, ctx->d_z, stride, ctx->cfg.gamma, ctx->stream);
+      case 1: return launch_linstate_1d(ctx->cfg.eq, ctx->ff, qt, ctx->d_z, stride, ctx->cfg.gamma, ctx->mesh.roe,
+                                         ctx->stream);
+      case 2: return launch_linstate_2d(ctx->cfg.eq, ctx->ff, qt, ctx->d_z, stride, ctx->cfg.gamma, ctx->mesh.roe,
+                                         ctx->stream);
+      case 3: return launch_linstate_3d(ctx->cfg.eq, ctx->ff, qt, ctx->d_z, stride, ctx->cfg.gamma, ctx->mesh.roe,
+                                         ctx->stream);
     }
     return cudaErrorInvalidValue;
   });
@@ -450,6 +454,8 @@ expdg_status validate(const expdg_config* c) {
   if (!(c->kappa >= 0.0) || !std::isfinite(c->kappa)) return EXPDG_EINVAL;
   if (c->bc != EXPDG_BC_PERIODIC && c->bc != EXPDG_BC_DIRICHLET) return EXPDG_EINVAL;
   if ((c->kappa > 0.0 || c->bc != EXPDG_BC_PERIODIC) && c->eq != EXPDG_BURGERS) return EXPDG_EINVAL;
+  if (c->flux != EXPDG_FLUX_LF && c->flux != EXPDG_FLUX_ROE) return EXPDG_EINVAL;
+  if (c->flux == EXPDG_FLUX_ROE && c->eq != EXPDG_EULER) return EXPDG_EINVAL;
   return EXPDG_OK;
 }
 
@@ -629,6 +635,7 @@ expdg_status expdg_create(const expdg_config* cfg, expdg_ctx** out) {
   m.stride = ctx->nelem * ctx->NP;
   m.kappa = cfg->kappa;
   m.dirichlet = (cfg->bc == EXPDG_BC_DIRICHLET) ? 1 : 0;
+  m.roe = (cfg->flux == EXPDG_FLUX_ROE) ? 1 : 0;
 
   const size_t N = ctx->N;
 #define ALLOC(call)                         \
@@ -680,6 +687,7 @@ expdg_status expdg_create(const expdg_config* cfg, expdg_ctx** out) {
   ctx->h_ks = static_cast<KState*>(hk);
   std::memset(ctx->h_ks, 0, sizeof(KState));
   ALLOC(cudaStreamSynchronize(0));  // the zero-fills above are complete
+
 #undef ALLOC
   *out = ctx;
   return EXPDG_OK;

@@ -85,6 +85,7 @@ struct DGArgs {
   double kappa;          // viscosity (1D Burgers; 0: inviscid)
   int dirichlet;         // zero Dirichlet data at both ends (1D Burgers)
   const double* src;     // residual: forcing added to R (FP64, N values) or nullptr
+  int roe;               // Euler: Roe flux (the linearisation state then ends with sqrt(rho))
 };
 
 // A vector in the FP64 form (d) or the float-float form (h + l).
@@ -144,11 +145,18 @@ struct KState {
 cudaError_t launch_dg_1d(bool linear, bool fp32, int eq, int p, const DGArgs& a, const Tab& t, cudaStream_t s);
 cudaError_t launch_dg_2d(bool linear, bool fp32, int eq, int p, const DGArgs& a, const Tab& t, cudaStream_t s);
 cudaError_t launch_dg_3d(bool linear, bool fp32, int eq, int p, const DGArgs& a, const Tab& t, cudaStream_t s);
-// Linearisation state z of the FP64 state q for the linear operator (FP32 when
-// fp32, else FP64; same layout and size as q).  stride = unknowns per field.
-cudaError_t launch_linstate_1d(int eq, bool fp32, const double* q, void* z, size_t stride, double gamma, cudaStream_t s);
-cudaError_t launch_linstate_2d(int eq, bool fp32, const double* q, void* z, size_t stride, double gamma, cudaStream_t s);
-cudaError_t launch_linstate_3d(int eq, bool fp32, const double* q, void* z, size_t stride, double gamma, cudaStream_t s);
+// The Roe-flux kernels (Euler; dg_roe_1d.cu, dg_roe_2d.cu, dg_roe_3d.cu), reached
+// through launch_dg_Nd when a.roe is set.
+cudaError_t launch_dg_roe_1d(bool linear, bool fp32, int p, const DGArgs& a, const Tab& t, cudaStream_t s);
+cudaError_t launch_dg_roe_2d(bool linear, bool fp32, int p, const DGArgs& a, const Tab& t, cudaStream_t s);
+cudaError_t launch_dg_roe_3d(bool linear, bool fp32, int p, const DGArgs& a, const Tab& t, cudaStream_t s);
+// Euler: z = (u, H, a), or (u, H, sqrt(rho)) with roe.
+cudaError_t launch_linstate_1d(int eq, bool fp32, const double* q, void* z, size_t stride, double gamma, int roe,
+                               cudaStream_t s);
+cudaError_t launch_linstate_2d(int eq, bool fp32, const double* q, void* z, size_t stride, double gamma, int roe,
+                               cudaStream_t s);
+cudaError_t launch_linstate_3d(int eq, bool fp32, const double* q, void* z, size_t stride, double gamma, int roe,
+                               cudaStream_t s);
 
 // ---- Krylov and vector kernels (krylov.cu); ff selects the float-float form ----
 // partial-sum buffer entries needed by the reduction kernels

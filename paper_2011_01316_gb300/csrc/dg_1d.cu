@@ -5,14 +5,15 @@ namespace expdg {
 
 cudaError_t launch_dg_1d(bool linear, bool fp32, int eq, int p, const DGArgs& a, const Tab& t, cudaStream_t s) {
   if (eq == EXPDG_BURGERS) return launch_dg_dim<1, EXPDG_BURGERS>(linear, fp32, p, a, t, s);
+  if (eq == EXPDG_EULER && a.roe) return launch_dg_roe_1d(linear, fp32, p, a, t, s);
   if (eq == EXPDG_EULER) return launch_dg_dim<1, EXPDG_EULER>(linear, fp32, p, a, t, s);
   return cudaErrorInvalidValue;
 }
 
-cudaError_t launch_linstate_1d(int eq, bool fp32, const double* q, void* z, size_t stride, double gamma,
+cudaError_t launch_linstate_1d(int eq, bool fp32, const double* q, void* z, size_t stride, double gamma, int roe,
                                cudaStream_t s) {
-  if (eq == EXPDG_BURGERS) return launch_linstate_dim<1, EXPDG_BURGERS>(fp32, q, z, stride, gamma, s);
-  if (eq == EXPDG_EULER) return launch_linstate_dim<1, EXPDG_EULER>(fp32, q, z, stride, gamma, s);
+  if (eq == EXPDG_BURGERS) return launch_linstate_dim<1, EXPDG_BURGERS>(fp32, q, z, stride, gamma, roe, s);
+  if (eq == EXPDG_EULER) return launch_linstate_dim<1, EXPDG_EULER>(fp32, q, z, stride, gamma, roe, s);
   return cudaErrorInvalidValue;
 }
 

@@ -138,13 +138,58 @@ struct Phys {
   __device__ __forceinline__ static T lin_wave(const T* z, int d) {
     return EULER ? fabs(z[d]) + z[DIM + 1] : fabs(z[0]);
   }
+
+  // Roe dissipation |A(q*_Roe)| dq in direction e_d (Sec. 3.2): the Roe
+  // average of two states given by velocity, total enthalpy and sqrt(rho),
+  // then the waves of the flux Jacobian at (u*, H*): acoustic u_n -+ a with
+  // strengths (dp -+ a (dm_n - u_n drho)) / (2 a^2), entropy u_n with
+  // drho - dp / a^2, shear u_n with dm_t - u_t drho, where
+  // dp = (gamma - 1)(dE - u.dm + |u|^2 drho / 2); right eigenvectors
+  // (1, u -+ a e_d, H -+ u_n a), (1, u, |u|^2 / 2), (0, e_t, u_t).
+  __device__ __forceinline__ static void roe_dissipation(const T* uL, T HL, T sL, const T* uR, T HR, T sR, const T* dq,
+                                                         int d, T gm1, T* out) {
+    const T inv = T(1) / (sL + sR);
+    T u[DIM];
+    T uu = T(0), udm = T(0);
+#pragma unroll
+    for (int k = 0; k < DIM; ++k) {
+      u[k] = (sL * uL[k] + sR * uR[k]) * inv;
+      uu += u[k] * u[k];
+      udm += u[k] * dq[1 + k];
+    }
+    const T H = (sL * HL + sR * HR) * inv;
+    const T a2 = gm1 * (H - T(0.5) * uu);
+    const T a = sqrt(a2), ia2 = T(1) / a2;
+    const T un = u[d];
+    const T dr = dq[0];
+    const T dp = gm1 * (dq[DIM + 1] - udm + T(0.5) * uu * dr);
+    const T dun = dq[1 + d] - un * dr;
+    const T wm = fabs(un - a) * T(0.5) * (dp - a * dun) * ia2;
+    const T wp = fabs(un + a) * T(0.5) * (dp + a * dun) * ia2;
+    const T l0 = fabs(un), w0 = l0 * (dr - dp * ia2);
+    const T ws = wm + w0 + wp;
+    out[0] = ws;
+    T shearE = T(0);
+#pragma unroll
+    for (int k = 0; k < DIM; ++k) {
+      if (k == d) {
+        out[1 + k] = ws * u[k] + (wp - wm) * a;
+      } else {
+        const T st = dq[1 + k] - u[k] * dr;
+        out[1 + k] = ws * u[k] + l0 * st;
+        shearE += u[k] * st;
+      }
+    }
+    out[DIM + 1] = (wm + wp) * H + (wp - wm) * un * a + w0 * T(0.5) * uu + l0 * shearE;
+  }
 };
 
 // Linearisation state z of q (FP64 in, T out), node by node; stride =
-// unknowns per field.  Computed in FP64 and rounded once.
+// unknowns per field.  Computed in FP64 and rounded once.  Euler: (u, H, a),
+// or (u, H, sqrt(rho)) for the Roe flux (its average weights).
 template <int DIM, int EQ, typename T>
 __global__ void __launch_bounds__(256) k_linstate(const double* __restrict__ q, T* __restrict__ z, size_t stride,
-                                                  double gamma) {
+                                                  double gamma, int roe) {
   constexpr int M = NFields<DIM, EQ>::value;
   griddep_wait();
   const size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
@@ -165,18 +210,20 @@ __global__ void __launch_bounds__(256) k_linstate(const double* __restrict__ q, 
       }
       const double p = (gamma - 1.0) * (qv[DIM + 1] - 0.5 * ke);
       z[DIM * stride + i] = (T)((qv[DIM + 1] + p) * inv);
-      z[(DIM + 1) * stride + i] = (T)sqrt(gamma * p * inv);
+      z[(DIM + 1) * stride + i] = (T)(roe ? sqrt(qv[0]) : sqrt(gamma * p * inv));
     }
   }
   griddep_launch();
 }
 
 template <int DIM, int EQ>
-cudaError_t launch_linstate_dim(bool fp32, const double* q, void* z, size_t stride, double gamma, cudaStream_t s) {
+cudaError_t launch_linstate_dim(bool fp32, const double* q, void* z, size_t stride, double gamma, int roe,
+                               cudaStream_t s) {
   if (stride == 0) return cudaSuccess;
   const dim3 grid((unsigned)((stride + 255) / 256));
-  if (fp32) return pdl_launch(k_linstate<DIM, EQ, float>, grid, dim3(256), 0, s, q, static_cast<float*>(z), stride, gamma);
-  return pdl_launch(k_linstate<DIM, EQ, double>, grid, dim3(256), 0, s, q, static_cast<double*>(z), stride, gamma);
+  if (fp32)
+    return pdl_launch(k_linstate<DIM, EQ, float>, grid, dim3(256), 0, s, q, static_cast<float*>(z), stride, gamma, roe);
+  return pdl_launch(k_linstate<DIM, EQ, double>, grid, dim3(256), 0, s, q, static_cast<double*>(z), stride, gamma, roe);
 }
 
 // Neighbour element across each face of the CTA's EPB elements e0, e0+1, ...
@@ -209,7 +256,7 @@ __device__ __forceinline__ void build_neighbours(const DGArgs& a, int e0, int* s
 // variables (residual); nb_v(f, gi): the linear input of field f at node gi
 // (index within the field plane) of a neighbour element.  Outside a Dirichlet
 // end the neighbour's state and input are the boundary data 0.
-template <int DIM, int P, int EQ, typename T, bool LINEAR, class NbV>
+template <int DIM, int P, int EQ, typename T, bool LINEAR, bool ROE, class NbV>
 __device__ __forceinline__ void node_terms(const DGArgs& a, T lift, const T* __restrict__ qin, const T* sF,
                                            const T* sD, const int* sNb, int tid, int le, int n,
                                            const T (&qv)[NFields<DIM, EQ>::value],
@@ -258,20 +305,35 @@ __device__ __forceinline__ void node_terms(const DGArgs& a, T lift, const T* __r
         if (LINEAR) vn[f] = (en < 0) ? T(0) : nb_v(f, nb);
         Fm[f] = sF[(d * M + f) * SLOT + tid];
       }
-      T lam;
+      T Dj[M];  // dissipation term: lam (q^- - q^+) (LF) or |A(q*_Roe)| (q^- - q^+) (Roe)
+      T dq[M];
+#pragma unroll
+      for (int f = 0; f < M; ++f) dq[f] = LINEAR ? (vv[f] - vn[f]) : (qv[f] - qn[f]);
       if (LINEAR) {
         PH::lin_flux(qn, vn, PH::lin_dp(qn, vn, gm1), d, Fp);
-        lam = fmax(PH::lin_wave(qv, d), PH::lin_wave(qn, d));
+        if constexpr (ROE) {  // z = (u, H, sqrt(rho)) on both sides
+          PH::roe_dissipation(qv, qv[M - 2], qv[M - 1], qn, qn[M - 2], qn[M - 1], dq, d, gm1, Dj);
+        } else {
+          const T lam = fmax(PH::lin_wave(qv, d), PH::lin_wave(qn, d));
+#pragma unroll
+          for (int f = 0; f < M; ++f) Dj[f] = lam * dq[f];
+        }
       } else {
         const typename PH::Prim wn = PH::prim(qn, gamma);
         PH::flux(qn, wn, d, Fp);
-        lam = fmax(PH::wave(w, d), PH::wave(wn, d));
+        if constexpr (ROE) {  // the Roe average of the two states (H = (E + p) / rho)
+          PH::roe_dissipation(w.u, (qv[M - 1] + w.p) / qv[0], sqrt(qv[0]), wn.u, (qn[M - 1] + wn.p) / qn[0],
+                              sqrt(qn[0]), dq, d, gm1, Dj);
+        } else {
+          const T lam = fmax(PH::wave(w, d), PH::wave(wn, d));
+#pragma unroll
+          for (int f = 0; f < M; ++f) Dj[f] = lam * dq[f];
+        }
       }
       const T sgn = hi ? T(1) : T(-1);
 #pragma unroll
       for (int f = 0; f < M; ++f) {
-        const T jump = LINEAR ? (vv[f] - vn[f]) : (qv[f] - qn[f]);
-        const T fstar_n = T(0.5) * (Fm[f] + Fp[f]) * sgn + T(0.5) * lam * jump;
+        const T fstar_n = T(0.5) * (Fm[f] + Fp[f]) * sgn + T(0.5) * Dj[f];
         acc[f] -= c2h * lift * (fstar_n - Fm[f] * sgn);
       }
     }
@@ -353,9 +415,33 @@ __host__ __device__ constexpr int visc_smem_entries() {
 // a.q = the linearisation state z of qt (k_linstate), a.v = v.
 // T = double: FP64 form (double in, double out); T = float: mixed form (float
 // in, float-float out).
-template <int DIM, int P, int EQ, typename T, bool LINEAR>
-__global__ void __launch_bounds__(dg_threads<DIM, P>())
-k_dg(const DGArgs a, const Tab tab) {
+// Shared-memory layout of the DG kernels (T units, then ints).
+template <int DIM, int P, int EQ, typename T>
+struct DgSmem {
+  static constexpr int NP1 = P + 1, NP = ipow(NP1, DIM), M = NFields<DIM, EQ>::value;
+  static constexpr int SLOT = elems_per_block<DIM, P>() * NP;
+  __host__ __device__ static constexpr size_t bytes() {
+    return sizeof(T) * ((size_t)DIM * M * SLOT + NP1 * NP1 + visc_smem_entries<DIM, P, EQ>()) +
+           sizeof(int) * elems_per_block<DIM, P>() * 2 * DIM;
+  }
+  T* sF;    // [DIM][M][SLOT] fluxes
+  T* sD;    // [NP1][NP1] derivative matrix
+  T* sV;    // viscous halo (1D Burgers)
+  int* sNb; // [EPB][2 DIM] neighbour elements
+  __device__ explicit DgSmem(unsigned char* raw) {
+    sF = reinterpret_cast<T*>(raw);
+    sD = sF + DIM * M * SLOT;
+    sV = sD + NP1 * NP1;
+    sNb = reinterpret_cast<int*>(sV + visc_smem_entries<DIM, P, EQ>());
+  }
+};
+
+// One element group (the EPB elements from e0) of the DG operator; sD must
+// hold the derivative matrix.  Every thread of the CTA calls it (it
+// synchronises the CTA); trigger: signal dependent launches after the fluxes.
+template <int DIM, int P, int EQ, typename T, bool LINEAR, bool ROE>
+__device__ __forceinline__ void dg_group(const DGArgs& a, const Tab& tab, int e0, const DgSmem<DIM, P, EQ, T>& sm,
+                                         bool trigger) {
   constexpr int NP1 = P + 1;
   constexpr int NP = ipow(NP1, DIM);
   constexpr int M = NFields<DIM, EQ>::value;
@@ -363,17 +449,12 @@ k_dg(const DGArgs a, const Tab tab) {
   constexpr int SLOT = EPB * NP;  // nodes held by the CTA
   constexpr bool FF = !std::is_same<T, double>::value;
   using PH = Phys<DIM, EQ, T>;
-
-  griddep_wait();
-  extern __shared__ __align__(16) unsigned char smem_raw[];
-  T* sF = reinterpret_cast<T*>(smem_raw);             // [DIM][M][SLOT]
-  T* sD = sF + DIM * M * SLOT;                        // [NP1][NP1]
-  T* sV = sD + NP1 * NP1;                             // viscous halo (1D Burgers)
-  int* sNb = reinterpret_cast<int*>(sV + visc_smem_entries<DIM, P, EQ>());  // [EPB][2 DIM]
+  T* sF = sm.sF;
+  const T* sD = sm.sD;
+  T* sV = sm.sV;
+  int* sNb = sm.sNb;
 
   const int tid = threadIdx.x;
-  for (int k = tid; k < NP1 * NP1; k += blockDim.x) sD[k] = (T)tab.D[k];
-  const int e0 = blockIdx.x * EPB;
   build_neighbours<DIM, P>(a, e0, sNb);
 
   const int le = tid / NP;
@@ -415,17 +496,17 @@ k_dg(const DGArgs a, const Tab tab) {
     }
   }
   __syncthreads();
-  griddep_launch();
+  if (trigger) griddep_launch();
   T visc = T(0);
   if constexpr (DIM == 1 && EQ == EXPDG_BURGERS) {
     constexpr int NH2 = visc_smem_entries<DIM, P, EQ>() / 2;
     if (a.kappa != 0.0)  // uniform
       visc = visc_term<P, T>(a, LINEAR ? vin : qin, sD, (T)tab.lift, sV, sV + NH2, e0, tid, le, n, active);
   }
-  if (!active) return;
+  if (!active) return;  // no further synchronisation below
 
   T acc[M];
-  node_terms<DIM, P, EQ, T, LINEAR>(a, (T)tab.lift, qin, sF, sD, sNb, tid, le, n, qv, vv, w,
+  node_terms<DIM, P, EQ, T, LINEAR, ROE>(a, (T)tab.lift, qin, sF, sD, sNb, tid, le, n, qv, vv, w,
                                     [&](int f, size_t gi) { return vin[f * stride + gi]; }, acc);
   acc[0] += visc;
 
@@ -453,7 +534,7 @@ k_dg(const DGArgs a, const Tab tab) {
       }
       a.out[f * stride + base] = o;
     }
-    if (aug && blockIdx.x == 0 && tid == 0)
+    if (aug && e0 == 0 && tid == 0)
       for (int k = 0; k < a.paug; ++k) a.out_tail_d[k] = (k + 1 < a.paug) ? vs * a.tail_d[k + 1] : 0.0;
   } else {
     const ff vs = (LINEAR && a.vs_h != nullptr) ? ff{*a.vs_h, *a.vs_l} : ff{1.0f, 0.0f};
@@ -490,7 +571,7 @@ k_dg(const DGArgs a, const Tab tab) {
       a.out_h[f * stride + base] = o.h;
       a.out_l[f * stride + base] = o.l;
     }
-    if (aug && blockIdx.x == 0 && tid == 0)
+    if (aug && e0 == 0 && tid == 0)
       for (int k = 0; k < a.paug; ++k) {
         ff t = (k + 1 < a.paug) ? ff_mul(vs, ff{a.tail_h[k + 1], a.tail_l[k + 1]}) : ff{0.0f, 0.0f};
         a.out_tail_h[k] = t.h;
@@ -499,16 +580,25 @@ k_dg(const DGArgs a, const Tab tab) {
   }
 }
 
-template <int DIM, int P, int EQ, typename T, bool LINEAR>
+template <int DIM, int P, int EQ, typename T, bool LINEAR, bool ROE>
+__global__ void __launch_bounds__(dg_threads<DIM, P>())
+k_dg(const DGArgs a, const Tab tab) {
+  griddep_wait();
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  const DgSmem<DIM, P, EQ, T> sm(smem_raw);
+  for (int k = threadIdx.x; k < (P + 1) * (P + 1); k += blockDim.x) sm.sD[k] = (T)tab.D[k];
+  dg_group<DIM, P, EQ, T, LINEAR, ROE>(a, tab, blockIdx.x * elems_per_block<DIM, P>(), sm, true);
+}
+
+template <int DIM, int P, int EQ, typename T, bool LINEAR, bool ROE>
 cudaError_t launch_dg_t(const DGArgs& a, const Tab& t, cudaStream_t s) {
   constexpr int NP = ipow(P + 1, DIM);
   constexpr int M = NFields<DIM, EQ>::value;
   constexpr int EPB = elems_per_block<DIM, P>();
   const int threads = dg_threads<DIM, P>();
-  const size_t smem = sizeof(T) * ((size_t)DIM * M * EPB * NP + (P + 1) * (P + 1) + visc_smem_entries<DIM, P, EQ>()) +
-                      sizeof(int) * EPB * 2 * DIM;
+  const size_t smem = DgSmem<DIM, P, EQ, T>::bytes();
   const int blocks = (a.nelem + EPB - 1) / EPB;
-  auto kern = k_dg<DIM, P, EQ, T, LINEAR>;
+  auto kern = k_dg<DIM, P, EQ, T, LINEAR, ROE>;
   // once per instantiation, thread-safe (function-local static initialisation)
   static const cudaError_t configured =
       cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
@@ -517,26 +607,29 @@ cudaError_t launch_dg_t(const DGArgs& a, const Tab& t, cudaStream_t s) {
   return pdl_launch(kern, dim3(blocks), dim3(threads), smem, s, a, t);
 }
 
-template <int DIM, int EQ, typename T, bool LINEAR>
+template <int DIM, int EQ, typename T, bool LINEAR, bool ROE>
 cudaError_t launch_dg_p(int p, const DGArgs& a, const Tab& t, cudaStream_t s) {
   switch (p) {
-    case 1: return launch_dg_t<DIM, 1, EQ, T, LINEAR>(a, t, s);
-    case 2: return launch_dg_t<DIM, 2, EQ, T, LINEAR>(a, t, s);
-    case 3: return launch_dg_t<DIM, 3, EQ, T, LINEAR>(a, t, s);
-    case 4: return launch_dg_t<DIM, 4, EQ, T, LINEAR>(a, t, s);
-    case 5: return launch_dg_t<DIM, 5, EQ, T, LINEAR>(a, t, s);
-    case 6: return launch_dg_t<DIM, 6, EQ, T, LINEAR>(a, t, s);
-    case 7: return launch_dg_t<DIM, 7, EQ, T, LINEAR>(a, t, s);
-    case 8: return launch_dg_t<DIM, 8, EQ, T, LINEAR>(a, t, s);
+    case 1: return launch_dg_t<DIM, 1, EQ, T, LINEAR, ROE>(a, t, s);
+    case 2: return launch_dg_t<DIM, 2, EQ, T, LINEAR, ROE>(a, t, s);
+    case 3: return launch_dg_t<DIM, 3, EQ, T, LINEAR, ROE>(a, t, s);
+    case 4: return launch_dg_t<DIM, 4, EQ, T, LINEAR, ROE>(a, t, s);
+    case 5: return launch_dg_t<DIM, 5, EQ, T, LINEAR, ROE>(a, t, s);
+    case 6: return launch_dg_t<DIM, 6, EQ, T, LINEAR, ROE>(a, t, s);
+    case 7: return launch_dg_t<DIM, 7, EQ, T, LINEAR, ROE>(a, t, s);
+    case 8: return launch_dg_t<DIM, 8, EQ, T, LINEAR, ROE>(a, t, s);
     default: return cudaErrorInvalidValue;
   }
 }
 
-template <int DIM, int EQ>
+// ROE: the Roe-flux instantiations (Euler), built in their own translation units.
+template <int DIM, int EQ, bool ROE = false>
 cudaError_t launch_dg_dim(bool linear, bool fp32, int p, const DGArgs& a, const Tab& t, cudaStream_t s) {
   if (fp32)
-    return linear ? launch_dg_p<DIM, EQ, float, true>(p, a, t, s) : launch_dg_p<DIM, EQ, float, false>(p, a, t, s);
-  return linear ? launch_dg_p<DIM, EQ, double, true>(p, a, t, s) : launch_dg_p<DIM, EQ, double, false>(p, a, t, s);
+    return linear ? launch_dg_p<DIM, EQ, float, true, ROE>(p, a, t, s)
+                  : launch_dg_p<DIM, EQ, float, false, ROE>(p, a, t, s);
+  return linear ? launch_dg_p<DIM, EQ, double, true, ROE>(p, a, t, s)
+                : launch_dg_p<DIM, EQ, double, false, ROE>(p, a, t, s);
 }
 
 }  // namespace expdg

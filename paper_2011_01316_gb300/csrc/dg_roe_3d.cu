@@ -1,0 +1,10 @@
+// DG operator kernels with the Roe flux (Euler), instantiated for dimension 3.
+#include "dg_impl.cuh"
+
+namespace expdg {
+
+cudaError_t launch_dg_roe_3d(bool linear, bool fp32, int p, const DGArgs& a, const Tab& t, cudaStream_t s) {
+  return launch_dg_dim<3, EXPDG_EULER, true>(linear, fp32, p, a, t, s);
+}
+
+}  // namespace expdg

@@ -68,6 +68,7 @@ extern "C" expdg_status expdg_residual_noalloc(const expdg_config* cfg, const do
   if (cfg->prec != EXPDG_FP64 && cfg->prec != EXPDG_MIXED) return EXPDG_EINVAL;
   if (!(cfg->kappa >= 0.0) || (cfg->bc != EXPDG_BC_PERIODIC && cfg->bc != EXPDG_BC_DIRICHLET)) return EXPDG_EINVAL;
   if ((cfg->kappa > 0.0 || cfg->bc != EXPDG_BC_PERIODIC) && cfg->eq != EXPDG_BURGERS) return EXPDG_EINVAL;
+  if (cfg->flux != EXPDG_FLUX_LF && (cfg->flux != EXPDG_FLUX_ROE || cfg->eq != EXPDG_EULER)) return EXPDG_EINVAL;
   size_t nelem = 1;
   int np = 1;
   for (int d = 0; d < dim; ++d) {
@@ -104,6 +105,7 @@ extern "C" expdg_status expdg_residual_noalloc(const expdg_config* cfg, const do
   a.gamma = cfg->gamma;
   a.kappa = cfg->kappa;
   a.dirichlet = (cfg->bc == EXPDG_BC_DIRICHLET) ? 1 : 0;
+  a.roe = (cfg->flux == EXPDG_FLUX_ROE) ? 1 : 0;
   a.stride = nelem * np;
   a.alpha = 1.0;
   a.alpha_h = 1.0f;

@@ -20,6 +20,7 @@ EXPDG_BURGERS, EXPDG_EULER = 1, 2
 EXPDG_EPI2, EXPDG_EXPRB32, EXPDG_EXPRB42 = 2, 3, 4
 EXPDG_FP64, EXPDG_MIXED = 0, 1
 EXPDG_BC_PERIODIC, EXPDG_BC_DIRICHLET = 0, 1
+EXPDG_FLUX_LF, EXPDG_FLUX_ROE = 0, 1
 EXPDG_MAX_ORDER, EXPDG_MAX_KRYLOV, EXPDG_MAX_PHI, EXPDG_MAX_IOP = 8, 64, 3, 8
 STATUS_NAMES = {0: "EXPDG_OK", 1: "EXPDG_EINVAL", 2: "EXPDG_ENOMEM", 3: "EXPDG_EKRYLOV",
                 4: "EXPDG_ENONPHYSICAL", 5: "EXPDG_ETIMEOUT", 6: "EXPDG_ECUDA"}
@@ -31,7 +32,7 @@ class expdg_config(ctypes.Structure):
                 ("gamma", ctypes.c_double), ("scheme", ctypes.c_int), ("prec", ctypes.c_int),
                 ("krylov_tol", ctypes.c_double), ("m_max", ctypes.c_int), ("m_step", ctypes.c_int),
                 ("max_substeps", ctypes.c_int), ("iop", ctypes.c_int), ("kappa", ctypes.c_double),
-                ("bc", ctypes.c_int)]
+                ("bc", ctypes.c_int), ("flux", ctypes.c_int)]
 
 
 class expdg_stats(ctypes.Structure):
