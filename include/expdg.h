@@ -199,9 +199,10 @@ expdg_status expdg_phi(expdg_ctx* ctx, const double* qt, double tau, const doubl
  * q (in place): EPI2 q += dt phi_1(dt L) R(q) (Sec. 5.1 footnote), EXPRB32 /
  * EXPRB42 (Sec. 5.1 / 5.2 footnotes).  replay / trace as in expdg_phi, with
  * the solve index distinguishing the two stages.  Without replay, the error
- * checks of each stage's first sub-step start at max(m_step, m_prev - m_step),
- * m_prev the m that stage accepted in this context's previous step (steps in a
- * row need similar m; starting later can only give a more accurate result). */
+ * checks of each stage's first sub-step start at m_prev, the m that stage
+ * accepted in this context's previous step, and every fourth step at
+ * max(m_step, m_prev - m_step) so that a falling m is found (steps in a row
+ * need similar m; starting later can only give a more accurate result). */
 expdg_status expdg_step(expdg_ctx* ctx, double* q, double dt, expdg_stats* stats,
                         const expdg_trace_entry* replay, int nreplay,
                         expdg_trace_entry* trace, int trace_cap, int* ntrace);

@@ -44,6 +44,7 @@ struct expdg_ctx {
   void* part = nullptr;
   KState* h_ks = nullptr;  // pinned mirror (host-visible block only is refreshed)
   int m_hint[2] = {0, 0};  // m accepted by each stage's first sub-step in the previous step
+  int hint_uses[2] = {0, 0};  // steps that used the hint (every 4th also probes m_prev - m_step)
   std::vector<void*> allocs;
   std::string err;
   // profiling
@@ -338,8 +339,10 @@ expdg_status phi_solve(expdg_ctx* ctx, const void* qt_T, double tau, const bool*
     const int limit = replay ? m_fix : cfg.m_max;
     int m_first = cfg.m_step;
     const bool first_sub = (sv == 0.0 && rejected == 0);
-    if (use_hint && first_sub && !replay && ctx->m_hint[solve_id & 1] > 0)
-      m_first = std::max(cfg.m_step, ctx->m_hint[solve_id & 1] - cfg.m_step);
+    if (use_hint && first_sub && !replay && ctx->m_hint[solve_id & 1] > 0) {
+      const bool probe = (ctx->hint_uses[solve_id & 1]++ % 4) == 0;
+      m_first = std::max(cfg.m_step, ctx->m_hint[solve_id & 1] - (probe ? cfg.m_step : 0));
+    }
     bool accepted = false;
     int m_acc = 0;
     double err = 0.0;
@@ -890,6 +893,7 @@ expdg_status expdg_advance(expdg_ctx* ctx, double* q, double dt, int nsteps, exp
   Replay rp;
   // a solve's decisions depend only on its own inputs, not on earlier calls
   ctx->m_hint[0] = ctx->m_hint[1] = 0;
+  ctx->hint_uses[0] = ctx->hint_uses[1] = 0;
   for (int k = 0; k < nsteps; ++k) {
     expdg_status r = step_dev(ctx, qd, dt, rp, &st, nullptr);
     if (r != EXPDG_OK) return r;

@@ -297,12 +297,14 @@ __device__ __forceinline__ void node_terms(const DGArgs& a, T lift, const T* __r
       const bool hi = ii[d] == P;
       const int en = sNb[le * NF + 2 * d + (hi ? 1 : 0)];
       const int nn = n + (hi ? -P : P) * sd;
-      const size_t nb = (size_t)(en < 0 ? 0 : en) * NP + nn;
+      // Dirichlet ends exist only for Burgers: the Euler kernels keep plain loads
+      const bool outside = (EQ == EXPDG_BURGERS) && en < 0;
+      const size_t nb = (size_t)(outside ? 0 : en) * NP + nn;
       T qn[M], vn[M], Fp[M], Fm[M];
 #pragma unroll
       for (int f = 0; f < M; ++f) {
-        qn[f] = (en < 0) ? T(0) : qin[f * stride + nb];
-        if (LINEAR) vn[f] = (en < 0) ? T(0) : nb_v(f, nb);
+        qn[f] = outside ? T(0) : qin[f * stride + nb];
+        if (LINEAR) vn[f] = outside ? T(0) : nb_v(f, nb);
         Fm[f] = sF[(d * M + f) * SLOT + tid];
       }
       T Dj[M];  // dissipation term: lam (q^- - q^+) (LF) or |A(q*_Roe)| (q^- - q^+) (Roe)
