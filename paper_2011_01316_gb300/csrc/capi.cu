@@ -4,6 +4,7 @@
 #include <cmath>
 #include <cstdio>
 #include <cstring>
+#include <map>
 #include <string>
 #include <vector>
 
@@ -45,6 +46,10 @@ struct expdg_ctx {
   KState* h_ks = nullptr;  // pinned mirror (host-visible block only is refreshed)
   int m_hint[2] = {0, 0};  // m accepted by each stage's first sub-step in the previous step
   int hint_uses[2] = {0, 0};  // steps that used the hint (every 4th also probes m_prev - m_step)
+  // CUDA graphs of Arnoldi segments (steps j0 .. j1-1), keyed by (j0, j1, P)
+  std::map<long long, cudaGraphExec_t> graphs;
+  cudaStream_t cap_stream = nullptr;  // private stream for graph capture
+  bool graphs_ok = true;
   std::vector<void*> allocs;
   std::string err;
   // profiling
@@ -128,6 +133,50 @@ cudaError_t launch_dg(expdg_ctx* ctx, bool linear, const DGArgs& a, bool fp32) {
 }
 
 cudaError_t launch_dg(expdg_ctx* ctx, bool linear, const DGArgs& a) { return launch_dg(ctx, linear, a, ctx->ff); }
+
+// The operator kernel on an explicit stream (graph capture).
+cudaError_t launch_dg_on(expdg_ctx* ctx, bool linear, const DGArgs& a, cudaStream_t s) {
+  const int p = ctx->cfg.p, eq = ctx->cfg.eq;
+  switch (ctx->cfg.dim) {
+    case 1: return launch_dg_1d(linear, ctx->ff, eq, p, a, ctx->tab, s);
+    case 2: return launch_dg_2d(linear, ctx->ff, eq, p, a, ctx->tab, s);
+    case 3: return launch_dg_3d(linear, ctx->ff, eq, p, a, ctx->tab, s);
+  }
+  return cudaErrorInvalidValue;
+}
+
+// Instantiated graph of Arnoldi steps j0 .. j1-1 for P augmentation vectors,
+// captured once on the context's private stream from `launches(j, stream,
+// counted = false)` and reused by every later sub-step (their launch
+// arguments are the same; the sub-step scalars live in device memory).
+// nullptr when capture is not available (the caller launches directly).
+template <class F>
+cudaGraphExec_t segment_graph(expdg_ctx* ctx, int j0, int j1, int P, F&& launches) {
+  if (!ctx->graphs_ok) return nullptr;
+  const long long key = ((long long)j0 * 1024 + j1) * 8 + P;
+  auto it = ctx->graphs.find(key);
+  if (it != ctx->graphs.end()) return it->second;
+  if (!ctx->cap_stream && cudaStreamCreateWithFlags(&ctx->cap_stream, cudaStreamNonBlocking) != cudaSuccess) {
+    cudaGetLastError();
+    ctx->graphs_ok = false;
+    return nullptr;
+  }
+  cudaGraph_t graph = nullptr;
+  cudaGraphExec_t exec = nullptr;
+  bool ok = cudaStreamBeginCapture(ctx->cap_stream, cudaStreamCaptureModeThreadLocal) == cudaSuccess;
+  for (int j = j0; ok && j < j1; ++j) ok = launches(j, ctx->cap_stream, false) == cudaSuccess;
+  const bool ended = cudaStreamEndCapture(ctx->cap_stream, &graph) == cudaSuccess;
+  ok = ok && ended && graph != nullptr && cudaGraphInstantiate(&exec, graph, 0) == cudaSuccess;
+  if (graph) cudaGraphDestroy(graph);
+  if (!ok) {
+    if (exec) cudaGraphExecDestroy(exec);
+    cudaGetLastError();
+    ctx->graphs_ok = false;  // launch directly from now on
+    return nullptr;
+  }
+  ctx->graphs.emplace(key, exec);
+  return exec;
+}
 
 
 cudaEvent_t pool_event(expdg_ctx* ctx) {
@@ -335,7 +384,7 @@ expdg_status phi_solve(expdg_ctx* ctx, const void* qt_T, double tau, const bool*
     }
     const int iop = cfg.iop;
     const double s0 = iop ? 1.0 / beta : 1.0;  // incomplete orthogonalisation: slot 0 holds beta v_0
-    RUN(ctx, EXPDG_K_VECTOR, 16.0 * N, launch_start(F, ctx->ks, ctx->U, ctx->w, N, P, eta, s0, s));
+    RUN(ctx, EXPDG_K_VECTOR, 16.0 * N, launch_start(F, ctx->ks, ctx->U, ctx->w, N, P, eta, s0, sigma * tau, s));
     const int limit = replay ? m_fix : cfg.m_max;
     int m_first = cfg.m_step;
     const bool first_sub = (sv == 0.0 && rejected == 0);
@@ -346,9 +395,14 @@ expdg_status phi_solve(expdg_ctx* ctx, const void* qt_T, double tau, const bool*
     bool accepted = false;
     int m_acc = 0;
     double err = 0.0;
-    for (int j = 0; j < limit; ++j) {
+    // One Arnoldi step j on stream ss: operator apply, then the two
+    // orthogonalisation passes.  The sub-step scalars come from KState (the
+    // start kernel wrote them), so a step's launches are the same for every
+    // sub-step and a run of steps can be replayed as a CUDA graph.
+    const double vb = 8.0 * (double)n_aug;  // one vector: FP64 or float-float pair
+    auto step_launches = [&](int j, cudaStream_t ss, bool counted) -> cudaError_t {
       DGArgs a = ctx->mesh;
-      set_alpha(a, sigma * tau);
+      a.scal = &ctx->ks->jv;
       a.q = qt_T;
       const Vec vj = ctx->U.at(j), vo = ctx->U.at(j + 1);
       if (F) {
@@ -366,7 +420,6 @@ expdg_status phi_solve(expdg_ctx* ctx, const void* qt_T, double tau, const bool*
       }
       if (P > 0) {
         a.paug = P;
-        a.eta = eta;
         if (F) {
           a.tail_h = vj.h + N;
           a.tail_l = vj.l + N;
@@ -382,23 +435,53 @@ expdg_status phi_solve(expdg_ctx* ctx, const void* qt_T, double tau, const bool*
           a.W_l[i] = ctx->b[i].l;
         }
       }
-      RUN(ctx, EXPDG_K_JV, (F ? 16.0 : 24.0) * N, launch_dg(ctx, true, a));
-      const double vb = 8.0 * (double)n_aug;  // one vector: FP64 or float-float pair
-      if (iop) {
-        const int nwin = std::min(iop, j + 1);
-        RUN(ctx, EXPDG_K_DOTS, (nwin + 1) * vb, launch_iom_dots(F, iop, ctx->ks, ctx->part, ctx->U, j, n_aug, s));
-        RUN(ctx, EXPDG_K_UPDATE, (nwin + 2) * vb,
-            launch_iom_update(F, iop, ctx->ks, ctx->part, ctx->U, j, n_aug, s));
-      } else {
-        RUN(ctx, EXPDG_K_DOTS, (j + 2) * vb, launch_dots(F, ctx->ks, ctx->part, ctx->U, j, n_aug, s));
-        RUN(ctx, EXPDG_K_UPDATE, (j + 4) * vb, launch_update(F, ctx->ks, ctx->part, ctx->U, j, n_aug, s));
+      const int nwin = iop ? std::min(iop, j + 1) : 0;
+      const double bytes[3] = {(F ? 16.0 : 24.0) * N, (iop ? nwin + 1 : j + 2) * vb, (iop ? nwin + 2 : j + 4) * vb};
+      auto l0 = [&]() { return launch_dg_on(ctx, true, a, ss); };
+      auto l1 = [&]() {
+        return iop ? launch_iom_dots(F, iop, ctx->ks, ctx->part, ctx->U, j, n_aug, ss)
+                   : launch_dots(F, ctx->ks, ctx->part, ctx->U, j, n_aug, ss);
+      };
+      auto l2 = [&]() {
+        return iop ? launch_iom_update(F, iop, ctx->ks, ctx->part, ctx->U, j, n_aug, ss)
+                   : launch_update(F, ctx->ks, ctx->part, ctx->U, j, n_aug, ss);
+      };
+      cudaError_t e;
+      if (counted) {  // direct launches, counted (and timed when profiling)
+        if ((e = run(ctx, EXPDG_K_JV, bytes[0], l0)) != cudaSuccess) return e;
+        if ((e = run(ctx, EXPDG_K_DOTS, bytes[1], l1)) != cudaSuccess) return e;
+        return run(ctx, EXPDG_K_UPDATE, bytes[2], l2);
       }
-      const int J = j + 1;
-      st->krylov_iters++;
-      st->jv_applies++;
-      const int m = J;
-      const bool check = replay ? (m == m_fix) : (m == cfg.m_max || (m >= m_first && m % cfg.m_step == 0));
-      if (!check) continue;
+      if ((e = l0()) != cudaSuccess) return e;
+      if ((e = l1()) != cudaSuccess) return e;
+      return l2();
+    };
+    auto due = [&](int m) {
+      return replay ? (m == m_fix) : (m == cfg.m_max || (m >= m_first && m % cfg.m_step == 0));
+    };
+    int j = 0;
+    while (j < limit) {
+      int m = j + 1;  // next error check (due at m == limit at the latest)
+      while (m < limit && !due(m)) ++m;
+      cudaGraphExec_t g = ctx->prof_on ? nullptr : segment_graph(ctx, j, m, P, step_launches);
+      if (g) {
+        CU(ctx, cudaGraphLaunch(g, s));
+        for (int jj = j; jj < m; ++jj) {  // count the replayed launches like direct ones
+          const int nwin = iop ? std::min(iop, jj + 1) : 0;
+          ctx->prof[EXPDG_K_JV].launches++;
+          ctx->prof[EXPDG_K_JV].bytes += (F ? 16.0 : 24.0) * N;
+          ctx->prof[EXPDG_K_DOTS].launches++;
+          ctx->prof[EXPDG_K_DOTS].bytes += (iop ? nwin + 1 : jj + 2) * vb;
+          ctx->prof[EXPDG_K_UPDATE].launches++;
+          ctx->prof[EXPDG_K_UPDATE].bytes += (iop ? nwin + 2 : jj + 4) * vb;
+        }
+      } else {
+        for (int jj = j; jj < m; ++jj) CU(ctx, step_launches(jj, s, true));
+      }
+      st->krylov_iters += m - j;
+      st->jv_applies += m - j;
+      j = m;
+      if (!due(m)) continue;
       // mixed form: the FP32 operator's rounding noise inflates Saad's estimate, so a
       // converged change between consecutive checks also accepts
       RUN(ctx, EXPDG_K_PHI, 8.0 * m * m, launch_phi(ctx->ks, m, beta, cfg.krylov_tol, replay ? 1 : 0, F ? 1 : 0, s));
@@ -699,6 +782,8 @@ expdg_status expdg_create(const expdg_config* cfg, expdg_ctx** out) {
 void expdg_destroy(expdg_ctx* ctx) {
   if (!ctx) return;
   if (ctx->stream) cudaStreamSynchronize(ctx->stream);
+  for (auto& kv : ctx->graphs) cudaGraphExecDestroy(kv.second);
+  if (ctx->cap_stream) cudaStreamDestroy(ctx->cap_stream);
   for (void* p : ctx->allocs) cudaFree(p);
   for (cudaEvent_t e : ctx->ev_pool) cudaEventDestroy(e);
   if (ctx->h_ks) cudaFreeHost(ctx->h_ks);

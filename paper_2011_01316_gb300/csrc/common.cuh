@@ -53,6 +53,16 @@ struct Tab {
 //   aug (Krylov augmented matrix, only when paug > 0):
 //     out      += eta * sum_{k=1}^{paug} (vs * tail[k-1]) * W[paug+1-k]
 //     out_tail  = J (vs * tail)   (upper shift; written by block 0)
+// Scalars of the operator applies of one Krylov sub-step, kept in device
+// memory (KState) so the launches of an Arnoldi segment do not change between
+// sub-steps (they are replayed as CUDA graphs).
+struct JvScalars {
+  double alpha;  // sigma tau
+  double eta;    // tail scale of the augmented matrix
+  float alpha_h; // alpha as float-float
+  float alpha_l;
+};
+
 struct DGArgs {
   const void* q;         // T*: residual state q, or linearisation state z of qt
   const void* v;         // T*: linear input vector (top part)
@@ -86,6 +96,7 @@ struct DGArgs {
   int dirichlet;         // zero Dirichlet data at both ends (1D Burgers)
   const double* src;     // residual: forcing added to R (FP64, N values) or nullptr
   int roe;               // Euler: Roe flux (the linearisation state then ends with sqrt(rho))
+  const JvScalars* scal; // linear: alpha and eta read from here instead of the fields above (or nullptr)
 };
 
 // A vector in the FP64 form (d) or the float-float form (h + l).
@@ -118,6 +129,7 @@ struct KState {
   double ucoef[MMAX + 1];   // z_k - (c/r) s_k: projection coefficients of the next vector
   double ycoef[MMAX + 1];   // beta * y_i for the final combination
   double yprev[MMAX + 1];   // y = exp(H_m) e_1 of the previous check (mixed-form rule)
+  JvScalars jv;             // alpha and eta of the current sub-step (written by the start kernel)
   double vscale[MMAX + 1];  // basis vector i = vscale_i * slot i (incomplete orthogonalisation; 1 otherwise)
   float vs_h[MMAX + 1];     // vscale as float-float pairs (mixed-form operator applies)
   float vs_l[MMAX + 1];
@@ -172,7 +184,7 @@ cudaError_t launch_ff_to_f64(double* out, Vec x, size_t n, cudaStream_t s);
 // Arnoldi start: u_0 = [b0; e_P / eta] (b0 null: zero top); clears the Krylov scalars;
 // vscale_0 = s0 (1 / beta for incomplete orthogonalisation, else 1), vscale_i = 1 for i > 0.
 cudaError_t launch_start(bool use_ff, KState* ks, Basis U, Vec b0, size_t N, int P, double eta, double s0,
-                         cudaStream_t s);
+                         double alpha, cudaStream_t s);
 // Arnoldi step j by classical Gram-Schmidt with delayed re-orthogonalisation
 // (DCGS2).  On entry basis slots 0..j-1 hold the orthonormal q_i, slot j the
 // once-orthogonalised u_j, slot j+1 the operator image w = A_hat u_j.

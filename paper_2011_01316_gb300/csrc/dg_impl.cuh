@@ -514,14 +514,17 @@ __device__ __forceinline__ void dg_group(const DGArgs& a, const Tab& tab, int e0
 
   const size_t base = (size_t)e * NP + n;
   const bool aug = LINEAR && a.paug > 0 && (FF ? a.tail_h != nullptr : a.tail_d != nullptr);
+  const bool dev = LINEAR && a.scal != nullptr;  // sub-step scalars in device memory
+  const double alpha = dev ? a.scal->alpha : a.alpha;
+  const double eta = dev ? a.scal->eta : a.eta;
   if constexpr (!FF) {
     const double vs = (LINEAR && a.vs_d != nullptr) ? *a.vs_d : 1.0;
-    const double scale = a.alpha * vs;
+    const double scale = alpha * vs;
     double cf[EXPDG_MAX_PHI];
     bool any = false;
 #pragma unroll
     for (int k = 0; k < EXPDG_MAX_PHI; ++k) {
-      cf[k] = (aug && k < a.paug) ? a.eta * vs * a.tail_d[k] : 0.0;
+      cf[k] = (aug && k < a.paug) ? eta * vs * a.tail_d[k] : 0.0;
       any |= (cf[k] != 0.0);
     }
 #pragma unroll
@@ -540,7 +543,7 @@ __device__ __forceinline__ void dg_group(const DGArgs& a, const Tab& tab, int e0
       for (int k = 0; k < a.paug; ++k) a.out_tail_d[k] = (k + 1 < a.paug) ? vs * a.tail_d[k + 1] : 0.0;
   } else {
     const ff vs = (LINEAR && a.vs_h != nullptr) ? ff{*a.vs_h, *a.vs_l} : ff{1.0f, 0.0f};
-    const ff scale = ff_mul(ff{a.alpha_h, a.alpha_l}, vs);
+    const ff scale = ff_mul(dev ? ff{a.scal->alpha_h, a.scal->alpha_l} : ff{a.alpha_h, a.alpha_l}, vs);
     ff cf[EXPDG_MAX_PHI];
     bool any = false;
 #pragma unroll
@@ -548,8 +551,8 @@ __device__ __forceinline__ void dg_group(const DGArgs& a, const Tab& tab, int e0
       cf[k] = ff{0.0f, 0.0f};
       if (aug && k < a.paug) {
         ff t = ff_mul(vs, ff{a.tail_h[k], a.tail_l[k]});
-        const float eta = (float)a.eta;  // a power of two: exact
-        cf[k] = ff{t.h * eta, t.l * eta};
+        const float etaf = (float)eta;  // a power of two: exact
+        cf[k] = ff{t.h * etaf, t.l * etaf};
       }
       any |= (cf[k].h != 0.0f);
     }

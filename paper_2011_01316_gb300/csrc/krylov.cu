@@ -255,7 +255,8 @@ __global__ void k_ff_to_f64(double* out, Vec x, size_t n) {
 }
 
 template <bool FF>
-__global__ void __launch_bounds__(NT) k_start(KState* ks, Vec u0, Vec b0, size_t N, int P, double eta, double s0) {
+__global__ void __launch_bounds__(NT) k_start(KState* ks, Vec u0, Vec b0, size_t N, int P, double eta, double s0,
+                                              double alpha) {
   using A = Acc<FF>;
   const bool present = FF ? (b0.h != nullptr) : (b0.d != nullptr);
   const size_t n_aug = N + P;
@@ -277,6 +278,10 @@ __global__ void __launch_bounds__(NT) k_start(KState* ks, Vec u0, Vec b0, size_t
       ks->vs_l[k] = f.l;
     }
     if (threadIdx.x == 0) {
+      ks->jv.alpha = alpha;
+      ks->jv.eta = eta;
+      ks->jv.alpha_h = (float)alpha;
+      ks->jv.alpha_l = (float)(alpha - (double)(float)alpha);
       ks->breakdown_at = 0;
       ks->mprev = 0;
       ks->accept = 0;
@@ -1307,12 +1312,12 @@ cudaError_t launch_ff_to_f64(double* out, Vec x, size_t n, cudaStream_t s) {
 }
 
 cudaError_t launch_start(bool use_ff, KState* ks, Basis U, Vec b0, size_t N, int P, double eta, double s0,
-                         cudaStream_t s) {
+                         double alpha, cudaStream_t s) {
   const int g = grid_for(N + P);
   if (use_ff)
-    k_start<true><<<g, NT, 0, s>>>(ks, U.at(0), b0, N, P, eta, s0);
+    k_start<true><<<g, NT, 0, s>>>(ks, U.at(0), b0, N, P, eta, s0, alpha);
   else
-    k_start<false><<<g, NT, 0, s>>>(ks, U.at(0), b0, N, P, eta, s0);
+    k_start<false><<<g, NT, 0, s>>>(ks, U.at(0), b0, N, P, eta, s0, alpha);
   return cudaGetLastError();
 }
 
