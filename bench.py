@@ -8,7 +8,7 @@ flux, EPI2 steps of dt = 0.05 with Krylov tolerance 1e-8.  One step = one
 residual, one adaptive augmented-Krylov phi_1 solve (Jv applies,
 orthogonalisation, phi(H) checks) and the state update.
 
-`value` times the mixed form (FP32 R/Jv, float-float Krylov basis and
+`value` times the mixed form (float-float R, FP32 Jv, float-float Krylov basis and
 orthogonalisation, FP64 phi(H) and FP64 state update) with incomplete
 orthogonalisation over the last 4 basis vectors (the procedure of KIOPS, the
 Krylov solver of the paper, Sec. 1 and 2.3), the production form; its relative
@@ -510,7 +510,7 @@ def main():
                 "warmup": args.warmup, "ms_per_step": 1e3 * t_max / args.steps, "higher_is_better": True,
                 "scaling": "weak", "vs_baseline": None, "dtype": "f32+ff(48-bit)+f64",
                 "data": "synthetic",
-                "config": {"workload": WORKLOAD, "precision": "mixed: FP32 R/Jv, float-float Krylov, FP64 phi(H)",
+                "config": {"workload": WORKLOAD, "precision": "mixed: float-float R, FP32 Jv, float-float Krylov, FP64 phi(H)",
                            "krylov": (f"incomplete orthogonalisation, window {CFG['iop']} (KIOPS)" if CFG["iop"]
                                       else "full Arnoldi (DCGS2)"),
                            "l2": "flushed between timed steps (512 MiB write)",

@@ -61,13 +61,14 @@ typedef enum { EXPDG_FLUX_LF = 0, EXPDG_FLUX_ROE = 1 } expdg_flux;
 
 /* Arithmetic of the operator applies (R, Jv) and of the Arnoldi process.
  *   EXPDG_FP64:  everything in FP64 (reference form).
- *   EXPDG_MIXED: Jv in FP32 (FP32 accumulation); expdg_residual in FP32;
+ *   EXPDG_MIXED: Jv in FP32 (FP32 accumulation); the residual R (in
+ *                expdg_residual and in every step) in float-float arithmetic;
  *                Krylov basis, inner products and orthogonalisation in
  *                float-float (pairs of FP32 numbers, 48-bit significand, FP32
  *                arithmetic with error-free transformations); phi(H) and the
- *                solution update in FP64.  Inside expdg_step / expdg_advance
- *                the stage residuals R(q^n), R(q2) are computed in FP64: their
- *                FP32 rounding noise would cost extra Arnoldi steps.
+ *                solution update in FP64.  An FP32 residual's rounding noise
+ *                would cost extra Arnoldi steps, FP64 arithmetic runs on
+ *                the slow FP64 pipe.
  *                On this GPU the FP64 pipe (and every f32<->f64 conversion)
  *                runs about 1/70 of the FP32 rate, so the streaming Krylov
  *                kernels avoid it. */
@@ -160,7 +161,7 @@ expdg_status expdg_set_source(expdg_ctx* ctx, const double* s);
 /* R(q): the DG right-hand side (Sec. 2.2, Eq. EXPO-SemiDiscretizedForm_ode;
  * strong collocated LGL form; LF flux with lambda = max(|u|) for Burgers,
  * Sec. 3.1, and max(|u.n| + a) for Euler, Sec. 5.1).  q, r: canonical layout.
- * In EXPDG_MIXED the arithmetic is FP32 (inputs and outputs stay FP64). */
+ * In EXPDG_MIXED the arithmetic is float-float (inputs and outputs stay FP64). */
 expdg_status expdg_residual(expdg_ctx* ctx, const double* q, double* r);
 
 /* L(qt) v: the frozen-flux linear DG operator (Sec. 2.2, Eq. linearflux, with
@@ -309,9 +310,9 @@ expdg_status expdg_probe_rates(expdg_rates* out);
  *     m * Ne * (p+1)^dim doubles in the canonical layout; host pointers are
  *     rejected with EXPDG_EINVAL.  cuda_stream: the stream to run on (NULL =
  *     legacy default stream); the call returns after that stream has finished.
- *   - Scratch (the FP32 state copy and float-float output of EXPDG_MIXED, and
+ *   - Scratch (the float-float state copy and output of EXPDG_MIXED, and
  *     the non-physical-state flag of both forms) is a fixed static device
- *     array of about 6 MiB that every GPU which loads the library keeps until
+ *     array of about 8 MiB that every GPU which loads the library keeps until
  *     the process exits.  EXPDG_MIXED is limited to
  *     EXPDG_NOALLOC_MAX_UNKNOWNS unknowns (larger sizes return EXPDG_EINVAL);
  *     EXPDG_FP64 has no size limit.

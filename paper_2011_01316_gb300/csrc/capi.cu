@@ -32,6 +32,7 @@ struct expdg_ctx {
   // FP32 buffers (mixed form)
   float* d_q32 = nullptr;
   float* d_q32b = nullptr;
+  float* d_qfx = nullptr;   // the state as interleaved float-float pairs (mixed-form residual)
   double* d_src = nullptr;  // forcing added to R (expdg_set_source), allocated on first use
   bool has_src = false;
   // linearisation state of the linear operator (compute form: float or double)
@@ -211,43 +212,37 @@ void set_alpha(DGArgs& a, double alpha) {
   a.alpha_l = (float)(alpha - (double)a.alpha_h);
 }
 
-// R(q) -> out.  q: FP64 state on device; mixed form converts it to FP32 first
-// (into q32).  out: Krylov storage form.
-cudaError_t residual_into(expdg_ctx* ctx, const double* q, float* q32, Vec out, double alpha) {
+// R(q) -> out (Krylov storage form), times alpha.  FP64 form: FP64 throughout.
+// Mixed form: the state is split once into float-float pairs and the residual
+// is computed in float-float arithmetic on the FP32 pipes (accurate to about
+// 1e-14 of the flux scale).  R of a smooth state is a small difference of
+// large fluxes: an FP32 residual (relative error 6e-5 on the 64^2 p = 4
+// vortex) puts broadband noise into the Krylov start vector that costs about
+// five extra Arnoldi steps; FP64 arithmetic runs on GB300's slow FP64 pipe.
+cudaError_t residual_into(expdg_ctx* ctx, const double* q, Vec out, double alpha) {
   DGArgs a = ctx->mesh;
   set_alpha(a, alpha);
   a.src = ctx->has_src ? ctx->d_src : nullptr;
   a.status = &ctx->ks->status;
-  if (ctx->ff) {
-    cudaError_t e = run(ctx, EXPDG_K_VECTOR, 12.0 * ctx->N, [&]() { return launch_to_f32(q32, q, ctx->N, ctx->stream); });
-    if (e != cudaSuccess) return e;
-    a.q = q32;
-    a.out_h = out.h;
-    a.out_l = out.l;
-  } else {
+  if (!ctx->ff) {
     a.q = q;
     a.out = out.d;
+    return run(ctx, EXPDG_K_RESIDUAL, 16.0 * ctx->N, [&]() { return launch_dg(ctx, false, a); });
   }
-  return run(ctx, EXPDG_K_RESIDUAL, (ctx->ff ? 12.0 : 16.0) * ctx->N, [&]() { return launch_dg(ctx, false, a); });
-}
-
-// R(q) for the exponential steps.  In the mixed form the residual is computed
-// in FP64 and stored as float-float: R of a smooth state is a small difference
-// of large fluxes, and its FP32 rounding (relative error 6e-5 on the 64^2
-// p = 4 vortex) puts broadband noise into the Krylov start vector that costs
-// about five extra Arnoldi steps; one FP64 residual per stage is cheaper.
-cudaError_t residual_for_step(expdg_ctx* ctx, const double* q, Vec out, double alpha) {
-  if (!ctx->ff) return residual_into(ctx, q, nullptr, out, alpha);
-  cudaError_t e;
-  DGArgs a = ctx->mesh;
-  set_alpha(a, alpha);
-  a.src = ctx->has_src ? ctx->d_src : nullptr;
-  a.status = &ctx->ks->status;
-  a.q = q;
-  a.out = ctx->d_t2;
-  e = run(ctx, EXPDG_K_RESIDUAL, 16.0 * ctx->N, [&]() { return launch_dg(ctx, false, a, false); });
+  cudaError_t e = run(ctx, EXPDG_K_VECTOR, 16.0 * ctx->N, [&]() { return launch_f64_to_fx(ctx->d_qfx, q, ctx->N, ctx->stream); });
   if (e != cudaSuccess) return e;
-  return run(ctx, EXPDG_K_VECTOR, 16.0 * ctx->N, [&]() { return launch_f64_to_ff(out, ctx->d_t2, ctx->N, ctx->stream); });
+  a.q = ctx->d_qfx;
+  a.out_h = out.h;
+  a.out_l = out.l;
+  return run(ctx, EXPDG_K_RESIDUAL, 16.0 * ctx->N, [&]() {
+    const int p = ctx->cfg.p, eq = ctx->cfg.eq;
+    switch (ctx->cfg.dim) {
+      case 1: return launch_dg_fx_1d(eq, p, a, ctx->tab, ctx->stream);
+      case 2: return launch_dg_fx_2d(eq, p, a, ctx->tab, ctx->stream);
+      case 3: return launch_dg_fx_3d(eq, p, a, ctx->tab, ctx->stream);
+    }
+    return cudaErrorInvalidValue;
+  });
 }
 
 // Linearisation state of qt (FP64, device) -> ctx->d_z, in compute form.
@@ -567,13 +562,13 @@ expdg_status step_dev(expdg_ctx* ctx, double* q, double dt, const Replay& rp, ex
   bool has[EXPDG_MAX_PHI + 1] = {false, false, false, false};
   const int scheme = ctx->cfg.scheme;
   if (scheme == EXPDG_EPI2) {
-    CU(ctx, residual_for_step(ctx, q, ctx->c[1], dt));
+    CU(ctx, residual_into(ctx, q, ctx->c[1], dt));
     st->residual_applies++;
     has[1] = true;
     return phi_solve(ctx, qt_T, dt, has, 1, dvec(q), dvec(q), 0, rp, st, trace, true);
   }
   // EXPRB32 / EXPRB42 share: R^n, stage 1, D_{n,2} = R(q2) - R^n - L (q2 - q)
-  CU(ctx, residual_for_step(ctx, q, ctx->rn, 1.0));
+  CU(ctx, residual_into(ctx, q, ctx->rn, 1.0));
   st->residual_applies++;
   const double a1 = (scheme == EXPDG_EXPRB32) ? dt : 0.75 * dt;
   {
@@ -585,7 +580,7 @@ expdg_status step_dev(expdg_ctx* ctx, double* q, double dt, const Replay& rp, ex
   expdg_status r = phi_solve(ctx, qt_T, a1, has, 1, dvec(q), dvec(ctx->d_q2), 0, rp, st, trace, true);
   if (r != EXPDG_OK) return r;
   // t1 = R(q2)
-  CU(ctx, residual_for_step(ctx, ctx->d_q2, ctx->t1, 1.0));
+  CU(ctx, residual_into(ctx, ctx->d_q2, ctx->t1, 1.0));
   st->residual_applies++;
   // t2 = q2 - q (FP64), t3 = L(q) t2
   {
@@ -667,7 +662,7 @@ size_t expdg_context_bytes(const expdg_config* cfg) {
   const size_t gran = (size_t)2 << 20;
   auto r = [&](size_t b) { return ((b + gran - 1) / gran) * gran; };
   size_t total = 5 * r(N * sizeof(double));                 // q, q2, t2, in, out
-  if (ff) total += 2 * r(N * sizeof(float));                // FP32 state copies
+  if (ff) total += 2 * r(N * sizeof(float)) + r(2 * N * sizeof(float));  // FP32 copies, float-float state
   total += r(N * (ff ? sizeof(float) : sizeof(double)));     // linearisation state
   const size_t nvec = 2 * (EXPDG_MAX_PHI + 1) + 4;          // c, b, w, rn, t1, t3
   total += nvec * (ff ? 2 * r(N * sizeof(float)) : r(N * sizeof(double)));
@@ -740,6 +735,7 @@ expdg_status expdg_create(const expdg_config* cfg, expdg_ctx** out) {
   if (ctx->ff) {
     ALLOC(dalloc(ctx, &ctx->d_q32, N));
     ALLOC(dalloc(ctx, &ctx->d_q32b, N));
+    ALLOC(dalloc(ctx, &ctx->d_qfx, 2 * N));
     float* z = nullptr;
     ALLOC(dalloc(ctx, &z, N));
     ctx->d_z = z;
@@ -876,10 +872,10 @@ expdg_status expdg_residual(expdg_ctx* ctx, const double* q, double* r) {
   double* rd = rdev ? r : ctx->d_out;
   CU(ctx, cudaMemsetAsync(&ctx->ks->status, 0, sizeof(int), ctx->stream));
   if (ctx->ff) {
-    CU(ctx, residual_into(ctx, qd, ctx->d_q32, ctx->t1, 1.0));
+    CU(ctx, residual_into(ctx, qd, ctx->t1, 1.0));
     RUN(ctx, EXPDG_K_VECTOR, 16.0 * ctx->N, launch_ff_to_f64(rd, ctx->t1, ctx->N, ctx->stream));
   } else {
-    CU(ctx, residual_into(ctx, qd, nullptr, dvec(rd), 1.0));
+    CU(ctx, residual_into(ctx, qd, dvec(rd), 1.0));
   }
   if (!rdev) CU(ctx, cudaMemcpyAsync(r, rd, ctx->N * sizeof(double), cudaMemcpyDeviceToHost, ctx->stream));
   return readback(ctx);

@@ -162,6 +162,14 @@ cudaError_t launch_dg_3d(bool linear, bool fp32, int eq, int p, const DGArgs& a,
 cudaError_t launch_dg_roe_1d(bool linear, bool fp32, int p, const DGArgs& a, const Tab& t, cudaStream_t s);
 cudaError_t launch_dg_roe_2d(bool linear, bool fp32, int p, const DGArgs& a, const Tab& t, cudaStream_t s);
 cudaError_t launch_dg_roe_3d(bool linear, bool fp32, int p, const DGArgs& a, const Tab& t, cudaStream_t s);
+// Residual in float-float (a.q: interleaved float-float state, out_h / out_l):
+// the mixed form's R, FP64-grade on the FP32 pipes.
+cudaError_t launch_dg_fx_1d(int eq, int p, const DGArgs& a, const Tab& t, cudaStream_t s);
+cudaError_t launch_dg_fx_2d(int eq, int p, const DGArgs& a, const Tab& t, cudaStream_t s);
+cudaError_t launch_dg_fx_3d(int eq, int p, const DGArgs& a, const Tab& t, cudaStream_t s);
+cudaError_t launch_dg_roe_fx_1d(int p, const DGArgs& a, const Tab& t, cudaStream_t s);
+cudaError_t launch_dg_roe_fx_2d(int p, const DGArgs& a, const Tab& t, cudaStream_t s);
+cudaError_t launch_dg_roe_fx_3d(int p, const DGArgs& a, const Tab& t, cudaStream_t s);
 // Euler: z = (u, H, a), or (u, H, sqrt(rho)) with roe.
 cudaError_t launch_linstate_1d(int eq, bool fp32, const double* q, void* z, size_t stride, double gamma, int roe,
                                cudaStream_t s);
@@ -181,6 +189,8 @@ cudaError_t launch_norms(bool use_ff, KState* ks, void* part, int nx, const Vec*
 cudaError_t launch_to_f32(float* out, const double* x, size_t n, cudaStream_t s);
 cudaError_t launch_f64_to_ff(Vec out, const double* x, size_t n, cudaStream_t s);
 cudaError_t launch_ff_to_f64(double* out, Vec x, size_t n, cudaStream_t s);
+// FP64 -> interleaved float-float pairs (out[2i], out[2i+1] = high, low part)
+cudaError_t launch_f64_to_fx(float* out, const double* x, size_t n, cudaStream_t s);
 // Arnoldi start: u_0 = [b0; e_P / eta] (b0 null: zero top); clears the Krylov scalars;
 // vscale_0 = s0 (1 / beta for incomplete orthogonalisation, else 1), vscale_i = 1 for i > 0.
 cudaError_t launch_start(bool use_ff, KState* ks, Basis U, Vec b0, size_t N, int P, double eta, double s0,

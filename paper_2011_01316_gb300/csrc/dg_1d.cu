@@ -17,4 +17,11 @@ cudaError_t launch_linstate_1d(int eq, bool fp32, const double* q, void* z, size
   return cudaErrorInvalidValue;
 }
 
+cudaError_t launch_dg_fx_1d(int eq, int p, const DGArgs& a, const Tab& t, cudaStream_t s) {
+  if (eq == EXPDG_BURGERS) return launch_dg_fx_dim<1, EXPDG_BURGERS>(p, a, t, s);
+  if (eq == EXPDG_EULER && a.roe) return launch_dg_roe_fx_1d(p, a, t, s);
+  if (eq == EXPDG_EULER) return launch_dg_fx_dim<1, EXPDG_EULER>(p, a, t, s);
+  return cudaErrorInvalidValue;
+}
+
 }  // namespace expdg

@@ -15,4 +15,10 @@ cudaError_t launch_linstate_2d(int eq, bool fp32, const double* q, void* z, size
   return cudaErrorInvalidValue;
 }
 
+cudaError_t launch_dg_fx_2d(int eq, int p, const DGArgs& a, const Tab& t, cudaStream_t s) {
+  if (eq == EXPDG_EULER && a.roe) return launch_dg_roe_fx_2d(p, a, t, s);
+  if (eq == EXPDG_EULER) return launch_dg_fx_dim<2, EXPDG_EULER>(p, a, t, s);
+  return cudaErrorInvalidValue;
+}
+
 }  // namespace expdg

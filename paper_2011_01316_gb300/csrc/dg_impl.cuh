@@ -24,6 +24,7 @@
 
 #include "common.cuh"
 #include "ff.cuh"
+#include "fx.cuh"
 
 namespace expdg {
 
@@ -413,10 +414,6 @@ __host__ __device__ constexpr int visc_smem_entries() {
   return (DIM == 1 && EQ == EXPDG_BURGERS) ? 2 * ((elems_per_block<1, P>() + 2) * (P + 1) + 2) : 0;
 }
 
-// LINEAR = false: residual R(q), a.q = q.  LINEAR = true: linear operator,
-// a.q = the linearisation state z of qt (k_linstate), a.v = v.
-// T = double: FP64 form (double in, double out); T = float: mixed form (float
-// in, float-float out).
 // Shared-memory layout of the DG kernels (T units, then ints).
 template <int DIM, int P, int EQ, typename T>
 struct DgSmem {
@@ -441,6 +438,11 @@ struct DgSmem {
 // One element group (the EPB elements from e0) of the DG operator; sD must
 // hold the derivative matrix.  Every thread of the CTA calls it (it
 // synchronises the CTA); trigger: signal dependent launches after the fluxes.
+// LINEAR = false: residual R(q), a.q = q.  LINEAR = true: linear operator,
+// a.q = the linearisation state z of qt (k_linstate), a.v = v.
+// T = double: FP64 form (double in, double out); T = float: mixed form (float
+// in, float-float out); T = fx: float-float in and out (the mixed form's
+// residual: FP64-grade accuracy on the FP32 pipes).
 template <int DIM, int P, int EQ, typename T, bool LINEAR, bool ROE>
 __device__ __forceinline__ void dg_group(const DGArgs& a, const Tab& tab, int e0, const DgSmem<DIM, P, EQ, T>& sm,
                                          bool trigger) {
@@ -513,6 +515,18 @@ __device__ __forceinline__ void dg_group(const DGArgs& a, const Tab& tab, int e0
   acc[0] += visc;
 
   const size_t base = (size_t)e * NP + n;
+  if constexpr (std::is_same<T, fx>::value) {  // residual in float-float: out = alpha (R + s)
+    static_assert(!LINEAR, "the float-float kernels compute the residual");
+    const fx al(a.alpha_h, a.alpha_l);
+#pragma unroll
+    for (int f = 0; f < M; ++f) {
+      fx o = al * acc[f];
+      if (a.src != nullptr) o = o + fx(a.alpha * a.src[f * stride + base]);
+      a.out_h[f * stride + base] = o.h;
+      a.out_l[f * stride + base] = o.l;
+    }
+    return;
+  } else {
   const bool aug = LINEAR && a.paug > 0 && (FF ? a.tail_h != nullptr : a.tail_d != nullptr);
   const bool dev = LINEAR && a.scal != nullptr;  // sub-step scalars in device memory
   const double alpha = dev ? a.scal->alpha : a.alpha;
@@ -583,6 +597,7 @@ __device__ __forceinline__ void dg_group(const DGArgs& a, const Tab& tab, int e0
         a.out_tail_l[k] = t.l;
       }
   }
+  }
 }
 
 template <int DIM, int P, int EQ, typename T, bool LINEAR, bool ROE>
@@ -625,6 +640,12 @@ cudaError_t launch_dg_p(int p, const DGArgs& a, const Tab& t, cudaStream_t s) {
     case 8: return launch_dg_t<DIM, 8, EQ, T, LINEAR, ROE>(a, t, s);
     default: return cudaErrorInvalidValue;
   }
+}
+
+// Float-float residual (the mixed form's R).
+template <int DIM, int EQ, bool ROE = false>
+cudaError_t launch_dg_fx_dim(int p, const DGArgs& a, const Tab& t, cudaStream_t s) {
+  return launch_dg_p<DIM, EQ, fx, false, ROE>(p, a, t, s);
 }
 
 // ROE: the Roe-flux instantiations (Euler), built in their own translation units.

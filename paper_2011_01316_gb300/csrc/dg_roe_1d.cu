@@ -7,4 +7,8 @@ cudaError_t launch_dg_roe_1d(bool linear, bool fp32, int p, const DGArgs& a, con
   return launch_dg_dim<1, EXPDG_EULER, true>(linear, fp32, p, a, t, s);
 }
 
+cudaError_t launch_dg_roe_fx_1d(int p, const DGArgs& a, const Tab& t, cudaStream_t s) {
+  return launch_dg_fx_dim<1, EXPDG_EULER, true>(p, a, t, s);
+}
+
 }  // namespace expdg

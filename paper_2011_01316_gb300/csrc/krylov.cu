@@ -1305,6 +1305,21 @@ cudaError_t launch_f64_to_ff(Vec out, const double* x, size_t n, cudaStream_t s)
   k_f64_to_ff<<<grid_for(n), NT, 0, s>>>(out, x, n);
   return cudaGetLastError();
 }
+namespace {
+__global__ void k_f64_to_fx(float2* out, const double* x, size_t n) {
+  for (size_t i = blockIdx.x * (size_t)NT + threadIdx.x; i < n; i += (size_t)gridDim.x * NT) {
+    const ff f = ff_from_double(x[i]);
+    out[i] = make_float2(f.h, f.l);
+  }
+}
+}  // namespace
+
+cudaError_t launch_f64_to_fx(float* out, const double* x, size_t n, cudaStream_t s) {
+  if (n == 0) return cudaSuccess;
+  k_f64_to_fx<<<grid_for(n), NT, 0, s>>>(reinterpret_cast<float2*>(out), x, n);
+  return cudaGetLastError();
+}
+
 cudaError_t launch_ff_to_f64(double* out, Vec x, size_t n, cudaStream_t s) {
   if (n == 0) return cudaSuccess;
   k_ff_to_f64<<<grid_for(n), NT, 0, s>>>(out, x, n);

@@ -1,10 +1,10 @@
 // expdg_residual_noalloc: the residual R(q) without a context and without any
 // device allocation, for callers that cannot allocate device memory.
 //
-// Its scratch - the FP32 copy of the state and the float-float output of the
-// mixed form, and the non-physical-state flag of both forms - lives in the
-// file-scope arrays below.  Every GPU that loads this library holds them
-// (about 6 MiB) until the process exits.
+// Its scratch - the float-float copy of the state and the float-float output
+// of the mixed form, and the non-physical-state flag of both forms - lives in
+// the file-scope arrays below.  Every GPU that loads this library holds them
+// (about 8 MiB) until the process exits.
 #include <cstring>
 
 #include "common.cuh"
@@ -15,8 +15,9 @@ namespace {
 constexpr size_t kMaxUnknowns = (size_t)1 << 19;  // EXPDG_NOALLOC_MAX_UNKNOWNS
 constexpr int kMaxDevices = 64;
 
-// [0, kMax): FP32 state; [kMax, 2 kMax): residual hi; [2 kMax, 3 kMax): residual lo
-static __device__ __align__(256) float g_scratch[3 * kMaxUnknowns];
+// [0, 2 kMax): float-float state (interleaved pairs); [2 kMax, 3 kMax): residual
+// hi; [3 kMax, 4 kMax): residual lo
+static __device__ __align__(256) float g_scratch[4 * kMaxUnknowns];
 static __device__ __align__(256) int g_status[64];
 
 // Device addresses of the arrays, per device ordinal (the host-side names of
@@ -114,26 +115,32 @@ extern "C" expdg_status expdg_residual_noalloc(const expdg_config* cfg, const do
 
   // the status word keeps the previous call's value: clear it first
   if (cudaMemsetAsync(ad->status, 0, sizeof(int), s) != cudaSuccess) return EXPDG_ECUDA;
-  float* q32 = ad->scratch;
-  float* rh = ad->scratch + kMaxUnknowns;
-  float* rl = ad->scratch + 2 * kMaxUnknowns;
+  float* qfx = ad->scratch;
+  float* rh = ad->scratch + 2 * kMaxUnknowns;
+  float* rl = ad->scratch + 3 * kMaxUnknowns;
   cudaError_t e = cudaSuccess;
-  if (mixed) {
-    e = launch_to_f32(q32, q, N, s);
-    a.q = q32;
+  if (mixed) {  // float-float residual, as expdg_residual computes it in the mixed form
+    e = launch_f64_to_fx(qfx, q, N, s);
+    a.q = qfx;
     a.out_h = rh;
     a.out_l = rl;
+    if (e == cudaSuccess) {
+      if (dim == 1)
+        e = launch_dg_fx_1d(cfg->eq, p, a, tab, s);
+      else if (dim == 2)
+        e = launch_dg_fx_2d(cfg->eq, p, a, tab, s);
+      else
+        e = launch_dg_fx_3d(cfg->eq, p, a, tab, s);
+    }
   } else {
     a.q = q;
     a.out = r;
-  }
-  if (e == cudaSuccess) {
     if (dim == 1)
-      e = launch_dg_1d(false, mixed, cfg->eq, p, a, tab, s);
+      e = launch_dg_1d(false, false, cfg->eq, p, a, tab, s);
     else if (dim == 2)
-      e = launch_dg_2d(false, mixed, cfg->eq, p, a, tab, s);
+      e = launch_dg_2d(false, false, cfg->eq, p, a, tab, s);
     else
-      e = launch_dg_3d(false, mixed, cfg->eq, p, a, tab, s);
+      e = launch_dg_3d(false, false, cfg->eq, p, a, tab, s);
   }
   if (e == cudaSuccess && mixed) {
     Vec v{};

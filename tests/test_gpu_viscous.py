@@ -58,11 +58,11 @@ def test_viscous_residual_and_jv_fp64(E, case):
 
 @pytest.mark.parametrize("case", list(CASES))
 def test_viscous_residual_mixed(E, case):
-    """FP32 residual (relative to the size of the terms it sums)."""
+    """Float-float residual (relative to the size of the terms it sums)."""
     ctx, mesh, q = make(E, case, prec=1)
     ref = dg.residual(mesh, q)
     scale = np.max(np.abs(ref)) + mesh.kappa * (2.0 / mesh.h[0]) ** 2 * (mesh.p + 1) ** 4 * np.max(np.abs(q))
-    assert np.max(np.abs(ctx.residual(q) - ref)) <= 1e-6 * scale
+    assert np.max(np.abs(ctx.residual(q) - ref)) <= 1e-13 * scale
 
 
 @pytest.mark.parametrize("iop", [0, 4])
