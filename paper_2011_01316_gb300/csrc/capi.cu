@@ -408,11 +408,6 @@ expdg_status phi_solve(expdg_ctx* ctx, const void* qt_T, double tau, const bool*
         a.v = vj.d;
         a.out = vo.d;
       }
-      if (iop) {  // slot j holds v_j / vscale_j
-        a.vs_d = &ctx->ks->vscale[j];
-        a.vs_h = &ctx->ks->vs_h[j];
-        a.vs_l = &ctx->ks->vs_l[j];
-      }
       if (P > 0) {
         a.paug = P;
         if (F) {
@@ -479,7 +474,9 @@ expdg_status phi_solve(expdg_ctx* ctx, const void* qt_T, double tau, const bool*
       if (!due(m)) continue;
       // mixed form: the FP32 operator's rounding noise inflates Saad's estimate, so a
       // converged change between consecutive checks also accepts
-      RUN(ctx, EXPDG_K_PHI, 8.0 * m * m, launch_phi(ctx->ks, m, beta, cfg.krylov_tol, replay ? 1 : 0, F ? 1 : 0, s));
+      RUN(ctx, EXPDG_K_PHI, 8.0 * m * m,
+          launch_phi(ctx->ks, m, beta, cfg.krylov_tol, replay ? 1 : 0, F ? 1 : 0, iop ? ctx->part : nullptr, F ? 1 : 0,
+                     iop ? iom_update_blocks(F, iop, n_aug) : 0, s));
       rs = readback(ctx);
       if (rs != EXPDG_OK) return rs;
       if (ctx->h_ks->accept) {
@@ -703,18 +700,18 @@ expdg_status expdg_create(const expdg_config* cfg, expdg_ctx** out) {
   ctx->ld = ((ctx->N + EXPDG_MAX_PHI + 63) / 64) * 64;  // 256-byte aligned vectors
   double D[(MAXP + 1) * (MAXP + 1)];
   build_lgl(p, ctx->lgl_r, ctx->lgl_w, D);
-  for (int k = 0; k < (p + 1) * (p + 1); ++k) ctx->tab.D[k] = D[k];
-  ctx->tab.lift = 1.0 / ctx->lgl_w[0];
+  fill_tab(ctx->tab, D, p, 1.0 / ctx->lgl_w[0]);
   DGArgs& m = ctx->mesh;
   std::memset(&m, 0, sizeof(m));
   for (int d = 0; d < 3; ++d) {
     m.ne[d] = ctx->cfg.ne[d];
-    m.two_over_h[d] = 2.0 / ((ctx->cfg.hi[d] - ctx->cfg.lo[d]) / ctx->cfg.ne[d]);
+    m.two_over_h[d] = make_cst(2.0 / ((ctx->cfg.hi[d] - ctx->cfg.lo[d]) / ctx->cfg.ne[d]));
   }
   m.nelem = (int)ctx->nelem;
-  m.gamma = cfg->gamma;
+  m.gamma = make_cst(cfg->gamma);
   m.stride = ctx->nelem * ctx->NP;
-  m.kappa = cfg->kappa;
+  m.kappa = make_cst(cfg->kappa);
+  m.viscous = cfg->kappa != 0.0 ? 1 : 0;
   m.dirichlet = (cfg->bc == EXPDG_BC_DIRICHLET) ? 1 : 0;
   m.roe = (cfg->flux == EXPDG_FLUX_ROE) ? 1 : 0;
 

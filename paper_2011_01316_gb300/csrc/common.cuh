@@ -41,18 +41,44 @@ constexpr int DOT_CHUNK = 8;          // basis vectors per block row in the mult
 
 // Reference-element data handed to the DG kernels by value (kernel parameter
 // space is constant memory; the kernels copy D into shared memory).
-struct Tab {
-  double D[(MAXP + 1) * (MAXP + 1)];  // row-major l_j'(r_i) for the context's order
-  double lift;                        // 1 / w_0
+// A constant of the operator in the kernels' compute types: FP64 (d) and its
+// float-float split (h, the FP32 value, plus l).  Each kernel reads the form
+// of its own type, so no thread converts an FP64 constant on the narrow FP64
+// pipe (a conversion costs as much there as an FP64 multiply).
+struct Cst {
+  double d;
+  float h, l;
 };
+inline Cst make_cst(double x) {
+  const float h = (float)x;
+  return Cst{x, h, (float)(x - (double)h)};
+}
+
+struct Tab {
+  double D[(MAXP + 1) * (MAXP + 1)];   // row-major l_j'(r_i) for the context's order
+  float Dh[(MAXP + 1) * (MAXP + 1)];   // its float-float split
+  float Dl[(MAXP + 1) * (MAXP + 1)];
+  Cst lift;                            // 1 / w_0
+};
+
+// D (row-major, (p+1)^2 entries) and 1 / w_0 into a Tab, with their splits.
+inline void fill_tab(Tab& t, const double* D, int p, double lift) {
+  for (int k = 0; k < (p + 1) * (p + 1); ++k) {
+    const Cst c = make_cst(D[k]);
+    t.D[k] = c.d;
+    t.Dh[k] = c.h;
+    t.Dl[k] = c.l;
+  }
+  t.lift = make_cst(lift);
+}
 
 // Arguments of one DG operator apply.  T is the compute and input type
 // (double: FP64 form; float: mixed form, output as float-float pairs).
 //   residual: out = alpha * R(q)
-//   linear:   out = alpha * vs * L(q) v  +  aug,   vs = device scalar (or 1)
+//   linear:   out = alpha * L(q) v  +  aug
 //   aug (Krylov augmented matrix, only when paug > 0):
-//     out      += eta * sum_{k=1}^{paug} (vs * tail[k-1]) * W[paug+1-k]
-//     out_tail  = J (vs * tail)   (upper shift; written by block 0)
+//     out      += eta * sum_{k=1}^{paug} tail[k-1] * W[paug+1-k]
+//     out_tail  = J tail   (upper shift; written by block 0)
 // Scalars of the operator applies of one Krylov sub-step, kept in device
 // memory (KState) so the launches of an Arnoldi segment do not change between
 // sub-steps (they are replayed as CUDA graphs).
@@ -61,14 +87,12 @@ struct JvScalars {
   double eta;    // tail scale of the augmented matrix
   float alpha_h; // alpha as float-float
   float alpha_l;
+  float eta_f;   // eta in FP32 (a power of two: exact)
 };
 
 struct DGArgs {
   const void* q;         // T*: residual state q, or linearisation state z of qt
   const void* v;         // T*: linear input vector (top part)
-  const double* vs_d;    // FP64 form: device scalar multiplying v (nullptr: 1)
-  const float* vs_h;     // mixed form: float-float device scalar (nullptr: 1)
-  const float* vs_l;
   double alpha;
   float alpha_h;         // alpha as float-float (mixed form)
   float alpha_l;
@@ -77,6 +101,7 @@ struct DGArgs {
   float* out_l;
   int paug;
   double eta;
+  float eta_f;           // eta in FP32 (a power of two: exact)
   const double* tail_d;  // tail of the input basis vector (paug entries) or nullptr
   const float* tail_h;
   const float* tail_l;
@@ -89,10 +114,11 @@ struct DGArgs {
   int* status;           // bit 0: non-physical state met (residual)
   int ne[3];
   int nelem;
-  double two_over_h[3];
-  double gamma;
+  Cst two_over_h[3];
+  Cst gamma;
   size_t stride;         // unknowns per field = nelem * Np
-  double kappa;          // viscosity (1D Burgers; 0: inviscid)
+  Cst kappa;             // viscosity (1D Burgers; 0: inviscid)
+  int viscous;           // kappa != 0
   int dirichlet;         // zero Dirichlet data at both ends (1D Burgers)
   const double* src;     // residual: forcing added to R (FP64, N values) or nullptr
   int roe;               // Euler: Roe flux (the linearisation state then ends with sqrt(rho))
@@ -131,8 +157,7 @@ struct KState {
   double yprev[MMAX + 1];   // y = exp(H_m) e_1 of the previous check (mixed-form rule)
   JvScalars jv;             // alpha and eta of the current sub-step (written by the start kernel)
   double vscale[MMAX + 1];  // basis vector i = vscale_i * slot i (incomplete orthogonalisation; 1 otherwise)
-  float vs_h[MMAX + 1];     // vscale as float-float pairs (mixed-form operator applies)
-  float vs_l[MMAX + 1];
+  double wnp[2];            // ||A_hat slot_j|| by the parity of j (incomplete orthogonalisation)
   int mprev;                // m of the previous check (0: none)
   int pad2;
   double cu;                // c / r (coefficient of u_j in the next vector)
@@ -220,11 +245,17 @@ cudaError_t launch_iom_dots(bool use_ff, int iop, KState* ks, void* part, Basis 
                             cudaStream_t s);
 cudaError_t launch_iom_update(bool use_ff, int iop, KState* ks, void* part, Basis U, int j, size_t n_aug,
                               cudaStream_t s);
+// Blocks of an incomplete-orthogonalisation update launch (0 for an invalid iop).
+int iom_update_blocks(bool use_ff, int iop, size_t n_aug);
 // FP64 phi kernel: E = exp(H_m) (Taylor-18 scaling and squaring), y = E e_1, error estimate,
 // acceptance (forced when force_accept), ycoef_i = beta y_i vscale_i.  Acceptance: Saad's
 // estimate beta h_{m+1,m} |y_m| <= tol beta; with diff_rule also when the change
 // from the previous check, beta |y - [y_prev; 0]|, is <= tol beta.
+// iom_part: the reduction scratch when the basis comes from incomplete
+// orthogonalisation (h_{m,m-1} is then finished from the last update launch's
+// partials; iom_gu = that launch's blocks, iom_ff its precision), else nullptr.
 cudaError_t launch_phi(KState* ks, int m, double beta, double tol, int force_accept, int diff_rule,
+                       const void* iom_part, int iom_ff, int iom_gu,
                        cudaStream_t s);
 // out = base + sum_{i < m_eff} ycoef_i u_i (first N entries; base may be null).
 // out and base may each be FP64 (d) or float-float (h, l).

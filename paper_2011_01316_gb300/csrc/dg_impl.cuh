@@ -28,6 +28,22 @@
 
 namespace expdg {
 
+// A constant (or an entry of D) in the compute type T.
+template <typename T>
+__device__ __forceinline__ T cst(const Cst& c);
+template <>
+__device__ __forceinline__ double cst<double>(const Cst& c) { return c.d; }
+template <>
+__device__ __forceinline__ float cst<float>(const Cst& c) { return c.h; }
+template <>
+__device__ __forceinline__ fx cst<fx>(const Cst& c) { return fx(c.h, c.l); }
+template <typename T>
+__device__ __forceinline__ T d_entry(const Tab& t, int k) {
+  if constexpr (std::is_same<T, double>::value) return t.D[k];
+  else if constexpr (std::is_same<T, float>::value) return t.Dh[k];
+  else return fx(t.Dh[k], t.Dl[k]);
+}
+
 template <int DIM, int EQ>
 struct NFields {
   static constexpr int value = (EQ == EXPDG_BURGERS) ? 1 : DIM + 2;
@@ -267,7 +283,7 @@ __device__ __forceinline__ void node_terms(const DGArgs& a, T lift, const T* __r
   constexpr int NP1 = P + 1, NP = ipow(NP1, DIM), M = NFields<DIM, EQ>::value;
   constexpr int SLOT = elems_per_block<DIM, P>() * NP, NF = 2 * DIM;
   using PH = Phys<DIM, EQ, T>;
-  const T gamma = (T)a.gamma, gm1 = gamma - T(1);
+  const T gamma = cst<T>(a.gamma), gm1 = gamma - T(1);
   const size_t stride = a.stride;
   int ii[DIM];
   {
@@ -283,7 +299,7 @@ __device__ __forceinline__ void node_terms(const DGArgs& a, T lift, const T* __r
 #pragma unroll
   for (int d = 0; d < DIM; ++d) {
     const int sd = (d == 0) ? 1 : (d == 1 ? NP1 : NP1 * NP1);
-    const T c2h = (T)a.two_over_h[d];
+    const T c2h = cst<T>(a.two_over_h[d]);
     const int lbase = tid - ii[d] * sd;
     const T* Drow = sD + ii[d] * NP1;
 #pragma unroll
@@ -358,7 +374,7 @@ __device__ T visc_term(const DGArgs& a, const T* __restrict__ uin, const T* sD, 
   constexpr int EPB = elems_per_block<1, P>();
   constexpr int NH = (EPB + 2) * NP1;  // halo slots: elements e0 - 1 .. e0 + EPB
   const int ne = a.ne[0];
-  const T c2h = (T)a.two_over_h[0];
+  const T c2h = cst<T>(a.two_over_h[0]);
   auto elem_val = [&](int ge, int i) -> T {  // u at node i of element ge (periodic / zero outside)
     if (ge < 0 || ge >= ne) {
       if (a.dirichlet) return T(0);
@@ -405,7 +421,7 @@ __device__ T visc_term(const DGArgs& a, const T* __restrict__ uin, const T* sD, 
     const T qs = (a.dirichlet && e == ne - 1) ? qP : T(0.5) * (qP + qo);
     r += c2h * lift * (qs - qP);
   }
-  return (T)a.kappa * r;
+  return cst<T>(a.kappa) * r;
 }
 
 // Extra shared memory of the 1D Burgers kernels (the viscous halo), in T units.
@@ -465,7 +481,7 @@ __device__ __forceinline__ void dg_group(const DGArgs& a, const Tab& tab, int e0
   const int n = tid - le * NP;
   const int e = e0 + le;
   const bool active = (tid < SLOT) && (e < a.nelem);
-  const T gamma = (T)a.gamma;
+  const T gamma = cst<T>(a.gamma);
   const T gm1 = gamma - T(1);
   const size_t stride = a.stride;
   const T* __restrict__ qin = static_cast<const T*>(a.q);
@@ -504,13 +520,13 @@ __device__ __forceinline__ void dg_group(const DGArgs& a, const Tab& tab, int e0
   T visc = T(0);
   if constexpr (DIM == 1 && EQ == EXPDG_BURGERS) {
     constexpr int NH2 = visc_smem_entries<DIM, P, EQ>() / 2;
-    if (a.kappa != 0.0)  // uniform
-      visc = visc_term<P, T>(a, LINEAR ? vin : qin, sD, (T)tab.lift, sV, sV + NH2, e0, tid, le, n, active);
+    if (a.viscous)  // uniform
+      visc = visc_term<P, T>(a, LINEAR ? vin : qin, sD, cst<T>(tab.lift), sV, sV + NH2, e0, tid, le, n, active);
   }
   if (!active) return;  // no further synchronisation below
 
   T acc[M];
-  node_terms<DIM, P, EQ, T, LINEAR, ROE>(a, (T)tab.lift, qin, sF, sD, sNb, tid, le, n, qv, vv, w,
+  node_terms<DIM, P, EQ, T, LINEAR, ROE>(a, cst<T>(tab.lift), qin, sF, sD, sNb, tid, le, n, qv, vv, w,
                                     [&](int f, size_t gi) { return vin[f * stride + gi]; }, acc);
   acc[0] += visc;
 
@@ -529,16 +545,15 @@ __device__ __forceinline__ void dg_group(const DGArgs& a, const Tab& tab, int e0
   } else {
   const bool aug = LINEAR && a.paug > 0 && (FF ? a.tail_h != nullptr : a.tail_d != nullptr);
   const bool dev = LINEAR && a.scal != nullptr;  // sub-step scalars in device memory
-  const double alpha = dev ? a.scal->alpha : a.alpha;
-  const double eta = dev ? a.scal->eta : a.eta;
   if constexpr (!FF) {
-    const double vs = (LINEAR && a.vs_d != nullptr) ? *a.vs_d : 1.0;
-    const double scale = alpha * vs;
+    const double alpha = dev ? a.scal->alpha : a.alpha;
+    const double eta = dev ? a.scal->eta : a.eta;
+    const double scale = alpha;
     double cf[EXPDG_MAX_PHI];
     bool any = false;
 #pragma unroll
     for (int k = 0; k < EXPDG_MAX_PHI; ++k) {
-      cf[k] = (aug && k < a.paug) ? eta * vs * a.tail_d[k] : 0.0;
+      cf[k] = (aug && k < a.paug) ? eta * a.tail_d[k] : 0.0;
       any |= (cf[k] != 0.0);
     }
 #pragma unroll
@@ -554,18 +569,17 @@ __device__ __forceinline__ void dg_group(const DGArgs& a, const Tab& tab, int e0
       a.out[f * stride + base] = o;
     }
     if (aug && e0 == 0 && tid == 0)
-      for (int k = 0; k < a.paug; ++k) a.out_tail_d[k] = (k + 1 < a.paug) ? vs * a.tail_d[k + 1] : 0.0;
+      for (int k = 0; k < a.paug; ++k) a.out_tail_d[k] = (k + 1 < a.paug) ? a.tail_d[k + 1] : 0.0;
   } else {
-    const ff vs = (LINEAR && a.vs_h != nullptr) ? ff{*a.vs_h, *a.vs_l} : ff{1.0f, 0.0f};
-    const ff scale = ff_mul(dev ? ff{a.scal->alpha_h, a.scal->alpha_l} : ff{a.alpha_h, a.alpha_l}, vs);
+    const ff scale = dev ? ff{a.scal->alpha_h, a.scal->alpha_l} : ff{a.alpha_h, a.alpha_l};
     ff cf[EXPDG_MAX_PHI];
     bool any = false;
 #pragma unroll
     for (int k = 0; k < EXPDG_MAX_PHI; ++k) {
       cf[k] = ff{0.0f, 0.0f};
       if (aug && k < a.paug) {
-        ff t = ff_mul(vs, ff{a.tail_h[k], a.tail_l[k]});
-        const float etaf = (float)eta;  // a power of two: exact
+        const ff t{a.tail_h[k], a.tail_l[k]};
+        const float etaf = dev ? a.scal->eta_f : a.eta_f;
         cf[k] = ff{t.h * etaf, t.l * etaf};
       }
       any |= (cf[k].h != 0.0f);
@@ -592,7 +606,7 @@ __device__ __forceinline__ void dg_group(const DGArgs& a, const Tab& tab, int e0
     }
     if (aug && e0 == 0 && tid == 0)
       for (int k = 0; k < a.paug; ++k) {
-        ff t = (k + 1 < a.paug) ? ff_mul(vs, ff{a.tail_h[k + 1], a.tail_l[k + 1]}) : ff{0.0f, 0.0f};
+        const ff t = (k + 1 < a.paug) ? ff{a.tail_h[k + 1], a.tail_l[k + 1]} : ff{0.0f, 0.0f};
         a.out_tail_h[k] = t.h;
         a.out_tail_l[k] = t.l;
       }
@@ -606,7 +620,7 @@ k_dg(const DGArgs a, const Tab tab) {
   griddep_wait();
   extern __shared__ __align__(16) unsigned char smem_raw[];
   const DgSmem<DIM, P, EQ, T> sm(smem_raw);
-  for (int k = threadIdx.x; k < (P + 1) * (P + 1); k += blockDim.x) sm.sD[k] = (T)tab.D[k];
+  for (int k = threadIdx.x; k < (P + 1) * (P + 1); k += blockDim.x) sm.sD[k] = d_entry<T>(tab, k);
   dg_group<DIM, P, EQ, T, LINEAR, ROE>(a, tab, blockIdx.x * elems_per_block<DIM, P>(), sm, true);
 }
 

@@ -270,16 +270,11 @@ __global__ void __launch_bounds__(NT) k_start(KState* ks, Vec u0, Vec b0, size_t
   }
   if (blockIdx.x == 0) {
     for (int k = threadIdx.x; k < (MMAX + 1) * MMAX; k += NT) ks->H[k] = 0.0;
-    for (int k = threadIdx.x; k <= MMAX; k += NT) {
-      const double v = (k == 0) ? s0 : 1.0;
-      const ff f = ff_from_double(v);
-      ks->vscale[k] = v;
-      ks->vs_h[k] = f.h;
-      ks->vs_l[k] = f.l;
-    }
+    for (int k = threadIdx.x; k <= MMAX; k += NT) ks->vscale[k] = (k == 0) ? s0 : 1.0;
     if (threadIdx.x == 0) {
       ks->jv.alpha = alpha;
       ks->jv.eta = eta;
+      ks->jv.eta_f = (float)eta;
       ks->jv.alpha_h = (float)alpha;
       ks->jv.alpha_l = (float)(alpha - (double)(float)alpha);
       ks->breakdown_at = 0;
@@ -770,49 +765,106 @@ __global__ void __launch_bounds__(NT, 3) k_update_ff(KState* ks, ff* part, Basis
 
 // ---- incomplete orthogonalisation (KIOPS's replacement for Arnoldi, Sec. 1) ----
 // Window of the last KW basis vectors.  Slot i holds an unnormalised vector,
-// v_i = vscale_i slot_i, so the normalisation costs no extra pass: the
-// operator apply of the next step takes vscale_{j+1} as its input scale and
-// the final combination folds it into its coefficients.  The window vectors
-// are mutually orthogonal in exact arithmetic, so one classical pass (all
-// window products at once, then one update) equals the modified sweep.
+// v_i = c_i slot_i with c_i = 1 / ||slot_i||, so the normalisation costs no
+// pass: the operator apply of step j takes slot_j as it is (w' = A_hat
+// slot_j = w / c_j), the update stores the unnormalised residual vector
+// slot_{j+1} = w_new = w - sum h_{i,j} v_i (so ||slot_{j+1}|| = h_{j+1,j}
+// stays the size of A_hat: no product of subdiagonals builds up in FP32),
+// and the final combination folds c_i into its coefficients.  The window vectors are
+// mutually orthogonal in exact arithmetic, so one classical pass (all window
+// products at once, then one update) equals the modified sweep.
+//
+// No launch of a step ends with a last-block reduction (a fence, a ticket and
+// one block summing every partial while the GPU idles): the window-products
+// launch only writes its per-block partial sums, and every block of the
+// update launch sums them itself, in the same order, so all blocks derive the
+// same coefficients; the update launch likewise leaves the partials of
+// ||slot_{j+1}||^2 to the next update launch (or to the phi kernel at a check).
 constexpr int IOP_MAX = EXPDG_MAX_IOP;
+// The update launches' norm partials follow the window products' partials in
+// the reduction scratch: two regions, by the parity of j.
+constexpr int IOM_UPD_OFF = (IOP_MAX + 1) * RB;
 
-// Last block of an incomplete-orthogonalisation dots launch.
+// Prologue of update launch j, in every block: sums the window products of
+// launch j (<slot_i, w'> for the window, then |w'|^2) and ||slot_j||^2 (the
+// partials of update launch j - 1), then
+//   c_j = 1 / ||slot_j||  (c_0: set by the start kernel),
+//   h_{j,j-1} = ||slot_j||, a breakdown when ||slot_j|| <= 1e-13 ||w_{j-1}||,
+//   h_{i,j} = c_i c_j <slot_i, w'>,
+// and the update slot_{j+1} = c_j w' + sum_i coef_i slot_i with
+//   coef_i = -c_j c_i^2 <slot_i, w'>.
+// Block 0 stores c_j, the H entries and ||w_j|| = c_j ||w'||.  Returns false
+// on a breakdown at j (then there is nothing to update).
 template <bool FF>
-__device__ void iom_dots_last_block(KState* ks, const typename Acc<FF>::T* part, int j, int lo, int nwin, int K,
-                                    int G) {
-  __shared__ double res[IOP_MAX + 1];
-  final_sums<FF>(part, K, G, res, red_stage<FF>());  // res[c] = <slot_{lo+c}, w>, res[K-1] = |w|^2
-  if ((int)threadIdx.x < nwin) {
-    const int i = lo + threadIdx.x;
-    const double sc = ks->vscale[i];
-    const double h = sc * res[threadIdx.x];
-    ks->H[j * (MMAX + 1) + i] = h;
-    ks->ucoef[threadIdx.x] = -h * sc;  // coefficient of slot_i in the update
+__device__ bool iom_prologue(KState* ks, const typename Acc<FF>::T* part, int j, int lo, int nwin, int K, int Gd,
+                             int Gu, double* coef /* shared, [IOP_MAX] */, double* cjs /* shared */) {
+  using A = Acc<FF>;
+  using T = typename A::T;
+  T* stage = red_stage<FF>();
+  __shared__ double res[IOP_MAX + 2];
+  __shared__ double cw[IOP_MAX];  // c_i of the window (c_j: computed below)
+  __shared__ double s_c0, s_wprev;
+  __shared__ int s_ok;
+  // every global load first (one round trip): partials, window scales, flags
+  const int nd = K * Gd, nu = (j > 0) ? Gu : 0;
+  const T* pu = part + IOM_UPD_OFF + ((j + 1) & 1) * RB;  // region of launch j - 1
+  for (int i = threadIdx.x; i < nd + nu; i += blockDim.x) {
+    const T* src = (i < nd) ? part + i : pu + (i - nd);
+    if constexpr (FF) {
+      const float2 t = __ldcg(reinterpret_cast<const float2*>(src));
+      stage[i] = ff{t.x, t.y};
+    } else {
+      stage[i] = __ldcg(src);
+    }
   }
+  if ((int)threadIdx.x < nwin) cw[threadIdx.x] = __ldcg(&ks->vscale[lo + threadIdx.x]);
+  if (threadIdx.x == 32) {
+    const int b = __ldcg(&ks->breakdown_at);
+    s_ok = (b > 0 && j >= b) ? 0 : 1;  // an earlier breakdown: nothing to do
+    s_c0 = __ldcg(&ks->vscale[0]);
+    s_wprev = __ldcg(&ks->wnp[(j + 1) & 1]);
+  }
+  __syncthreads();
+  if (!s_ok) return false;
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  const int rows = K + (j > 0 ? 1 : 0);
+  for (int k = w; k < rows; k += NW) {
+    const T* row = (k < K) ? stage + k * Gd : stage + nd;
+    const int G = (k < K) ? Gd : Gu;
+    T x = A::zero();
+    for (int g = lane; g < G; g += 32) x = A::add(x, row[g]);
+#pragma unroll
+    for (int off = 16; off > 0; off >>= 1) x = A::add(x, A::shfl(x, off));
+    if (lane == 0) res[k] = A::to_d(x);
+  }
+  __syncthreads();
   if (threadIdx.x == 0) {
-    ks->wnorm = sqrt(res[K - 1]);
-    ks->counter = 0;
+    bool ok = true;
+    double cj = s_c0;
+    if (j > 0) {
+      const double ns = sqrt(res[K]);
+      ok = !(ns <= 1e-13 * s_wprev || ns == 0.0);
+      cj = (ns > 0.0) ? 1.0 / ns : 0.0;
+      if (blockIdx.x == 0) {
+        ks->H[(j - 1) * (MMAX + 1) + j] = ns;
+        ks->vscale[j] = cj;
+        if (!ok && ks->breakdown_at == 0) ks->breakdown_at = j;
+      }
+    }
+    if (ok) {
+      for (int c = 0; c < nwin; ++c) {
+        const int i = lo + c;
+        const double ci = (i == j) ? cj : cw[c];
+        coef[c] = -cj * ci * ci * res[c];
+        if (blockIdx.x == 0) ks->H[j * (MMAX + 1) + i] = ci * cj * res[c];
+      }
+      if (blockIdx.x == 0) ks->wnp[j & 1] = cj * sqrt(res[K - 1]);
+    }
+    *cjs = cj;
+    s_ok = ok ? 1 : 0;
   }
-}
-
-// Last block of an incomplete-orthogonalisation update launch.
-template <bool FF>
-__device__ void iom_update_last_block(KState* ks, const typename Acc<FF>::T* part, int j, int G) {
-  __shared__ double res[1];
-  final_sums<FF>(part, 1, G, res, red_stage<FF>());
-  if (threadIdx.x == 0) {
-    const double h = sqrt(res[0]);
-    const bool brk = h <= 1e-13 * ks->wnorm || h == 0.0;
-    ks->H[j * (MMAX + 1) + j + 1] = h;
-    const double v = (h > 0.0) ? 1.0 / h : 0.0;
-    const ff f = ff_from_double(v);
-    ks->vscale[j + 1] = v;
-    ks->vs_h[j + 1] = f.h;
-    ks->vs_l[j + 1] = f.l;
-    if (brk && ks->breakdown_at == 0) ks->breakdown_at = j + 1;
-    ks->counter = 0;
-  }
+  __syncthreads();
+  return s_ok != 0;
 }
 
 // Float-float form: packed compensated products, four elements per thread
@@ -823,7 +875,7 @@ __global__ void __launch_bounds__(NT) k_iom_dots_ff(KState* ks, ff* part, Basis 
   constexpr int K = KW + 1;
   __shared__ ff sh[NW * K];
   __shared__ ff tot[K];
-  if (ks->breakdown_at > 0 && j >= ks->breakdown_at) return;
+  // (after a breakdown these partials are never read: no flag check up front)
   const int lo = max(0, j - KW + 1), nwin = j - lo + 1;
   float2 S[K], C[K];
 #pragma unroll
@@ -869,39 +921,66 @@ __global__ void __launch_bounds__(NT) k_iom_dots_ff(KState* ks, ff* part, Basis 
   const int G = gridDim.x;
   if (threadIdx.x < K) part[(size_t)threadIdx.x * G + blockIdx.x] = tot[threadIdx.x];
   griddep_launch();
-  if (last_block(&ks->counter, gridDim.x)) iom_dots_last_block<true>(ks, part, j, lo, nwin, K, G);
 }
 
 template <int KW>
-__global__ void __launch_bounds__(NT) k_iom_update_ff(KState* ks, ff* part, Basis U, int j, size_t n_aug) {
+__global__ void __launch_bounds__(NT) k_iom_update_ff(KState* ks, ff* part, Basis U, int j, size_t n_aug, int Gd) {
   griddep_wait();
   __shared__ float2 cf[KW];
+  __shared__ double coef[IOP_MAX];
+  __shared__ double cj;
+  __shared__ float2 cjf;
   __shared__ ff sh[NW];
   __shared__ ff tot[1];
-  if (ks->breakdown_at > 0 && j >= ks->breakdown_at) return;
   const int lo = max(0, j - KW + 1), nwin = j - lo + 1;
-  if ((int)threadIdx.x < nwin) {
-    const ff a = ff_from_double(ks->ucoef[threadIdx.x]);
-    cf[threadIdx.x] = make_float2(a.h, a.l);
-  }
-  __syncthreads();
-  float2 S = make_float2(0.f, 0.f), C = make_float2(0.f, 0.f);
   const size_t ld = U.ld, ng = n_aug / 4;
   float* __restrict__ Uh = U.h;
   float* __restrict__ Ul = U.l;
   const size_t tid = blockIdx.x * (size_t)NT + threadIdx.x, nthr = (size_t)gridDim.x * NT;
-  for (size_t g = tid; g < ng; g += nthr) {
-    const size_t o = 4 * g;
-    const float4 wh = *reinterpret_cast<const float4*>(Uh + (j + 1) * ld + o);
-    const float4 wl = *reinterpret_cast<const float4*>(Ul + (j + 1) * ld + o);
-    float4 xh[KW], xl[KW];
+  // the first trip's vectors are loaded before the prologue, so their latency
+  // overlaps the partial sums'
+  float4 pwh = make_float4(0.f, 0.f, 0.f, 0.f), pwl = pwh, pxh[KW], pxl[KW];
+  if (tid < ng) {
+    pwh = *reinterpret_cast<const float4*>(Uh + (j + 1) * ld + 4 * tid);
+    pwl = *reinterpret_cast<const float4*>(Ul + (j + 1) * ld + 4 * tid);
 #pragma unroll
     for (int c = 0; c < KW; ++c) {
-      const size_t vo = (size_t)(lo + (c < nwin ? c : 0)) * ld + o;
-      xh[c] = __ldg(reinterpret_cast<const float4*>(Uh + vo));
-      xl[c] = __ldg(reinterpret_cast<const float4*>(Ul + vo));
+      const size_t vo = (size_t)(lo + (c < nwin ? c : 0)) * ld + 4 * tid;
+      pxh[c] = __ldg(reinterpret_cast<const float4*>(Uh + vo));
+      pxl[c] = __ldg(reinterpret_cast<const float4*>(Ul + vo));
+    }
+  }
+  if (!iom_prologue<true>(ks, part, j, lo, nwin, KW + 1, Gd, gridDim.x, coef, &cj)) return;
+  if ((int)threadIdx.x < nwin) {
+    const ff a = ff_from_double(coef[threadIdx.x]);
+    cf[threadIdx.x] = make_float2(a.h, a.l);
+  }
+  if (threadIdx.x == 0) {
+    const ff a = ff_from_double(cj);
+    cjf = make_float2(a.h, a.l);
+  }
+  __syncthreads();
+  const float2 cjh = make_float2(cjf.x, cjf.x), cjl = make_float2(cjf.y, cjf.y);
+  float2 S = make_float2(0.f, 0.f), C = make_float2(0.f, 0.f);
+  for (size_t g = tid; g < ng; g += nthr) {
+    const size_t o = 4 * g;
+    float4 wh = pwh, wl = pwl, xh[KW], xl[KW];
+    if (g == tid) {
+#pragma unroll
+      for (int c = 0; c < KW; ++c) xh[c] = pxh[c], xl[c] = pxl[c];
+    } else {
+      wh = *reinterpret_cast<const float4*>(Uh + (j + 1) * ld + o);
+      wl = *reinterpret_cast<const float4*>(Ul + (j + 1) * ld + o);
+#pragma unroll
+      for (int c = 0; c < KW; ++c) {
+        const size_t vo = (size_t)(lo + (c < nwin ? c : 0)) * ld + o;
+        xh[c] = __ldg(reinterpret_cast<const float4*>(Uh + vo));
+        xl[c] = __ldg(reinterpret_cast<const float4*>(Ul + vo));
+      }
     }
     float2 uh0 = lo2(wh), uh1 = hi2(wh), ul0 = lo2(wl), ul1 = hi2(wl);
+    ff2_scale(uh0, ul0, cjh, cjl);  // w = c_j w'
+    ff2_scale(uh1, ul1, cjh, cjl);
 #pragma unroll
     for (int c = 0; c < KW; ++c)
       if (c < nwin) {
@@ -917,7 +996,7 @@ __global__ void __launch_bounds__(NT) k_iom_update_ff(KState* ks, ff* part, Basi
     dot2_acc(uh1, ul1, uh1, ul1, S, C);
   }
   for (size_t i = 4 * ng + tid; i < n_aug; i += nthr) {  // ragged end
-    ff x{Uh[(j + 1) * ld + i], Ul[(j + 1) * ld + i]};
+    ff x = ff_mul(ff{cjf.x, cjf.y}, ff{Uh[(j + 1) * ld + i], Ul[(j + 1) * ld + i]});
     for (int c = 0; c < nwin; ++c) {
       const size_t vo = (size_t)(lo + c) * ld + i;
       x = ff_fma(ff{cf[c].x, cf[c].y}, ff{Uh[vo], Ul[vo]}, x);
@@ -928,9 +1007,8 @@ __global__ void __launch_bounds__(NT) k_iom_update_ff(KState* ks, ff* part, Basi
   }
   ff v[1] = {dot2_value(S, C)};
   block_sum<true, 1>(v, sh, tot);
-  if (threadIdx.x == 0) part[blockIdx.x] = tot[0];
+  if (threadIdx.x == 0) part[IOM_UPD_OFF + (j & 1) * RB + blockIdx.x] = tot[0];
   griddep_launch();
-  if (last_block(&ks->counter, gridDim.x)) iom_update_last_block<true>(ks, part, j, gridDim.x);
 }
 
 // FP64 form: four elements per thread per trip, loads first.
@@ -940,7 +1018,6 @@ __global__ void __launch_bounds__(NT) k_iom_dots(KState* ks, double* part, Basis
   constexpr int K = KW + 1;
   __shared__ double sh[NW * K];
   __shared__ double tot[K];
-  if (ks->breakdown_at > 0 && j >= ks->breakdown_at) return;
   const int lo = max(0, j - KW + 1), nwin = j - lo + 1;
   double acc[K];
 #pragma unroll
@@ -971,19 +1048,17 @@ __global__ void __launch_bounds__(NT) k_iom_dots(KState* ks, double* part, Basis
   const int G = gridDim.x;
   if (threadIdx.x < K) part[(size_t)threadIdx.x * G + blockIdx.x] = tot[threadIdx.x];
   griddep_launch();
-  if (last_block(&ks->counter, gridDim.x)) iom_dots_last_block<false>(ks, part, j, lo, nwin, K, G);
 }
 
 template <int KW>
-__global__ void __launch_bounds__(NT) k_iom_update(KState* ks, double* part, Basis U, int j, size_t n_aug) {
+__global__ void __launch_bounds__(NT) k_iom_update(KState* ks, double* part, Basis U, int j, size_t n_aug, int Gd) {
   griddep_wait();
-  __shared__ double cf[KW];
+  __shared__ double cf[IOP_MAX];
   __shared__ double sh[NW];
   __shared__ double tot[1];
-  if (ks->breakdown_at > 0 && j >= ks->breakdown_at) return;
   const int lo = max(0, j - KW + 1), nwin = j - lo + 1;
-  if ((int)threadIdx.x < nwin) cf[threadIdx.x] = ks->ucoef[threadIdx.x];
-  __syncthreads();
+  __shared__ double cj;
+  if (!iom_prologue<false>(ks, part, j, lo, nwin, KW + 1, Gd, gridDim.x, cf, &cj)) return;
   double nrm[1] = {0.0};
   const size_t ng = n_aug / 4;
   const size_t tid = blockIdx.x * (size_t)NT + threadIdx.x, nthr = (size_t)gridDim.x * NT;
@@ -992,6 +1067,8 @@ __global__ void __launch_bounds__(NT) k_iom_update(KState* ks, double* part, Bas
     Quad<false> x[KW];
 #pragma unroll
     for (int c = 0; c < KW; ++c) x[c] = ldq<false>(U, lo + (c < nwin ? c : 0), g);
+#pragma unroll
+    for (int e = 0; e < 4; ++e) w.v[e] *= cj;  // w = c_j w'
 #pragma unroll
     for (int c = 0; c < KW; ++c)
       if (c < nwin)
@@ -1002,15 +1079,14 @@ __global__ void __launch_bounds__(NT) k_iom_update(KState* ks, double* part, Bas
     stq<false>(U, j + 1, g, w);
   }
   for (size_t i = 4 * ng + tid; i < n_aug; i += nthr) {
-    double w = ldb<false>(U, j + 1, i);
+    double w = cj * ldb<false>(U, j + 1, i);
     for (int c = 0; c < nwin; ++c) w = fma(cf[c], ldb<false>(U, lo + c, i), w);
     stb<false>(U, j + 1, i, w);
     nrm[0] = fma(w, w, nrm[0]);
   }
   block_sum<false, 1>(nrm, sh, tot);
-  if (threadIdx.x == 0) part[blockIdx.x] = tot[0];
+  if (threadIdx.x == 0) part[IOM_UPD_OFF + (j & 1) * RB + blockIdx.x] = tot[0];
   griddep_launch();
-  if (last_block(&ks->counter, gridDim.x)) iom_update_last_block<false>(ks, part, j, gridDim.x);
 }
 
 // Dense exponential of the m x m leading block of H: scaling and squaring,
@@ -1045,16 +1121,49 @@ __device__ void cl_matmul(cg::cluster_group& cl, const double* A, const double* 
 }
 
 __global__ void __cluster_dims__(PHI_CL, 1, 1) __launch_bounds__(PHI_NT)
-k_phi(KState* ks, int m_req, double beta, double tol, int force, int diff_rule) {
+k_phi(KState* ks, int m_req, double beta, double tol, int force, int diff_rule, const void* iom_part, int iom_ff,
+      int iom_gu) {
   cg::cluster_group cl = cg::this_cluster();
   extern __shared__ double sm[];
   __shared__ int s_m;
   __shared__ double s_norm;
+  __shared__ double s_hm;  // h_{m,m-1}
+  __shared__ int s_brk;
   if (threadIdx.x == 0) {
     const int b = ks->breakdown_at;
     s_m = (b > 0 && b < m_req) ? b : m_req;
+    s_brk = (b > 0 && b <= m_req) ? 1 : 0;
+    s_hm = ks->H[(s_m - 1) * (MMAX + 1) + s_m];
   }
   __syncthreads();
+  // Incomplete orthogonalisation: h_{m,m-1} = ||slot_m|| from the partials of
+  // the last update launch (every CTA sums them alike).
+  if (iom_part != nullptr && s_m == m_req && !s_brk) {
+    const int off = IOM_UPD_OFF + (((m_req - 1) & 1) ? RB : 0);
+    if (threadIdx.x < 32) {
+      double x = 0.0;
+      if (iom_ff) {
+        ff t{0.0f, 0.0f};
+        for (int g = threadIdx.x; g < iom_gu; g += 32) t = ff_add(t, static_cast<const ff*>(iom_part)[off + g]);
+        for (int o = 16; o > 0; o >>= 1) t = ff_add(t, ff_shfl_down(t, o));
+        x = ff_to_double(t);
+      } else {
+        for (int g = threadIdx.x; g < iom_gu; g += 32) x += static_cast<const double*>(iom_part)[off + g];
+        for (int o = 16; o > 0; o >>= 1) x += __shfl_down_sync(0xffffffffu, x, o);
+      }
+      if (threadIdx.x == 0) {
+        const double ns = sqrt(x);
+        const bool brk = ns <= 1e-13 * ks->wnp[(m_req - 1) & 1] || ns == 0.0;
+        s_hm = ns;
+        s_brk = brk ? 1 : 0;
+        if (cl.block_rank() == 0) {
+          ks->H[(m_req - 1) * (MMAX + 1) + m_req] = s_hm;
+          if (brk && ks->breakdown_at == 0) ks->breakdown_at = m_req;
+        }
+      }
+    }
+    __syncthreads();
+  }
   const int m = s_m, mm = m * m;
   double* X = sm;
   double* X2 = X + mm;
@@ -1130,8 +1239,8 @@ k_phi(KState* ks, int m_req, double beta, double tol, int force, int diff_rule) 
     if (threadIdx.x == 0) {
       double dsum = 0.0;
       for (int w = 0; w < PHI_NT / 32; ++w) dsum += s_d2[w];
-      const bool brk = ks->breakdown_at > 0 && ks->breakdown_at <= m;
-      const double hm = ks->H[(m - 1) * (MMAX + 1) + m];
+      const bool brk = s_brk != 0;
+      const double hm = s_hm;
       const double err = brk ? 0.0 : beta * hm * fabs(E[(m - 1) * m]);
       const double dif = (mp > 0) ? beta * sqrt(dsum) : 1.0 / 0.0;
       const bool ok = brk || err <= tol * beta || (diff_rule && dif <= tol * beta);
@@ -1389,29 +1498,41 @@ int one_wave(size_t need, size_t smem_max) {
 }
 
 template <int KW>
-cudaError_t iom_dots_kw(bool use_ff, KState* ks, void* part, Basis U, int j, size_t n_aug, cudaStream_t s) {
+int iom_dots_grid(bool use_ff, size_t n_aug) {
   const size_t need = (n_aug / 4 + NT - 1) / NT;
-  if (use_ff) {
-    const int g = one_wave<k_iom_dots_ff<KW>>(need, (size_t)(KW + 1) * RB * sizeof(ff));
-    return pdl_launch(k_iom_dots_ff<KW>, dim3(g), dim3(NT), (size_t)(KW + 1) * g * sizeof(ff), s, ks,
-                      static_cast<ff*>(part), U, j, n_aug);
-  }
-  const int g = one_wave<k_iom_dots<KW>>(need, (size_t)(KW + 1) * RB * sizeof(double));
-  return pdl_launch(k_iom_dots<KW>, dim3(g), dim3(NT), (size_t)(KW + 1) * g * sizeof(double), s, ks,
-                    static_cast<double*>(part), U, j, n_aug);
+  return use_ff ? one_wave<k_iom_dots_ff<KW>>(need, 0) : one_wave<k_iom_dots<KW>>(need, 0);
+}
+// the update's dynamic shared memory stages (KW + 1) Gd + Gu partials, Gd, Gu <= RB
+template <int KW>
+int iom_update_grid(bool use_ff, size_t n_aug) {
+  const size_t need = (n_aug / 4 + NT - 1) / NT;
+  const size_t smem = (size_t)(KW + 2) * RB * 8;
+  return use_ff ? one_wave<k_iom_update_ff<KW>>(need, smem) : one_wave<k_iom_update<KW>>(need, smem);
+}
+
+template <int KW>
+cudaError_t iom_dots_kw(bool use_ff, KState* ks, void* part, Basis U, int j, size_t n_aug, cudaStream_t s) {
+  const int g = iom_dots_grid<KW>(use_ff, n_aug);
+  if (use_ff)
+    return pdl_launch(k_iom_dots_ff<KW>, dim3(g), dim3(NT), 0, s, ks, static_cast<ff*>(part), U, j, n_aug);
+  return pdl_launch(k_iom_dots<KW>, dim3(g), dim3(NT), 0, s, ks, static_cast<double*>(part), U, j, n_aug);
 }
 
 template <int KW>
 cudaError_t iom_update_kw(bool use_ff, KState* ks, void* part, Basis U, int j, size_t n_aug, cudaStream_t s) {
-  const size_t need = (n_aug / 4 + NT - 1) / NT;
-  if (use_ff) {
-    const int g = one_wave<k_iom_update_ff<KW>>(need, (size_t)RB * sizeof(ff));
-    return pdl_launch(k_iom_update_ff<KW>, dim3(g), dim3(NT), (size_t)g * sizeof(ff), s, ks, static_cast<ff*>(part),
-                      U, j, n_aug);
-  }
-  const int g = one_wave<k_iom_update<KW>>(need, (size_t)RB * sizeof(double));
-  return pdl_launch(k_iom_update<KW>, dim3(g), dim3(NT), (size_t)g * sizeof(double), s, ks,
-                    static_cast<double*>(part), U, j, n_aug);
+  const int gd = iom_dots_grid<KW>(use_ff, n_aug), g = iom_update_grid<KW>(use_ff, n_aug);
+  const size_t smem = (size_t)((KW + 1) * gd + g) * 8;
+  static const cudaError_t configured = [] {
+    cudaError_t e = cudaFuncSetAttribute(k_iom_update_ff<KW>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         (int)((KW + 2) * RB * 8));
+    if (e == cudaSuccess)
+      e = cudaFuncSetAttribute(k_iom_update<KW>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)((KW + 2) * RB * 8));
+    return e;
+  }();
+  if (configured != cudaSuccess) return configured;
+  if (use_ff)
+    return pdl_launch(k_iom_update_ff<KW>, dim3(g), dim3(NT), smem, s, ks, static_cast<ff*>(part), U, j, n_aug, gd);
+  return pdl_launch(k_iom_update<KW>, dim3(g), dim3(NT), smem, s, ks, static_cast<double*>(part), U, j, n_aug, gd);
 }
 
 }  // namespace
@@ -1432,6 +1553,20 @@ cudaError_t launch_iom_dots(bool use_ff, int iop, KState* ks, void* part, Basis 
   }
 }
 
+int iom_update_blocks(bool use_ff, int iop, size_t n_aug) {
+  switch (iop) {
+    case 1: return iom_update_grid<1>(use_ff, n_aug);
+    case 2: return iom_update_grid<2>(use_ff, n_aug);
+    case 3: return iom_update_grid<3>(use_ff, n_aug);
+    case 4: return iom_update_grid<4>(use_ff, n_aug);
+    case 5: return iom_update_grid<5>(use_ff, n_aug);
+    case 6: return iom_update_grid<6>(use_ff, n_aug);
+    case 7: return iom_update_grid<7>(use_ff, n_aug);
+    case 8: return iom_update_grid<8>(use_ff, n_aug);
+    default: return 0;
+  }
+}
+
 cudaError_t launch_iom_update(bool use_ff, int iop, KState* ks, void* part, Basis U, int j, size_t n_aug,
                               cudaStream_t s) {
   if (j < 0 || j + 1 > MMAX) return cudaErrorInvalidValue;
@@ -1449,13 +1584,13 @@ cudaError_t launch_iom_update(bool use_ff, int iop, KState* ks, void* part, Basi
 }
 
 cudaError_t launch_phi(KState* ks, int m, double beta, double tol, int force_accept, int diff_rule,
-                       cudaStream_t s) {
+                       const void* iom_part, int iom_ff, int iom_gu, cudaStream_t s) {
   if (m < 1 || m > MMAX) return cudaErrorInvalidValue;
   const size_t smem = 6 * sizeof(double) * (size_t)m * m;
   static const cudaError_t configured =
       cudaFuncSetAttribute(k_phi, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)(6 * sizeof(double) * MMAX * MMAX));
   if (configured != cudaSuccess) return configured;
-  k_phi<<<PHI_CL, PHI_NT, smem, s>>>(ks, m, beta, tol, force_accept, diff_rule);
+  k_phi<<<PHI_CL, PHI_NT, smem, s>>>(ks, m, beta, tol, force_accept, diff_rule, iom_part, iom_ff, iom_gu);
   return cudaGetLastError();
 }
 

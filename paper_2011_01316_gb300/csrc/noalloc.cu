@@ -93,18 +93,18 @@ extern "C" expdg_status expdg_residual_noalloc(const expdg_config* cfg, const do
   Tab tab{};
   double rr[MAXP + 1], ww[MAXP + 1], D[(MAXP + 1) * (MAXP + 1)];
   build_lgl(p, rr, ww, D);
-  for (int k = 0; k < (p + 1) * (p + 1); ++k) tab.D[k] = D[k];
-  tab.lift = 1.0 / ww[0];
+  fill_tab(tab, D, p, 1.0 / ww[0]);
   DGArgs a;
   std::memset(&a, 0, sizeof(a));
   for (int d = 0; d < 3; ++d) {
     const bool used = d < dim;
     a.ne[d] = used ? cfg->ne[d] : 1;
-    a.two_over_h[d] = used ? 2.0 / ((cfg->hi[d] - cfg->lo[d]) / cfg->ne[d]) : 2.0;
+    a.two_over_h[d] = make_cst(used ? 2.0 / ((cfg->hi[d] - cfg->lo[d]) / cfg->ne[d]) : 2.0);
   }
   a.nelem = (int)nelem;
-  a.gamma = cfg->gamma;
-  a.kappa = cfg->kappa;
+  a.gamma = make_cst(cfg->gamma);
+  a.kappa = make_cst(cfg->kappa);
+  a.viscous = cfg->kappa != 0.0 ? 1 : 0;
   a.dirichlet = (cfg->bc == EXPDG_BC_DIRICHLET) ? 1 : 0;
   a.roe = (cfg->flux == EXPDG_FLUX_ROE) ? 1 : 0;
   a.stride = nelem * np;

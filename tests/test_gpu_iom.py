@@ -68,6 +68,10 @@ def test_phi_iom_adaptive_agrees(E, case, iop):
     ref, st = krylov.phi_sum(lambda x: tau * dg.jv(mesh, q, x).reshape(-1), c, tol=1e-10, iop=iop)
     got, gst, gtr = ctx.phi(q, tau, [None, np.ascontiguousarray(c[1])])
     assert rel(got, ref) <= 1e-9
+    # the same decisions: sub-steps, and Krylov dimensions within one check interval
+    assert len(gtr) == len(st.trace)
+    for (_, m, _, _), (_, mr, _) in zip(gtr, st.trace):
+        assert abs(m - mr) <= 5
 
 
 def test_phi_iom_substeps_parity(E):
@@ -142,8 +146,11 @@ def test_iom_vortex_full_size(E):
     full, _ = integrators.step(mesh, q, 0.05, tol=1e-10)
     ctx2, _ = make(E, "euler2d_full", 4, prec=1, tol=1e-8)
     got2 = q.copy()
-    ctx2.step(got2, 0.05)
+    st2, tr2 = ctx2.step(got2, 0.05)
     assert rel(got2, full) <= TOL_MIXED
+    # one sub-step of about the oracle's dimension (25 at tol 1e-10 with full
+    # orthogonalisation; the mixed form stops at a check interval of 5)
+    assert len(tr2) == 1 and tr2[0][1] <= 40
 
 
 def test_invalid_window_rejected(E):
