@@ -487,6 +487,35 @@ __device__ __forceinline__ void dg_group(const DGArgs& a, const Tab& tab, int e0
   const T* __restrict__ qin = static_cast<const T*>(a.q);
   const T* __restrict__ vin = static_cast<const T*>(a.v);
 
+  // Linear: the sub-step scalars (alpha, eta, the input's augmentation tail)
+  // are read here, so their latency overlaps the operator's instead of
+  // following it.  out = scale L v + sum_k cf_k W_{paug+1-k}.
+  const bool aug = LINEAR && a.paug > 0 && (FF ? a.tail_h != nullptr : a.tail_d != nullptr);
+  const bool dev = LINEAR && a.scal != nullptr;  // sub-step scalars in device memory
+  double d_scale = a.alpha, d_cf[EXPDG_MAX_PHI];
+  ff f_scale{a.alpha_h, a.alpha_l}, f_cf[EXPDG_MAX_PHI];
+  bool any = false;
+  if constexpr (LINEAR) {
+    if constexpr (!FF) {
+      const double eta = dev ? a.scal->eta : a.eta;
+      if (dev) d_scale = a.scal->alpha;
+#pragma unroll
+      for (int k = 0; k < EXPDG_MAX_PHI; ++k) {
+        d_cf[k] = (aug && k < a.paug) ? eta * a.tail_d[k] : 0.0;
+        any |= (d_cf[k] != 0.0);
+      }
+    } else {
+      const float etaf = dev ? a.scal->eta_f : a.eta_f;
+      if (dev) f_scale = ff{a.scal->alpha_h, a.scal->alpha_l};
+#pragma unroll
+      for (int k = 0; k < EXPDG_MAX_PHI; ++k) {
+        f_cf[k] = ff{0.0f, 0.0f};
+        if (aug && k < a.paug) f_cf[k] = ff{a.tail_h[k] * etaf, a.tail_l[k] * etaf};  // eta: a power of two
+        any |= (f_cf[k].h != 0.0f);
+      }
+    }
+  }
+
   T qv[M];  // residual: q at the node; linear: z at the node
   T vv[M];  // linear: v at the node
   typename PH::Prim w{};
@@ -543,19 +572,9 @@ __device__ __forceinline__ void dg_group(const DGArgs& a, const Tab& tab, int e0
     }
     return;
   } else {
-  const bool aug = LINEAR && a.paug > 0 && (FF ? a.tail_h != nullptr : a.tail_d != nullptr);
-  const bool dev = LINEAR && a.scal != nullptr;  // sub-step scalars in device memory
   if constexpr (!FF) {
-    const double alpha = dev ? a.scal->alpha : a.alpha;
-    const double eta = dev ? a.scal->eta : a.eta;
-    const double scale = alpha;
-    double cf[EXPDG_MAX_PHI];
-    bool any = false;
-#pragma unroll
-    for (int k = 0; k < EXPDG_MAX_PHI; ++k) {
-      cf[k] = (aug && k < a.paug) ? eta * a.tail_d[k] : 0.0;
-      any |= (cf[k] != 0.0);
-    }
+    const double scale = d_scale;
+    const double* cf = d_cf;
 #pragma unroll
     for (int f = 0; f < M; ++f) {
       double o = scale * (double)acc[f];
@@ -571,19 +590,8 @@ __device__ __forceinline__ void dg_group(const DGArgs& a, const Tab& tab, int e0
     if (aug && e0 == 0 && tid == 0)
       for (int k = 0; k < a.paug; ++k) a.out_tail_d[k] = (k + 1 < a.paug) ? a.tail_d[k + 1] : 0.0;
   } else {
-    const ff scale = dev ? ff{a.scal->alpha_h, a.scal->alpha_l} : ff{a.alpha_h, a.alpha_l};
-    ff cf[EXPDG_MAX_PHI];
-    bool any = false;
-#pragma unroll
-    for (int k = 0; k < EXPDG_MAX_PHI; ++k) {
-      cf[k] = ff{0.0f, 0.0f};
-      if (aug && k < a.paug) {
-        const ff t{a.tail_h[k], a.tail_l[k]};
-        const float etaf = dev ? a.scal->eta_f : a.eta_f;
-        cf[k] = ff{t.h * etaf, t.l * etaf};
-      }
-      any |= (cf[k].h != 0.0f);
-    }
+    const ff scale = f_scale;
+    const ff* cf = f_cf;
 #pragma unroll
     for (int f = 0; f < M; ++f) {
       // exact float * float-float product, then the augmentation in float-float
