@@ -51,9 +51,11 @@ CFG = dict(dim=2, p=4, ne=[64, 64, 1], lo=[0.0, 0.0, 0.0], hi=[10.0, 10.0, 1.0],
 DT = 0.05
 CLASSES = ["residual", "jv", "dots", "update", "phi", "combine", "vector"]
 # DRAM bytes per algorithmic byte of a kernel class on this workload, from one ncu
-# capture (profiles/ncu_vortex64_p4_kernels.md: k_iom_dots_ff<4>, 16.411648 MB read for
-# 16.384 MB algorithmic); used for roofline.traffic.  Refresh when the kernel changes.
-NCU_TRAFFIC_RATIO = {"dots": 16.411648 / 16.384}
+# capture each (profiles/ncu_vortex64_p4_kernels.md, full window: k_iom_update_ff<4>
+# 16.434432 MB read + 0 written for 6 x 3.276808 MB algorithmic, k_iom_dots_ff<4>
+# 16.402944 MB for 5 x 3.276808 MB); used for roofline.traffic.  Refresh when the
+# kernel changes.
+NCU_TRAFFIC_RATIO = {"update": 16.434432 / (6 * 3.276808), "dots": 16.402944 / (5 * 3.276808)}
 
 
 def max_over_ranks(x, world, device="cpu"):
