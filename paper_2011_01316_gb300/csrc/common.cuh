@@ -157,7 +157,8 @@ struct KState {
   double yprev[MMAX + 1];   // y = exp(H_m) e_1 of the previous check (mixed-form rule)
   JvScalars jv;             // alpha and eta of the current sub-step (written by the start kernel)
   double vscale[MMAX + 1];  // basis vector i = vscale_i * slot i (incomplete orthogonalisation; 1 otherwise)
-  double wnp[2];            // ||A_hat slot_j|| by the parity of j (incomplete orthogonalisation)
+  float2 vsf[MMAX + 1];     // vscale as float-float (h, l): the float-float update reads these
+  double wnp[2];            // ||w_j|| by the parity of j (incomplete orthogonalisation, breakdown scale)
   int mprev;                // m of the previous check (0: none)
   int pad2;
   double cu;                // c / r (coefficient of u_j in the next vector)
@@ -235,12 +236,14 @@ cudaError_t launch_dots(bool use_ff, KState* ks, void* part, Basis U, int j, siz
 cudaError_t launch_update(bool use_ff, KState* ks, void* part, Basis U, int j, size_t n_aug, cudaStream_t s);
 // Arnoldi step j by incomplete orthogonalisation over the window of the last
 // iop basis vectors, i = lo..j, lo = max(0, j - iop + 1) (1 <= iop <= EXPDG_MAX_IOP).
-// Slot i holds an unnormalised vector, v_i = vscale_i slot_i; on entry slot
-// j+1 holds w = A_hat v_j.
-//   iom_dots:   h_i = vscale_i <slot_i, w> -> H(i, j); |w| (breakdown scale).
-//   iom_update: slot j+1 = w - sum_i h_i v_i (in place); h = |slot j+1| ->
-//               H(j+1, j), vscale_{j+1} = 1 / h; happy breakdown when
-//               h <= 1e-13 |w|.
+// Slot i holds an unnormalised vector, v_i = c_i slot_i with c_i = vscale_i =
+// 1 / ||slot_i||; on entry slot j+1 holds w' = A_hat slot_j (= A_hat v_j / c_j).
+//   iom_dots:   per-block partial sums of <slot_i, w'> (window) and |w'|^2.
+//   iom_update: every block sums those and ||slot_j||^2 (the previous update's
+//               partials): c_j, H(j, j-1) = ||slot_j||, H(i, j) = c_i c_j <slot_i, w'>;
+//               slot j+1 = c_j w' - sum_i H(i, j) v_i (in place), per-block partials of
+//               its norm; happy breakdown when ||slot_j|| <= 1e-13 ||w_{j-1}||.
+//   gd: blocks of the window-products launch (0: as launch_iom_dots picks them).
 cudaError_t launch_iom_dots(bool use_ff, int iop, KState* ks, void* part, Basis U, int j, size_t n_aug,
                             cudaStream_t s);
 cudaError_t launch_iom_update(bool use_ff, int iop, KState* ks, void* part, Basis U, int j, size_t n_aug,

@@ -15,6 +15,7 @@
 
 #include "common.cuh"
 #include "ff.cuh"
+#include "fx.cuh"
 
 namespace cg = cooperative_groups;
 
@@ -270,7 +271,12 @@ __global__ void __launch_bounds__(NT) k_start(KState* ks, Vec u0, Vec b0, size_t
   }
   if (blockIdx.x == 0) {
     for (int k = threadIdx.x; k < (MMAX + 1) * MMAX; k += NT) ks->H[k] = 0.0;
-    for (int k = threadIdx.x; k <= MMAX; k += NT) ks->vscale[k] = (k == 0) ? s0 : 1.0;
+    for (int k = threadIdx.x; k <= MMAX; k += NT) {
+      const double v = (k == 0) ? s0 : 1.0;
+      const ff f = ff_from_double(v);
+      ks->vscale[k] = v;
+      ks->vsf[k] = make_float2(f.h, f.l);
+    }
     if (threadIdx.x == 0) {
       ks->jv.alpha = alpha;
       ks->jv.eta = eta;
@@ -867,6 +873,108 @@ __device__ bool iom_prologue(KState* ks, const typename Acc<FF>::T* part, int j,
   return s_ok != 0;
 }
 
+// Float-float form of iom_prologue: the same quantities, with every scalar
+// operation on the FP32 pipe (fx arithmetic: Dekker division and square
+// root), so the update's critical path carries no FP64 instruction (on GB300
+// one FP64 warp instruction holds the narrow FP64 pipe for tens of cycles,
+// active lanes or not).  cf[c] = coef_c as (h, l).  The FP64 copies for the
+// phi kernel (H entries, vscale_j, ||w_j||) are written after the update, one
+// item per block, by write_iom_scalars.
+struct IomScalars {
+  fx h[IOP_MAX];  // H(lo + c, j)
+  fx hsub;        // H(j, j-1) = ||slot_j||
+  fx cj;          // c_j
+  fx wn;          // ||w_j|| = c_j ||w'||
+  int ok;
+};
+// Returns -1 after an earlier breakdown (nothing to do), 0 on a breakdown at
+// j (to be recorded), 1 to update.
+__device__ int iom_prologue_ff(KState* ks, const ff* part, int j, int lo, int nwin, int K, int Gd, int Gu,
+                               float2* cf /* shared, [IOP_MAX] */, IomScalars* sc /* shared */) {
+  ff* stage = red_stage<true>();
+  __shared__ ff res[IOP_MAX + 2];
+  __shared__ float2 cw[IOP_MAX];  // c_i of the window (c_j: computed below)
+  __shared__ float2 s_c0;
+  __shared__ float s_wprev;
+  __shared__ int s_go;
+  const int nd = K * Gd, nu = (j > 0) ? Gu : 0;
+  const ff* pu = part + IOM_UPD_OFF + ((j + 1) & 1) * RB;  // region of launch j - 1
+  for (int i = threadIdx.x; i < nd + nu; i += blockDim.x) {
+    const ff* src = (i < nd) ? part + i : pu + (i - nd);
+    const float2 t = __ldcg(reinterpret_cast<const float2*>(src));
+    stage[i] = ff{t.x, t.y};
+  }
+  if ((int)threadIdx.x < nwin) cw[threadIdx.x] = __ldcg(&ks->vsf[lo + threadIdx.x]);
+  if (threadIdx.x == 32) {
+    const int b = __ldcg(&ks->breakdown_at);
+    s_go = (b > 0 && j >= b) ? 0 : 1;  // an earlier breakdown: nothing to do
+    s_c0 = __ldcg(&ks->vsf[0]);
+    s_wprev = (float)__ldcg(&ks->wnp[(j + 1) & 1]);
+  }
+  __syncthreads();
+  if (!s_go) return -1;
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  const int rows = K + (j > 0 ? 1 : 0);
+  for (int k = w; k < rows; k += NW) {
+    const ff* row = (k < K) ? stage + k * Gd : stage + nd;
+    const int G = (k < K) ? Gd : Gu;
+    ff x{0.0f, 0.0f};
+    for (int g = lane; g < G; g += 32) x = ff_add(x, row[g]);
+#pragma unroll
+    for (int off = 16; off > 0; off >>= 1) x = ff_add(x, ff_shfl_down(x, off));
+    if (lane == 0) res[k] = x;
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    bool ok = true;
+    fx cj(s_c0.x, s_c0.y), ns(0.0f, 0.0f);
+    if (j > 0) {
+      ns = sqrt(fx(res[K]));
+      ok = !(ns.h <= 1e-13f * s_wprev || ns.h == 0.0f);
+      cj = (ns.h > 0.0f) ? fx(1.0f) / ns : fx(0.0f, 0.0f);
+    }
+    sc->hsub = ns;
+    sc->cj = cj;
+    sc->wn = cj * sqrt(fx(res[K - 1]));
+    sc->ok = ok ? 1 : 0;
+    if (ok)
+      for (int c = 0; c < nwin; ++c) {
+        const int i = lo + c;
+        const fx ci = (i == j) ? cj : fx(cw[c].x, cw[c].y);
+        const fx h = ci * cj * fx(res[c]);
+        sc->h[c] = h;
+        const fx co = -(h * ci);
+        cf[c] = make_float2(co.h, co.l);
+      }
+  }
+  __syncthreads();
+  return sc->ok;
+}
+
+// The update's FP64 results for the phi kernel and the next launches, one item
+// per block (item k by block k mod gridDim.x): vscale_j (and its pair),
+// breakdown_at, H(j, j-1), ||w_j||, H(lo + c, j).
+__device__ void write_iom_scalars(KState* ks, const IomScalars& sc, int j, int lo, int nwin) {
+  if (threadIdx.x != 0) return;
+  const int items = 3 + nwin;
+  for (int k = blockIdx.x; k < items; k += gridDim.x) {
+    if (k == 0) {
+      if (j > 0) {
+        ks->vscale[j] = (double)sc.cj.h + (double)sc.cj.l;
+        ks->vsf[j] = make_float2(sc.cj.h, sc.cj.l);
+        if (!sc.ok && ks->breakdown_at == 0) ks->breakdown_at = j;
+      }
+    } else if (k == 1) {
+      if (j > 0) ks->H[(j - 1) * (MMAX + 1) + j] = (double)sc.hsub.h + (double)sc.hsub.l;
+    } else if (k == 2) {
+      if (sc.ok) ks->wnp[j & 1] = (double)sc.wn.h + (double)sc.wn.l;
+    } else if (sc.ok) {
+      const int c = k - 3;
+      ks->H[j * (MMAX + 1) + lo + c] = (double)sc.h[c].h + (double)sc.h[c].l;
+    }
+  }
+}
+
 // Float-float form: packed compensated products, four elements per thread
 // per trip, every load of a trip issued before the arithmetic.
 template <int KW>
@@ -927,9 +1035,7 @@ template <int KW>
 __global__ void __launch_bounds__(NT) k_iom_update_ff(KState* ks, ff* part, Basis U, int j, size_t n_aug, int Gd) {
   griddep_wait();
   __shared__ float2 cf[KW];
-  __shared__ double coef[IOP_MAX];
-  __shared__ double cj;
-  __shared__ float2 cjf;
+  __shared__ IomScalars sc;
   __shared__ ff sh[NW];
   __shared__ ff tot[1];
   const int lo = max(0, j - KW + 1), nwin = j - lo + 1;
@@ -950,17 +1056,12 @@ __global__ void __launch_bounds__(NT) k_iom_update_ff(KState* ks, ff* part, Basi
       pxl[c] = __ldg(reinterpret_cast<const float4*>(Ul + vo));
     }
   }
-  if (!iom_prologue<true>(ks, part, j, lo, nwin, KW + 1, Gd, gridDim.x, coef, &cj)) return;
-  if ((int)threadIdx.x < nwin) {
-    const ff a = ff_from_double(coef[threadIdx.x]);
-    cf[threadIdx.x] = make_float2(a.h, a.l);
+  const int go = iom_prologue_ff(ks, part, j, lo, nwin, KW + 1, Gd, gridDim.x, cf, &sc);
+  if (go <= 0) {
+    if (go == 0) write_iom_scalars(ks, sc, j, lo, nwin);  // a breakdown at j: record it
+    return;
   }
-  if (threadIdx.x == 0) {
-    const ff a = ff_from_double(cj);
-    cjf = make_float2(a.h, a.l);
-  }
-  __syncthreads();
-  const float2 cjh = make_float2(cjf.x, cjf.x), cjl = make_float2(cjf.y, cjf.y);
+  const float2 cjh = make_float2(sc.cj.h, sc.cj.h), cjl = make_float2(sc.cj.l, sc.cj.l);
   float2 S = make_float2(0.f, 0.f), C = make_float2(0.f, 0.f);
   for (size_t g = tid; g < ng; g += nthr) {
     const size_t o = 4 * g;
@@ -996,7 +1097,7 @@ __global__ void __launch_bounds__(NT) k_iom_update_ff(KState* ks, ff* part, Basi
     dot2_acc(uh1, ul1, uh1, ul1, S, C);
   }
   for (size_t i = 4 * ng + tid; i < n_aug; i += nthr) {  // ragged end
-    ff x = ff_mul(ff{cjf.x, cjf.y}, ff{Uh[(j + 1) * ld + i], Ul[(j + 1) * ld + i]});
+    ff x = ff_mul(ff{sc.cj.h, sc.cj.l}, ff{Uh[(j + 1) * ld + i], Ul[(j + 1) * ld + i]});
     for (int c = 0; c < nwin; ++c) {
       const size_t vo = (size_t)(lo + c) * ld + i;
       x = ff_fma(ff{cf[c].x, cf[c].y}, ff{Uh[vo], Ul[vo]}, x);
@@ -1009,6 +1110,7 @@ __global__ void __launch_bounds__(NT) k_iom_update_ff(KState* ks, ff* part, Basi
   block_sum<true, 1>(v, sh, tot);
   if (threadIdx.x == 0) part[IOM_UPD_OFF + (j & 1) * RB + blockIdx.x] = tot[0];
   griddep_launch();
+  write_iom_scalars(ks, sc, j, lo, nwin);
 }
 
 // FP64 form: four elements per thread per trip, loads first.
