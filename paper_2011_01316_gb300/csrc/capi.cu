@@ -399,6 +399,7 @@ expdg_status phi_solve(expdg_ctx* ctx, const void* qt_T, double tau, const bool*
       DGArgs a = ctx->mesh;
       a.scal = &ctx->ks->jv;
       a.q = qt_T;
+      a.z_early = 1;  // z was made before the solve's start kernel (a plain launch)
       const Vec vj = ctx->U.at(j), vo = ctx->U.at(j + 1);
       if (F) {
         a.v = vj.h;

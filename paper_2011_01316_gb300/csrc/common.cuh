@@ -123,6 +123,10 @@ struct DGArgs {
   const double* src;     // residual: forcing added to R (FP64, N values) or nullptr
   int roe;               // Euler: Roe flux (the linearisation state then ends with sqrt(rho))
   const JvScalars* scal; // linear: alpha and eta read from here instead of the fields above (or nullptr)
+  // Linear: the linearisation state was written by a launch that completed
+  // before this launch's predecessor started (inside an Arnoldi step), so it
+  // is read before griddepcontrol.wait.  0: read after the wait.
+  int z_early;
 };
 
 // A vector in the FP64 form (d) or the float-float form (h + l).

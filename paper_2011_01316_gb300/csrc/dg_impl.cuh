@@ -454,6 +454,8 @@ struct DgSmem {
 // One element group (the EPB elements from e0) of the DG operator; sD must
 // hold the derivative matrix.  Every thread of the CTA calls it (it
 // synchronises the CTA); trigger: signal dependent launches after the fluxes.
+// It executes griddepcontrol.wait before its first read of memory another
+// launch writes (after loading z when a.z_early).
 // LINEAR = false: residual R(q), a.q = q.  LINEAR = true: linear operator,
 // a.q = the linearisation state z of qt (k_linstate), a.v = v.
 // T = double: FP64 form (double in, double out); T = float: mixed form (float
@@ -486,6 +488,14 @@ __device__ __forceinline__ void dg_group(const DGArgs& a, const Tab& tab, int e0
   const size_t stride = a.stride;
   const T* __restrict__ qin = static_cast<const T*>(a.q);
   const T* __restrict__ vin = static_cast<const T*>(a.v);
+  T qv[M];  // residual: q at the node; linear: z at the node
+  const bool early = LINEAR && a.z_early;
+  if (early && active) {
+    const size_t base = (size_t)e * NP + n;
+#pragma unroll
+    for (int f = 0; f < M; ++f) qv[f] = qin[f * stride + base];
+  }
+  griddep_wait();
 
   // Linear: the sub-step scalars (alpha, eta, the input's augmentation tail)
   // are read here, so their latency overlaps the operator's instead of
@@ -516,7 +526,6 @@ __device__ __forceinline__ void dg_group(const DGArgs& a, const Tab& tab, int e0
     }
   }
 
-  T qv[M];  // residual: q at the node; linear: z at the node
   T vv[M];  // linear: v at the node
   typename PH::Prim w{};
   T dp = T(0);
@@ -524,7 +533,7 @@ __device__ __forceinline__ void dg_group(const DGArgs& a, const Tab& tab, int e0
     const size_t base = (size_t)e * NP + n;
 #pragma unroll
     for (int f = 0; f < M; ++f) {
-      qv[f] = qin[f * stride + base];
+      if (!early) qv[f] = qin[f * stride + base];
       vv[f] = LINEAR ? vin[f * stride + base] : qv[f];
     }
     if (LINEAR) {
@@ -625,7 +634,8 @@ __device__ __forceinline__ void dg_group(const DGArgs& a, const Tab& tab, int e0
 template <int DIM, int P, int EQ, typename T, bool LINEAR, bool ROE>
 __global__ void __launch_bounds__(dg_threads<DIM, P>())
 k_dg(const DGArgs a, const Tab tab) {
-  griddep_wait();
+  // the tables and the neighbour lists come from the parameters: set up before
+  // the wait (dg_group waits)
   extern __shared__ __align__(16) unsigned char smem_raw[];
   const DgSmem<DIM, P, EQ, T> sm(smem_raw);
   for (int k = threadIdx.x; k < (P + 1) * (P + 1); k += blockDim.x) sm.sD[k] = d_entry<T>(tab, k);

@@ -786,6 +786,15 @@ __global__ void __launch_bounds__(NT, 3) k_update_ff(KState* ks, ff* part, Basis
 // update launch sums them itself, in the same order, so all blocks derive the
 // same coefficients; the update launch likewise leaves the partials of
 // ||slot_{j+1}||^2 to the next update launch (or to the phi kernel at a check).
+//
+// Loads before griddepcontrol.wait.  Every launch of an Arnoldi step calls
+// griddepcontrol.launch_dependents only after its own griddepcontrol.wait,
+// so when a launch is scheduled every launch before its immediate
+// predecessor has completed (and a segment starts after a plain launch).  A
+// launch may therefore read before the wait what those earlier launches
+// wrote: the window-products launch the window slots (last written by the
+// previous update), the update launch w' and the window slots (the operator
+// apply and the previous update); only its predecessor's output waits.
 constexpr int IOP_MAX = EXPDG_MAX_IOP;
 // The update launches' norm partials follow the window products' partials in
 // the reduction scratch: two regions, by the parity of j.
@@ -979,7 +988,6 @@ __device__ void write_iom_scalars(KState* ks, const IomScalars& sc, int j, int l
 // per trip, every load of a trip issued before the arithmetic.
 template <int KW>
 __global__ void __launch_bounds__(NT) k_iom_dots_ff(KState* ks, ff* part, Basis U, int j, size_t n_aug) {
-  griddep_wait();
   constexpr int K = KW + 1;
   __shared__ ff sh[NW * K];
   __shared__ ff tot[K];
@@ -992,6 +1000,17 @@ __global__ void __launch_bounds__(NT) k_iom_dots_ff(KState* ks, ff* part, Basis 
   const float* __restrict__ Uh = U.h;
   const float* __restrict__ Ul = U.l;
   const size_t tid = blockIdx.x * (size_t)NT + threadIdx.x, nthr = (size_t)gridDim.x * NT;
+  // the first trip's window slots before the wait (see above), w' after it
+  float4 pxh[KW], pxl[KW];
+  if (tid < ng) {
+#pragma unroll
+    for (int c = 0; c < KW; ++c) {
+      const size_t vo = (size_t)(lo + (c < nwin ? c : 0)) * ld + 4 * tid;
+      pxh[c] = __ldg(reinterpret_cast<const float4*>(Uh + vo));
+      pxl[c] = __ldg(reinterpret_cast<const float4*>(Ul + vo));
+    }
+  }
+  griddep_wait();
   for (size_t g = tid; g < ng; g += nthr) {
     const size_t o = 4 * g;
     const float4 wh = __ldg(reinterpret_cast<const float4*>(Uh + (j + 1) * ld + o));
@@ -999,9 +1018,14 @@ __global__ void __launch_bounds__(NT) k_iom_dots_ff(KState* ks, ff* part, Basis 
     float4 xh[KW], xl[KW];
 #pragma unroll
     for (int c = 0; c < KW; ++c) {
-      const size_t vo = (size_t)(lo + (c < nwin ? c : 0)) * ld + o;
-      xh[c] = __ldg(reinterpret_cast<const float4*>(Uh + vo));
-      xl[c] = __ldg(reinterpret_cast<const float4*>(Ul + vo));
+      if (g == tid) {
+        xh[c] = pxh[c];
+        xl[c] = pxl[c];
+      } else {
+        const size_t vo = (size_t)(lo + (c < nwin ? c : 0)) * ld + o;
+        xh[c] = __ldg(reinterpret_cast<const float4*>(Uh + vo));
+        xl[c] = __ldg(reinterpret_cast<const float4*>(Ul + vo));
+      }
     }
 #pragma unroll
     for (int c = 0; c < KW; ++c)
@@ -1033,7 +1057,6 @@ __global__ void __launch_bounds__(NT) k_iom_dots_ff(KState* ks, ff* part, Basis 
 
 template <int KW>
 __global__ void __launch_bounds__(NT) k_iom_update_ff(KState* ks, ff* part, Basis U, int j, size_t n_aug, int Gd) {
-  griddep_wait();
   __shared__ float2 cf[KW];
   __shared__ IomScalars sc;
   __shared__ ff sh[NW];
@@ -1043,8 +1066,8 @@ __global__ void __launch_bounds__(NT) k_iom_update_ff(KState* ks, ff* part, Basi
   float* __restrict__ Uh = U.h;
   float* __restrict__ Ul = U.l;
   const size_t tid = blockIdx.x * (size_t)NT + threadIdx.x, nthr = (size_t)gridDim.x * NT;
-  // the first trip's vectors are loaded before the prologue, so their latency
-  // overlaps the partial sums'
+  // the first trip's vectors (w' and the window slots: see above) before
+  // the wait; the window products' partials (the predecessor's) after it
   float4 pwh = make_float4(0.f, 0.f, 0.f, 0.f), pwl = pwh, pxh[KW], pxl[KW];
   if (tid < ng) {
     pwh = *reinterpret_cast<const float4*>(Uh + (j + 1) * ld + 4 * tid);
@@ -1056,6 +1079,7 @@ __global__ void __launch_bounds__(NT) k_iom_update_ff(KState* ks, ff* part, Basi
       pxl[c] = __ldg(reinterpret_cast<const float4*>(Ul + vo));
     }
   }
+  griddep_wait();
   const int go = iom_prologue_ff(ks, part, j, lo, nwin, KW + 1, Gd, gridDim.x, cf, &sc);
   if (go <= 0) {
     if (go == 0) write_iom_scalars(ks, sc, j, lo, nwin);  // a breakdown at j: record it
