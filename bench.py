@@ -229,10 +229,11 @@ def wave3d_workload(steps=2, hbm=6788.6, ne=32, iop=0):
             gbs = v["bytes"] / (v["ms"] * 1e-3) / 1e9
             rates[k] = {"GB/s": gbs, "frac_of_measured_hbm": gbs / hbm, "us_per_launch": 1e3 * v["ms"] / v["launches"],
                         "launches": v["launches"]}
-    n = ctx.n
+    n, tile = ctx.n, ctx.tile
     ctx.close()
     return {"workload": f"3D Euler density wave, {ne}^3 hexes, p=3, {n} unknowns, EPI2 dt=0.1, tol 1e-8, mixed",
             "ms_per_step": ms, "dof_steps_per_s": n / (ms * 1e-3), "krylov_iters_per_step": iters / steps,
+            "jv_tile": {1: "256", 2: "128", 3: "512"}.get(tile, "?") + " threads per CTA (autotuned)",
             "kernels": rates}
 
 
@@ -360,7 +361,7 @@ def main():
     ap.add_argument("--fp64-steps", type=int, default=3)
     ap.add_argument("--tol", type=float, default=None, help="Krylov tolerance (default: the workload's)")
     ap.add_argument("--serve-requests", type=int, default=48, help="requests of the serving workload (0: skip)")
-    ap.add_argument("--batch-instances", type=int, default=64, help="instances of the batched workload (0: skip)")
+    ap.add_argument("--batch-instances", type=int, default=256, help="instances of the batched workload (0: skip)")
     ap.add_argument("--no-3d", action="store_true", help="skip the 3D HBM-roofline workload")
     ap.add_argument("--legs", default="main,wave3d,burgers,serving,batched",
                     help="comma list of legs to run (main = the timed workload; profiling runs pick one)")
@@ -516,6 +517,7 @@ def main():
                            "krylov": (f"incomplete orthogonalisation, window {CFG['iop']} (KIOPS)" if CFG["iop"]
                                       else "full Arnoldi (DCGS2)"),
                            "l2": "flushed between timed steps (512 MiB write)",
+                           "jv_tile": {1: "256", 2: "128", 3: "512"}.get(ctx.tile, "?") + " threads per CTA (autotuned)",
                            "parallelism": "replicas" if world > 1 else "single GPU"},
                 "err_vs_fp64": err_vs_fp64, "fp64_form": fp64, "e2e": e2e, "gpu_launches": launches,
                 "serving": serving, "batched": batched, "wave3d": wave3d, "burgers": burgers,

@@ -96,7 +96,21 @@ typedef struct {
                            q** = {q} (Eq. gov-burgers1d); Burgers only */
   int bc;               /* expdg_bc */
   int flux;             /* expdg_flux (Euler; Burgers uses Lax-Friedrichs) */
+  int tile;             /* expdg_tile: CTA size of the EXPDG_MIXED operator apply */
 } expdg_config;
+
+/* CTA size (elements per CTA, one thread per node) of the EXPDG_MIXED
+ * operator apply L(qt) v.  EXPDG_TILE_AUTO times the three sizes on the
+ * context's own mesh when it is created (about 20 operator applies on zero
+ * data) and keeps the fastest; the choice is cached per mesh shape for the
+ * process, so later contexts of the same shape do not time again.  The
+ * EXPDG_FP64 form and the other kernels always use EXPDG_TILE_256. */
+typedef enum {
+  EXPDG_TILE_AUTO = 0,
+  EXPDG_TILE_256 = 1,  /* about 256 threads per CTA */
+  EXPDG_TILE_128 = 2,
+  EXPDG_TILE_512 = 3
+} expdg_tile;
 
 #define EXPDG_MAX_ORDER 8
 #define EXPDG_MAX_KRYLOV 64
@@ -328,6 +342,10 @@ expdg_status expdg_residual_noalloc(const expdg_config* cfg, const double* q, do
 
 /* Message of the last failing call on this context ("" if none). */
 const char* expdg_last_error(const expdg_ctx* ctx);
+
+/* The expdg_tile the context's operator apply uses (never EXPDG_TILE_AUTO);
+ * 0 for a null context. */
+int expdg_tile_in_use(const expdg_ctx* ctx);
 
 /* Library version string. */
 const char* expdg_version(void);

@@ -5,6 +5,7 @@
 #include <cstdio>
 #include <cstring>
 #include <map>
+#include <mutex>
 #include <string>
 #include <vector>
 
@@ -535,6 +536,7 @@ expdg_status validate(const expdg_config* c) {
   if ((c->kappa > 0.0 || c->bc != EXPDG_BC_PERIODIC) && c->eq != EXPDG_BURGERS) return EXPDG_EINVAL;
   if (c->flux != EXPDG_FLUX_LF && c->flux != EXPDG_FLUX_ROE) return EXPDG_EINVAL;
   if (c->flux == EXPDG_FLUX_ROE && c->eq != EXPDG_EULER) return EXPDG_EINVAL;
+  if (c->tile < EXPDG_TILE_AUTO || c->tile > EXPDG_TILE_512) return EXPDG_EINVAL;
   return EXPDG_OK;
 }
 
@@ -670,6 +672,74 @@ size_t expdg_context_bytes(const expdg_config* cfg) {
   return total;
 }
 
+// Tile class of the mixed-form operator apply for this context: the one
+// asked for, or (EXPDG_TILE_AUTO) the fastest of the three on the context's
+// own mesh, timed with CUDA events over five applies each after two warm-up
+// applies, on zero data (the apply's time does not depend on the values).
+// The default class is kept unless another is 3 % faster.  Results are
+// cached per mesh shape for the process.
+std::mutex g_tile_mu;
+std::map<std::vector<long>, int> g_tile_cache;
+
+cudaError_t choose_tile(expdg_ctx* ctx) {
+  const expdg_config& c = ctx->cfg;
+  ctx->mesh.tile = 0;
+  if (!ctx->ff) return cudaSuccess;
+  if (c.tile != EXPDG_TILE_AUTO) {
+    ctx->mesh.tile = c.tile - 1;
+    return cudaSuccess;
+  }
+  const std::vector<long> key = {c.dim, c.p, c.eq, c.flux, c.bc, c.kappa != 0.0 ? 1 : 0, c.ne[0], c.ne[1], c.ne[2]};
+  {
+    std::lock_guard<std::mutex> lk(g_tile_mu);
+    auto it = g_tile_cache.find(key);
+    if (it != g_tile_cache.end()) {
+      ctx->mesh.tile = it->second;
+      return cudaSuccess;
+    }
+  }
+  const cudaStream_t s = ctx->stream;
+  cudaError_t e = cudaMemsetAsync(ctx->d_z, 0, ctx->N * sizeof(float), s);
+  if (e == cudaSuccess) e = cudaMemsetAsync(ctx->U.h, 0, ctx->N * sizeof(float), s);
+  if (e != cudaSuccess) return e;
+  DGArgs a = ctx->mesh;
+  a.q = ctx->d_z;
+  a.v = ctx->U.h;
+  a.out_h = ctx->U.h + ctx->ld;
+  a.out_l = ctx->U.l + ctx->ld;
+  set_alpha(a, 1.0);
+  cudaEvent_t e0 = nullptr, e1 = nullptr;
+  if ((e = cudaEventCreate(&e0)) != cudaSuccess) return e;
+  if ((e = cudaEventCreate(&e1)) != cudaSuccess) {
+    cudaEventDestroy(e0);
+    return e;
+  }
+  int best = 0;
+  float best_ms = 0.0f;
+  for (int tk = 0; tk < 3 && e == cudaSuccess; ++tk) {
+    if (tk > 0 && tile_elems_per_block(ctx->NP, tk) == tile_elems_per_block(ctx->NP, 0)) continue;  // same kernel
+    a.tile = tk;
+    for (int r = 0; r < 2 && e == cudaSuccess; ++r) e = launch_dg(ctx, true, a);
+    if (e == cudaSuccess) e = cudaEventRecord(e0, s);
+    for (int r = 0; r < 5 && e == cudaSuccess; ++r) e = launch_dg(ctx, true, a);
+    if (e == cudaSuccess) e = cudaEventRecord(e1, s);
+    if (e == cudaSuccess) e = cudaEventSynchronize(e1);
+    float ms = 0.0f;
+    if (e == cudaSuccess) e = cudaEventElapsedTime(&ms, e0, e1);
+    if (e == cudaSuccess && (tk == 0 || ms < 0.97f * best_ms)) {
+      best = tk;
+      best_ms = ms;
+    }
+  }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  if (e != cudaSuccess) return e;
+  ctx->mesh.tile = best;
+  std::lock_guard<std::mutex> lk(g_tile_mu);
+  g_tile_cache[key] = best;
+  return cudaSuccess;
+}
+
 expdg_status expdg_create(const expdg_config* cfg, expdg_ctx** out) {
   if (!out) return EXPDG_EINVAL;
   *out = nullptr;
@@ -767,6 +837,7 @@ expdg_status expdg_create(const expdg_config* cfg, expdg_ctx** out) {
   ctx->h_ks = static_cast<KState*>(hk);
   std::memset(ctx->h_ks, 0, sizeof(KState));
   ALLOC(cudaStreamSynchronize(0));  // the zero-fills above are complete
+  ALLOC(choose_tile(ctx));  // CTA size of the mixed-form operator apply
 
 #undef ALLOC
   *out = ctx;
@@ -791,6 +862,7 @@ expdg_status expdg_set_stream(expdg_ctx* ctx, void* stream) {
 }
 
 size_t expdg_num_unknowns(const expdg_ctx* ctx) { return ctx ? ctx->N : 0; }
+int expdg_tile_in_use(const expdg_ctx* ctx) { return ctx ? ctx->mesh.tile + 1 : 0; }
 int expdg_num_fields(const expdg_ctx* ctx) { return ctx ? ctx->M : 0; }
 size_t expdg_num_elements(const expdg_ctx* ctx) { return ctx ? ctx->nelem : 0; }
 int expdg_nodes_per_element(const expdg_ctx* ctx) { return ctx ? ctx->NP : 0; }

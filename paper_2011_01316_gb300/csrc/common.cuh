@@ -54,6 +54,11 @@ inline Cst make_cst(double x) {
   return Cst{x, h, (float)(x - (double)h)};
 }
 
+// Tile classes of the DG operator kernels: CTAs of about 256 (0, the
+// default), 128 (1) or 512 (2) threads, one thread per node.
+__host__ __device__ constexpr int tile_threads(int tk) { return tk == 1 ? 128 : (tk == 2 ? 512 : 256); }
+inline int tile_elems_per_block(int np, int tk) { return tile_threads(tk) / np > 0 ? tile_threads(tk) / np : 1; }
+
 struct Tab {
   double D[(MAXP + 1) * (MAXP + 1)];   // row-major l_j'(r_i) for the context's order
   float Dh[(MAXP + 1) * (MAXP + 1)];   // its float-float split
@@ -127,6 +132,7 @@ struct DGArgs {
   // before this launch's predecessor started (inside an Arnoldi step), so it
   // is read before griddepcontrol.wait.  0: read after the wait.
   int z_early;
+  int tile;              // tile class of the mixed-form operator apply: CTAs of about 256 (0), 128 (1), 512 (2) threads
 };
 
 // A vector in the FP64 form (d) or the float-float form (h + l).

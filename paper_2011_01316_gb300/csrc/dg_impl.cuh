@@ -51,15 +51,15 @@ struct NFields {
 
 __host__ __device__ constexpr int ipow(int b, int e) { return e == 0 ? 1 : b * ipow(b, e - 1); }
 
-// Elements per CTA: about 256 threads.
-template <int DIM, int P>
+// Elements per CTA for tile class TK (tile_threads): at least one element.
+template <int DIM, int P, int TK = 0>
 __host__ __device__ constexpr int elems_per_block() {
-  return (256 / ipow(P + 1, DIM)) > 0 ? (256 / ipow(P + 1, DIM)) : 1;
+  return (tile_threads(TK) / ipow(P + 1, DIM)) > 0 ? (tile_threads(TK) / ipow(P + 1, DIM)) : 1;
 }
 // Threads per CTA: one per node of its elements, whole warps.
-template <int DIM, int P>
+template <int DIM, int P, int TK = 0>
 __host__ __device__ constexpr int dg_threads() {
-  return ((elems_per_block<DIM, P>() * ipow(P + 1, DIM) + 31) / 32) * 32;
+  return ((elems_per_block<DIM, P, TK>() * ipow(P + 1, DIM) + 31) / 32) * 32;
 }
 
 // ---------------------------------------------------------------- physics ---
@@ -246,9 +246,9 @@ cudaError_t launch_linstate_dim(bool fp32, const double* q, void* z, size_t stri
 // Neighbour element across each face of the CTA's EPB elements e0, e0+1, ...
 // into sNb[EPB][2 DIM], face (d, side) at 2 d + (side > 0): periodic box, or
 // -1 outside a Dirichlet end.
-template <int DIM, int P>
+template <int DIM, int P, int TK>
 __device__ __forceinline__ void build_neighbours(const DGArgs& a, int e0, int* sNb) {
-  constexpr int EPB = elems_per_block<DIM, P>(), NF = 2 * DIM;
+  constexpr int EPB = elems_per_block<DIM, P, TK>(), NF = 2 * DIM;
   for (int k = threadIdx.x; k < EPB * NF; k += blockDim.x) {
     const int el = k / NF, d = (k - el * NF) >> 1, hi = k & 1;
     int t = e0 + el, ec[3] = {0, 0, 0};
@@ -273,7 +273,7 @@ __device__ __forceinline__ void build_neighbours(const DGArgs& a, int e0, int* s
 // variables (residual); nb_v(f, gi): the linear input of field f at node gi
 // (index within the field plane) of a neighbour element.  Outside a Dirichlet
 // end the neighbour's state and input are the boundary data 0.
-template <int DIM, int P, int EQ, typename T, bool LINEAR, bool ROE, class NbV>
+template <int DIM, int P, int EQ, typename T, bool LINEAR, bool ROE, int TK, class NbV>
 __device__ __forceinline__ void node_terms(const DGArgs& a, T lift, const T* __restrict__ qin, const T* sF,
                                            const T* sD, const int* sNb, int tid, int le, int n,
                                            const T (&qv)[NFields<DIM, EQ>::value],
@@ -281,7 +281,7 @@ __device__ __forceinline__ void node_terms(const DGArgs& a, T lift, const T* __r
                                            const typename Phys<DIM, EQ, T>::Prim& w, NbV nb_v,
                                            T (&acc)[NFields<DIM, EQ>::value]) {
   constexpr int NP1 = P + 1, NP = ipow(NP1, DIM), M = NFields<DIM, EQ>::value;
-  constexpr int SLOT = elems_per_block<DIM, P>() * NP, NF = 2 * DIM;
+  constexpr int SLOT = elems_per_block<DIM, P, TK>() * NP, NF = 2 * DIM;
   using PH = Phys<DIM, EQ, T>;
   const T gamma = cst<T>(a.gamma), gm1 = gamma - T(1);
   const size_t stride = a.stride;
@@ -367,11 +367,11 @@ __device__ __forceinline__ void node_terms(const DGArgs& a, T lift, const T* __r
 // R, the input vector for L) in the compute type.  The CTA forms q on its
 // elements and one halo element on each side (sU, sQ: (EPB + 2)(P + 1) + 2
 // entries each); every thread of the CTA must call it.
-template <int P, typename T>
+template <int P, typename T, int TK>
 __device__ T visc_term(const DGArgs& a, const T* __restrict__ uin, const T* sD, T lift, T* sU, T* sQ, int e0,
                        int tid, int le, int n, bool active) {
   constexpr int NP1 = P + 1;
-  constexpr int EPB = elems_per_block<1, P>();
+  constexpr int EPB = elems_per_block<1, P, TK>();
   constexpr int NH = (EPB + 2) * NP1;  // halo slots: elements e0 - 1 .. e0 + EPB
   const int ne = a.ne[0];
   const T c2h = cst<T>(a.two_over_h[0]);
@@ -425,19 +425,19 @@ __device__ T visc_term(const DGArgs& a, const T* __restrict__ uin, const T* sD, 
 }
 
 // Extra shared memory of the 1D Burgers kernels (the viscous halo), in T units.
-template <int DIM, int P, int EQ>
+template <int DIM, int P, int EQ, int TK = 0>
 __host__ __device__ constexpr int visc_smem_entries() {
-  return (DIM == 1 && EQ == EXPDG_BURGERS) ? 2 * ((elems_per_block<1, P>() + 2) * (P + 1) + 2) : 0;
+  return (DIM == 1 && EQ == EXPDG_BURGERS) ? 2 * ((elems_per_block<1, P, TK>() + 2) * (P + 1) + 2) : 0;
 }
 
 // Shared-memory layout of the DG kernels (T units, then ints).
-template <int DIM, int P, int EQ, typename T>
+template <int DIM, int P, int EQ, typename T, int TK = 0>
 struct DgSmem {
   static constexpr int NP1 = P + 1, NP = ipow(NP1, DIM), M = NFields<DIM, EQ>::value;
-  static constexpr int SLOT = elems_per_block<DIM, P>() * NP;
+  static constexpr int SLOT = elems_per_block<DIM, P, TK>() * NP;
   __host__ __device__ static constexpr size_t bytes() {
-    return sizeof(T) * ((size_t)DIM * M * SLOT + NP1 * NP1 + visc_smem_entries<DIM, P, EQ>()) +
-           sizeof(int) * elems_per_block<DIM, P>() * 2 * DIM;
+    return sizeof(T) * ((size_t)DIM * M * SLOT + NP1 * NP1 + visc_smem_entries<DIM, P, EQ, TK>()) +
+           sizeof(int) * elems_per_block<DIM, P, TK>() * 2 * DIM;
   }
   T* sF;    // [DIM][M][SLOT] fluxes
   T* sD;    // [NP1][NP1] derivative matrix
@@ -447,7 +447,7 @@ struct DgSmem {
     sF = reinterpret_cast<T*>(raw);
     sD = sF + DIM * M * SLOT;
     sV = sD + NP1 * NP1;
-    sNb = reinterpret_cast<int*>(sV + visc_smem_entries<DIM, P, EQ>());
+    sNb = reinterpret_cast<int*>(sV + visc_smem_entries<DIM, P, EQ, TK>());
   }
 };
 
@@ -461,13 +461,13 @@ struct DgSmem {
 // T = double: FP64 form (double in, double out); T = float: mixed form (float
 // in, float-float out); T = fx: float-float in and out (the mixed form's
 // residual: FP64-grade accuracy on the FP32 pipes).
-template <int DIM, int P, int EQ, typename T, bool LINEAR, bool ROE>
-__device__ __forceinline__ void dg_group(const DGArgs& a, const Tab& tab, int e0, const DgSmem<DIM, P, EQ, T>& sm,
+template <int DIM, int P, int EQ, typename T, bool LINEAR, bool ROE, int TK = 0>
+__device__ __forceinline__ void dg_group(const DGArgs& a, const Tab& tab, int e0, const DgSmem<DIM, P, EQ, T, TK>& sm,
                                          bool trigger) {
   constexpr int NP1 = P + 1;
   constexpr int NP = ipow(NP1, DIM);
   constexpr int M = NFields<DIM, EQ>::value;
-  constexpr int EPB = elems_per_block<DIM, P>();
+  constexpr int EPB = elems_per_block<DIM, P, TK>();
   constexpr int SLOT = EPB * NP;  // nodes held by the CTA
   constexpr bool FF = !std::is_same<T, double>::value;
   using PH = Phys<DIM, EQ, T>;
@@ -477,7 +477,7 @@ __device__ __forceinline__ void dg_group(const DGArgs& a, const Tab& tab, int e0
   int* sNb = sm.sNb;
 
   const int tid = threadIdx.x;
-  build_neighbours<DIM, P>(a, e0, sNb);
+  build_neighbours<DIM, P, TK>(a, e0, sNb);
 
   const int le = tid / NP;
   const int n = tid - le * NP;
@@ -557,14 +557,14 @@ __device__ __forceinline__ void dg_group(const DGArgs& a, const Tab& tab, int e0
   if (trigger) griddep_launch();
   T visc = T(0);
   if constexpr (DIM == 1 && EQ == EXPDG_BURGERS) {
-    constexpr int NH2 = visc_smem_entries<DIM, P, EQ>() / 2;
+    constexpr int NH2 = visc_smem_entries<DIM, P, EQ, TK>() / 2;
     if (a.viscous)  // uniform
-      visc = visc_term<P, T>(a, LINEAR ? vin : qin, sD, cst<T>(tab.lift), sV, sV + NH2, e0, tid, le, n, active);
+      visc = visc_term<P, T, TK>(a, LINEAR ? vin : qin, sD, cst<T>(tab.lift), sV, sV + NH2, e0, tid, le, n, active);
   }
   if (!active) return;  // no further synchronisation below
 
   T acc[M];
-  node_terms<DIM, P, EQ, T, LINEAR, ROE>(a, cst<T>(tab.lift), qin, sF, sD, sNb, tid, le, n, qv, vv, w,
+  node_terms<DIM, P, EQ, T, LINEAR, ROE, TK>(a, cst<T>(tab.lift), qin, sF, sD, sNb, tid, le, n, qv, vv, w,
                                     [&](int f, size_t gi) { return vin[f * stride + gi]; }, acc);
   acc[0] += visc;
 
@@ -631,26 +631,24 @@ __device__ __forceinline__ void dg_group(const DGArgs& a, const Tab& tab, int e0
   }
 }
 
-template <int DIM, int P, int EQ, typename T, bool LINEAR, bool ROE>
-__global__ void __launch_bounds__(dg_threads<DIM, P>())
+template <int DIM, int P, int EQ, typename T, bool LINEAR, bool ROE, int TK>
+__global__ void __launch_bounds__(dg_threads<DIM, P, TK>())
 k_dg(const DGArgs a, const Tab tab) {
   // the tables and the neighbour lists come from the parameters: set up before
   // the wait (dg_group waits)
   extern __shared__ __align__(16) unsigned char smem_raw[];
-  const DgSmem<DIM, P, EQ, T> sm(smem_raw);
+  const DgSmem<DIM, P, EQ, T, TK> sm(smem_raw);
   for (int k = threadIdx.x; k < (P + 1) * (P + 1); k += blockDim.x) sm.sD[k] = d_entry<T>(tab, k);
-  dg_group<DIM, P, EQ, T, LINEAR, ROE>(a, tab, blockIdx.x * elems_per_block<DIM, P>(), sm, true);
+  dg_group<DIM, P, EQ, T, LINEAR, ROE, TK>(a, tab, blockIdx.x * elems_per_block<DIM, P, TK>(), sm, true);
 }
 
-template <int DIM, int P, int EQ, typename T, bool LINEAR, bool ROE>
+template <int DIM, int P, int EQ, typename T, bool LINEAR, bool ROE, int TK = 0>
 cudaError_t launch_dg_t(const DGArgs& a, const Tab& t, cudaStream_t s) {
-  constexpr int NP = ipow(P + 1, DIM);
-  constexpr int M = NFields<DIM, EQ>::value;
-  constexpr int EPB = elems_per_block<DIM, P>();
-  const int threads = dg_threads<DIM, P>();
-  const size_t smem = DgSmem<DIM, P, EQ, T>::bytes();
+  constexpr int EPB = elems_per_block<DIM, P, TK>();
+  const int threads = dg_threads<DIM, P, TK>();
+  const size_t smem = DgSmem<DIM, P, EQ, T, TK>::bytes();
   const int blocks = (a.nelem + EPB - 1) / EPB;
-  auto kern = k_dg<DIM, P, EQ, T, LINEAR, ROE>;
+  auto kern = k_dg<DIM, P, EQ, T, LINEAR, ROE, TK>;
   // once per instantiation, thread-safe (function-local static initialisation)
   static const cudaError_t configured =
       cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
@@ -659,17 +657,28 @@ cudaError_t launch_dg_t(const DGArgs& a, const Tab& t, cudaStream_t s) {
   return pdl_launch(kern, dim3(blocks), dim3(threads), smem, s, a, t);
 }
 
+// The mixed-form operator apply in the tile class a.tile (0, 1, 2: CTAs of
+// about 256, 128, 512 threads); the other kernels use class 0.
+template <int DIM, int P, int EQ, typename T, bool LINEAR, bool ROE>
+cudaError_t launch_dg_tile(const DGArgs& a, const Tab& t, cudaStream_t s) {
+  if constexpr (LINEAR && std::is_same<T, float>::value) {
+    if (a.tile == 1) return launch_dg_t<DIM, P, EQ, T, LINEAR, ROE, 1>(a, t, s);
+    if (a.tile == 2) return launch_dg_t<DIM, P, EQ, T, LINEAR, ROE, 2>(a, t, s);
+  }
+  return launch_dg_t<DIM, P, EQ, T, LINEAR, ROE, 0>(a, t, s);
+}
+
 template <int DIM, int EQ, typename T, bool LINEAR, bool ROE>
 cudaError_t launch_dg_p(int p, const DGArgs& a, const Tab& t, cudaStream_t s) {
   switch (p) {
-    case 1: return launch_dg_t<DIM, 1, EQ, T, LINEAR, ROE>(a, t, s);
-    case 2: return launch_dg_t<DIM, 2, EQ, T, LINEAR, ROE>(a, t, s);
-    case 3: return launch_dg_t<DIM, 3, EQ, T, LINEAR, ROE>(a, t, s);
-    case 4: return launch_dg_t<DIM, 4, EQ, T, LINEAR, ROE>(a, t, s);
-    case 5: return launch_dg_t<DIM, 5, EQ, T, LINEAR, ROE>(a, t, s);
-    case 6: return launch_dg_t<DIM, 6, EQ, T, LINEAR, ROE>(a, t, s);
-    case 7: return launch_dg_t<DIM, 7, EQ, T, LINEAR, ROE>(a, t, s);
-    case 8: return launch_dg_t<DIM, 8, EQ, T, LINEAR, ROE>(a, t, s);
+    case 1: return launch_dg_tile<DIM, 1, EQ, T, LINEAR, ROE>(a, t, s);
+    case 2: return launch_dg_tile<DIM, 2, EQ, T, LINEAR, ROE>(a, t, s);
+    case 3: return launch_dg_tile<DIM, 3, EQ, T, LINEAR, ROE>(a, t, s);
+    case 4: return launch_dg_tile<DIM, 4, EQ, T, LINEAR, ROE>(a, t, s);
+    case 5: return launch_dg_tile<DIM, 5, EQ, T, LINEAR, ROE>(a, t, s);
+    case 6: return launch_dg_tile<DIM, 6, EQ, T, LINEAR, ROE>(a, t, s);
+    case 7: return launch_dg_tile<DIM, 7, EQ, T, LINEAR, ROE>(a, t, s);
+    case 8: return launch_dg_tile<DIM, 8, EQ, T, LINEAR, ROE>(a, t, s);
     default: return cudaErrorInvalidValue;
   }
 }

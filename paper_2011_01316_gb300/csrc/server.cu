@@ -38,7 +38,7 @@ bool same_shape(const expdg_config& a, const expdg_config& b) {
   if (a.m_max != b.m_max || a.m_step != b.m_step || a.max_substeps != b.max_substeps || a.iop != b.iop)
     return false;
   if (a.gamma != b.gamma || a.krylov_tol != b.krylov_tol || a.kappa != b.kappa || a.bc != b.bc) return false;
-  if (a.flux != b.flux) return false;
+  if (a.flux != b.flux || a.tile != b.tile) return false;
   for (int d = 0; d < a.dim; ++d)
     if (a.ne[d] != b.ne[d] || a.lo[d] != b.lo[d] || a.hi[d] != b.hi[d]) return false;
   return true;

@@ -21,6 +21,7 @@ EXPDG_EPI2, EXPDG_EXPRB32, EXPDG_EXPRB42 = 2, 3, 4
 EXPDG_FP64, EXPDG_MIXED = 0, 1
 EXPDG_BC_PERIODIC, EXPDG_BC_DIRICHLET = 0, 1
 EXPDG_FLUX_LF, EXPDG_FLUX_ROE = 0, 1
+EXPDG_TILE_AUTO, EXPDG_TILE_256, EXPDG_TILE_128, EXPDG_TILE_512 = 0, 1, 2, 3
 EXPDG_MAX_ORDER, EXPDG_MAX_KRYLOV, EXPDG_MAX_PHI, EXPDG_MAX_IOP = 8, 64, 3, 8
 STATUS_NAMES = {0: "EXPDG_OK", 1: "EXPDG_EINVAL", 2: "EXPDG_ENOMEM", 3: "EXPDG_EKRYLOV",
                 4: "EXPDG_ENONPHYSICAL", 5: "EXPDG_ETIMEOUT", 6: "EXPDG_ECUDA"}
@@ -32,7 +33,7 @@ class expdg_config(ctypes.Structure):
                 ("gamma", ctypes.c_double), ("scheme", ctypes.c_int), ("prec", ctypes.c_int),
                 ("krylov_tol", ctypes.c_double), ("m_max", ctypes.c_int), ("m_step", ctypes.c_int),
                 ("max_substeps", ctypes.c_int), ("iop", ctypes.c_int), ("kappa", ctypes.c_double),
-                ("bc", ctypes.c_int), ("flux", ctypes.c_int)]
+                ("bc", ctypes.c_int), ("flux", ctypes.c_int), ("tile", ctypes.c_int)]
 
 
 class expdg_stats(ctypes.Structure):
@@ -84,6 +85,7 @@ def _load():
         "expdg_destroy": (None, [P]),
         "expdg_set_stream": (ctypes.c_int, [P, P]),
         "expdg_num_unknowns": (ctypes.c_size_t, [P]),
+        "expdg_tile_in_use": (ctypes.c_int, [P]),
         "expdg_num_fields": (ctypes.c_int, [P]),
         "expdg_num_elements": (ctypes.c_size_t, [P]),
         "expdg_nodes_per_element": (ctypes.c_int, [P]),
@@ -205,6 +207,7 @@ class Context:
         self.m = _lib.expdg_num_fields(h)
         self.nelem = _lib.expdg_num_elements(h)
         self.np = _lib.expdg_nodes_per_element(h)
+        self.tile = _lib.expdg_tile_in_use(h)  # expdg_tile of the operator apply (autotuned when AUTO)
 
     def close(self):
         if getattr(self, "h", None):
