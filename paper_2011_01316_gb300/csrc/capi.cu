@@ -31,8 +31,7 @@ struct expdg_ctx {
   double* d_in = nullptr;  // API input scratch
   double* d_out = nullptr; // API output scratch
   // FP32 buffers (mixed form)
-  float* d_q32 = nullptr;
-  float* d_q32b = nullptr;
+  float* d_q32b = nullptr;  // FP32 operand of the operator apply (expdg_jv, the EXPRB stage correction)
   float* d_qfx = nullptr;   // the state as interleaved float-float pairs (mixed-form residual)
   double* d_src = nullptr;  // forcing added to R (expdg_set_source), allocated on first use
   bool has_src = false;
@@ -478,7 +477,7 @@ expdg_status phi_solve(expdg_ctx* ctx, const void* qt_T, double tau, const bool*
       // converged change between consecutive checks also accepts
       RUN(ctx, EXPDG_K_PHI, 8.0 * m * m,
           launch_phi(ctx->ks, m, beta, cfg.krylov_tol, replay ? 1 : 0, F ? 1 : 0, iop ? ctx->part : nullptr, F ? 1 : 0,
-                     iop ? iom_update_blocks(F, iop, n_aug) : 0, s));
+                     iop ? iom_update_blocks(F, iop, n_aug) : 0, F, s));
       rs = readback(ctx);
       if (rs != EXPDG_OK) return rs;
       if (ctx->h_ks->accept) {
@@ -662,7 +661,7 @@ size_t expdg_context_bytes(const expdg_config* cfg) {
   const size_t gran = (size_t)2 << 20;
   auto r = [&](size_t b) { return ((b + gran - 1) / gran) * gran; };
   size_t total = 5 * r(N * sizeof(double));                 // q, q2, t2, in, out
-  if (ff) total += 2 * r(N * sizeof(float)) + r(2 * N * sizeof(float));  // FP32 copies, float-float state
+  if (ff) total += r(N * sizeof(float)) + r(2 * N * sizeof(float));  // FP32 operand, float-float state
   total += r(N * (ff ? sizeof(float) : sizeof(double)));     // linearisation state
   const size_t nvec = 2 * (EXPDG_MAX_PHI + 1) + 4;          // c, b, w, rn, t1, t3
   total += nvec * (ff ? 2 * r(N * sizeof(float)) : r(N * sizeof(double)));
@@ -801,7 +800,6 @@ expdg_status expdg_create(const expdg_config* cfg, expdg_ctx** out) {
   ALLOC(dalloc(ctx, &ctx->d_in, N));
   ALLOC(dalloc(ctx, &ctx->d_out, N));
   if (ctx->ff) {
-    ALLOC(dalloc(ctx, &ctx->d_q32, N));
     ALLOC(dalloc(ctx, &ctx->d_q32b, N));
     ALLOC(dalloc(ctx, &ctx->d_qfx, 2 * N));
     float* z = nullptr;

@@ -267,9 +267,9 @@ int iom_update_blocks(bool use_ff, int iop, size_t n_aug);
 // iom_part: the reduction scratch when the basis comes from incomplete
 // orthogonalisation (h_{m,m-1} is then finished from the last update launch's
 // partials; iom_gu = that launch's blocks, iom_ff its precision), else nullptr.
+// ff_arith: float-float arithmetic on the FP32 pipes (the mixed form), else FP64.
 cudaError_t launch_phi(KState* ks, int m, double beta, double tol, int force_accept, int diff_rule,
-                       const void* iom_part, int iom_ff, int iom_gu,
-                       cudaStream_t s);
+                       const void* iom_part, int iom_ff, int iom_gu, bool ff_arith, cudaStream_t s);
 // out = base + sum_{i < m_eff} ycoef_i u_i (first N entries; base may be null).
 // out and base may each be FP64 (d) or float-float (h, l).
 cudaError_t launch_combine(bool use_ff, const KState* ks, Basis U, Vec base, Vec out, size_t N, cudaStream_t s);

@@ -1221,38 +1221,93 @@ __global__ void __launch_bounds__(NT) k_iom_update(KState* ks, double* part, Bas
 //   T(X) = B_0 + X^4 (B_1 + X^4 (B_2 + X^4 (B_3 + X^4 B_4))),
 //   B_j = sum_{i<4} X^i / (4j+i)!,  B_4 = I/16! + X/17! + X^2/18!,
 // i.e. 3 products for X^2, X^3, X^4 and 4 Horner products instead of 18.
-// FP64 on a cluster of PHI_CL CTAs: every CTA keeps full copies of the
-// matrices in shared memory; each product is split by rows across the CTAs
-// and every CTA writes its rows into all CTAs' copies (distributed shared
+// On a cluster of PHI_CL CTAs: every CTA keeps full copies of the matrices in
+// shared memory; each product is split by rows across the CTAs, each entry's
+// sum over k across PHI_KS adjacent lanes (shorter dependent chains), and
+// every CTA writes its rows into all CTAs' copies (distributed shared
 // memory), followed by one cluster barrier.  Results alternate between two
 // buffers, so a CTA never overwrites a copy another CTA may still read.
+// The arithmetic is FP64 (FP64 form) or float-float on the FP32 pipes (mixed
+// form: 48-bit significands, far below its tolerances; GB300's FP64 pipe
+// runs about 2 FMA per SM per clock).
 constexpr int PHI_CL = 8;
 constexpr int PHI_NT = 256;
+constexpr int PHI_KS = 4;
 
-__device__ void cl_matmul(cg::cluster_group& cl, const double* A, const double* B, double* C, int m) {
+// 1/k!, k = 0..18, as FP64 and as float-float pairs (computed on the host).
+struct PhiConst {
+  double d[19];
+  float2 f[19];
+};
+
+template <typename T>
+struct PhiT;
+template <>
+struct PhiT<double> {
+  using S = double;  // scalar type of norms and power-of-two scales
+  __device__ static double zero() { return 0.0; }
+  __device__ static double cnst(const PhiConst& c, int k) { return c.d[k]; }
+  __device__ static double mad(double a, double b, double c) { return fma(a, b, c); }
+  __device__ static double add(double a, double b) { return a + b; }
+  __device__ static double pow2(double a, double s) { return a * s; }
+  __device__ static double from_d(double x) { return x; }
+  __device__ static double to_d(double x) { return x; }
+  __device__ static double mag(double x) { return fabs(x); }
+  __device__ static double shfl_xor(double x, int m) { return __shfl_xor_sync(0xffffffffu, x, m); }
+};
+template <>
+struct PhiT<ff> {
+  using S = float;
+  __device__ static ff zero() { return ff{0.0f, 0.0f}; }
+  __device__ static ff cnst(const PhiConst& c, int k) { return ff{c.f[k].x, c.f[k].y}; }
+  __device__ static ff mad(ff a, ff b, ff c) { return ff_fma(a, b, c); }
+  __device__ static ff add(ff a, ff b) { return ff_add(a, b); }
+  __device__ static ff pow2(ff a, float s) { return ff{a.h * s, a.l * s}; }
+  __device__ static ff from_d(double x) { return ff_from_double(x); }
+  __device__ static double to_d(ff x) { return ff_to_double(x); }
+  __device__ static float mag(ff x) { return fabsf(x.h); }
+  __device__ static ff shfl_xor(ff x, int m) {
+    return ff{__shfl_xor_sync(0xffffffffu, x.h, m), __shfl_xor_sync(0xffffffffu, x.l, m)};
+  }
+};
+
+template <typename T>
+__device__ void cl_matmul(cg::cluster_group& cl, const T* A, const T* B, T* C, int m) {
+  using PT = PhiT<T>;
   const int rank = (int)cl.block_rank();
   const int r0 = (m * rank) / PHI_CL, r1 = (m * (rank + 1)) / PHI_CL;
-  double* dst[PHI_CL];
+  T* dst[PHI_CL];
 #pragma unroll
   for (int t = 0; t < PHI_CL; ++t) dst[t] = cl.map_shared_rank(C, t);
   const int nout = (r1 - r0) * m;
-  for (int idx = threadIdx.x; idx < nout; idx += blockDim.x) {
-    const int r = r0 + idx / m, c = idx - (idx / m) * m;
-    double acc = 0.0;
-    for (int k = 0; k < m; ++k) acc = fma(A[r * m + k], B[k * m + c], acc);
+  const int rounds = (nout * PHI_KS + blockDim.x - 1) / blockDim.x;  // the same for every thread
+  for (int rd = 0; rd < rounds; ++rd) {
+    const int g = rd * blockDim.x + threadIdx.x;
+    const int o = g / PHI_KS, q = g - o * PHI_KS;  // entry o, part q of its sum
+    const int r = r0 + o / m, c = o - (o / m) * m;
+    T acc = PT::zero();
+    if (o < nout)
+      for (int k = q; k < m; k += PHI_KS) acc = PT::mad(A[r * m + k], B[k * m + c], acc);
 #pragma unroll
-    for (int t = 0; t < PHI_CL; ++t) dst[t][r * m + c] = acc;
+    for (int off = 1; off < PHI_KS; off <<= 1) acc = PT::add(acc, PT::shfl_xor(acc, off));
+    if (o < nout && q == 0) {
+#pragma unroll
+      for (int t = 0; t < PHI_CL; ++t) dst[t][r * m + c] = acc;
+    }
   }
   cl.sync();
 }
 
+template <typename T>
 __global__ void __cluster_dims__(PHI_CL, 1, 1) __launch_bounds__(PHI_NT)
 k_phi(KState* ks, int m_req, double beta, double tol, int force, int diff_rule, const void* iom_part, int iom_ff,
-      int iom_gu) {
+      int iom_gu, const PhiConst pc) {
+  using PT = PhiT<T>;
+  using SC = typename PT::S;
   cg::cluster_group cl = cg::this_cluster();
-  extern __shared__ double sm[];
+  extern __shared__ __align__(16) unsigned char phi_smem[];
   __shared__ int s_m;
-  __shared__ double s_norm;
+  __shared__ SC s_norm;
   __shared__ double s_hm;  // h_{m,m-1}
   __shared__ int s_brk;
   if (threadIdx.x == 0) {
@@ -1291,62 +1346,65 @@ k_phi(KState* ks, int m_req, double beta, double tol, int force, int diff_rule, 
     __syncthreads();
   }
   const int m = s_m, mm = m * m;
-  double* X = sm;
-  double* X2 = X + mm;
-  double* X3 = X2 + mm;
-  double* X4 = X3 + mm;
-  double* T0 = X4 + mm;
-  double* T1 = T0 + mm;
+  T* X = reinterpret_cast<T*>(phi_smem);
+  T* X2 = X + mm;
+  T* X3 = X2 + mm;
+  T* X4 = X3 + mm;
+  T* T0 = X4 + mm;
+  T* T1 = T0 + mm;
   for (int idx = threadIdx.x; idx < mm; idx += blockDim.x) {
     const int r = idx / m, c = idx - r * m;
-    X[idx] = ks->H[c * (MMAX + 1) + r];
+    X[idx] = PT::from_d(ks->H[c * (MMAX + 1) + r]);
   }
   __syncthreads();
   if (threadIdx.x < 32) {
-    double mx = 0.0;
+    SC mx = 0;
     for (int c = threadIdx.x; c < m; c += 32) {
-      double cs = 0.0;
-      for (int r = 0; r < m; ++r) cs += fabs(X[r * m + c]);
-      mx = fmax(mx, cs);
+      SC cs = 0;
+      for (int r = 0; r < m; ++r) cs += PT::mag(X[r * m + c]);
+      mx = cs > mx ? cs : mx;
     }
-    for (int off = 16; off > 0; off >>= 1) mx = fmax(mx, __shfl_down_sync(0xffffffffu, mx, off));
+    for (int off = 16; off > 0; off >>= 1) {
+      const SC o = __shfl_down_sync(0xffffffffu, mx, off);
+      mx = o > mx ? o : mx;
+    }
     if (threadIdx.x == 0) s_norm = mx;
   }
   __syncthreads();
   int sq = 0;
-  if (s_norm > 0.5) sq = (int)ceil(log2(s_norm / 0.5));
-  const double scale = ldexp(1.0, -sq);
-  for (int idx = threadIdx.x; idx < mm; idx += blockDim.x) X[idx] *= scale;
+  if (s_norm > SC(0.5)) sq = (int)ceil(log2(s_norm / SC(0.5)));
+  const SC scale = (SC)ldexp(1.0f, -sq);  // a power of two: exact in both types
+  for (int idx = threadIdx.x; idx < mm; idx += blockDim.x) X[idx] = PT::pow2(X[idx], scale);
   cl.sync();  // every CTA has its scaled copy before any remote write lands
   cl_matmul(cl, X, X, X2, m);
   cl_matmul(cl, X2, X, X3, m);
   cl_matmul(cl, X2, X2, X4, m);
-  double ifact[19];
-  ifact[0] = 1.0;
-  for (int k = 1; k <= 18; ++k) ifact[k] = ifact[k - 1] / k;
   // E = B_4
   for (int idx = threadIdx.x; idx < mm; idx += blockDim.x) {
     const int r = idx / m, c = idx - r * m;
-    T0[idx] = ((r == c) ? ifact[16] : 0.0) + ifact[17] * X[idx] + ifact[18] * X2[idx];
+    const T diag = (r == c) ? PT::cnst(pc, 16) : PT::zero();
+    T0[idx] = PT::mad(PT::cnst(pc, 18), X2[idx], PT::mad(PT::cnst(pc, 17), X[idx], diag));
   }
   __syncthreads();
-  double* E = T0;
-  double* F = T1;
+  T* E = T0;
+  T* F = T1;
   for (int j = 3; j >= 0; --j) {
     cl_matmul(cl, X4, E, F, m);
+    const T c0 = PT::cnst(pc, 4 * j), c1 = PT::cnst(pc, 4 * j + 1), c2 = PT::cnst(pc, 4 * j + 2),
+            c3 = PT::cnst(pc, 4 * j + 3);
     for (int idx = threadIdx.x; idx < mm; idx += blockDim.x) {
       const int r = idx / m, c = idx - r * m;
-      F[idx] += ((r == c) ? ifact[4 * j] : 0.0) + ifact[4 * j + 1] * X[idx] + ifact[4 * j + 2] * X2[idx] +
-                ifact[4 * j + 3] * X3[idx];
+      const T f = (r == c) ? PT::add(F[idx], c0) : F[idx];
+      F[idx] = PT::mad(c3, X3[idx], PT::mad(c2, X2[idx], PT::mad(c1, X[idx], f)));
     }
     __syncthreads();
-    double* t = E;
+    T* t = E;
     E = F;
     F = t;
   }
   for (int k = 0; k < sq; ++k) {
     cl_matmul(cl, E, E, F, m);
-    double* t = E;
+    T* t = E;
     E = F;
     F = t;
   }
@@ -1356,7 +1414,7 @@ k_phi(KState* ks, int m_req, double beta, double tol, int force, int diff_rule, 
     double d2 = 0.0;
     const int mp = ks->mprev;
     for (int i = threadIdx.x; i < m; i += blockDim.x) {
-      const double di = E[i * m] - ((i < mp) ? ks->yprev[i] : 0.0);
+      const double di = PT::to_d(E[i * m]) - ((i < mp) ? ks->yprev[i] : 0.0);
       d2 += di * di;
     }
     for (int off = 16; off > 0; off >>= 1) d2 += __shfl_down_sync(0xffffffffu, d2, off);
@@ -1367,19 +1425,20 @@ k_phi(KState* ks, int m_req, double beta, double tol, int force, int diff_rule, 
       for (int w = 0; w < PHI_NT / 32; ++w) dsum += s_d2[w];
       const bool brk = s_brk != 0;
       const double hm = s_hm;
-      const double err = brk ? 0.0 : beta * hm * fabs(E[(m - 1) * m]);
+      const double err = brk ? 0.0 : beta * hm * fabs(PT::to_d(E[(m - 1) * m]));
       const double dif = (mp > 0) ? beta * sqrt(dsum) : 1.0 / 0.0;
       const bool ok = brk || err <= tol * beta || (diff_rule && dif <= tol * beta);
       ks->err = diff_rule ? fmin(err, dif) : err;
       ks->accept = (force || ok) ? 1 : 0;
       ks->m_eff = m;
-      ks->norm1 = s_norm;
+      ks->norm1 = (double)s_norm;
       ks->squarings = sq;
     }
     __syncthreads();
     for (int i = threadIdx.x; i < m; i += blockDim.x) {
-      ks->ycoef[i] = beta * E[i * m] * ks->vscale[i];
-      ks->yprev[i] = E[i * m];
+      const double y = PT::to_d(E[i * m]);
+      ks->ycoef[i] = beta * y * ks->vscale[i];
+      ks->yprev[i] = y;
     }
     if (threadIdx.x == 0) ks->mprev = m;
   }
@@ -1710,13 +1769,33 @@ cudaError_t launch_iom_update(bool use_ff, int iop, KState* ks, void* part, Basi
 }
 
 cudaError_t launch_phi(KState* ks, int m, double beta, double tol, int force_accept, int diff_rule,
-                       const void* iom_part, int iom_ff, int iom_gu, cudaStream_t s) {
+                       const void* iom_part, int iom_ff, int iom_gu, bool ff_arith, cudaStream_t s) {
   if (m < 1 || m > MMAX) return cudaErrorInvalidValue;
+  static const PhiConst pc = [] {
+    PhiConst c{};
+    double f = 1.0;
+    for (int k = 0; k <= 18; ++k) {
+      if (k > 0) f /= k;
+      const float h = (float)f;
+      c.d[k] = f;
+      c.f[k] = make_float2(h, (float)(f - (double)h));
+    }
+    return c;
+  }();
+  static_assert(sizeof(double) == sizeof(ff), "the two forms use the same shared memory");
   const size_t smem = 6 * sizeof(double) * (size_t)m * m;
-  static const cudaError_t configured =
-      cudaFuncSetAttribute(k_phi, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)(6 * sizeof(double) * MMAX * MMAX));
+  const int smax = (int)(6 * sizeof(double) * MMAX * MMAX);
+  static const cudaError_t configured = [smax] {
+    cudaError_t e = cudaFuncSetAttribute(k_phi<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, smax);
+    if (e == cudaSuccess) e = cudaFuncSetAttribute(k_phi<ff>, cudaFuncAttributeMaxDynamicSharedMemorySize, smax);
+    return e;
+  }();
   if (configured != cudaSuccess) return configured;
-  k_phi<<<PHI_CL, PHI_NT, smem, s>>>(ks, m, beta, tol, force_accept, diff_rule, iom_part, iom_ff, iom_gu);
+  if (ff_arith)
+    k_phi<ff><<<PHI_CL, PHI_NT, smem, s>>>(ks, m, beta, tol, force_accept, diff_rule, iom_part, iom_ff, iom_gu, pc);
+  else
+    k_phi<double><<<PHI_CL, PHI_NT, smem, s>>>(ks, m, beta, tol, force_accept, diff_rule, iom_part, iom_ff, iom_gu,
+                                               pc);
   return cudaGetLastError();
 }
 
