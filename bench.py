@@ -164,7 +164,7 @@ def oracle_step_rate(steps=1):
     return mesh.n_unknowns * steps / dt, dt
 
 
-def burgers_workload(steps=50):
+def burgers_workload(steps=50, iop=0):
     """1D Burgers, 64 elements, p = 2 on the periodic [0, 2 pi] (192
     unknowns), u0 = 0.5 + sin x, LF flux, EPI2 steps of dt = 1e-2 with Krylov
     tol 1e-10, FP64 form: a launch-latency-bound solve.  Reports us per step
@@ -174,7 +174,7 @@ def burgers_workload(steps=50):
     from paper_2011_01316_gb300 import expdg, inputs
     ctx = expdg.Context(dim=1, p=2, ne=[64, 1, 1], lo=[0.0, 0.0, 0.0], hi=[2 * math.pi, 1.0, 1.0],
                         eq=expdg.EXPDG_BURGERS, scheme=expdg.EXPDG_EPI2, prec=expdg.EXPDG_FP64, krylov_tol=1e-10,
-                        m_max=64, m_step=5, max_substeps=32)
+                        m_max=64, m_step=5, max_substeps=32, iop=iop)
     stream = torch.cuda.current_stream()
     ctx.set_stream(stream)
     q0 = torch.from_numpy(np.ascontiguousarray(inputs.burgers_sine(ctx.node_coords()))).cuda()
@@ -188,7 +188,8 @@ def burgers_workload(steps=50):
     ev1.record(stream)
     ev1.synchronize()
     ms = ev0.elapsed_time(ev1)
-    return {"workload": "1D Burgers, 64 elements, p=2, 192 unknowns, u0 = 0.5 + sin x, EPI2 dt=1e-2, tol 1e-10, FP64",
+    return {"workload": "1D Burgers, 64 elements, p=2, 192 unknowns, u0 = 0.5 + sin x, EPI2 dt=1e-2, tol 1e-10, FP64, "
+                        + (f"window {iop} (KIOPS)" if iop else "full orthogonalisation"),
             "steps": steps, "us_per_step": 1e3 * ms / steps, "dof_steps_per_s": ctx.n * steps / (ms * 1e-3),
             "krylov_iters_per_step": st["krylov_iters"] / steps}
 
@@ -406,6 +407,8 @@ def main():
     ap.add_argument("--fp64-steps", type=int, default=3)
     ap.add_argument("--tol", type=float, default=None, help="Krylov tolerance (default: the workload's)")
     ap.add_argument("--serve-requests", type=int, default=48, help="requests of the serving workload (0: skip)")
+    ap.add_argument("--serve-workers", type=int, default=8, help="solves in flight in the served form")
+    ap.add_argument("--burgers-iop", type=int, default=4, help="orthogonalisation window of the Burgers leg (0: full)")
     ap.add_argument("--batch-instances", type=int, default=256, help="instances of the batched workload (0: skip)")
     ap.add_argument("--no-3d", action="store_true", help="skip the 3D HBM-roofline workload")
     ap.add_argument("--legs", default="main,wave3d,burgers,exprb32,serving,batched",
@@ -444,11 +447,11 @@ def main():
         if "wave3d" in args.legs:
             out["wave3d"] = wave3d_workload(steps=args.wave3d_steps, hbm=hbm, ne=args.wave3d_ne, iop=args.iop)
         if "serving" in args.legs:
-            out["serving"] = serving_workload(args.serve_requests)
+            out["serving"] = serving_workload(args.serve_requests, workers=args.serve_workers)
         if "batched" in args.legs:
             out["batched"] = batched_workload(args.batch_instances)
         if "burgers" in args.legs:
-            out["burgers"] = burgers_workload()
+            out["burgers"] = burgers_workload(iop=args.burgers_iop)
         if "exprb32" in args.legs:
             out["exprb32"] = exprb32_workload()
         if rank == 0:
@@ -547,9 +550,10 @@ def main():
     wave3d = None
     if "wave3d" in legs and not args.no_3d:
         wave3d = wave3d_workload(steps=args.wave3d_steps, hbm=hbm, ne=args.wave3d_ne, iop=args.iop)
-    serving = serving_workload(args.serve_requests) if args.serve_requests > 0 and "serving" in legs else None
+    serving = (serving_workload(args.serve_requests, workers=args.serve_workers)
+               if args.serve_requests > 0 and "serving" in legs else None)
     batched = batched_workload(args.batch_instances) if args.batch_instances > 0 and "batched" in legs else None
-    burgers = burgers_workload() if "burgers" in legs else None
+    burgers = burgers_workload(iop=args.burgers_iop) if "burgers" in legs else None
     exprb32 = exprb32_workload() if "exprb32" in legs else None
 
     cpu = None
