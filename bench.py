@@ -52,10 +52,10 @@ DT = 0.05
 CLASSES = ["residual", "jv", "dots", "update", "phi", "combine", "vector"]
 # DRAM bytes per algorithmic byte of a kernel class on this workload, from one ncu
 # capture each (profiles/ncu_vortex64_p4_kernels.md, full window: k_iom_update_ff<4>
-# 16.434432 MB read + 0 written for 6 x 3.276808 MB algorithmic, k_iom_dots_ff<4>
+# 16.438784 MB read + 0 written for 6 x 3.276808 MB algorithmic, k_iom_dots_ff<4>
 # 16.402944 MB for 5 x 3.276808 MB); used for roofline.traffic.  Refresh when the
 # kernel changes.
-NCU_TRAFFIC_RATIO = {"update": 16.434432 / (6 * 3.276808), "dots": 16.402944 / (5 * 3.276808)}
+NCU_TRAFFIC_RATIO = {"update": 16.438784 / (6 * 3.276808), "dots": 16.402944 / (5 * 3.276808)}
 
 
 def max_over_ranks(x, world, device="cpu"):
