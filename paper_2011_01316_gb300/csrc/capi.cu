@@ -287,11 +287,6 @@ expdg_status readback(expdg_ctx* ctx) {
   return EXPDG_OK;
 }
 
-double tail_scale(double nrm) {
-  if (!(nrm > 0.0) || !std::isfinite(nrm)) return 1.0;
-  return std::ldexp(1.0, -(int)std::lround(std::log2(nrm)));
-}
-
 struct Replay {
   const expdg_trace_entry* e = nullptr;
   int n = 0;
@@ -360,26 +355,33 @@ expdg_status phi_solve(expdg_ctx* ctx, const void* qt_T, double tau, const bool*
       Vec xs[EXPDG_MAX_PHI + 1];
       xs[0] = ctx->w;
       for (int i = 1; i <= P; ++i) xs[i] = ctx->b[i];
-      RUN(ctx, EXPDG_K_VECTOR, 8.0 * (P + 1) * N, launch_norms(F, ctx->ks, ctx->part, P + 1, xs, N, s));
+      // adaptive: the norms kernel also forms eta and beta on the device, so the
+      // Arnoldi steps follow without a host round trip
+      RUN(ctx, EXPDG_K_VECTOR, 8.0 * (P + 1) * N,
+          launch_norms(F, ctx->ks, ctx->part, P + 1, xs, N, replay ? -1 : P, s));
     }
-    expdg_status rs = readback(ctx);
-    if (rs != EXPDG_OK) return rs;
-    if (!replay) {
-      double mx = 0.0;
-      for (int i = 1; i <= P; ++i) mx = std::fmax(mx, std::sqrt(ctx->h_ks->red[i]));
-      eta = tail_scale(mx);
-    }
-    const double beta = std::sqrt(ctx->h_ks->red[0] + (P > 0 ? 1.0 / (eta * eta) : 0.0));
+    expdg_status rs = EXPDG_OK;
     const bool last = (sv + sigma >= 1.0);
-    if (beta == 0.0) {  // P == 0 and c_0 == 0: the result is zero
-      sv += sigma;
-      st->substeps++;
-      if (trace) trace->push_back(expdg_trace_entry{solve_id, 0, sigma, eta});
-      continue;
-    }
     const int iop = cfg.iop;
-    const double s0 = iop ? 1.0 / beta : 1.0;  // incomplete orthogonalisation: slot 0 holds beta v_0
-    RUN(ctx, EXPDG_K_VECTOR, 16.0 * N, launch_start(F, ctx->ks, ctx->U, ctx->w, N, P, eta, s0, sigma * tau, s));
+    double beta = -1.0;  // adaptive: in KState (the phi kernel reads it there)
+    if (replay) {
+      rs = readback(ctx);
+      if (rs != EXPDG_OK) return rs;
+      beta = std::sqrt(ctx->h_ks->red[0] + (P > 0 ? 1.0 / (eta * eta) : 0.0));
+      if (beta == 0.0) {  // P == 0 and c_0 == 0: the result is zero
+        sv += sigma;
+        st->substeps++;
+        if (trace) trace->push_back(expdg_trace_entry{solve_id, 0, sigma, eta});
+        continue;
+      }
+      const double s0 = iop ? 1.0 / beta : 1.0;  // incomplete orthogonalisation: slot 0 holds beta v_0
+      RUN(ctx, EXPDG_K_VECTOR, 16.0 * N, launch_start(F, ctx->ks, ctx->U, ctx->w, N, P, eta, s0, sigma * tau, 0, s));
+    } else {
+      // a zero start vector (P == 0, c_0 == 0) gives s0 = 0: the Arnoldi steps
+      // break down at once and the combination adds zero
+      RUN(ctx, EXPDG_K_VECTOR, 16.0 * N,
+          launch_start(F, ctx->ks, ctx->U, ctx->w, N, P, 0.0, 0.0, sigma * tau, iop ? 1 : 2, s));
+    }
     const int limit = replay ? m_fix : cfg.m_max;
     int m_first = cfg.m_step;
     const bool first_sub = (sv == 0.0 && rejected == 0);
@@ -478,12 +480,20 @@ expdg_status phi_solve(expdg_ctx* ctx, const void* qt_T, double tau, const bool*
       RUN(ctx, EXPDG_K_PHI, 8.0 * m * m,
           launch_phi(ctx->ks, m, beta, cfg.krylov_tol, replay ? 1 : 0, F ? 1 : 0, iop ? ctx->part : nullptr, F ? 1 : 0,
                      iop ? iom_update_blocks(F, iop, n_aug) : 0, F, s));
+      // the combination follows the check at once and writes only if it
+      // accepted, so an accepted check needs no second host round trip; its
+      // bytes are counted once the decision is known
+      const bool fin = last && fin_out.d != nullptr;
+      RUN(ctx, EXPDG_K_COMBINE, 0.0,
+          launch_combine(F, ctx->ks, ctx->U, fin ? fin_base : null_vec(), fin ? fin_out : ctx->w, N, true, s));
       rs = readback(ctx);
       if (rs != EXPDG_OK) return rs;
+      if (!replay) eta = ctx->h_ks->eta;
       if (ctx->h_ks->accept) {
         accepted = true;
         m_acc = ctx->h_ks->m_eff;
         err = ctx->h_ks->err;
+        ctx->prof[EXPDG_K_COMBINE].bytes += 8.0 * (m_acc + (fin ? 2 : 1)) * N;
         break;
       }
     }
@@ -493,11 +503,6 @@ expdg_status phi_solve(expdg_ctx* ctx, const void* qt_T, double tau, const bool*
         return fail(ctx, EXPDG_EKRYLOV, "Krylov solve did not converge within the sub-step budget");
       sigma *= 0.5;
       continue;
-    }
-    if (last && fin_out.d != nullptr) {
-      RUN(ctx, EXPDG_K_COMBINE, 8.0 * (m_acc + 2) * N, launch_combine(F, ctx->ks, ctx->U, fin_base, fin_out, N, s));
-    } else {
-      RUN(ctx, EXPDG_K_COMBINE, 8.0 * (m_acc + 1) * N, launch_combine(F, ctx->ks, ctx->U, null_vec(), ctx->w, N, s));
     }
     if (use_hint && first_sub && !replay) ctx->m_hint[solve_id & 1] = m_acc;
     sv += sigma;

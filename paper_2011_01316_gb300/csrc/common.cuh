@@ -178,6 +178,8 @@ struct KState {
   unsigned int pad0;
   // ---- host-visible block ----
   double red[8];            // results of the norms kernel
+  double beta;              // ||[c_0; e_P / eta]|| of the sub-step (computed on the device when adaptive)
+  double eta;               // tail scale of the sub-step (likewise)
   double err;               // error estimate at the last check
   double norm1;             // 1-norm of the last H_m
   int accept;               // set by the phi kernel
@@ -220,7 +222,17 @@ size_t reduction_scratch_entries();
 // out = sum_k a[k] x[k] (k < nx <= 5; x[k] with null pointers counts as 0), n entries
 cudaError_t launch_lincomb(bool use_ff, Vec out, int nx, const Vec* x, const double* a, size_t n, cudaStream_t s);
 // ks->red[k] = ||x_k||^2 (k < nx <= 5; null x[k] gives 0), n entries each
-cudaError_t launch_norms(bool use_ff, KState* ks, void* part, int nx, const Vec* x, size_t n, cudaStream_t s);
+// dev_P >= 0: also eta = 2^-round(log2 max_{1<=i<=P} ||x_i||) and
+// beta = sqrt(||x_0||^2 + (P > 0 ? 1/eta^2 : 0)) into KState (no host read needed).
+cudaError_t launch_norms(bool use_ff, KState* ks, void* part, int nx, const Vec* x, size_t n, int dev_P,
+                         cudaStream_t s);
+// 2^-round(log2 nrm) (1 for nrm <= 0 or not finite), the same on host and device.
+__host__ __device__ inline double tail_scale_of(double nrm) {
+  if (!(nrm > 0.0) || !(nrm < 1.0 / 0.0)) return 1.0;
+  int e = 0;
+  const double f = frexp(nrm, &e);  // nrm = f 2^e, f in [1/2, 1)
+  return ldexp(1.0, -(f >= 0.70710678118654752440 ? e : e - 1));
+}
 // format conversions (these use the FP64 pipe; only at API and step boundaries)
 cudaError_t launch_to_f32(float* out, const double* x, size_t n, cudaStream_t s);
 cudaError_t launch_f64_to_ff(Vec out, const double* x, size_t n, cudaStream_t s);
@@ -229,8 +241,10 @@ cudaError_t launch_ff_to_f64(double* out, Vec x, size_t n, cudaStream_t s);
 cudaError_t launch_f64_to_fx(float* out, const double* x, size_t n, cudaStream_t s);
 // Arnoldi start: u_0 = [b0; e_P / eta] (b0 null: zero top); clears the Krylov scalars;
 // vscale_0 = s0 (1 / beta for incomplete orthogonalisation, else 1), vscale_i = 1 for i > 0.
+// mode 0: eta and s0 as given; 1: eta from KState, s0 = 1 / beta (0 when beta = 0:
+// the zero start vector of incomplete orthogonalisation); 2: eta from KState, s0 = 1.
 cudaError_t launch_start(bool use_ff, KState* ks, Basis U, Vec b0, size_t N, int P, double eta, double s0,
-                         double alpha, cudaStream_t s);
+                         double alpha, int mode, cudaStream_t s);
 // Arnoldi step j by classical Gram-Schmidt with delayed re-orthogonalisation
 // (DCGS2).  On entry basis slots 0..j-1 hold the orthonormal q_i, slot j the
 // once-orthogonalised u_j, slot j+1 the operator image w = A_hat u_j.
@@ -272,6 +286,8 @@ cudaError_t launch_phi(KState* ks, int m, double beta, double tol, int force_acc
                        const void* iom_part, int iom_ff, int iom_gu, bool ff_arith, cudaStream_t s);
 // out = base + sum_{i < m_eff} ycoef_i u_i (first N entries; base may be null).
 // out and base may each be FP64 (d) or float-float (h, l).
-cudaError_t launch_combine(bool use_ff, const KState* ks, Basis U, Vec base, Vec out, size_t N, cudaStream_t s);
+// if_accepted: write nothing unless the last phi kernel accepted.
+cudaError_t launch_combine(bool use_ff, const KState* ks, Basis U, Vec base, Vec out, size_t N, bool if_accepted,
+                           cudaStream_t s);
 
 }  // namespace expdg

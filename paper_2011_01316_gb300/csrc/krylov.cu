@@ -189,6 +189,7 @@ struct LinArgs {
   float ah[NORMS_MAX], al[NORMS_MAX];
   int nx;
   size_t n;
+  int dev_P;  // norms: also eta and beta of P augmentation vectors into KState (-1: no)
 };
 
 template <bool FF>
@@ -235,7 +236,16 @@ __global__ void __launch_bounds__(NT) k_norms(KState* ks, typename Acc<FF>::T* p
     final_sums<FF>(part, NORMS_MAX, gridDim.x, res, red_stage<FF>());
     __syncthreads();
     if (threadIdx.x < NORMS_MAX) ks->red[threadIdx.x] = (threadIdx.x < a.nx) ? res[threadIdx.x] : 0.0;
-    if (threadIdx.x == 0) ks->counter = 0;
+    if (threadIdx.x == 0) {
+      if (a.dev_P >= 0) {
+        double mx = 0.0;
+        for (int i = 1; i <= a.dev_P; ++i) mx = fmax(mx, sqrt(res[i]));
+        const double eta = tail_scale_of(mx);
+        ks->eta = eta;
+        ks->beta = sqrt(res[0] + (a.dev_P > 0 ? 1.0 / (eta * eta) : 0.0));
+      }
+      ks->counter = 0;
+    }
   }
 }
 
@@ -256,8 +266,12 @@ __global__ void k_ff_to_f64(double* out, Vec x, size_t n) {
 }
 
 template <bool FF>
-__global__ void __launch_bounds__(NT) k_start(KState* ks, Vec u0, Vec b0, size_t N, int P, double eta, double s0,
-                                              double alpha) {
+__global__ void __launch_bounds__(NT) k_start(KState* ks, Vec u0, Vec b0, size_t N, int P, double eta_in,
+                                              double s0_in, double alpha, int mode) {
+  // mode 1, 2: the sub-step's eta and beta come from the norms kernel
+  const double eta = mode ? ks->eta : eta_in;
+  const double beta = mode ? ks->beta : 0.0;
+  const double s0 = mode == 1 ? (beta > 0.0 ? 1.0 / beta : 0.0) : (mode == 2 ? 1.0 : s0_in);
   using A = Acc<FF>;
   const bool present = FF ? (b0.h != nullptr) : (b0.d != nullptr);
   const size_t n_aug = N + P;
@@ -1305,6 +1319,7 @@ k_phi(KState* ks, int m_req, double beta, double tol, int force, int diff_rule, 
   using PT = PhiT<T>;
   using SC = typename PT::S;
   cg::cluster_group cl = cg::this_cluster();
+  if (beta < 0.0) beta = ks->beta;  // computed on the device by the norms kernel
   extern __shared__ __align__(16) unsigned char phi_smem[];
   __shared__ int s_m;
   __shared__ SC s_norm;
@@ -1446,7 +1461,9 @@ k_phi(KState* ks, int m_req, double beta, double tol, int force, int diff_rule, 
 }
 
 template <bool FF>
-__global__ void __launch_bounds__(NT) k_combine(const KState* ks, Basis U, Vec base, Vec out, size_t N) {
+__global__ void __launch_bounds__(NT) k_combine(const KState* ks, Basis U, Vec base, Vec out, size_t N,
+                                                int if_accepted) {
+  if (if_accepted && ks->accept == 0) return;
   using A = Acc<FF>;
   __shared__ typename A::T cf[MMAX + 1];
   const int m = ks->m_eff;
@@ -1480,7 +1497,9 @@ __global__ void __launch_bounds__(NT) k_combine(const KState* ks, Basis U, Vec b
 // issued before this one's arithmetic; packed compensated accumulation), then
 // out = base + x, out FP64 (d) or float-float (h, l), base FP64, float-float or
 // absent.
-__global__ void __launch_bounds__(NT) k_combine_ff(const KState* ks, Basis U, Vec base, Vec out, size_t N) {
+__global__ void __launch_bounds__(NT) k_combine_ff(const KState* ks, Basis U, Vec base, Vec out, size_t N,
+                                                   int if_accepted) {
+  if (if_accepted && ks->accept == 0) return;
   __shared__ float2 cf[MMAX + 1];
   const int m = ks->m_eff;
   for (int i = threadIdx.x; i < m; i += NT) {
@@ -1574,11 +1593,13 @@ cudaError_t launch_lincomb(bool use_ff, Vec out, int nx, const Vec* x, const dou
   return cudaGetLastError();
 }
 
-cudaError_t launch_norms(bool use_ff, KState* ks, void* part, int nx, const Vec* x, size_t n, cudaStream_t s) {
-  if (nx > NORMS_MAX) return cudaErrorInvalidValue;
+cudaError_t launch_norms(bool use_ff, KState* ks, void* part, int nx, const Vec* x, size_t n, int dev_P,
+                         cudaStream_t s) {
+  if (nx > NORMS_MAX || dev_P >= nx) return cudaErrorInvalidValue;
   LinArgs la{};
   la.nx = nx;
   la.n = n;
+  la.dev_P = dev_P;
   for (int k = 0; k < nx; ++k) la.x[k] = x[k];
   const int g = grid_for(n);
   const size_t smem = (size_t)NORMS_MAX * g * 8;
@@ -1621,12 +1642,12 @@ cudaError_t launch_ff_to_f64(double* out, Vec x, size_t n, cudaStream_t s) {
 }
 
 cudaError_t launch_start(bool use_ff, KState* ks, Basis U, Vec b0, size_t N, int P, double eta, double s0,
-                         double alpha, cudaStream_t s) {
+                         double alpha, int mode, cudaStream_t s) {
   const int g = grid_for(N + P);
   if (use_ff)
-    k_start<true><<<g, NT, 0, s>>>(ks, U.at(0), b0, N, P, eta, s0, alpha);
+    k_start<true><<<g, NT, 0, s>>>(ks, U.at(0), b0, N, P, eta, s0, alpha, mode);
   else
-    k_start<false><<<g, NT, 0, s>>>(ks, U.at(0), b0, N, P, eta, s0, alpha);
+    k_start<false><<<g, NT, 0, s>>>(ks, U.at(0), b0, N, P, eta, s0, alpha, mode);
   return cudaGetLastError();
 }
 
@@ -1799,12 +1820,13 @@ cudaError_t launch_phi(KState* ks, int m, double beta, double tol, int force_acc
   return cudaGetLastError();
 }
 
-cudaError_t launch_combine(bool use_ff, const KState* ks, Basis U, Vec base, Vec out, size_t N, cudaStream_t s) {
+cudaError_t launch_combine(bool use_ff, const KState* ks, Basis U, Vec base, Vec out, size_t N, bool if_accepted,
+                           cudaStream_t s) {
   if (N == 0) return cudaSuccess;
   if (use_ff)
-    k_combine_ff<<<grid_for(N / 4 + 1), NT, 0, s>>>(ks, U, base, out, N);
+    k_combine_ff<<<grid_for(N / 4 + 1), NT, 0, s>>>(ks, U, base, out, N, if_accepted ? 1 : 0);
   else
-    k_combine<false><<<grid_for(N), NT, 0, s>>>(ks, U, base, out, N);
+    k_combine<false><<<grid_for(N), NT, 0, s>>>(ks, U, base, out, N, if_accepted ? 1 : 0);
   return cudaGetLastError();
 }
 
