@@ -624,15 +624,6 @@ __global__ void __launch_bounds__(NT, 3) k_dots_ff(KState* ks, ff* part, Basis U
   if (last_block(&ks->counter, gridDim.x)) dots_last_block<true>(ks, part, j, G);
 }
 
-// (h, l) += (bh, bl) for float-float pairs, left un-normalised.
-__device__ __forceinline__ void ff2_add_acc(float2& h, float2& l, float2 bh, float2 bl) {
-  const float2 s = add2(h, bh);
-  const float2 bb = sub2(s, h);
-  const float2 e = add2(sub2(h, sub2(s, bb)), sub2(bh, bb));
-  h = s;
-  l = add2(l, add2(e, bl));
-}
-
 constexpr int UKG = 4;         // thread groups sharing one quad's basis loop
 constexpr int UQB = NT / UKG;  // quads per block tile
 
@@ -814,7 +805,8 @@ constexpr int IOP_MAX = EXPDG_MAX_IOP;
 // the reduction scratch: two regions, by the parity of j.
 constexpr int IOM_UPD_OFF = (IOP_MAX + 1) * RB;
 
-// Prologue of update launch j, in every block: sums the window products of
+// Prologue of update launch j (FP64 form; the float-float form uses
+// iom_prologue_ff below), in every block: sums the window products of
 // launch j (<slot_i, w'> for the window, then |w'|^2) and ||slot_j||^2 (the
 // partials of update launch j - 1), then
 //   c_j = 1 / ||slot_j||  (c_0: set by the start kernel),
