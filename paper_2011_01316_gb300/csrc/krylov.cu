@@ -1,15 +1,17 @@
 // Krylov kernels: Gram-Schmidt passes of the Arnoldi process on the
-// augmented matrix, the dense FP64 exponential of the projected Hessenberg
-// matrix, and the vector combinations of the phi-sum (paper Sec. 2.3).
+// augmented matrix, the dense exponential of the projected Hessenberg matrix,
+// and the vector combinations of the phi-sum (paper Sec. 2.3).
 //
 // Two storage forms share every kernel (template parameter FF):
 //   FP64 form:   vectors are double arrays, arithmetic on the FP64 pipe.
 //   mixed form:  vectors are float-float pairs (h, l); products and sums use
 //                the error-free transformations of ff.cuh on the FP32 pipe,
 //                which runs 74x faster than the FP64 pipe on this GPU.
-// Reductions are deterministic: each block writes one partial per value, the
-// last block to finish (atomic ticket) sums the partials in block order, one
-// warp per value.
+// Reductions are deterministic: each block writes one partial per value and
+// the partials are summed in block order, one warp per value - by the last
+// block to finish (atomic ticket) in the full-orthogonalisation and norm
+// kernels, by every block of the consuming launch in incomplete
+// orthogonalisation (see there).
 #include <algorithm>
 #include <cooperative_groups.h>
 
