@@ -158,3 +158,24 @@ def test_invalid_window_rejected(E):
         with pytest.raises(E.ExpdgError) as ei:
             E.Context(iop=bad)
         assert ei.value.status == E.EXPDG_EINVAL
+
+
+@pytest.mark.parametrize("prec", [0, 1])
+@pytest.mark.parametrize("iop", [0, 4])
+def test_zero_start_vector_adaptive(E, prec, iop):
+    """An adaptive phi-sum whose start vector is zero (P = 0 and c_0 = 0, or
+    P = 1 with c_1 = 0 and c_0 = 0): beta and eta are formed on the device, the
+    Arnoldi steps break down at once, and the result is exactly zero; a
+    following non-zero solve on the same context is unaffected."""
+    rng = np.random.default_rng(67)
+    ctx, mesh = make(E, "euler2d_p4", iop, prec=prec)
+    q = state(mesh, rng).reshape(-1)
+    z = np.zeros_like(q)
+    got, st, tr = ctx.phi(q, 0.05, [np.ascontiguousarray(z)])
+    assert np.all(got == 0.0)
+    got, st, tr = ctx.phi(q, 0.05, [None, np.ascontiguousarray(z)])
+    assert np.all(got == 0.0)
+    c = [np.zeros_like(q), rng.standard_normal(q.size) * 0.1]
+    ref, _ = krylov.phi_sum(lambda x: 0.05 * dg.jv(mesh, q, x).reshape(-1), c, tol=1e-10, iop=iop or None)
+    got, _, _ = ctx.phi(q, 0.05, [None, np.ascontiguousarray(c[1])])
+    assert rel(got, ref) <= (1e-9 if prec == 0 else TOL_MIXED)
