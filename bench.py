@@ -410,6 +410,7 @@ def main():
     ap.add_argument("--serve-workers", type=int, default=8, help="solves in flight in the served form")
     ap.add_argument("--burgers-iop", type=int, default=4, help="orthogonalisation window of the Burgers leg (0: full)")
     ap.add_argument("--batch-instances", type=int, default=256, help="instances of the batched workload (0: skip)")
+    ap.add_argument("--batch-workers", type=int, default=16, help="instances in flight in the batched workload")
     ap.add_argument("--no-3d", action="store_true", help="skip the 3D HBM-roofline workload")
     ap.add_argument("--legs", default="main,wave3d,burgers,exprb32,serving,batched",
                     help="comma list of legs to run (main = the timed workload; profiling runs pick one)")
@@ -449,7 +450,7 @@ def main():
         if "serving" in args.legs:
             out["serving"] = serving_workload(args.serve_requests, workers=args.serve_workers)
         if "batched" in args.legs:
-            out["batched"] = batched_workload(args.batch_instances)
+            out["batched"] = batched_workload(args.batch_instances, workers=args.batch_workers)
         if "burgers" in args.legs:
             out["burgers"] = burgers_workload(iop=args.burgers_iop)
         if "exprb32" in args.legs:
@@ -552,7 +553,8 @@ def main():
         wave3d = wave3d_workload(steps=args.wave3d_steps, hbm=hbm, ne=args.wave3d_ne, iop=args.iop)
     serving = (serving_workload(args.serve_requests, workers=args.serve_workers)
                if args.serve_requests > 0 and "serving" in legs else None)
-    batched = batched_workload(args.batch_instances) if args.batch_instances > 0 and "batched" in legs else None
+    batched = (batched_workload(args.batch_instances, workers=args.batch_workers)
+               if args.batch_instances > 0 and "batched" in legs else None)
     burgers = burgers_workload(iop=args.burgers_iop) if "burgers" in legs else None
     exprb32 = exprb32_workload() if "exprb32" in legs else None
 
