@@ -65,8 +65,8 @@ typedef enum { EXPDG_FLUX_LF = 0, EXPDG_FLUX_ROE = 1 } expdg_flux;
  *                expdg_residual and in every step) in float-float arithmetic;
  *                Krylov basis, inner products and orthogonalisation in
  *                float-float (pairs of FP32 numbers, 48-bit significand, FP32
- *                arithmetic with error-free transformations); phi(H) and the
- *                solution update in FP64.  An FP32 residual's rounding noise
+ *                arithmetic with error-free transformations); phi(H) in
+ *                float-float, the solution update in FP64.  An FP32 residual's rounding noise
  *                would cost extra Arnoldi steps, FP64 arithmetic runs on
  *                the slow FP64 pipe.
  *                On this GPU the FP64 pipe (and every f32<->f64 conversion)
@@ -198,10 +198,13 @@ expdg_status expdg_jv(expdg_ctx* ctx, const double* qt, const double* v, double*
  * breakdown).  In EXPDG_MIXED a check is also accepted when the approximation
  * changed by at most krylov_tol * beta since the previous check
  * (beta |y_m - [y_prev; 0]|): the FP32 operator's rounding noise inflates
- * Saad's estimate there without slowing the convergence of the approximation.  Reaching m_max halves the sub-step sigma; after an accepted
+ * Saad's estimate there without slowing the convergence of the approximation.
+ * Reaching m_max halves the sub-step sigma; after an accepted
  * sub-step with m <= m_max/2 sigma doubles (never past the end).  Sub-step
  * vectors: b_0 = w(s), b_i = sigma^i sum_j s^j/j! c_{i+j}.  The tail scale
- * eta = 2^-round(log2(max_i ||b_i||)).  If replay != NULL, the nreplay
+ * eta = 2^-round(log2(max_i ||b_i||)) (formed on the device when deciding
+ * adaptively; an accepted sub-step then costs one device-to-host read, the
+ * check's).  If replay != NULL, the nreplay
  * records (all with solve == 0) are followed instead of deciding; otherwise,
  * if trace != NULL, up to trace_cap accepted sub-steps are written there and
  * *ntrace is set. */
