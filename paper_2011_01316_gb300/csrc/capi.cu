@@ -46,7 +46,8 @@ struct expdg_ctx {
   void* part = nullptr;
   KState* h_ks = nullptr;  // pinned mirror (host-visible block only is refreshed)
   int m_hint[2] = {0, 0};  // m accepted by each stage's first sub-step in the previous step
-  int hint_uses[2] = {0, 0};  // steps that used the hint (every 4th also probes m_prev - m_step)
+  int hint_uses[2] = {0, 0};  // steps that used the hint (every 4th also probes one check lower)
+  bool probe_next[2] = {false, false};  // the last probe was accepted: probe again
   // CUDA graphs of Arnoldi segments (steps j0 .. j1-1), keyed by (j0, j1, P)
   std::map<long long, cudaGraphExec_t> graphs;
   cudaStream_t cap_stream = nullptr;  // private stream for graph capture
@@ -146,6 +147,15 @@ cudaError_t launch_dg_on(expdg_ctx* ctx, bool linear, const DGArgs& a, cudaStrea
   return cudaErrorInvalidValue;
 }
 
+long long graph_key(int j0, int j1, int P) { return ((long long)j0 * 1024 + j1) * 8 + P; }
+
+// The cached graph of Arnoldi steps j0 .. j1-1, or null.
+cudaGraphExec_t find_graph(expdg_ctx* ctx, int j0, int j1, int P) {
+  if (!ctx->graphs_ok) return nullptr;
+  auto it = ctx->graphs.find(graph_key(j0, j1, P));
+  return it == ctx->graphs.end() ? nullptr : it->second;
+}
+
 // Instantiated graph of Arnoldi steps j0 .. j1-1 for P augmentation vectors,
 // captured once on the context's private stream from `launches(j, stream,
 // counted = false)` and reused by every later sub-step (their launch
@@ -154,7 +164,7 @@ cudaError_t launch_dg_on(expdg_ctx* ctx, bool linear, const DGArgs& a, cudaStrea
 template <class F>
 cudaGraphExec_t segment_graph(expdg_ctx* ctx, int j0, int j1, int P, F&& launches) {
   if (!ctx->graphs_ok) return nullptr;
-  const long long key = ((long long)j0 * 1024 + j1) * 8 + P;
+  const long long key = graph_key(j0, j1, P);
   auto it = ctx->graphs.find(key);
   if (it != ctx->graphs.end()) return it->second;
   if (!ctx->cap_stream && cudaStreamCreateWithFlags(&ctx->cap_stream, cudaStreamNonBlocking) != cudaSuccess) {
@@ -278,13 +288,20 @@ cudaError_t jv_into(expdg_ctx* ctx, const void* qt_T, const void* v_T, Vec out, 
   return run(ctx, EXPDG_K_JV, (ctx->ff ? 16.0 : 24.0) * ctx->N, [&]() { return launch_dg(ctx, true, a); });
 }
 
-expdg_status readback(expdg_ctx* ctx) {
+// while_waiting: host work done after the copy is queued and before the wait
+// (the device is still busy with the queued launches).
+template <class W>
+expdg_status readback(expdg_ctx* ctx, W&& while_waiting) {
   const size_t off = offsetof(KState, red);
   CU(ctx, cudaMemcpyAsync(reinterpret_cast<char*>(ctx->h_ks) + off, reinterpret_cast<char*>(ctx->ks) + off,
                           sizeof(KState) - off, cudaMemcpyDeviceToHost, ctx->stream));
+  while_waiting();
   CU(ctx, cudaStreamSynchronize(ctx->stream));
   if (ctx->h_ks->status & 1) return fail(ctx, EXPDG_ENONPHYSICAL, "non-physical state (rho <= 0 or p <= 0)");
   return EXPDG_OK;
+}
+expdg_status readback(expdg_ctx* ctx) {
+  return readback(ctx, [] {});
 }
 
 struct Replay {
@@ -292,12 +309,16 @@ struct Replay {
   int n = 0;
 };
 
+
 // w = sum_{i=0}^P phi_i(tau L(qt)) c_i  (c_i in ctx->c, has[i] false: zero).
 // On the final sub-step the combination writes fin_out = fin_base + w instead
 // of ctx->w (fin_out null: result left in ctx->w).
-// use_hint: start the error checks of the first sub-step at
-// max(m_step, m_prev - m_step), m_prev the m this stage accepted in the previous
-// step (consecutive steps need similar m; a later acceptance is only more exact).
+// use_hint: start the error checks of the first sub-step at m_prev, the m this
+// stage accepted in the previous step (consecutive steps need similar m; a
+// later acceptance is only more exact); every 4th step, and the step after an
+// accepted probe, probes one check lower first (m_prev - 1 in the float-float
+// form, whose checks evaluate H_{m-1} and H_m together, else
+// max(m_step, m_prev - m_step)).
 expdg_status phi_solve(expdg_ctx* ctx, const void* qt_T, double tau, const bool* has, int P, Vec fin_base,
                        Vec fin_out, int solve_id, const Replay& rp, expdg_stats* st,
                        std::vector<expdg_trace_entry>* trace, bool use_hint = false) {
@@ -383,11 +404,18 @@ expdg_status phi_solve(expdg_ctx* ctx, const void* qt_T, double tau, const bool*
           launch_start(F, ctx->ks, ctx->U, ctx->w, N, P, 0.0, 0.0, sigma * tau, iop ? 1 : 2, s));
     }
     const int limit = replay ? m_fix : cfg.m_max;
-    int m_first = cfg.m_step;
+    // checks at m_first, m_again, m_late, then at the multiples of m_step
+    int m_first = cfg.m_step, m_again = 0, m_late = 0;
     const bool first_sub = (sv == 0.0 && rejected == 0);
-    if (use_hint && first_sub && !replay && ctx->m_hint[solve_id & 1] > 0) {
-      const bool probe = (ctx->hint_uses[solve_id & 1]++ % 4) == 0;
-      m_first = std::max(cfg.m_step, ctx->m_hint[solve_id & 1] - (probe ? cfg.m_step : 0));
+    const int sid = solve_id & 1;
+    bool probe = false;
+    if (use_hint && first_sub && !replay && ctx->m_hint[sid] > 0) {
+      probe = ctx->probe_next[sid] || (ctx->hint_uses[sid] % 4) == 0;
+      ctx->hint_uses[sid]++;
+      const int h = ctx->m_hint[sid];
+      m_first = F ? std::max(1, h - (probe ? 1 : 0)) : std::max(cfg.m_step, h - (probe ? cfg.m_step : 0));
+      m_again = h;
+      if (F) m_late = h + 2;  // the float-float form's checks carry their own pair: cheap to retry
     }
     bool accepted = false;
     int m_acc = 0;
@@ -450,43 +478,59 @@ expdg_status phi_solve(expdg_ctx* ctx, const void* qt_T, double tau, const bool*
       return l2();
     };
     auto due = [&](int m) {
-      return replay ? (m == m_fix) : (m == cfg.m_max || (m >= m_first && m % cfg.m_step == 0));
+      return replay ? (m == m_fix)
+                    : (m == cfg.m_max || m == m_first || m == m_again || m == m_late ||
+                       (m > m_first && m % cfg.m_step == 0));
+    };
+    // Arnoldi steps j0 .. j1 - 1: one graph replay, or direct launches when
+    // the range has no graph yet (it is captured while the host next waits
+    // for the device, so a new range never waits for a capture)
+    std::vector<std::pair<int, int>> to_capture;
+    auto segment = [&](int j0, int j1) -> cudaError_t {
+      cudaGraphExec_t g = ctx->prof_on ? nullptr : find_graph(ctx, j0, j1, P);
+      if (!g && !ctx->prof_on && ctx->graphs_ok) to_capture.emplace_back(j0, j1);
+      if (!g) {
+        for (int jj = j0; jj < j1; ++jj) {
+          const cudaError_t e = step_launches(jj, s, true);
+          if (e != cudaSuccess) return e;
+        }
+        return cudaSuccess;
+      }
+      for (int jj = j0; jj < j1; ++jj) {  // count the replayed launches like direct ones
+        const int nwin = iop ? std::min(iop, jj + 1) : 0;
+        ctx->prof[EXPDG_K_JV].launches++;
+        ctx->prof[EXPDG_K_JV].bytes += (F ? 16.0 : 24.0) * N;
+        ctx->prof[EXPDG_K_DOTS].launches++;
+        ctx->prof[EXPDG_K_DOTS].bytes += (iop ? nwin + 1 : jj + 2) * vb;
+        ctx->prof[EXPDG_K_UPDATE].launches++;
+        ctx->prof[EXPDG_K_UPDATE].bytes += (iop ? nwin + 2 : jj + 4) * vb;
+      }
+      return cudaGraphLaunch(g, s);
     };
     int j = 0;
     while (j < limit) {
       int m = j + 1;  // next error check (due at m == limit at the latest)
       while (m < limit && !due(m)) ++m;
-      cudaGraphExec_t g = ctx->prof_on ? nullptr : segment_graph(ctx, j, m, P, step_launches);
-      if (g) {
-        CU(ctx, cudaGraphLaunch(g, s));
-        for (int jj = j; jj < m; ++jj) {  // count the replayed launches like direct ones
-          const int nwin = iop ? std::min(iop, jj + 1) : 0;
-          ctx->prof[EXPDG_K_JV].launches++;
-          ctx->prof[EXPDG_K_JV].bytes += (F ? 16.0 : 24.0) * N;
-          ctx->prof[EXPDG_K_DOTS].launches++;
-          ctx->prof[EXPDG_K_DOTS].bytes += (iop ? nwin + 1 : jj + 2) * vb;
-          ctx->prof[EXPDG_K_UPDATE].launches++;
-          ctx->prof[EXPDG_K_UPDATE].bytes += (iop ? nwin + 2 : jj + 4) * vb;
-        }
-      } else {
-        for (int jj = j; jj < m; ++jj) CU(ctx, step_launches(jj, s, true));
-      }
+      CU(ctx, segment(j, m));
       st->krylov_iters += m - j;
       st->jv_applies += m - j;
       j = m;
       if (!due(m)) continue;
       // mixed form: the FP32 operator's rounding noise inflates Saad's estimate, so a
-      // converged change between consecutive checks also accepts
+      // converged change since m - 1 also accepts (the check evaluates both)
       RUN(ctx, EXPDG_K_PHI, 8.0 * m * m,
           launch_phi(ctx->ks, m, beta, cfg.krylov_tol, replay ? 1 : 0, F ? 1 : 0, iop ? ctx->part : nullptr, F ? 1 : 0,
-                     iop ? iom_update_blocks(F, iop, n_aug) : 0, F, s));
+                     iop ? iom_update_blocks(F, iop, n_aug) : 0, F, F && !replay, s));
       // the combination follows the check at once and writes only if it
       // accepted, so an accepted check needs no second host round trip; its
       // bytes are counted once the decision is known
       const bool fin = last && fin_out.d != nullptr;
       RUN(ctx, EXPDG_K_COMBINE, 0.0,
           launch_combine(F, ctx->ks, ctx->U, fin ? fin_base : null_vec(), fin ? fin_out : ctx->w, N, true, s));
-      rs = readback(ctx);
+      rs = readback(ctx, [&] {
+        for (const auto& r : to_capture) segment_graph(ctx, r.first, r.second, P, step_launches);
+        to_capture.clear();
+      });
       if (rs != EXPDG_OK) return rs;
       if (!replay) eta = ctx->h_ks->eta;
       if (ctx->h_ks->accept) {
@@ -504,7 +548,10 @@ expdg_status phi_solve(expdg_ctx* ctx, const void* qt_T, double tau, const bool*
       sigma *= 0.5;
       continue;
     }
-    if (use_hint && first_sub && !replay) ctx->m_hint[solve_id & 1] = m_acc;
+    if (use_hint && first_sub && !replay) {
+      ctx->m_hint[sid] = m_acc;
+      ctx->probe_next[sid] = probe && m_acc == m_first;  // m still falling: probe again next step
+    }
     sv += sigma;
     st->substeps++;
     st->err_est = std::fmax(st->err_est, err);
@@ -1048,6 +1095,7 @@ expdg_status expdg_advance(expdg_ctx* ctx, double* q, double dt, int nsteps, exp
   // a solve's decisions depend only on its own inputs, not on earlier calls
   ctx->m_hint[0] = ctx->m_hint[1] = 0;
   ctx->hint_uses[0] = ctx->hint_uses[1] = 0;
+  ctx->probe_next[0] = ctx->probe_next[1] = false;
   for (int k = 0; k < nsteps; ++k) {
     expdg_status r = step_dev(ctx, qd, dt, rp, &st, nullptr);
     if (r != EXPDG_OK) return r;

@@ -1241,6 +1241,11 @@ __global__ void __launch_bounds__(NT) k_iom_update(KState* ks, double* part, Bas
 constexpr int PHI_CL = 8;
 constexpr int PHI_NT = 256;
 constexpr int PHI_KS = 4;
+// Largest m whose pair (H_{m-1} and H_m, six copies each) fits the 227 KB of
+// shared memory a CTA may have.
+constexpr int PHI_PAIR_MAX = 49;
+static_assert(6 * 8 * (PHI_PAIR_MAX * PHI_PAIR_MAX + (PHI_PAIR_MAX - 1) * (PHI_PAIR_MAX - 1)) + 256 <= 227 * 1024,
+              "the pair fits one CTA's shared memory");
 
 // 1/k!, k = 0..18, as FP64 and as float-float pairs (computed on the host).
 struct PhiConst {
@@ -1279,28 +1284,54 @@ struct PhiT<ff> {
   }
 };
 
+// The matrices of one evaluation: nb (1 or 2) square diagonal blocks stored
+// packed, block 0 n0 x n0 row-major from offset 0, block 1 n1 x n1 from off1,
+// tot entries in all.  With two blocks exp(H_{m-1}) and exp(H_m) are formed
+// together (the change of the approximation since m - 1 for the float-float
+// form's test).
+struct PhiBlocks {
+  int nb, n0, n1, off1, tot;
+  __device__ int n(int b) const { return b ? n1 : n0; }
+  __device__ int off(int b) const { return b ? off1 : 0; }
+  __device__ void rc(int idx, int& b, int& r, int& c) const {
+    b = (nb > 1 && idx >= off1) ? 1 : 0;
+    const int o = idx - off(b), nn = n(b);
+    r = o / nn;
+    c = o - r * nn;
+  }
+};
+
+// C = A B blockwise.  The entries are split evenly across the CTAs, each
+// entry's sum over k across PHI_KS adjacent lanes; every CTA writes its
+// entries into all CTAs' copies, then one cluster barrier.
 template <typename T>
-__device__ void cl_matmul(cg::cluster_group& cl, const T* A, const T* B, T* C, int m) {
+__device__ void cl_matmul(cg::cluster_group& cl, const T* A, const T* B, T* C, const PhiBlocks& bk) {
   using PT = PhiT<T>;
   const int rank = (int)cl.block_rank();
-  const int r0 = (m * rank) / PHI_CL, r1 = (m * (rank + 1)) / PHI_CL;
+  const int e0 = (bk.tot * rank) / PHI_CL, e1 = (bk.tot * (rank + 1)) / PHI_CL;
   T* dst[PHI_CL];
 #pragma unroll
   for (int t = 0; t < PHI_CL; ++t) dst[t] = cl.map_shared_rank(C, t);
-  const int nout = (r1 - r0) * m;
+  const int nout = e1 - e0;
   const int rounds = (nout * PHI_KS + blockDim.x - 1) / blockDim.x;  // the same for every thread
   for (int rd = 0; rd < rounds; ++rd) {
     const int g = rd * blockDim.x + threadIdx.x;
-    const int o = g / PHI_KS, q = g - o * PHI_KS;  // entry o, part q of its sum
-    const int r = r0 + o / m, c = o - (o / m) * m;
+    const int o = g / PHI_KS, q = g - o * PHI_KS;  // entry e0 + o, part q of its sum
+    const int idx = e0 + o;
     T acc = PT::zero();
-    if (o < nout)
-      for (int k = q; k < m; k += PHI_KS) acc = PT::mad(A[r * m + k], B[k * m + c], acc);
+    if (o < nout) {
+      int b, r, c;
+      bk.rc(idx, b, r, c);
+      const int n = bk.n(b);
+      const T* Ab = A + bk.off(b) + r * n;
+      const T* Bb = B + bk.off(b) + c;
+      for (int k = q; k < n; k += PHI_KS) acc = PT::mad(Ab[k], Bb[k * n], acc);
+    }
 #pragma unroll
     for (int off = 1; off < PHI_KS; off <<= 1) acc = PT::add(acc, PT::shfl_xor(acc, off));
     if (o < nout && q == 0) {
 #pragma unroll
-      for (int t = 0; t < PHI_CL; ++t) dst[t][r * m + c] = acc;
+      for (int t = 0; t < PHI_CL; ++t) dst[t][idx] = acc;
     }
   }
   cl.sync();
@@ -1309,7 +1340,7 @@ __device__ void cl_matmul(cg::cluster_group& cl, const T* A, const T* B, T* C, i
 template <typename T>
 __global__ void __cluster_dims__(PHI_CL, 1, 1) __launch_bounds__(PHI_NT)
 k_phi(KState* ks, int m_req, double beta, double tol, int force, int diff_rule, const void* iom_part, int iom_ff,
-      int iom_gu, const PhiConst pc) {
+      int iom_gu, int pair, const PhiConst pc) {
   using PT = PhiT<T>;
   using SC = typename PT::S;
   cg::cluster_group cl = cg::this_cluster();
@@ -1354,23 +1385,36 @@ k_phi(KState* ks, int m_req, double beta, double tol, int force, int diff_rule, 
     }
     __syncthreads();
   }
-  const int m = s_m, mm = m * m;
+  const int m = s_m;
+  // pair: H_{m-1} as block 0 beside H_m (block 1), the same scaling for both
+  // (the leading block's 1-norm is at most H_m's)
+  const bool two = pair && m >= 2 && !s_brk;
+  PhiBlocks bk;
+  bk.nb = two ? 2 : 1;
+  bk.n0 = two ? m - 1 : m;
+  bk.n1 = m;
+  bk.off1 = two ? (m - 1) * (m - 1) : 0;
+  bk.tot = bk.off1 + m * m;
+  const int tot = bk.tot, ncol = bk.n0 + (two ? m : 0);
   T* X = reinterpret_cast<T*>(phi_smem);
-  T* X2 = X + mm;
-  T* X3 = X2 + mm;
-  T* X4 = X3 + mm;
-  T* T0 = X4 + mm;
-  T* T1 = T0 + mm;
-  for (int idx = threadIdx.x; idx < mm; idx += blockDim.x) {
-    const int r = idx / m, c = idx - r * m;
+  T* X2 = X + tot;
+  T* X3 = X2 + tot;
+  T* X4 = X3 + tot;
+  T* T0 = X4 + tot;
+  T* T1 = T0 + tot;
+  for (int idx = threadIdx.x; idx < tot; idx += blockDim.x) {
+    int b, r, c;
+    bk.rc(idx, b, r, c);
     X[idx] = PT::from_d(ks->H[c * (MMAX + 1) + r]);
   }
   __syncthreads();
-  if (threadIdx.x < 32) {
+  if (threadIdx.x < 32) {  // largest column sum over both blocks
     SC mx = 0;
-    for (int c = threadIdx.x; c < m; c += 32) {
+    for (int cc = threadIdx.x; cc < ncol; cc += 32) {
+      const int b = (cc >= bk.n0) ? 1 : 0, c = cc - (b ? bk.n0 : 0), n = bk.n(b);
+      const T* Xb = X + bk.off(b);
       SC cs = 0;
-      for (int r = 0; r < m; ++r) cs += PT::mag(X[r * m + c]);
+      for (int r = 0; r < n; ++r) cs += PT::mag(Xb[r * n + c]);
       mx = cs > mx ? cs : mx;
     }
     for (int off = 16; off > 0; off >>= 1) {
@@ -1383,14 +1427,15 @@ k_phi(KState* ks, int m_req, double beta, double tol, int force, int diff_rule, 
   int sq = 0;
   if (s_norm > SC(0.5)) sq = (int)ceil(log2(s_norm / SC(0.5)));
   const SC scale = (SC)ldexp(1.0f, -sq);  // a power of two: exact in both types
-  for (int idx = threadIdx.x; idx < mm; idx += blockDim.x) X[idx] = PT::pow2(X[idx], scale);
+  for (int idx = threadIdx.x; idx < tot; idx += blockDim.x) X[idx] = PT::pow2(X[idx], scale);
   cl.sync();  // every CTA has its scaled copy before any remote write lands
-  cl_matmul(cl, X, X, X2, m);
-  cl_matmul(cl, X2, X, X3, m);
-  cl_matmul(cl, X2, X2, X4, m);
+  cl_matmul(cl, X, X, X2, bk);
+  cl_matmul(cl, X2, X, X3, bk);
+  cl_matmul(cl, X2, X2, X4, bk);
   // E = B_4
-  for (int idx = threadIdx.x; idx < mm; idx += blockDim.x) {
-    const int r = idx / m, c = idx - r * m;
+  for (int idx = threadIdx.x; idx < tot; idx += blockDim.x) {
+    int b, r, c;
+    bk.rc(idx, b, r, c);
     const T diag = (r == c) ? PT::cnst(pc, 16) : PT::zero();
     T0[idx] = PT::mad(PT::cnst(pc, 18), X2[idx], PT::mad(PT::cnst(pc, 17), X[idx], diag));
   }
@@ -1398,11 +1443,12 @@ k_phi(KState* ks, int m_req, double beta, double tol, int force, int diff_rule, 
   T* E = T0;
   T* F = T1;
   for (int j = 3; j >= 0; --j) {
-    cl_matmul(cl, X4, E, F, m);
+    cl_matmul(cl, X4, E, F, bk);
     const T c0 = PT::cnst(pc, 4 * j), c1 = PT::cnst(pc, 4 * j + 1), c2 = PT::cnst(pc, 4 * j + 2),
             c3 = PT::cnst(pc, 4 * j + 3);
-    for (int idx = threadIdx.x; idx < mm; idx += blockDim.x) {
-      const int r = idx / m, c = idx - r * m;
+    for (int idx = threadIdx.x; idx < tot; idx += blockDim.x) {
+      int b, r, c;
+      bk.rc(idx, b, r, c);
       const T f = (r == c) ? PT::add(F[idx], c0) : F[idx];
       F[idx] = PT::mad(c3, X3[idx], PT::mad(c2, X2[idx], PT::mad(c1, X[idx], f)));
     }
@@ -1412,18 +1458,22 @@ k_phi(KState* ks, int m_req, double beta, double tol, int force, int diff_rule, 
     F = t;
   }
   for (int k = 0; k < sq; ++k) {
-    cl_matmul(cl, E, E, F, m);
+    cl_matmul(cl, E, E, F, bk);
     T* t = E;
     E = F;
     F = t;
   }
   if (cl.block_rank() == 0) {
     __shared__ double s_d2[PHI_NT / 32];
-    // squared change of y from the previous check (entries beyond m_prev count fully)
+    // y = exp(H_m) e_1: column 0 of the last block
+    const T* Em = E + bk.off1;
+    // squared change of y since m - 1 (pair) or since the previous check
+    // (entries beyond the shorter vector count fully)
     double d2 = 0.0;
-    const int mp = ks->mprev;
+    const int mp = two ? m - 1 : ks->mprev;
     for (int i = threadIdx.x; i < m; i += blockDim.x) {
-      const double di = PT::to_d(E[i * m]) - ((i < mp) ? ks->yprev[i] : 0.0);
+      const double yo = (i < mp) ? (two ? PT::to_d(E[i * (m - 1)]) : ks->yprev[i]) : 0.0;
+      const double di = PT::to_d(Em[i * m]) - yo;
       d2 += di * di;
     }
     for (int off = 16; off > 0; off >>= 1) d2 += __shfl_down_sync(0xffffffffu, d2, off);
@@ -1434,7 +1484,7 @@ k_phi(KState* ks, int m_req, double beta, double tol, int force, int diff_rule, 
       for (int w = 0; w < PHI_NT / 32; ++w) dsum += s_d2[w];
       const bool brk = s_brk != 0;
       const double hm = s_hm;
-      const double err = brk ? 0.0 : beta * hm * fabs(PT::to_d(E[(m - 1) * m]));
+      const double err = brk ? 0.0 : beta * hm * fabs(PT::to_d(Em[(m - 1) * m]));
       const double dif = (mp > 0) ? beta * sqrt(dsum) : 1.0 / 0.0;
       const bool ok = brk || err <= tol * beta || (diff_rule && dif <= tol * beta);
       ks->err = diff_rule ? fmin(err, dif) : err;
@@ -1445,7 +1495,7 @@ k_phi(KState* ks, int m_req, double beta, double tol, int force, int diff_rule, 
     }
     __syncthreads();
     for (int i = threadIdx.x; i < m; i += blockDim.x) {
-      const double y = PT::to_d(E[i * m]);
+      const double y = PT::to_d(Em[i * m]);
       ks->ycoef[i] = beta * y * ks->vscale[i];
       ks->yprev[i] = y;
     }
@@ -1784,8 +1834,9 @@ cudaError_t launch_iom_update(bool use_ff, int iop, KState* ks, void* part, Basi
 }
 
 cudaError_t launch_phi(KState* ks, int m, double beta, double tol, int force_accept, int diff_rule,
-                       const void* iom_part, int iom_ff, int iom_gu, bool ff_arith, cudaStream_t s) {
+                       const void* iom_part, int iom_ff, int iom_gu, bool ff_arith, bool pair, cudaStream_t s) {
   if (m < 1 || m > MMAX) return cudaErrorInvalidValue;
+  pair = pair && m >= 2 && m <= PHI_PAIR_MAX;
   static const PhiConst pc = [] {
     PhiConst c{};
     double f = 1.0;
@@ -1798,8 +1849,9 @@ cudaError_t launch_phi(KState* ks, int m, double beta, double tol, int force_acc
     return c;
   }();
   static_assert(sizeof(double) == sizeof(ff), "the two forms use the same shared memory");
-  const size_t smem = 6 * sizeof(double) * (size_t)m * m;
-  const int smax = (int)(6 * sizeof(double) * MMAX * MMAX);
+  const size_t smem = 6 * sizeof(double) * ((size_t)m * m + (pair ? (size_t)(m - 1) * (m - 1) : 0));
+  const int smax = (int)(6 * sizeof(double) *
+                         std::max(MMAX * MMAX, PHI_PAIR_MAX * PHI_PAIR_MAX + (PHI_PAIR_MAX - 1) * (PHI_PAIR_MAX - 1)));
   static const cudaError_t configured = [smax] {
     cudaError_t e = cudaFuncSetAttribute(k_phi<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, smax);
     if (e == cudaSuccess) e = cudaFuncSetAttribute(k_phi<ff>, cudaFuncAttributeMaxDynamicSharedMemorySize, smax);
@@ -1807,10 +1859,11 @@ cudaError_t launch_phi(KState* ks, int m, double beta, double tol, int force_acc
   }();
   if (configured != cudaSuccess) return configured;
   if (ff_arith)
-    k_phi<ff><<<PHI_CL, PHI_NT, smem, s>>>(ks, m, beta, tol, force_accept, diff_rule, iom_part, iom_ff, iom_gu, pc);
+    k_phi<ff><<<PHI_CL, PHI_NT, smem, s>>>(ks, m, beta, tol, force_accept, diff_rule, iom_part, iom_ff, iom_gu,
+                                           pair ? 1 : 0, pc);
   else
     k_phi<double><<<PHI_CL, PHI_NT, smem, s>>>(ks, m, beta, tol, force_accept, diff_rule, iom_part, iom_ff, iom_gu,
-                                               pc);
+                                               pair ? 1 : 0, pc);
   return cudaGetLastError();
 }
 
