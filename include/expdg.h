@@ -198,9 +198,10 @@ expdg_status expdg_jv(expdg_ctx* ctx, const double* qt, const double* v, double*
  * breakdown).  In EXPDG_MIXED a check at m is also accepted when the
  * approximation changed by at most krylov_tol * beta since m - 1
  * (beta |y_m - [y_{m-1}; 0]|, y_{m-1} = exp(H_{m-1}) e_1 evaluated in the same
- * launch for m <= 49, else the previous check's): the FP32 operator's rounding
- * noise inflates Saad's estimate there without slowing the convergence of the
- * approximation.  Reaching m_max halves the sub-step sigma; after an accepted
+ * launch, for m <= 49 on problems of at least 131072 unknowns), else when it
+ * changed by at most that since the previous check: the FP32 operator's
+ * rounding noise inflates Saad's estimate there without slowing the
+ * convergence of the approximation.  Reaching m_max halves the sub-step sigma; after an accepted
  * sub-step with m <= m_max/2 sigma doubles (never past the end).  Sub-step
  * vectors: b_0 = w(s), b_i = sigma^i sum_j s^j/j! c_{i+j}.  The tail scale
  * eta = 2^-round(log2(max_i ||b_i||)) (formed on the device when deciding
@@ -219,12 +220,12 @@ expdg_status expdg_phi(expdg_ctx* ctx, const double* qt, double tau, const doubl
  * EXPRB42 (Sec. 5.1 / 5.2 footnotes).  replay / trace as in expdg_phi, with
  * the solve index distinguishing the two stages.  Without replay, the error
  * checks of each stage's first sub-step start at m_prev, the m that stage
- * accepted in this context's previous step, and every fourth step (and after
- * a probe that was accepted) one check lower (m_prev - 1 in EXPDG_MIXED,
- * max(m_step, m_prev - m_step) in EXPDG_FP64) so that a falling m is found
+ * accepted in this context's previous step, and every eighth step (and after
+ * a probe that was accepted) one check lower (m_prev - 1 with paired checks,
+ * else max(m_step, m_prev - m_step)) so that a falling m is found
  * (steps in a row need similar m; starting later can only give a more
- * accurate result).  Then m_prev itself, in EXPDG_MIXED m_prev + 2, and the
- * multiples of m_step. */
+ * accurate result).  Then m_prev itself, with paired checks (above) m_prev + 2
+ * and m_prev + 4, and the multiples of m_step. */
 expdg_status expdg_step(expdg_ctx* ctx, double* q, double dt, expdg_stats* stats,
                         const expdg_trace_entry* replay, int nreplay,
                         expdg_trace_entry* trace, int trace_cap, int* ntrace);

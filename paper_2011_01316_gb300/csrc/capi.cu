@@ -46,7 +46,7 @@ struct expdg_ctx {
   void* part = nullptr;
   KState* h_ks = nullptr;  // pinned mirror (host-visible block only is refreshed)
   int m_hint[2] = {0, 0};  // m accepted by each stage's first sub-step in the previous step
-  int hint_uses[2] = {0, 0};  // steps that used the hint (every 4th also probes one check lower)
+  int hint_uses[2] = {0, 0};  // steps that used the hint (every 8th also probes one check lower)
   bool probe_next[2] = {false, false};  // the last probe was accepted: probe again
   // CUDA graphs of Arnoldi segments (steps j0 .. j1-1), keyed by (j0, j1, P)
   std::map<long long, cudaGraphExec_t> graphs;
@@ -309,16 +309,17 @@ struct Replay {
   int n = 0;
 };
 
+constexpr size_t kPairMinUnknowns = 131072;
+
 
 // w = sum_{i=0}^P phi_i(tau L(qt)) c_i  (c_i in ctx->c, has[i] false: zero).
 // On the final sub-step the combination writes fin_out = fin_base + w instead
 // of ctx->w (fin_out null: result left in ctx->w).
 // use_hint: start the error checks of the first sub-step at m_prev, the m this
 // stage accepted in the previous step (consecutive steps need similar m; a
-// later acceptance is only more exact); every 4th step, and the step after an
-// accepted probe, probes one check lower first (m_prev - 1 in the float-float
-// form, whose checks evaluate H_{m-1} and H_m together, else
-// max(m_step, m_prev - m_step)).
+// later acceptance is only more exact); every 8th step, and the step after an
+// accepted probe, probes one check lower first (m_prev - 1 with paired checks,
+// which evaluate H_{m-1} and H_m together, else max(m_step, m_prev - m_step)).
 expdg_status phi_solve(expdg_ctx* ctx, const void* qt_T, double tau, const bool* has, int P, Vec fin_base,
                        Vec fin_out, int solve_id, const Replay& rp, expdg_stats* st,
                        std::vector<expdg_trace_entry>* trace, bool use_hint = false) {
@@ -404,18 +405,23 @@ expdg_status phi_solve(expdg_ctx* ctx, const void* qt_T, double tau, const bool*
           launch_start(F, ctx->ks, ctx->U, ctx->w, N, P, 0.0, 0.0, sigma * tau, iop ? 1 : 2, s));
     }
     const int limit = replay ? m_fix : cfg.m_max;
-    // checks at m_first, m_again, m_late, then at the multiples of m_step
+    // checks at m_first, m_again, m_late and m_late + 2, then at the multiples of m_step
     int m_first = cfg.m_step, m_again = 0, m_late = 0;
+    // Paired checks (the float-float form's change since m - 1, evaluated in the
+    // check's launch) on problems of at least kPairMinUnknowns: there an Arnoldi
+    // step costs more than the second exponential.  Below that, when many
+    // small solves share the GPU, the extra cluster time outweighs the saved steps.
+    const bool pairs = F && !replay && N >= kPairMinUnknowns;
     const bool first_sub = (sv == 0.0 && rejected == 0);
     const int sid = solve_id & 1;
     bool probe = false;
     if (use_hint && first_sub && !replay && ctx->m_hint[sid] > 0) {
-      probe = ctx->probe_next[sid] || (ctx->hint_uses[sid] % 4) == 0;
+      probe = ctx->probe_next[sid] || (ctx->hint_uses[sid] % 8) == 0;
       ctx->hint_uses[sid]++;
       const int h = ctx->m_hint[sid];
-      m_first = F ? std::max(1, h - (probe ? 1 : 0)) : std::max(cfg.m_step, h - (probe ? cfg.m_step : 0));
+      m_first = pairs ? std::max(1, h - (probe ? 1 : 0)) : std::max(cfg.m_step, h - (probe ? cfg.m_step : 0));
       m_again = h;
-      if (F) m_late = h + 2;  // the float-float form's checks carry their own pair: cheap to retry
+      if (pairs) m_late = h + 2;  // checks carry their own pair: cheap to retry
     }
     bool accepted = false;
     int m_acc = 0;
@@ -479,8 +485,8 @@ expdg_status phi_solve(expdg_ctx* ctx, const void* qt_T, double tau, const bool*
     };
     auto due = [&](int m) {
       return replay ? (m == m_fix)
-                    : (m == cfg.m_max || m == m_first || m == m_again || m == m_late ||
-                       (m > m_first && m % cfg.m_step == 0));
+                    : (m == cfg.m_max || m == m_first || m == m_again ||
+                       (m_late > 0 && (m == m_late || m == m_late + 2)) || (m > m_first && m % cfg.m_step == 0));
     };
     // Arnoldi steps j0 .. j1 - 1: one graph replay, or direct launches when
     // the range has no graph yet (it is captured while the host next waits
@@ -520,7 +526,7 @@ expdg_status phi_solve(expdg_ctx* ctx, const void* qt_T, double tau, const bool*
       // converged change since m - 1 also accepts (the check evaluates both)
       RUN(ctx, EXPDG_K_PHI, 8.0 * m * m,
           launch_phi(ctx->ks, m, beta, cfg.krylov_tol, replay ? 1 : 0, F ? 1 : 0, iop ? ctx->part : nullptr, F ? 1 : 0,
-                     iop ? iom_update_blocks(F, iop, n_aug) : 0, F, F && !replay, s));
+                     iop ? iom_update_blocks(F, iop, n_aug) : 0, F, pairs, s));
       // the combination follows the check at once and writes only if it
       // accepted, so an accepted check needs no second host round trip; its
       // bytes are counted once the decision is known
@@ -550,7 +556,7 @@ expdg_status phi_solve(expdg_ctx* ctx, const void* qt_T, double tau, const bool*
     }
     if (use_hint && first_sub && !replay) {
       ctx->m_hint[sid] = m_acc;
-      ctx->probe_next[sid] = probe && m_acc == m_first;  // m still falling: probe again next step
+      ctx->probe_next[sid] = probe && m_acc == m_first;  // m may still fall: probe again next step
     }
     sv += sigma;
     st->substeps++;
