@@ -179,3 +179,27 @@ def test_zero_start_vector_adaptive(E, prec, iop):
     ref, _ = krylov.phi_sum(lambda x: 0.05 * dg.jv(mesh, q, x).reshape(-1), c, tol=1e-10, iop=iop or None)
     got, _, _ = ctx.phi(q, 0.05, [None, np.ascontiguousarray(c[1])])
     assert rel(got, ref) <= (1e-9 if prec == 0 else TOL_MIXED)
+
+
+def test_mixed_paired_checks_trajectory(E):
+    """Six EPI2 steps of the vortex on 40 x 40 elements, p = 4 (160,000
+    unknowns: the mixed form's checks evaluate exp(H_{m-1}) beside exp(H_m) and
+    accept on the change since m - 1), with the schedule that starts at the
+    previous step's m, probes below it and retries above it.  Every step stays
+    within 1e-7 of the oracle's FP64 full-Arnoldi trajectory at tol 1e-10 (ten
+    times the Krylov tolerance 1e-8), and every Krylov dimension is within 3 of
+    the smallest one the oracle accepts at tol 1e-8 (the same window, a check
+    at every m)."""
+    CASES["euler2d_40"] = dict(eq=2, dim=2, p=4, ne=(40, 40), lo=(0.0, 0.0), hi=(10.0, 10.0))
+    ctx, mesh = make(E, "euler2d_40", 4, prec=1, tol=1e-8)
+    q = np.ascontiguousarray(inputs.isentropic_vortex(dg.node_coords(mesh), 0.0))
+    ref = q.copy()
+    got = q.copy()
+    for k in range(6):
+        _, smin = integrators.step(mesh, ref, 0.08, tol=1e-8, m_step=1, iop=4)
+        ref, _ = integrators.step(mesh, ref, 0.08, tol=1e-10)
+        gst, gtr = ctx.step(got, 0.08)
+        assert rel(got, ref) <= 1e-7, k
+        assert len(gtr) == 1 and len(smin.traces) == 1 and len(smin.traces[0]) == 1
+        m, mr = gtr[0][1], smin.traces[0][0][1]
+        assert abs(m - mr) <= 3, (k, m, mr)
