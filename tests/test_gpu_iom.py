@@ -203,3 +203,19 @@ def test_mixed_paired_checks_trajectory(E):
         assert len(gtr) == 1 and len(smin.traces) == 1 and len(smin.traces[0]) == 1
         m, mr = gtr[0][1], smin.traces[0][0][1]
         assert abs(m - mr) <= 3, (k, m, mr)
+
+
+@pytest.mark.parametrize("dt", [0.2, 0.3])
+def test_mixed_large_krylov_dimension(E, dt):
+    """Long steps on the 40 x 40, p = 4 vortex (160,000 unknowns): the Krylov
+    dimension passes 49, where the paired checks give way to the change since
+    the previous check (dt = 0.2: one sub-step near m_max = 64; dt = 0.3: the
+    sub-step is halved).  One mixed-form step against the oracle's FP64 step."""
+    CASES["euler2d_40"] = dict(eq=2, dim=2, p=4, ne=(40, 40), lo=(0.0, 0.0), hi=(10.0, 10.0))
+    ctx, mesh = make(E, "euler2d_40", 4, prec=1, tol=1e-8)
+    q = np.ascontiguousarray(inputs.isentropic_vortex(dg.node_coords(mesh), 0.0))
+    ref, _ = integrators.step(mesh, q, dt, tol=1e-10)
+    got = q.copy()
+    gst, gtr = ctx.step(got, dt)
+    assert rel(got, ref) <= TOL_MIXED
+    assert max(m for (_, m, _, _) in gtr) > 49
