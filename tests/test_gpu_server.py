@@ -106,3 +106,29 @@ def test_server_matches_context_advance(mods):
     q = q0.copy()
     ctx.advance(q, dt, 4)
     np.testing.assert_array_equal(res[0][0], q)
+
+
+def test_served_sample_against_oracle(mods):
+    """The serving workload's CPU-oracle check: a seeded 5 % sample (3 of the
+    48 requests of the bench's stream, seed 1: sides 112, 23 and 57 at p = 4,
+    3, 3) served in the mixed form through the server, against the oracle's
+    FP64 solve of the same request (tol 1e-10, full Arnoldi).  Two of each
+    request's 50 EPI2 steps (the oracle's time)."""
+    from oracle import dg, integrators
+    from tests.test_gpu_parity import TOL_MIXED, rel
+    expdg, inputs, serve = mods
+    rng = np.random.default_rng(1)
+    reqs = [serve.vortex_request(rng, 1, iop=4) for _ in range(48)]
+    pick = np.random.default_rng(7).choice(48, size=3, replace=False)
+    sub = [(reqs[i][0], reqs[i][1], reqs[i][2], 2) for i in pick]
+    srv = serve.Server(workers=3)
+    res, _ = serve.run_stream(srv, sub, 0.0, np.random.default_rng(2), check=False)
+    srv.close()
+    for (cfg, q0, dt, nsteps), r in zip(sub, res):
+        assert r[3] == 0
+        side = cfg.ne[0]
+        mesh = dg.Mesh(dim=2, p=cfg.p, ne=(side, side), lo=(0.0, 0.0), hi=(10.0, 10.0), eq="euler")
+        ref = q0.copy()
+        for _ in range(nsteps):
+            ref, _ = integrators.step(mesh, ref, dt, tol=1e-10)
+        assert rel(r[0], ref) <= TOL_MIXED, (side, cfg.p)
