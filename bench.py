@@ -150,6 +150,56 @@ class ClockSampler:
                 "window": "timed region, then the same steps untimed until 6 samples"}
 
 
+def host_info():
+    """The host the CPU baseline ran on: logical CPUs and the CPU model."""
+    import platform
+    model = platform.processor() or ""
+    try:
+        with open("/proc/cpuinfo") as fh:
+            for line in fh:
+                key = line.split(":")[0].strip().lower()
+                if key in ("model name", "cpu part", "hardware"):
+                    model = line.split(":", 1)[1].strip()
+                    break
+    except OSError:
+        pass
+    return {"nproc": os.cpu_count(), "machine": platform.machine(), "cpu": model}
+
+
+def oracle_other_rates():
+    """Single-thread oracle timings of the other workloads, bounded: the 1D
+    Burgers solve (64 elements, p = 2, FP64, tol 1e-10, 50 EPI2 steps of
+    dt = 1e-2) in full, and the 3D wave (32^3, p = 3) as one residual and three
+    operator applies, extrapolated to a step of m applies at the GPU's m."""
+    from oracle import dg, integrators
+    from paper_2011_01316_gb300 import inputs
+    out = {}
+    mesh = dg.Mesh(dim=1, p=2, ne=(64,), lo=(0.0,), hi=(2 * math.pi,), eq="burgers")
+    q = np.asarray(inputs.burgers_sine(dg.node_coords(mesh)), np.float64).reshape(-1)
+    t0 = time.perf_counter()
+    for _ in range(50):
+        q, _ = integrators.step(mesh, q, 1e-2, tol=1e-10, iop=4)
+    t = time.perf_counter() - t0
+    out["burgers1d_64_p2"] = {"us_per_step": 1e6 * t / 50, "dof_steps_per_s": mesh.n_unknowns * 50 / t,
+                              "sample": "50 full EPI2 steps"}
+    mesh = dg.Mesh(dim=3, p=3, ne=(32, 32, 32), lo=(0.0,) * 3, hi=(2 * math.pi,) * 3, eq="euler")
+    q = np.asarray(inputs.density_wave(dg.node_coords(mesh)), np.float64)
+    v = np.ones_like(q)
+    t0 = time.perf_counter()
+    dg.residual(mesh, q)
+    t_res = time.perf_counter() - t0
+    t0 = time.perf_counter()
+    for _ in range(3):
+        dg.jv(mesh, q, v)
+    t_jv = (time.perf_counter() - t0) / 3
+    m = 32
+    t_step = t_res + m * t_jv
+    out["wave3d_32_p3"] = {"s_per_step": t_step, "dof_steps_per_s": mesh.n_unknowns / t_step,
+                           "sample": (f"one residual ({t_res:.1f} s) and three operator applies ({t_jv:.1f} s each), "
+                                      f"extrapolated to a step of {m} applies (the GPU's Krylov dimension)")}
+    return out
+
+
 def oracle_step_rate(steps=1):
     """FP64 CPU oracle: DOF-steps/s over `steps` EPI2 steps of the workload."""
     from oracle import dg, integrators
@@ -562,14 +612,18 @@ def main():
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         r, tt = oracle_step_rate(1)
         cpu = {"value": r, "unit": UNIT, "cores": 1, "kind": "oracle",
-               "sample": f"one full EPI2 step of the workload ({tt:.1f} s, single thread, numpy FP64)"}
+               "sample": f"one full EPI2 step of the workload ({tt:.1f} s, single thread, numpy FP64)",
+               "host": host_info()}
+        if "burgers" in legs or "wave3d" in legs:
+            cpu["other_workloads"] = oracle_other_rates()
 
     if rank == 0:
         line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
                 "warmup": args.warmup, "ms_per_step": 1e3 * t_max / args.steps, "higher_is_better": True,
                 "scaling": "weak", "vs_baseline": None, "dtype": "f32+ff(48-bit)+f64",
                 "data": "synthetic",
-                "config": {"workload": WORKLOAD, "precision": "mixed: float-float R, FP32 Jv, float-float Krylov, FP64 phi(H)",
+                "config": {"workload": WORKLOAD,
+                           "precision": "mixed: float-float R, FP32 Jv, float-float Krylov and phi(H), FP64 update",
                            "krylov": (f"incomplete orthogonalisation, window {CFG['iop']} (KIOPS)" if CFG["iop"]
                                       else "full Arnoldi (DCGS2)"),
                            "l2": "flushed between timed steps (512 MiB write)",
@@ -580,6 +634,7 @@ def main():
                 "roofline": roofline, "kernels": kern, "cpu_baseline": cpu, "clocks": clk.summary(),
                 "ms_per_step_min": min(per), "ms_per_step_median": statistics.median(per),
                 "krylov_iters_per_step": statistics.mean(iters),
+                "jv_per_s": sum(iters) / (sum(per) / 1e3),
                 "ms_per_step_profiled": sum(per_prof) / len(per_prof)}
         print(json.dumps(line), flush=True)
     if world > 1:
