@@ -163,7 +163,8 @@ def host_info():
                     break
     except OSError:
         pass
-    return {"nproc": os.cpu_count(), "machine": platform.machine(), "cpu": model}
+    arm_parts = {"0xd4f": "Arm Neoverse V2", "0xd40": "Arm Neoverse V1", "0xd0c": "Arm Neoverse N1"}
+    return {"nproc": os.cpu_count(), "machine": platform.machine(), "cpu": arm_parts.get(model.lower(), model)}
 
 
 def oracle_other_rates():
