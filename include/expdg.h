@@ -198,7 +198,7 @@ expdg_status expdg_jv(expdg_ctx* ctx, const double* qt, const double* v, double*
  * breakdown).  In EXPDG_MIXED a check at m is also accepted when the
  * approximation changed by at most krylov_tol * beta since m - 1
  * (beta |y_m - [y_{m-1}; 0]|, y_{m-1} = exp(H_{m-1}) e_1 evaluated in the same
- * launch, for m <= 49 on problems of at least 131072 unknowns), else when it
+ * launch, on problems of at least 131072 unknowns), else when it
  * changed by at most that since the previous check: the FP32 operator's
  * rounding noise inflates Saad's estimate there without slowing the
  * convergence of the approximation.  Reaching m_max halves the sub-step sigma; after an accepted

@@ -282,9 +282,10 @@ int iom_update_blocks(bool use_ff, int iop, size_t n_aug);
 // orthogonalisation (h_{m,m-1} is then finished from the last update launch's
 // partials; iom_gu = that launch's blocks, iom_ff its precision), else nullptr.
 // ff_arith: float-float arithmetic on the FP32 pipes (the mixed form), else FP64.
-// pair: also exp(H_{m-1}) e_1 in the same launch (2 <= m <= 49), so that the
-// change with diff_rule is the one since m - 1; otherwise since the previous
-// check (y_prev, m_prev).
+// pair: also exp(H_{m-1}) e_1 in the same launch (m >= 2; on a cluster of two
+// groups of CTAs, one matrix each, where such clusters fit the GPU, else both
+// packed on one group for m <= 49), so that the change with diff_rule is the
+// one since m - 1; otherwise since the previous check (y_prev, m_prev).
 cudaError_t launch_phi(KState* ks, int m, double beta, double tol, int force_accept, int diff_rule,
                        const void* iom_part, int iom_ff, int iom_gu, bool ff_arith, bool pair, cudaStream_t s);
 // out = base + sum_{i < m_eff} ycoef_i u_i (first N entries; base may be null).

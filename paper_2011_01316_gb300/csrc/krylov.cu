@@ -1301,17 +1301,19 @@ struct PhiBlocks {
   }
 };
 
-// C = A B blockwise.  The entries are split evenly across the CTAs, each
-// entry's sum over k across PHI_KS adjacent lanes; every CTA writes its
-// entries into all CTAs' copies, then one cluster barrier.
+// C = A B blockwise within the group of PHI_CL CTAs from cluster rank base
+// (which all hold the same matrices).  The entries are split evenly across
+// the group's CTAs, each entry's sum over k across PHI_KS adjacent lanes;
+// every CTA writes its entries into all the group's copies, then one
+// barrier of the whole cluster.
 template <typename T>
-__device__ void cl_matmul(cg::cluster_group& cl, const T* A, const T* B, T* C, const PhiBlocks& bk) {
+__device__ void cl_matmul(cg::cluster_group& cl, const T* A, const T* B, T* C, const PhiBlocks& bk, int base) {
   using PT = PhiT<T>;
-  const int rank = (int)cl.block_rank();
+  const int rank = (int)cl.block_rank() - base;
   const int e0 = (bk.tot * rank) / PHI_CL, e1 = (bk.tot * (rank + 1)) / PHI_CL;
   T* dst[PHI_CL];
 #pragma unroll
-  for (int t = 0; t < PHI_CL; ++t) dst[t] = cl.map_shared_rank(C, t);
+  for (int t = 0; t < PHI_CL; ++t) dst[t] = cl.map_shared_rank(C, base + t);
   const int nout = e1 - e0;
   const int rounds = (nout * PHI_KS + blockDim.x - 1) / blockDim.x;  // the same for every thread
   for (int rd = 0; rd < rounds; ++rd) {
@@ -1337,8 +1339,13 @@ __device__ void cl_matmul(cg::cluster_group& cl, const T* A, const T* B, T* C, c
   cl.sync();
 }
 
-template <typename T>
-__global__ void __cluster_dims__(PHI_CL, 1, 1) __launch_bounds__(PHI_NT)
+// GROUPS = 1: one cluster of PHI_CL CTAs (pair: H_{m-1} and H_m packed
+// together).  GROUPS = 2: a cluster of 2 PHI_CL CTAs, the first group
+// evaluating H_{m-1}, the second H_m, each at a single matrix's cost; the
+// second group's first CTA reads y_{m-1} from the first group's shared memory.
+// Launched with the cluster size as a launch attribute.
+template <typename T, int GROUPS>
+__global__ void __launch_bounds__(PHI_NT)
 k_phi(KState* ks, int m_req, double beta, double tol, int force, int diff_rule, const void* iom_part, int iom_ff,
       int iom_gu, int pair, const PhiConst pc) {
   using PT = PhiT<T>;
@@ -1386,36 +1393,50 @@ k_phi(KState* ks, int m_req, double beta, double tol, int force, int diff_rule, 
     __syncthreads();
   }
   const int m = s_m;
-  // pair: H_{m-1} as block 0 beside H_m (block 1), the same scaling for both
-  // (the leading block's 1-norm is at most H_m's)
-  const bool two = pair && m >= 2 && !s_brk;
+  const int grp = (GROUPS == 2) ? (int)cl.block_rank() / PHI_CL : 0, base = grp * PHI_CL;
+  const int lead = (GROUPS == 2) ? PHI_CL : 0;  // the CTA that forms the decision
+  // pair (one group): H_{m-1} as block 0 beside H_m (block 1), the same
+  // scaling for both (the leading block's 1-norm is at most H_m's).  Two
+  // groups: this group's matrix alone, in buffers of m x m entries in both
+  // groups (the same offsets, for the remote read of y_{m-1}).
+  const bool two = (GROUPS == 1) && pair && m >= 2 && !s_brk;
+  const int mg = (GROUPS == 2 && grp == 0) ? m - 1 : m;
   PhiBlocks bk;
   bk.nb = two ? 2 : 1;
-  bk.n0 = two ? m - 1 : m;
+  bk.n0 = two ? m - 1 : mg;
   bk.n1 = m;
   bk.off1 = two ? (m - 1) * (m - 1) : 0;
-  bk.tot = bk.off1 + m * m;
+  bk.tot = two ? bk.off1 + m * m : mg * mg;
   const int tot = bk.tot, ncol = bk.n0 + (two ? m : 0);
+  const int stride = (GROUPS == 2) ? m * m : tot;
   T* X = reinterpret_cast<T*>(phi_smem);
-  T* X2 = X + tot;
-  T* X3 = X2 + tot;
-  T* X4 = X3 + tot;
-  T* T0 = X4 + tot;
-  T* T1 = T0 + tot;
+  T* X2 = X + stride;
+  T* X3 = X2 + stride;
+  T* X4 = X3 + stride;
+  T* T0 = X4 + stride;
+  T* T1 = T0 + stride;
   for (int idx = threadIdx.x; idx < tot; idx += blockDim.x) {
     int b, r, c;
     bk.rc(idx, b, r, c);
     X[idx] = PT::from_d(ks->H[c * (MMAX + 1) + r]);
   }
   __syncthreads();
-  if (threadIdx.x < 32) {  // largest column sum over both blocks
+  if (threadIdx.x < 32) {  // largest column sum over both blocks (two groups: of H_m, in every CTA alike)
     SC mx = 0;
-    for (int cc = threadIdx.x; cc < ncol; cc += 32) {
-      const int b = (cc >= bk.n0) ? 1 : 0, c = cc - (b ? bk.n0 : 0), n = bk.n(b);
-      const T* Xb = X + bk.off(b);
-      SC cs = 0;
-      for (int r = 0; r < n; ++r) cs += PT::mag(Xb[r * n + c]);
-      mx = cs > mx ? cs : mx;
+    if (GROUPS == 2) {
+      for (int c = threadIdx.x; c < m; c += 32) {
+        SC cs = 0;
+        for (int r = 0; r < m; ++r) cs += PT::mag(PT::from_d(ks->H[c * (MMAX + 1) + r]));
+        mx = cs > mx ? cs : mx;
+      }
+    } else {
+      for (int cc = threadIdx.x; cc < ncol; cc += 32) {
+        const int b = (cc >= bk.n0) ? 1 : 0, c = cc - (b ? bk.n0 : 0), n = bk.n(b);
+        const T* Xb = X + bk.off(b);
+        SC cs = 0;
+        for (int r = 0; r < n; ++r) cs += PT::mag(Xb[r * n + c]);
+        mx = cs > mx ? cs : mx;
+      }
     }
     for (int off = 16; off > 0; off >>= 1) {
       const SC o = __shfl_down_sync(0xffffffffu, mx, off);
@@ -1429,9 +1450,9 @@ k_phi(KState* ks, int m_req, double beta, double tol, int force, int diff_rule, 
   const SC scale = (SC)ldexp(1.0f, -sq);  // a power of two: exact in both types
   for (int idx = threadIdx.x; idx < tot; idx += blockDim.x) X[idx] = PT::pow2(X[idx], scale);
   cl.sync();  // every CTA has its scaled copy before any remote write lands
-  cl_matmul(cl, X, X, X2, bk);
-  cl_matmul(cl, X2, X, X3, bk);
-  cl_matmul(cl, X2, X2, X4, bk);
+  cl_matmul(cl, X, X, X2, bk, base);
+  cl_matmul(cl, X2, X, X3, bk, base);
+  cl_matmul(cl, X2, X2, X4, bk, base);
   // E = B_4
   for (int idx = threadIdx.x; idx < tot; idx += blockDim.x) {
     int b, r, c;
@@ -1443,7 +1464,7 @@ k_phi(KState* ks, int m_req, double beta, double tol, int force, int diff_rule, 
   T* E = T0;
   T* F = T1;
   for (int j = 3; j >= 0; --j) {
-    cl_matmul(cl, X4, E, F, bk);
+    cl_matmul(cl, X4, E, F, bk, base);
     const T c0 = PT::cnst(pc, 4 * j), c1 = PT::cnst(pc, 4 * j + 1), c2 = PT::cnst(pc, 4 * j + 2),
             c3 = PT::cnst(pc, 4 * j + 3);
     for (int idx = threadIdx.x; idx < tot; idx += blockDim.x) {
@@ -1458,21 +1479,24 @@ k_phi(KState* ks, int m_req, double beta, double tol, int force, int diff_rule, 
     F = t;
   }
   for (int k = 0; k < sq; ++k) {
-    cl_matmul(cl, E, E, F, bk);
+    cl_matmul(cl, E, E, F, bk, base);
     T* t = E;
     E = F;
     F = t;
   }
-  if (cl.block_rank() == 0) {
+  if ((int)cl.block_rank() == lead) {
     __shared__ double s_d2[PHI_NT / 32];
     // y = exp(H_m) e_1: column 0 of the last block
     const T* Em = E + bk.off1;
+    // y_{m-1}: column 0 of block 0 (pair), or of the first group's matrix
+    const bool paired = two || GROUPS == 2;
+    const T* Ep = (GROUPS == 2) ? cl.map_shared_rank(E, 0) : E;
     // squared change of y since m - 1 (pair) or since the previous check
     // (entries beyond the shorter vector count fully)
     double d2 = 0.0;
-    const int mp = two ? m - 1 : ks->mprev;
+    const int mp = paired ? m - 1 : ks->mprev;
     for (int i = threadIdx.x; i < m; i += blockDim.x) {
-      const double yo = (i < mp) ? (two ? PT::to_d(E[i * (m - 1)]) : ks->yprev[i]) : 0.0;
+      const double yo = (i < mp) ? (paired ? PT::to_d(Ep[i * (m - 1)]) : ks->yprev[i]) : 0.0;
       const double di = PT::to_d(Em[i * m]) - yo;
       d2 += di * di;
     }
@@ -1833,10 +1857,59 @@ cudaError_t launch_iom_update(bool use_ff, int iop, KState* ks, void* part, Basi
   }
 }
 
+// One phi kernel instantiation, launched as clusters of `cl` CTAs.
+template <typename T, int GROUPS>
+cudaError_t phi_launch(int cl, size_t smem, cudaStream_t s, KState* ks, int m, double beta, double tol, int force,
+                       int diff_rule, const void* iom_part, int iom_ff, int iom_gu, int pair, const PhiConst& pc) {
+  cudaLaunchConfig_t lc = {};
+  lc.gridDim = dim3(cl);
+  lc.blockDim = dim3(PHI_NT);
+  lc.dynamicSmemBytes = smem;
+  lc.stream = s;
+  cudaLaunchAttribute at[1];
+  at[0].id = cudaLaunchAttributeClusterDimension;
+  at[0].val.clusterDim.x = cl;
+  at[0].val.clusterDim.y = 1;
+  at[0].val.clusterDim.z = 1;
+  lc.attrs = at;
+  lc.numAttrs = 1;
+  return cudaLaunchKernelEx(&lc, k_phi<T, GROUPS>, ks, m, beta, tol, force, diff_rule, iom_part, iom_ff, iom_gu, pair,
+                            pc);
+}
+
+template <typename T>
+cudaError_t phi_configure(int smax) {
+  cudaError_t e = cudaFuncSetAttribute(k_phi<T, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize, smax);
+  if (e == cudaSuccess) e = cudaFuncSetAttribute(k_phi<T, 2>, cudaFuncAttributeMaxDynamicSharedMemorySize, smax);
+  if (e == cudaSuccess) e = cudaFuncSetAttribute(k_phi<T, 2>, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
+  return e;
+}
+
+// Whether clusters of 2 PHI_CL CTAs with the largest shared memory fit the GPU.
+template <typename T>
+bool phi_two_groups_fit(int smax) {
+  cudaLaunchConfig_t lc = {};
+  lc.gridDim = dim3(2 * PHI_CL);
+  lc.blockDim = dim3(PHI_NT);
+  lc.dynamicSmemBytes = smax;
+  cudaLaunchAttribute at[1];
+  at[0].id = cudaLaunchAttributeClusterDimension;
+  at[0].val.clusterDim.x = 2 * PHI_CL;
+  at[0].val.clusterDim.y = 1;
+  at[0].val.clusterDim.z = 1;
+  lc.attrs = at;
+  lc.numAttrs = 1;
+  int n = 0;
+  if (cudaOccupancyMaxActiveClusters(&n, k_phi<T, 2>, &lc) != cudaSuccess) {
+    cudaGetLastError();
+    return false;
+  }
+  return n > 0;
+}
+
 cudaError_t launch_phi(KState* ks, int m, double beta, double tol, int force_accept, int diff_rule,
                        const void* iom_part, int iom_ff, int iom_gu, bool ff_arith, bool pair, cudaStream_t s) {
   if (m < 1 || m > MMAX) return cudaErrorInvalidValue;
-  pair = pair && m >= 2 && m <= PHI_PAIR_MAX;
   static const PhiConst pc = [] {
     PhiConst c{};
     double f = 1.0;
@@ -1849,22 +1922,33 @@ cudaError_t launch_phi(KState* ks, int m, double beta, double tol, int force_acc
     return c;
   }();
   static_assert(sizeof(double) == sizeof(ff), "the two forms use the same shared memory");
-  const size_t smem = 6 * sizeof(double) * ((size_t)m * m + (pair ? (size_t)(m - 1) * (m - 1) : 0));
   const int smax = (int)(6 * sizeof(double) *
                          std::max(MMAX * MMAX, PHI_PAIR_MAX * PHI_PAIR_MAX + (PHI_PAIR_MAX - 1) * (PHI_PAIR_MAX - 1)));
   static const cudaError_t configured = [smax] {
-    cudaError_t e = cudaFuncSetAttribute(k_phi<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, smax);
-    if (e == cudaSuccess) e = cudaFuncSetAttribute(k_phi<ff>, cudaFuncAttributeMaxDynamicSharedMemorySize, smax);
+    cudaError_t e = phi_configure<double>(smax);
+    if (e == cudaSuccess) e = phi_configure<ff>(smax);
     return e;
   }();
   if (configured != cudaSuccess) return configured;
+  // the pair on two groups of CTAs (one matrix each) where such clusters fit,
+  // else packed on one group up to m = PHI_PAIR_MAX
+  static const bool two_fit = phi_two_groups_fit<ff>(6 * (int)sizeof(double) * MMAX * MMAX) &&
+                              phi_two_groups_fit<double>(6 * (int)sizeof(double) * MMAX * MMAX);
+  pair = pair && m >= 2;
+  const bool two_groups = pair && two_fit;
+  pair = pair && (two_groups || m <= PHI_PAIR_MAX);
+  const size_t smem =
+      6 * sizeof(double) * ((size_t)m * m + (pair && !two_groups ? (size_t)(m - 1) * (m - 1) : 0));
+  const int cl = two_groups ? 2 * PHI_CL : PHI_CL;
   if (ff_arith)
-    k_phi<ff><<<PHI_CL, PHI_NT, smem, s>>>(ks, m, beta, tol, force_accept, diff_rule, iom_part, iom_ff, iom_gu,
-                                           pair ? 1 : 0, pc);
-  else
-    k_phi<double><<<PHI_CL, PHI_NT, smem, s>>>(ks, m, beta, tol, force_accept, diff_rule, iom_part, iom_ff, iom_gu,
-                                               pair ? 1 : 0, pc);
-  return cudaGetLastError();
+    return two_groups ? phi_launch<ff, 2>(cl, smem, s, ks, m, beta, tol, force_accept, diff_rule, iom_part, iom_ff,
+                                          iom_gu, 1, pc)
+                      : phi_launch<ff, 1>(cl, smem, s, ks, m, beta, tol, force_accept, diff_rule, iom_part, iom_ff,
+                                          iom_gu, pair ? 1 : 0, pc);
+  return two_groups ? phi_launch<double, 2>(cl, smem, s, ks, m, beta, tol, force_accept, diff_rule, iom_part, iom_ff,
+                                            iom_gu, 1, pc)
+                    : phi_launch<double, 1>(cl, smem, s, ks, m, beta, tol, force_accept, diff_rule, iom_part, iom_ff,
+                                            iom_gu, pair ? 1 : 0, pc);
 }
 
 cudaError_t launch_combine(bool use_ff, const KState* ks, Basis U, Vec base, Vec out, size_t N, bool if_accepted,

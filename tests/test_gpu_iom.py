@@ -208,9 +208,10 @@ def test_mixed_paired_checks_trajectory(E):
 @pytest.mark.parametrize("dt", [0.2, 0.3])
 def test_mixed_large_krylov_dimension(E, dt):
     """Long steps on the 40 x 40, p = 4 vortex (160,000 unknowns): the Krylov
-    dimension passes 49, where the paired checks give way to the change since
-    the previous check (dt = 0.2: one sub-step near m_max = 64; dt = 0.3: the
-    sub-step is halved).  One mixed-form step against the oracle's FP64 step."""
+    dimension passes 49, where the paired checks run on two groups of CTAs
+    (or, where 16-CTA clusters do not fit, give way to the change since the
+    previous check); dt = 0.2: one sub-step near m_max = 64; dt = 0.3: the
+    sub-step is halved.  One mixed-form step against the oracle's FP64 step."""
     CASES["euler2d_40"] = dict(eq=2, dim=2, p=4, ne=(40, 40), lo=(0.0, 0.0), hi=(10.0, 10.0))
     ctx, mesh = make(E, "euler2d_40", 4, prec=1, tol=1e-8)
     q = np.ascontiguousarray(inputs.isentropic_vortex(dg.node_coords(mesh), 0.0))
