@@ -229,7 +229,8 @@ void set_alpha(DGArgs& a, double alpha) {
 // large fluxes: an FP32 residual (relative error 6e-5 on the 64^2 p = 4
 // vortex) puts broadband noise into the Krylov start vector that costs about
 // five extra Arnoldi steps; FP64 arithmetic runs on GB300's slow FP64 pipe.
-cudaError_t residual_into(expdg_ctx* ctx, const double* q, Vec out, double alpha) {
+// converted: ctx->d_qfx already holds q (written by linstate_into).
+cudaError_t residual_into(expdg_ctx* ctx, const double* q, Vec out, double alpha, bool converted = false) {
   DGArgs a = ctx->mesh;
   set_alpha(a, alpha);
   a.src = ctx->has_src ? ctx->d_src : nullptr;
@@ -239,8 +240,11 @@ cudaError_t residual_into(expdg_ctx* ctx, const double* q, Vec out, double alpha
     a.out = out.d;
     return run(ctx, EXPDG_K_RESIDUAL, 16.0 * ctx->N, [&]() { return launch_dg(ctx, false, a); });
   }
-  cudaError_t e = run(ctx, EXPDG_K_VECTOR, 16.0 * ctx->N, [&]() { return launch_f64_to_fx(ctx->d_qfx, q, ctx->N, ctx->stream); });
-  if (e != cudaSuccess) return e;
+  if (!converted) {
+    const cudaError_t e =
+        run(ctx, EXPDG_K_VECTOR, 16.0 * ctx->N, [&]() { return launch_f64_to_fx(ctx->d_qfx, q, ctx->N, ctx->stream); });
+    if (e != cudaSuccess) return e;
+  }
   a.q = ctx->d_qfx;
   a.out_h = out.h;
   a.out_l = out.l;
@@ -255,18 +259,21 @@ cudaError_t residual_into(expdg_ctx* ctx, const double* q, Vec out, double alpha
   });
 }
 
-// Linearisation state of qt (FP64, device) -> ctx->d_z, in compute form.
-cudaError_t linstate_into(expdg_ctx* ctx, const double* qt) {
-  const double bytes = (8.0 + (ctx->ff ? 4.0 : 8.0)) * ctx->N;
+// Linearisation state of qt (FP64, device) -> ctx->d_z, in compute form;
+// with_fx (mixed form): qt as float-float pairs into ctx->d_qfx as well, for
+// a residual at qt that follows.
+cudaError_t linstate_into(expdg_ctx* ctx, const double* qt, bool with_fx = false) {
+  float* qfx = (with_fx && ctx->ff) ? ctx->d_qfx : nullptr;
+  const double bytes = (8.0 + (ctx->ff ? 4.0 : 8.0) + (qfx ? 8.0 : 0.0)) * ctx->N;
   return run(ctx, EXPDG_K_VECTOR, bytes, [&]() {
     const size_t stride = ctx->mesh.stride;
     switch (ctx->cfg.dim) {
       case 1: return launch_linstate_1d(ctx->cfg.eq, ctx->ff, qt, ctx->d_z, stride, ctx->cfg.gamma, ctx->mesh.roe,
-                                         ctx->stream);
+                                         qfx, ctx->stream);
       case 2: return launch_linstate_2d(ctx->cfg.eq, ctx->ff, qt, ctx->d_z, stride, ctx->cfg.gamma, ctx->mesh.roe,
-                                         ctx->stream);
+                                         qfx, ctx->stream);
       case 3: return launch_linstate_3d(ctx->cfg.eq, ctx->ff, qt, ctx->d_z, stride, ctx->cfg.gamma, ctx->mesh.roe,
-                                         ctx->stream);
+                                         qfx, ctx->stream);
     }
     return cudaErrorInvalidValue;
   });
@@ -614,18 +621,18 @@ expdg_status step_dev(expdg_ctx* ctx, double* q, double dt, const Replay& rp, ex
   const cudaStream_t s = ctx->stream;
   CU(ctx, cudaMemsetAsync(&ctx->ks->status, 0, sizeof(int), s));
   // Linearisation state of the Jacobian point q, shared by every stage.
-  CU(ctx, linstate_into(ctx, q));
+  CU(ctx, linstate_into(ctx, q, true));  // and q as float-float pairs for R(q)
   const void* qt_T = ctx->d_z;
   bool has[EXPDG_MAX_PHI + 1] = {false, false, false, false};
   const int scheme = ctx->cfg.scheme;
   if (scheme == EXPDG_EPI2) {
-    CU(ctx, residual_into(ctx, q, ctx->c[1], dt));
+    CU(ctx, residual_into(ctx, q, ctx->c[1], dt, ctx->ff));
     st->residual_applies++;
     has[1] = true;
     return phi_solve(ctx, qt_T, dt, has, 1, dvec(q), dvec(q), 0, rp, st, trace, true);
   }
   // EXPRB32 / EXPRB42 share: R^n, stage 1, D_{n,2} = R(q2) - R^n - L (q2 - q)
-  CU(ctx, residual_into(ctx, q, ctx->rn, 1.0));
+  CU(ctx, residual_into(ctx, q, ctx->rn, 1.0, ctx->ff));
   st->residual_applies++;
   const double a1 = (scheme == EXPDG_EXPRB32) ? dt : 0.75 * dt;
   {

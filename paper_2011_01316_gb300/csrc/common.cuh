@@ -210,11 +210,11 @@ cudaError_t launch_dg_roe_fx_2d(int p, const DGArgs& a, const Tab& t, cudaStream
 cudaError_t launch_dg_roe_fx_3d(int p, const DGArgs& a, const Tab& t, cudaStream_t s);
 // Euler: z = (u, H, a), or (u, H, sqrt(rho)) with roe.
 cudaError_t launch_linstate_1d(int eq, bool fp32, const double* q, void* z, size_t stride, double gamma, int roe,
-                               cudaStream_t s);
+                               float* qfx, cudaStream_t s);
 cudaError_t launch_linstate_2d(int eq, bool fp32, const double* q, void* z, size_t stride, double gamma, int roe,
-                               cudaStream_t s);
+                               float* qfx, cudaStream_t s);
 cudaError_t launch_linstate_3d(int eq, bool fp32, const double* q, void* z, size_t stride, double gamma, int roe,
-                               cudaStream_t s);
+                               float* qfx, cudaStream_t s);
 
 // ---- Krylov and vector kernels (krylov.cu); ff selects the float-float form ----
 // partial-sum buffer entries needed by the reduction kernels

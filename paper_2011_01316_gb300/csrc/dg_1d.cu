@@ -11,9 +11,9 @@ cudaError_t launch_dg_1d(bool linear, bool fp32, int eq, int p, const DGArgs& a,
 }
 
 cudaError_t launch_linstate_1d(int eq, bool fp32, const double* q, void* z, size_t stride, double gamma, int roe,
-                               cudaStream_t s) {
-  if (eq == EXPDG_BURGERS) return launch_linstate_dim<1, EXPDG_BURGERS>(fp32, q, z, stride, gamma, roe, s);
-  if (eq == EXPDG_EULER) return launch_linstate_dim<1, EXPDG_EULER>(fp32, q, z, stride, gamma, roe, s);
+                               float* qfx, cudaStream_t s) {
+  if (eq == EXPDG_BURGERS) return launch_linstate_dim<1, EXPDG_BURGERS>(fp32, q, z, stride, gamma, roe, qfx, s);
+  if (eq == EXPDG_EULER) return launch_linstate_dim<1, EXPDG_EULER>(fp32, q, z, stride, gamma, roe, qfx, s);
   return cudaErrorInvalidValue;
 }
 

@@ -10,8 +10,8 @@ cudaError_t launch_dg_3d(bool linear, bool fp32, int eq, int p, const DGArgs& a,
 }
 
 cudaError_t launch_linstate_3d(int eq, bool fp32, const double* q, void* z, size_t stride, double gamma, int roe,
-                               cudaStream_t s) {
-  if (eq == EXPDG_EULER) return launch_linstate_dim<3, EXPDG_EULER>(fp32, q, z, stride, gamma, roe, s);
+                               float* qfx, cudaStream_t s) {
+  if (eq == EXPDG_EULER) return launch_linstate_dim<3, EXPDG_EULER>(fp32, q, z, stride, gamma, roe, qfx, s);
   return cudaErrorInvalidValue;
 }
 

@@ -203,10 +203,11 @@ struct Phys {
 
 // Linearisation state z of q (FP64 in, T out), node by node; stride =
 // unknowns per field.  Computed in FP64 and rounded once.  Euler: (u, H, a),
-// or (u, H, sqrt(rho)) for the Roe flux (its average weights).
+// or (u, H, sqrt(rho)) for the Roe flux (its average weights).  qfx (may be
+// null): q as float-float pairs as well (the mixed form's residual operand).
 template <int DIM, int EQ, typename T>
 __global__ void __launch_bounds__(256) k_linstate(const double* __restrict__ q, T* __restrict__ z, size_t stride,
-                                                  double gamma, int roe) {
+                                                  double gamma, int roe, float2* __restrict__ qfx) {
   constexpr int M = NFields<DIM, EQ>::value;
   griddep_wait();
   const size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
@@ -214,6 +215,12 @@ __global__ void __launch_bounds__(256) k_linstate(const double* __restrict__ q, 
     double qv[M];
 #pragma unroll
     for (int f = 0; f < M; ++f) qv[f] = q[f * stride + i];
+    if (qfx != nullptr)
+#pragma unroll
+      for (int f = 0; f < M; ++f) {
+        const ff x = ff_from_double(qv[f]);
+        qfx[f * stride + i] = make_float2(x.h, x.l);
+      }
     if (EQ != EXPDG_EULER) {
       z[i] = (T)qv[0];
     } else {
@@ -235,12 +242,15 @@ __global__ void __launch_bounds__(256) k_linstate(const double* __restrict__ q, 
 
 template <int DIM, int EQ>
 cudaError_t launch_linstate_dim(bool fp32, const double* q, void* z, size_t stride, double gamma, int roe,
-                               cudaStream_t s) {
+                               float* qfx, cudaStream_t s) {
   if (stride == 0) return cudaSuccess;
   const dim3 grid((unsigned)((stride + 255) / 256));
+  float2* qf = reinterpret_cast<float2*>(qfx);
   if (fp32)
-    return pdl_launch(k_linstate<DIM, EQ, float>, grid, dim3(256), 0, s, q, static_cast<float*>(z), stride, gamma, roe);
-  return pdl_launch(k_linstate<DIM, EQ, double>, grid, dim3(256), 0, s, q, static_cast<double*>(z), stride, gamma, roe);
+    return pdl_launch(k_linstate<DIM, EQ, float>, grid, dim3(256), 0, s, q, static_cast<float*>(z), stride, gamma, roe,
+                      qf);
+  return pdl_launch(k_linstate<DIM, EQ, double>, grid, dim3(256), 0, s, q, static_cast<double*>(z), stride, gamma, roe,
+                    qf);
 }
 
 // Neighbour element across each face of the CTA's EPB elements e0, e0+1, ...
