@@ -181,3 +181,128 @@ def test_linear_advection_energy_dissipation(c, p, ne):
     jumps = v[0, :, p] - np.roll(v[0, :, 0], -1)
     rhs = -0.5 * abs(c) * np.sum(jumps ** 2)
     assert abs(lhs - rhs) <= 1e-13 * max(1.0, abs(rhs))
+
+
+# ---- the Lax-Friedrichs coefficient of the Euler operator (Sec. 3.2, Sec. 5.1) ----
+# The dissipation coefficient lambda of the Euler LF flux multiplies the jump
+# only, so free stream, conservation, homogeneity and the complex-step pin
+# (which freeze the same lambda on both sides) cannot see it.  These pins fix
+# its value from the paper's printed flux Jacobian (Sec. 3.2): lambda at a face
+# node pair is the larger spectral radius of A_n(q^-) and A_n(q^+).
+
+def _spectral_radius(q, d, gamma):
+    n = np.zeros(len(q) - 2)
+    n[d] = 1.0
+    return float(np.max(np.abs(np.linalg.eigvals(paper_A(q, n, gamma)))))
+
+
+def _piecewise_constant_state(dim, ne, p, rng, gamma=1.4):
+    """Euler states constant on each element, drawn per element: rho and p in
+    [0.6, 1.6], every velocity component in [-1, 1] (both signs of u.n)."""
+    nel, nn = int(np.prod(ne)), (p + 1) ** dim
+    rho = rng.uniform(0.6, 1.6, (nel, 1))
+    pr = rng.uniform(0.6, 1.6, (nel, 1))
+    vel = [rng.uniform(-1.0, 1.0, (nel, 1)) for _ in range(dim)]
+    return np.ascontiguousarray(np.broadcast_to(inputs.conservative(rho, vel, pr, gamma), (dim + 2, nel, nn)))
+
+
+def _face_probe_node(mesh, d, side):
+    """Node index with i_d = 0 (side 0) or p (side 1) and every other index
+    interior (1), so only the face normal to x_d touches it."""
+    idx = [1] * mesh.dim
+    idx[d] = 0 if side == 0 else mesh.p
+    n, mult = 0, 1
+    for k in range(mesh.dim):
+        n += idx[k] * mult
+        mult *= mesh.p + 1
+    return n
+
+
+def _neighbour(mesh, e, d, side):
+    ec, t = [], e
+    for k in range(mesh.dim):
+        ec.append(t % mesh.ne[k])
+        t //= mesh.ne[k]
+    ec[d] = (ec[d] + (1 if side else -1)) % mesh.ne[d]
+    out, mult = 0, 1
+    for k in range(mesh.dim):
+        out += ec[k] * mult
+        mult *= mesh.ne[k]
+    return out
+
+
+def _face_column(mesh, qt, f, e, n, d):
+    """-(h_d w_0) L(q~) e_{f,e,n} at node (e, n): at a face node whose other
+    indices are interior, the volume term (D_pp = 1/(2 w_0), SBP) cancels the
+    lifted own-side flux, so this is the face's dissipation matrix applied to
+    e_f: lambda e_f for LF, |A(q*_Roe)| e_f for Roe."""
+    v = np.zeros((mesh.m, mesh.n_elem, mesh.n_node))
+    v[f, e, n] = 1.0
+    Lv = dg.jv(mesh, qt, v)
+    return -mesh.h[d] * mesh.w[0] * Lv[:, e, n]
+
+
+@pytest.mark.parametrize("dim,p,ne", [(1, 2, (4,)), (2, 2, (3, 3)), (2, 3, (3, 2)), (3, 2, (3, 3, 2))])
+def test_euler_lf_coefficient_is_larger_spectral_radius(dim, p, ne):
+    """On a state that is constant per element but jumps between elements, the
+    LF coefficient read off the operator at every probed face node equals
+    max(rho(A_n(q^-)), rho(A_n(q^+))), rho the spectral radius of the printed
+    Jacobian (its eigenvalues u.n - a, u.n, u.n + a: so |u.n| + a, the max
+    over the two sides, not a mean and not |u.n| alone)."""
+    rng = np.random.default_rng(11)
+    mesh = make_mesh("euler", dim, p, ne)
+    qt = _piecewise_constant_state(dim, ne, p, rng, mesh.gamma)
+    elems = rng.choice(mesh.n_elem, size=min(3, mesh.n_elem), replace=False)
+    nprobe = 0
+    for d in range(dim):
+        for side in (0, 1):
+            n = _face_probe_node(mesh, d, side)
+            for e in elems:
+                e = int(e)
+                en = _neighbour(mesh, e, d, side)
+                lam = max(_spectral_radius(qt[:, e, 0], d, mesh.gamma), _spectral_radius(qt[:, en, 0], d, mesh.gamma))
+                for f in range(mesh.m):
+                    col = _face_column(mesh, qt, f, e, n, d)
+                    ref = np.zeros(mesh.m)
+                    ref[f] = lam
+                    np.testing.assert_allclose(col, ref, rtol=1e-12, atol=1e-12 * lam)
+                    nprobe += 1
+    assert nprobe == 2 * dim * len(elems) * mesh.m
+
+
+@pytest.mark.parametrize("dim,d", [(1, 0), (2, 0), (2, 1), (3, 2)])
+def test_euler_lf_characteristic_energy(dim, d):
+    """Linearised about a constant state and applied to data that varies along
+    x_d only, L splits in the characteristic variables w = R^-1 v of the
+    printed Jacobian A_{e_d} into scalar LF advections with speeds Lambda_k and
+    the common coefficient lambda = max_k |Lambda_k|; with the LGL (SBP) mass
+    each satisfies w_k^T M (R^-1 L v)_k = -1/2 lambda sum_faces |face| [w_k]^2
+    (the energy-rate identity of the Burgers pin above, per characteristic
+    field)."""
+    rng = np.random.default_rng(12)
+    p, ne = 3, (4, 3, 2)[:dim]
+    mesh = make_mesh("euler", dim, p, ne)
+    qc = inputs.conservative(np.array(1.1), [0.7, -0.4, 0.3][:dim], np.array(0.8), mesh.gamma)
+    qt = np.broadcast_to(qc.reshape(-1, 1, 1), (mesh.m, mesh.n_elem, mesh.n_node)).copy()
+    nvec = np.zeros(dim)
+    nvec[d] = 1.0
+    Lam, Rv = np.linalg.eig(paper_A(qc, nvec, mesh.gamma))
+    Lam, Rv = np.real(Lam), np.real(Rv)
+    lam = np.max(np.abs(Lam))
+    # w: random along x_d (element index along d and node index along d), constant otherwise
+    Q = mesh.to_grid(np.zeros((mesh.m, mesh.n_elem, mesh.n_node)))
+    eax, nax = mesh.elem_axis(d), mesh.node_axis(d)
+    prof = rng.standard_normal((mesh.m, mesh.ne[d], p + 1))
+    shp = [mesh.m] + [1] * (2 * dim)
+    shp[eax], shp[nax] = mesh.ne[d], p + 1
+    W = np.broadcast_to(prof.reshape(shp), Q.shape)
+    V = np.einsum("ij,j...->i...", Rv, W)
+    Lv = mesh.to_grid(dg.jv(mesh, qt, mesh.from_grid(V)))
+    Wl = np.einsum("ij,j...->i...", np.linalg.inv(Rv), Lv)
+    M = mesh.to_grid(np.broadcast_to(dg.mass_weights(mesh)[None], (1, mesh.n_elem, mesh.n_node)), m=1)[0]
+    face = float(np.prod([mesh.hi[k] - mesh.lo[k] for k in range(dim) if k != d]))
+    for k in range(mesh.m):
+        lhs = float(np.sum(W[k] * M * Wl[k]))
+        jumps = prof[k, :, p] - np.roll(prof[k, :, 0], -1)
+        rhs = -0.5 * lam * face * float(np.sum(jumps ** 2))
+        assert abs(lhs - rhs) <= 1e-12 * max(1.0, abs(rhs)), (k, Lam[k], lhs, rhs)

@@ -141,3 +141,28 @@ def test_roe_residual_consistent_with_pde(dim, p):
         errs.append(np.max(np.abs(dg.residual(mesh, q0) - dqdt)))
     rates = np.log2(np.array(errs[:-1]) / np.array(errs[1:]))
     assert np.all(rates > p - 0.3), (errs, rates)
+
+
+@pytest.mark.parametrize("dim,p,ne", [(1, 2, (4,)), (2, 2, (3, 3)), (3, 2, (3, 2, 2))])
+def test_roe_face_matrix_from_operator(dim, p, ne):
+    """On a state that is constant per element, the face dissipation matrix
+    read off the linear operator at a face node (whose other indices are
+    interior: the volume term cancels the lifted own-side flux there) is
+    R |Lambda| R^-1 of the printed Jacobian at the Roe average of the two
+    elements' states, column by column."""
+    from tests.test_oracle_dg import _face_column, _face_probe_node, _neighbour, _piecewise_constant_state
+    rng = np.random.default_rng(95)
+    mesh = rmesh(dim, p, ne)
+    qt = _piecewise_constant_state(dim, ne, p, rng, mesh.gamma)
+    for d in range(dim):
+        nvec = np.zeros(dim)
+        nvec[d] = 1.0
+        for side in (0, 1):
+            n = _face_probe_node(mesh, d, side)
+            e = int(rng.integers(mesh.n_elem))
+            qs = roe_state(qt[:, e, 0], qt[:, _neighbour(mesh, e, d, side), 0], dim, mesh.gamma)
+            lam, R = np.linalg.eig(paper_A(qs, nvec, mesh.gamma))
+            absA = np.real(R @ np.diag(np.abs(np.real(lam))) @ np.linalg.inv(R))
+            for f in range(mesh.m):
+                np.testing.assert_allclose(_face_column(mesh, qt, f, e, n, d), absA[:, f], rtol=1e-10,
+                                           atol=1e-11 * np.max(np.abs(absA)))
