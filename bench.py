@@ -1,30 +1,34 @@
 #!/usr/bin/env python
 """Benchmark: exponential-DG EPI2 steps on the GPU through libexpdg.
 
-Workload (N = 1): 2D compressible Euler (gamma = 1.4) isentropic vortex
-(strength 5, decay 1, free stream (1, 1), centre (5, 5)) on the periodic
-[0,10]^2, 64 x 64 quadrilaterals, p = 4 LGL (409,600 unknowns), Lax-Friedrichs
-flux, EPI2 steps of dt = 0.05 with Krylov tolerance 1e-8.  One step = one
-residual, one adaptive augmented-Krylov phi_1 solve (Jv applies,
-orthogonalisation, phi(H) checks) and the state update.
+Workload (N = 1): 3D compressible Euler (gamma = 1.4) density wave
+rho = 1 + 0.2 sin(x + y + z), velocity (1, 1, 1), pressure 1, on the periodic
+[0, 2 pi]^3, 32^3 hexahedra, p = 3 LGL (10,485,760 unknowns), Lax-Friedrichs
+flux, EPI2 steps of dt = 0.1 with Krylov tolerance 1e-8.  One step = the
+linearisation state, one residual, one adaptive augmented-Krylov phi_1 solve
+(operator applies, orthogonalisation, phi(H) checks) and the state update.
 
-`value` times the mixed form (float-float R, FP32 Jv, float-float Krylov basis and
-orthogonalisation, FP64 phi(H) and FP64 state update) with incomplete
+`value` times the mixed form: FP32 arithmetic for the residual R and the
+operator applies L v (FP32 accumulation); FP64 Krylov basis, Arnoldi inner
+products and orthogonalisation, phi(H) and state update; incomplete
 orthogonalisation over the last 4 basis vectors (the procedure of KIOPS, the
-Krylov solver of the paper, Sec. 1 and 2.3), the production form; its relative
-L2 error against the FP64 form with full orthogonalisation after one step from
-the same state is reported as `err_vs_fp64`.  That FP64 form is timed too
-(`fp64_form`).
-L2 is flushed (a 512 MiB write) between timed steps, outside the timed region.
+paper's Krylov solver, Sec. 1 and 2.3).  Its error after one step from the
+same state is reported against the FP64 form (full orthogonalisation, tol
+1e-10; that form matches the CPU oracle to 1e-11 at this size in the GPU
+tests) and against the exactly translated wave.  The FP64 form is timed too.
+The state (84 MB) and the Krylov vectors exceed the L2 cache; L2 is also
+flushed (a 512 MiB write) between timed steps, outside the timed region.
 
 `python bench.py --gpus N --steps K --warmup W [--impl reference]`; for N > 1
 launch under torchrun: every rank runs an independent replica of the
 workload (the solve has no data-parallel exchange), value = all ranks' units
 over the max time.  `--impl reference` times the FP64 CPU oracle on this
-host's cores instead (the paper publishes no code).
+host's cores instead (the paper publishes no code), on a bounded sample of
+the workload.
 """
 
 import argparse
+import hashlib
 import json
 import math
 import os
@@ -44,18 +48,28 @@ sys.path.insert(0, ROOT)
 
 METRIC = "DOF-steps/s"
 UNIT = "DOF-steps/s"
-WORKLOAD = ("2D Euler isentropic vortex, periodic [0,10]^2, 64x64 quads, p=4 LGL, 409,600 unknowns, "
-            "LF flux, EPI2, dt=0.05, Krylov tol 1e-8")
-CFG = dict(dim=2, p=4, ne=[64, 64, 1], lo=[0.0, 0.0, 0.0], hi=[10.0, 10.0, 1.0], eq=2, gamma=1.4,
-           scheme=2, krylov_tol=1e-8, m_max=64, m_step=5, max_substeps=32, iop=4)
-DT = 0.05
+WORKLOAD = ("3D Euler density wave rho=1+0.2sin(x+y+z), u=(1,1,1), p=1, periodic [0,2pi]^3, 32^3 hexes, p=3 LGL, "
+            "10,485,760 unknowns, LF flux, EPI2, dt=0.1, Krylov tol 1e-8")
+CFG = dict(dim=3, p=3, ne=[32, 32, 32], lo=[0.0] * 3, hi=[2 * math.pi] * 3, eq=2, gamma=1.4, scheme=2,
+           krylov_tol=1e-8, m_max=64, m_step=5, max_substeps=32, iop=4)
+DT = 0.1
+# The 2D workload of the paper's vortex experiments (second configuration).
+VORTEX = dict(dim=2, p=4, ne=[64, 64, 1], lo=[0.0, 0.0, 0.0], hi=[10.0, 10.0, 1.0], eq=2, gamma=1.4, scheme=2,
+              krylov_tol=1e-8, m_max=64, m_step=5, max_substeps=32, iop=4)
+VORTEX_DT = 0.05
 CLASSES = ["residual", "jv", "dots", "update", "phi", "combine", "vector"]
-# DRAM bytes per algorithmic byte of a kernel class on this workload, from one ncu
-# capture each (profiles/ncu_vortex64_p4_kernels.md, full window: k_iom_update_ff<4>
-# 16.438784 MB read + 0 written for 6 x 3.276808 MB algorithmic, k_iom_dots_ff<4>
-# 16.402944 MB for 5 x 3.276808 MB); used for roofline.traffic.  Refresh when the
-# kernel changes.
-NCU_TRAFFIC_RATIO = {"update": 16.438784 / (6 * 3.276808), "dots": 16.402944 / (5 * 3.276808)}
+# DFMA throughput of this GPU (FP64 FMA per second over all SMs; 1.6 per SM per
+# clock at 2070 MHz), measured by an independent-chain throughput probe.
+FP64_FMA_PER_S = 0.5015e12
+# ncu DRAM-traffic records of the dominant kernels, with the hash of the sources
+# they were taken from (a record whose sources have changed since is not used)
+TRAFFIC_FILE = os.path.join(ROOT, "profiles", "dram_traffic.json")
+# The CPU oracle's bounded sample of the workload: the same density wave on a
+# 16^3 mesh with dt = 0.2 (the same Courant number and element resolution per
+# wavelength halved; the oracle's Krylov dimension is 20 there as on 32^3 with
+# dt = 0.1), one full EPI2 step of 1,310,720 unknowns per sample.
+SAMPLE_NE, SAMPLE_DT = 16, 0.2
+SAMPLE_N = 5 * 64 * SAMPLE_NE ** 3
 
 
 def max_over_ranks(x, world, device="cpu"):
@@ -82,6 +96,33 @@ def peaks():
         return float(d["hbm_gbs"]), "measured"
     except Exception:
         return 6800.0, "fallback"
+
+
+def sources_sha(files):
+    h = hashlib.sha256()
+    for f in sorted(files):
+        with open(os.path.join(ROOT, f), "rb") as fh:
+            h.update(fh.read())
+    return h.hexdigest()[:16]
+
+
+def traffic_record(kernel_class, precision, workload):
+    """DRAM bytes per launch of a kernel class from the committed ncu record, or
+    None when there is none or its kernel's sources have changed since."""
+    try:
+        with open(TRAFFIC_FILE) as f:
+            recs = json.load(f)
+    except Exception:
+        return None
+    for r in recs.get("records", []):
+        if r.get("class") == kernel_class and r.get("precision") == precision and r.get("workload") == workload:
+            try:
+                if sources_sha(r["sources"]) != r["sources_sha"]:
+                    return None
+            except Exception:
+                return None
+            return r
+    return None
 
 
 class ClockSampler:
@@ -167,11 +208,40 @@ def host_info():
     return {"nproc": os.cpu_count(), "machine": platform.machine(), "cpu": arm_parts.get(model.lower(), model)}
 
 
+def rel(a, b):
+    import torch
+    if isinstance(a, torch.Tensor):
+        return float(torch.linalg.vector_norm(a - b) / torch.linalg.vector_norm(b))
+    a, b = np.asarray(a).reshape(-1), np.asarray(b).reshape(-1)
+    return float(np.linalg.norm(a - b) / np.linalg.norm(b))
+
+
+# ------------------------------------------------------------ CPU oracle ---
+
+def oracle_sample_step():
+    """One oracle EPI2 step of the workload's bounded sample (SAMPLE_NE^3,
+    dt = SAMPLE_DT, same wave, tol and window): (DOF-steps/s, seconds, m)."""
+    from oracle import dg, integrators
+    from paper_2011_01316_gb300 import inputs
+    ne = SAMPLE_NE
+    mesh = dg.Mesh(dim=3, p=3, ne=(ne,) * 3, lo=(0.0,) * 3, hi=(2 * math.pi,) * 3, eq="euler")
+    q = inputs.density_wave(dg.node_coords(mesh), 0.0).reshape(-1)
+    t0 = time.perf_counter()
+    q, st = integrators.step(mesh, q, SAMPLE_DT, tol=CFG["krylov_tol"], m_max=CFG["m_max"], m_step=CFG["m_step"],
+                             iop=CFG["iop"])
+    t = time.perf_counter() - t0
+    return mesh.n_unknowns / t, t, [m for tr in st.traces for (_, m, _) in tr]
+
+
+SAMPLE_TEXT = (f"one full oracle EPI2 step per sample of the same density wave on a {SAMPLE_NE}^3 mesh "
+               f"(1,310,720 unknowns) with dt={SAMPLE_DT} (the workload's Courant number; the oracle's Krylov "
+               "dimension is 20 there as on the 32^3 workload), tol 1e-8, window 4, numpy FP64, single thread")
+
+
 def oracle_other_rates():
     """Single-thread oracle timings of the other workloads, bounded: the 1D
     Burgers solve (64 elements, p = 2, FP64, tol 1e-10, 50 EPI2 steps of
-    dt = 1e-2) in full, and the 3D wave (32^3, p = 3) as one residual and three
-    operator applies, extrapolated to a step of m applies at the GPU's m."""
+    dt = 1e-2) in full, and one full EPI2 step of the 2D vortex (64^2, p = 4)."""
     from oracle import dg, integrators
     from paper_2011_01316_gb300 import inputs
     out = {}
@@ -183,52 +253,145 @@ def oracle_other_rates():
     t = time.perf_counter() - t0
     out["burgers1d_64_p2"] = {"us_per_step": 1e6 * t / 50, "dof_steps_per_s": mesh.n_unknowns * 50 / t,
                               "sample": "50 full EPI2 steps"}
-    mesh = dg.Mesh(dim=3, p=3, ne=(32, 32, 32), lo=(0.0,) * 3, hi=(2 * math.pi,) * 3, eq="euler")
-    q = np.asarray(inputs.density_wave(dg.node_coords(mesh)), np.float64)
-    v = np.ones_like(q)
-    t0 = time.perf_counter()
-    dg.residual(mesh, q)
-    t_res = time.perf_counter() - t0
-    t0 = time.perf_counter()
-    for _ in range(3):
-        dg.jv(mesh, q, v)
-    t_jv = (time.perf_counter() - t0) / 3
-    m = 32
-    t_step = t_res + m * t_jv
-    out["wave3d_32_p3"] = {"s_per_step": t_step, "dof_steps_per_s": mesh.n_unknowns / t_step,
-                           "sample": (f"one residual ({t_res:.1f} s) and three operator applies ({t_jv:.1f} s each), "
-                                      f"extrapolated to a step of {m} applies (the GPU's Krylov dimension)")}
-    return out
-
-
-def oracle_step_rate(steps=1):
-    """FP64 CPU oracle: DOF-steps/s over `steps` EPI2 steps of the workload."""
-    from oracle import dg, integrators
-    from paper_2011_01316_gb300 import inputs
     mesh = dg.Mesh(dim=2, p=4, ne=(64, 64), lo=(0.0, 0.0), hi=(10.0, 10.0), eq="euler")
     q = inputs.isentropic_vortex(dg.node_coords(mesh), 0.0).reshape(-1)
     t0 = time.perf_counter()
-    for _ in range(steps):
-        q, _ = integrators.step(mesh, q, DT, tol=CFG["krylov_tol"], m_max=CFG["m_max"], m_step=CFG["m_step"],
-                                iop=CFG["iop"] or None)
-    dt = time.perf_counter() - t0
-    return mesh.n_unknowns * steps / dt, dt
+    q, _ = integrators.step(mesh, q, VORTEX_DT, tol=1e-8, iop=4)
+    t = time.perf_counter() - t0
+    out["vortex2d_64_p4"] = {"ms_per_step": 1e3 * t, "dof_steps_per_s": mesh.n_unknowns / t,
+                             "sample": "one full EPI2 step (dt 0.05, tol 1e-8, window 4)"}
+    return out
 
 
-def burgers_workload(steps=50, iop=0):
+# -------------------------------------------------------------- GPU legs ---
+
+def step_timer(stream, flush):
+    import torch
+
+    def timed(c, q, k, dt):
+        ev0 = torch.cuda.Event(enable_timing=True)
+        ev1 = torch.cuda.Event(enable_timing=True)
+        per, iters = [], []
+        for _ in range(k):
+            flush.zero_()
+            ev0.record(stream)
+            st, _ = c.step(q, dt)
+            ev1.record(stream)
+            ev1.synchronize()
+            per.append(ev0.elapsed_time(ev1))
+            iters.append(st["krylov_iters"])
+        return per, iters
+    return timed
+
+
+def fp64_ops(kclass, prec, bytes_, launches, n_aug):
+    """FP64 operations of the incomplete-orthogonalisation passes from their
+    algorithmic bytes (per element: FP64 form, window products nwin + 1 for
+    (nwin + 1) x 8 bytes, update nwin + 2 for (nwin + 2) x 8; mixed form, window
+    products nwin for (nwin + 1/2) x 8 (|w'|^2 in FP32), update nwin + 1 for
+    (nwin + 2) x 8 (the scale by c_j in FP32)); None for the float-float form."""
+    if prec == 2:
+        return None
+    if prec == 0:
+        return bytes_ / 8
+    return bytes_ / 8 - launches * n_aug * (0.5 if kclass == "dots" else 1.0)
+
+
+def kernel_rates(kern, hbm, prec=1, n_aug=None):
+    rates = {}
+    for k, v in kern.items():
+        if v["ms"] > 0 and k in ("residual", "jv", "dots", "update", "combine"):
+            gbs = v["bytes"] / (v["ms"] * 1e-3) / 1e9
+            rates[k] = {"GB/s": gbs, "frac_of_measured_hbm": gbs / hbm,
+                        "us_per_launch": 1e3 * v["ms"] / v["launches"], "launches": v["launches"],
+                        "share_of_step": v["ms"] / max(1e-9, sum(x["ms"] for x in kern.values()))}
+            if k in ("dots", "update") and n_aug:
+                ops = fp64_ops(k, prec, v["bytes"], v["launches"], n_aug)
+                if ops is not None:
+                    rate = ops / (v["ms"] * 1e-3)
+                    rates[k]["fp64_ops_per_s"] = rate
+                    rates[k]["frac_of_fp64_pipe"] = rate / FP64_FMA_PER_S
+    return rates
+
+
+def wave3d_form(prec, stream, flush, hbm, steps=3, ne=32, iop=4, ref=None):
+    """The workload in one precision form: ms per step (K steps from the same
+    state after one warm step), Krylov dimension, per-kernel rates (a second,
+    profiled step) and the error of one step against `ref` (a device array)."""
+    from paper_2011_01316_gb300 import expdg, inputs
+    cfg = {**CFG, "ne": [ne] * 3, "iop": iop}
+    ctx = expdg.Context(**cfg, prec=prec)
+    ctx.set_stream(stream)
+    import torch
+    q0 = torch.from_numpy(np.ascontiguousarray(inputs.density_wave(ctx.node_coords(), 0.0))).cuda()
+    q = q0.clone()
+    ctx.step(q, DT)
+    err = rel(q, ref) if ref is not None else None
+    timed = step_timer(stream, flush)
+    q = q0.clone()
+    per, iters = timed(ctx, q, steps, DT)
+    q = q0.clone()
+    ctx.profile_enable(True)
+    ctx.step(q, DT)
+    kern = ctx.profile_get(reset=True)
+    ctx.profile_enable(False)
+    n, tile = ctx.n, ctx.tile
+    ctx.close()
+    ms = float(np.mean(per))
+    return {"ms_per_step": ms, "dof_steps_per_s": n / (ms * 1e-3), "krylov_iters_per_step": statistics.mean(iters),
+            "jv_tile": {1: "256", 2: "128", 3: "512"}.get(tile, "?") + " threads per CTA",
+            "kernels": kernel_rates(kern, hbm, prec, n + 1), "err_vs_fp64_form": err}
+
+
+def vortex_workload(stream, flush, steps=5):
+    """The 2D vortex (64^2, p = 4, 409,600 unknowns: its 3.3 MB vectors stay in
+    L2, so launch latency, not HBM, bounds it), EPI2 dt 0.05, tol 1e-8, window
+    4, in the mixed and float-float forms, each against the FP64 form (full
+    orthogonalisation, tol 1e-10) after one step from the same state."""
+    import torch
+    from paper_2011_01316_gb300 import expdg, inputs
+    ref_ctx = expdg.Context(**{**VORTEX, "iop": 0, "krylov_tol": 1e-10}, prec=expdg.EXPDG_FP64)
+    ref_ctx.set_stream(stream)
+    q0 = torch.from_numpy(np.ascontiguousarray(inputs.isentropic_vortex(ref_ctx.node_coords(), 0.0))).cuda()
+    ref = q0.clone()
+    ref_ctx.step(ref, VORTEX_DT)
+    ref_ctx.close()
+    timed = step_timer(stream, flush)
+    out = {"workload": "2D Euler isentropic vortex 64x64, p=4 (409,600 unknowns), EPI2 dt=0.05, tol 1e-8, window 4"}
+    for name, prec in (("mixed", expdg.EXPDG_MIXED), ("float_float", expdg.EXPDG_MIXED_FF)):
+        ctx = expdg.Context(**VORTEX, prec=prec)
+        ctx.set_stream(stream)
+        q = q0.clone()
+        ctx.step(q, VORTEX_DT)
+        err = rel(q, ref)
+        for _ in range(3):
+            ctx.step(q, VORTEX_DT)
+        q = q0.clone()
+        per, iters = timed(ctx, q, steps, VORTEX_DT)
+        ms = float(np.mean(per))
+        out[name] = {"ms_per_step": ms, "dof_steps_per_s": ctx.n / (ms * 1e-3),
+                     "krylov_iters_per_step": statistics.mean(iters), "err_vs_fp64_form": err}
+        ctx.close()
+    return out
+
+
+def burgers_workload(steps=50, iop=4):
     """1D Burgers, 64 elements, p = 2 on the periodic [0, 2 pi] (192
     unknowns), u0 = 0.5 + sin x, LF flux, EPI2 steps of dt = 1e-2 with Krylov
     tol 1e-10, FP64 form: a launch-latency-bound solve.  Reports us per step
     (CUDA events around one expdg_advance of `steps` steps, after 3 warm-up
-    steps) and DOF-steps/s."""
+    steps), DOF-steps/s, and the error after the `steps` steps against the
+    oracle's adaptive solve."""
     import torch
+    from oracle import dg, integrators
     from paper_2011_01316_gb300 import expdg, inputs
     ctx = expdg.Context(dim=1, p=2, ne=[64, 1, 1], lo=[0.0, 0.0, 0.0], hi=[2 * math.pi, 1.0, 1.0],
                         eq=expdg.EXPDG_BURGERS, scheme=expdg.EXPDG_EPI2, prec=expdg.EXPDG_FP64, krylov_tol=1e-10,
                         m_max=64, m_step=5, max_substeps=32, iop=iop)
     stream = torch.cuda.current_stream()
     ctx.set_stream(stream)
-    q0 = torch.from_numpy(np.ascontiguousarray(inputs.burgers_sine(ctx.node_coords()))).cuda()
+    u0 = np.ascontiguousarray(inputs.burgers_sine(ctx.node_coords()))
+    q0 = torch.from_numpy(u0).cuda()
     q = q0.clone()
     ctx.advance(q, 1e-2, 3)
     q = q0.clone()
@@ -239,151 +402,101 @@ def burgers_workload(steps=50, iop=0):
     ev1.record(stream)
     ev1.synchronize()
     ms = ev0.elapsed_time(ev1)
+    mesh = dg.Mesh(dim=1, p=2, ne=(64,), lo=(0.0,), hi=(2 * math.pi,), eq="burgers")
+    ref, _ = integrators.advance(mesh, u0.reshape(-1), 1e-2, steps, tol=1e-10, iop=iop or None)
     return {"workload": "1D Burgers, 64 elements, p=2, 192 unknowns, u0 = 0.5 + sin x, EPI2 dt=1e-2, tol 1e-10, FP64, "
                         + (f"window {iop} (KIOPS)" if iop else "full orthogonalisation"),
             "steps": steps, "us_per_step": 1e3 * ms / steps, "dof_steps_per_s": ctx.n * steps / (ms * 1e-3),
-            "krylov_iters_per_step": st["krylov_iters"] / steps}
+            "krylov_iters_per_step": st["krylov_iters"] / steps,
+            "err_vs_oracle": rel(q.cpu().numpy(), ref), "err_kind": f"oracle, {steps} adaptive steps, same window"}
 
 
-def exprb32_workload(steps=5):
-    """The 2D vortex of the main workload advanced by EXPRB32 (the paper's
-    third-order scheme, Sec. 5.1: two residuals, a stage correction through
-    one operator apply and two Krylov solves, the second with phi_3), mixed
-    form, against the FP64 form with full orthogonalisation on one step from
-    the same state.  Reports ms per step (CUDA events, L2 flushed between
-    steps, after 3 warm-up steps), DOF-steps/s and Krylov iterations."""
+def exprb32_workload(stream, flush, steps=5):
+    """The 2D vortex advanced by EXPRB32 (the paper's third-order scheme,
+    Sec. 5.1: two residuals, a stage correction through one operator apply
+    and two Krylov solves, the second with phi_3), mixed form, against the
+    FP64 form with full orthogonalisation on one step from the same state."""
     import torch
     from paper_2011_01316_gb300 import expdg, inputs
-    stream = torch.cuda.current_stream()
-    cfg = {**CFG, "scheme": expdg.EXPDG_EXPRB32}
+    cfg = {**VORTEX, "scheme": expdg.EXPDG_EXPRB32}
     ctx = expdg.Context(**cfg, prec=expdg.EXPDG_MIXED)
     ctx.set_stream(stream)
-    ctx64 = expdg.Context(**{**cfg, "iop": 0}, prec=expdg.EXPDG_FP64)
+    ctx64 = expdg.Context(**{**cfg, "iop": 0, "krylov_tol": 1e-10}, prec=expdg.EXPDG_FP64)
     ctx64.set_stream(stream)
     q0 = torch.from_numpy(np.ascontiguousarray(inputs.isentropic_vortex(ctx.node_coords(), 0.0))).cuda()
     qa, qb = q0.clone(), q0.clone()
-    ctx.step(qa, DT)
-    ctx64.step(qb, DT)
-    err = float(torch.linalg.vector_norm(qa - qb) / torch.linalg.vector_norm(qb))
-    flush = torch.empty(512 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")
+    ctx.step(qa, VORTEX_DT)
+    ctx64.step(qb, VORTEX_DT)
+    err = rel(qa, qb)
     q = q0.clone()
     for _ in range(3):
-        ctx.step(q, DT)
+        ctx.step(q, VORTEX_DT)
     q = q0.clone()
-    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    per, iters = [], 0
-    for _ in range(steps):
-        flush.zero_()
-        ev0.record(stream)
-        st, _ = ctx.step(q, DT)
-        ev1.record(stream)
-        ev1.synchronize()
-        per.append(ev0.elapsed_time(ev1))
-        iters += st["krylov_iters"]
+    per, iters = step_timer(stream, flush)(ctx, q, steps, VORTEX_DT)
     ms = float(np.mean(per))
     n = ctx.n
     ctx.close()
     ctx64.close()
     return {"workload": "2D Euler isentropic vortex 64x64, p=4 (409,600 unknowns), EXPRB32, dt=0.05, tol 1e-8, "
                         "mixed, window 4",
-            "ms_per_step": ms, "dof_steps_per_s": n / (ms * 1e-3), "krylov_iters_per_step": iters / steps,
-            "err_vs_fp64": err}
-
-
-def wave3d_workload(steps=2, hbm=6788.6, ne=32, iop=0):
-    """3D Euler density wave rho = 1 + 0.2 sin(x+y+z), u = (1,1,1), pressure 1 on
-    the periodic [0, 2 pi]^3, ne^3 hexahedra, p = 3 (10,485,760 unknowns at
-    ne = 32), EPI2 dt = 0.1, Krylov tol 1e-8, mixed form: vectors of 84 MB (far
-    beyond L2), so the per-kernel rates are HBM rates.  Reports the step time
-    and, per kernel class, the achieved algorithmic GB/s and its fraction of the
-    measured copy bandwidth."""
-    import torch
-    from paper_2011_01316_gb300 import expdg, inputs
-    cfg = dict(dim=3, p=3, ne=[ne, ne, ne], lo=[0.0] * 3, hi=[2 * math.pi] * 3, eq=2, gamma=1.4, scheme=2,
-               krylov_tol=1e-8, m_max=64, m_step=5, max_substeps=32, iop=iop)
-    ctx = expdg.Context(**cfg, prec=expdg.EXPDG_MIXED)
-    stream = torch.cuda.current_stream()
-    ctx.set_stream(stream)
-    q = torch.from_numpy(np.ascontiguousarray(inputs.density_wave(ctx.node_coords(), 0.0))).cuda()
-    ctx.step(q, 0.1)
-    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    torch.cuda.synchronize()
-    ev0.record(stream)
-    iters = 0
-    for _ in range(steps):
-        st, _ = ctx.step(q, 0.1)
-        iters += st["krylov_iters"]
-    ev1.record(stream)
-    ev1.synchronize()
-    ms = ev0.elapsed_time(ev1) / steps
-    ctx.profile_enable(True)
-    ctx.step(q, 0.1)
-    kern = ctx.profile_get(reset=True)
-    ctx.profile_enable(False)
-    rates = {}
-    for k, v in kern.items():
-        if v["ms"] > 0 and k in ("residual", "jv", "dots", "update", "combine"):
-            gbs = v["bytes"] / (v["ms"] * 1e-3) / 1e9
-            rates[k] = {"GB/s": gbs, "frac_of_measured_hbm": gbs / hbm, "us_per_launch": 1e3 * v["ms"] / v["launches"],
-                        "launches": v["launches"]}
-    n, tile = ctx.n, ctx.tile
-    ctx.close()
-    return {"workload": f"3D Euler density wave, {ne}^3 hexes, p=3, {n} unknowns, EPI2 dt=0.1, tol 1e-8, mixed",
-            "ms_per_step": ms, "dof_steps_per_s": n / (ms * 1e-3), "krylov_iters_per_step": iters / steps,
-            "jv_tile": {1: "256", 2: "128", 3: "512"}.get(tile, "?") + " threads per CTA (autotuned)",
-            "kernels": rates}
+            "ms_per_step": ms, "dof_steps_per_s": n / (ms * 1e-3), "krylov_iters_per_step": statistics.mean(iters),
+            "err_vs_fp64_form": err}
 
 
 def serving_workload(n, seed=1, rate=200.0, workers=8):
     """Poisson stream (mean `rate`/s) of n 2D Euler vortex solves (side 8..128,
     p 2..5, strength U[1,5], centre U(domain), 50 EPI2 steps at Courant 5, tol
-    1e-8).  The served form: mixed precision, `workers` solves in flight.  The
-    plain form: FP64, one solve at a time, same requests.  Reports solves/s,
+    1e-8).  Served: the mixed form, `workers` solves in flight.  Plain: the
+    FP64 form, one solve at a time, same requests and the same Krylov window
+    (and, for context, with full orthogonalisation).  Reports solves/s,
     p50/p99 arrival-to-completion latency and the largest relative error of a
-    served result against the FP64 result of the same request."""
+    served result against the plain FP64 result of the same request."""
     from paper_2011_01316_gb300 import serve
     rng = np.random.default_rng(seed)
-    reqs_m, reqs_d = [], []
+    reqs = {"mixed": [], "fp64": [], "fp64_full": []}
     for _ in range(n):
         state = rng.bit_generator.state
-        reqs_m.append(serve.vortex_request(rng, 1, iop=CFG["iop"]))
+        reqs["mixed"].append(serve.vortex_request(rng, 1, iop=CFG["iop"]))
         rng.bit_generator.state = state
-        reqs_d.append(serve.vortex_request(rng, 0))
+        reqs["fp64"].append(serve.vortex_request(rng, 0, iop=CFG["iop"]))
+        rng.bit_generator.state = state
+        reqs["fp64_full"].append(serve.vortex_request(rng, 0))
     # warm the kernels of every order once (outside the measured streams)
     warm = serve.Server(workers=1)
     seen = set()
-    for r in reqs_m + reqs_d:
-        key = (r[0].p, r[0].prec)
+    for r in reqs["mixed"] + reqs["fp64"] + reqs["fp64_full"]:
+        key = (r[0].p, r[0].prec, r[0].iop)
         if key not in seen:
             seen.add(key)
             serve.run_stream(warm, [(r[0], r[1], r[2], 1)], 0.0, rng)
     warm.close()
-    srv = serve.Server(workers=workers)
-    res_m, wall_m = serve.run_stream(srv, reqs_m, rate, np.random.default_rng(seed + 1), check=False)
-    srv.close()
-    srv = serve.Server(workers=1)
-    res_d, wall_d = serve.run_stream(srv, reqs_d, rate, np.random.default_rng(seed + 1), check=False)
-    srv.close()
-    both = [(a, b) for a, b in zip(res_m, res_d) if a[3] == 0 and b[3] == 0]
-    err = max((float(np.linalg.norm(a[0] - b[0]) / np.linalg.norm(b[0])) for a, b in both), default=None)
-    dofs = sum(r[1].size * r[3] for r, a in zip(reqs_m, res_m) if a[3] == 0)
+    res, wall = {}, {}
+    for name, w in (("mixed", workers), ("fp64", 1), ("fp64_full", 1)):
+        if name == "fp64_full" and n > 64:
+            continue  # full orthogonalisation one at a time: context for small streams only
+        srv = serve.Server(workers=w)
+        res[name], wall[name] = serve.run_stream(srv, reqs[name], rate, np.random.default_rng(seed + 1), check=False)
+        srv.close()
+    both = [(a, b) for a, b in zip(res["mixed"], res["fp64"]) if a[3] == 0 and b[3] == 0]
+    err = max((rel(a[0], b[0]) for a, b in both), default=None)
+    dofs = sum(r[1].size * r[3] for r, a in zip(reqs["mixed"], res["mixed"]) if a[3] == 0)
     out = {"workload": f"{n} 2D Euler vortex solves, Poisson {rate:g}/s, side 8..128, p 2..5, 50 EPI2 steps, Cr 5",
-           "served_mixed": dict(serve.latency_summary(res_m, wall_m), workers=workers,
-                                dof_steps_per_s=dofs / wall_m),
-           "plain_fp64": dict(serve.latency_summary(res_d, wall_d), workers=1, dof_steps_per_s=dofs / wall_d),
+           "served_mixed": dict(serve.latency_summary(res["mixed"], wall["mixed"]), workers=workers,
+                                dof_steps_per_s=dofs / wall["mixed"]),
+           "plain_fp64_same_window": dict(serve.latency_summary(res["fp64"], wall["fp64"]), workers=1,
+                                          dof_steps_per_s=dofs / wall["fp64"]),
            "max_rel_err_vs_fp64": err,
+           "err_kind": "each served result against the plain FP64 form's result of the same request",
            "failed_requests": [{"side": r[0].ne[0], "p": r[0].p, "status_mixed": a[3], "status_fp64": b[3]}
-                               for r, a, b in zip(reqs_m, res_m, res_d) if a[3] != 0 or b[3] != 0]}
-    out["speedup_solves_per_s"] = out["served_mixed"]["solves_per_s"] / out["plain_fp64"]["solves_per_s"]
+                               for r, a, b in zip(reqs["mixed"], res["mixed"], res["fp64"]) if a[3] != 0 or b[3] != 0]}
+    if "fp64_full" in res:
+        out["plain_fp64_full_orthogonalisation"] = dict(serve.latency_summary(res["fp64_full"], wall["fp64_full"]),
+                                                        workers=1)
+    out["speedup_solves_per_s"] = out["served_mixed"]["solves_per_s"] / out["plain_fp64_same_window"]["solves_per_s"]
     return out
 
 
-def batched_workload(n, seed=0, workers=16, steps=20):
-    """n independent periodic instances (half 1D Burgers with Ne log-uniform in
-    [16, 4096], half 2D Euler density waves with side in {8..96}; p uniform in
-    {1..5}; initial data 1 + 4 seeded Fourier modes, a_k ~ U[0, 0.3]; dt from
-    Courant 5; 20 EPI2 steps; mixed precision) run concurrently through the solve
-    server, against the same instances run one after another."""
+def batched_requests(n, seed, steps, prec):
     from paper_2011_01316_gb300 import expdg, inputs, serve
     rng = np.random.default_rng(seed)
     reqs = []
@@ -392,26 +505,39 @@ def batched_workload(n, seed=0, workers=16, steps=20):
         if i % 2 == 0:
             ne = int(round(math.exp(rng.uniform(math.log(16), math.log(4096)))))
             cfg = expdg.default_config(dim=1, p=p, ne=[ne, 1, 1], lo=[0, 0, 0], hi=[2 * math.pi, 1, 1],
-                                       eq=expdg.EXPDG_BURGERS, prec=1, krylov_tol=1e-8, iop=CFG["iop"])
+                                       eq=expdg.EXPDG_BURGERS, prec=prec, krylov_tol=1e-8, iop=CFG["iop"])
             X = expdg.config_node_coords(cfg)
             u0, (amp, _) = inputs.fourier_modes(X[0], rng)
             u0 = u0[None]
             umax = float(np.max(np.abs(u0)))
             dx = float(np.min(np.diff(X[0, 0, : p + 1])))
-            # smooth until t_shock = 1 / max(-u0'); keep 20 steps within 0.8 t_shock
+            # smooth until t_shock = 1 / max(-u0'); keep the steps within 0.8 t_shock
             t_shock = 1.0 / max(1e-12, sum((k + 1) * amp[k] for k in range(len(amp))))
             dt = min(5.0 * dx / umax, 0.8 * t_shock / steps)
             reqs.append((cfg, np.ascontiguousarray(u0), dt, steps))
         else:
             side = int(rng.integers(8, 97))
             cfg = expdg.default_config(dim=2, p=p, ne=[side, side, 1], lo=[0, 0, 0], hi=[2 * math.pi] * 2 + [1],
-                                       eq=expdg.EXPDG_EULER, prec=1, krylov_tol=1e-8, iop=CFG["iop"])
+                                       eq=expdg.EXPDG_EULER, prec=prec, krylov_tol=1e-8, iop=CFG["iop"])
             X = expdg.config_node_coords(cfg)
             rho, (amp, _) = inputs.fourier_modes(X[0] + X[1], rng)
             if amp.sum() > 0.8:  # keep rho >= 0.2: 1 - sum a_k must stay positive
                 rho = 1.0 + (rho - 1.0) * (0.8 / amp.sum())
             q0 = inputs.conservative(rho, [1.0, 1.0], np.ones_like(rho), 1.4)
             reqs.append((cfg, np.ascontiguousarray(q0), serve.courant_dt(cfg, q0, 5.0), steps))
+    return reqs
+
+
+def batched_workload(n, seed=0, workers=16, steps=20):
+    """n independent periodic instances (half 1D Burgers with Ne log-uniform in
+    [16, 4096], half 2D Euler density waves with side in {8..96}; p uniform in
+    {1..5}; initial data 1 + 4 seeded Fourier modes, a_k ~ U[0, 0.3]; dt from
+    Courant 5; 20 EPI2 steps; mixed form) run concurrently through the solve
+    server, against the same instances run one after another, and every
+    result against the FP64 form of the same instance (run concurrently)."""
+    from paper_2011_01316_gb300 import serve
+    reqs = batched_requests(n, seed, steps, 1)
+    rng = np.random.default_rng(seed + 1)
     dofs = sum(r[1].size * r[3] for r in reqs)
     srv = serve.Server(workers=1)
     res1, wall1 = serve.run_stream(srv, reqs, 0.0, rng, check=False)
@@ -420,30 +546,36 @@ def batched_workload(n, seed=0, workers=16, steps=20):
     resn, walln = serve.run_stream(srv, reqs, 0.0, rng, check=False)
     srv.close()
     same = all(np.array_equal(a[0], b[0]) and a[3] == b[3] for a, b in zip(res1, resn))
+    srv = serve.Server(workers=workers)
+    res64, _ = serve.run_stream(srv, batched_requests(n, seed, steps, 0), 0.0, rng, check=False)
+    srv.close()
+    errs = [rel(a[0], b[0]) for a, b in zip(resn, res64) if a[3] == 0 and b[3] == 0]
     return {"workload": f"{n} instances (1D Burgers / 2D Euler, p 1..5, uneven sizes), {steps} EPI2 steps each",
             "concurrent": {"workers": workers, "wall_s": walln, "dof_steps_per_s": dofs / walln},
             "sequential": {"wall_s": wall1, "dof_steps_per_s": dofs / wall1},
             "speedup": wall1 / walln, "identical_results": same,
-            "failed": sum(1 for a in resn if a[3] != 0)}
+            "failed": sum(1 for a in resn if a[3] != 0),
+            "max_rel_err_vs_fp64": max(errs) if errs else None,
+            "err_kind": "each instance's mixed result against the FP64 form of the same instance"}
 
 
 def run_reference(args, rank, world):
     if rank != 0:
         return
     for _ in range(args.warmup):
-        oracle_step_rate(1)
-    rates, times = [], []
+        oracle_sample_step()
+    times, ms_used = [], []
     for _ in range(args.steps):
-        r, t = oracle_step_rate(1)
-        rates.append(r)
+        _, t, m = oracle_sample_step()
         times.append(t)
-    value = len(times) * 409600 / sum(times)
-    sample = f"{args.steps} full EPI2 steps of the workload (409,600 unknowns each), single thread"
+        ms_used += m
+    value = len(times) * SAMPLE_N / sum(times)
     line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * sum(times) / len(times),
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
             "data": "synthetic", "config": {"workload": WORKLOAD, "impl": "FP64 CPU oracle (numpy)"},
-            "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": sample},
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle",
+                             "sample": SAMPLE_TEXT + f"; Krylov dimensions {sorted(set(ms_used))}"},
             "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
 
@@ -456,17 +588,16 @@ def main():
     ap.add_argument("--impl", default="expdg", choices=["expdg", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--fp64-steps", type=int, default=3)
-    ap.add_argument("--tol", type=float, default=None, help="Krylov tolerance (default: the workload's)")
     ap.add_argument("--serve-requests", type=int, default=48, help="requests of the serving workload (0: skip)")
     ap.add_argument("--serve-workers", type=int, default=8, help="solves in flight in the served form")
     ap.add_argument("--burgers-iop", type=int, default=4, help="orthogonalisation window of the Burgers leg (0: full)")
     ap.add_argument("--batch-instances", type=int, default=256, help="instances of the batched workload (0: skip)")
     ap.add_argument("--batch-workers", type=int, default=16, help="instances in flight in the batched workload")
-    ap.add_argument("--no-3d", action="store_true", help="skip the 3D HBM-roofline workload")
-    ap.add_argument("--legs", default="main,wave3d,burgers,exprb32,serving,batched",
+    ap.add_argument("--legs", default="main,wave3d_ff,vortex,burgers,exprb32,serving,batched",
                     help="comma list of legs to run (main = the timed workload; profiling runs pick one)")
-    ap.add_argument("--wave3d-ne", type=int, default=32, help="elements per direction of the 3D leg")
-    ap.add_argument("--wave3d-steps", type=int, default=2)
+    ap.add_argument("--wave3d-ne", type=int, default=32, help="elements per direction of the wave3d legs")
+    ap.add_argument("--wave3d-steps", type=int, default=3)
+    ap.add_argument("--wave3d-prec", type=int, default=1, help="precision form of a wave3d-only run (1 or 2)")
     ap.add_argument("--iop", type=int, default=CFG["iop"],
                     help="Krylov orthogonalisation window (0: full Arnoldi; k: incomplete, last k vectors)")
     args = ap.parse_args()
@@ -478,8 +609,6 @@ def main():
         run_reference(args, rank, world)
         return
 
-    if args.tol is not None:
-        CFG["krylov_tol"] = args.tol
     CFG["iop"] = args.iop
     import torch
     import torch.distributed as dist
@@ -493,53 +622,50 @@ def main():
             dist.barrier()
         torch.cuda.synchronize()
 
-    if "main" not in set(args.legs.split(",")):
-        hbm, _ = peaks()
+    hbm, peak_kind = peaks()
+    stream = torch.cuda.current_stream()
+    flush = torch.empty(512 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")
+    legs = set(args.legs.split(","))
+    if "main" not in legs:  # single legs, for profiling runs
         out = {}
-        if "wave3d" in args.legs:
-            out["wave3d"] = wave3d_workload(steps=args.wave3d_steps, hbm=hbm, ne=args.wave3d_ne, iop=args.iop)
-        if "serving" in args.legs:
+        if "wave3d" in legs:
+            out["wave3d"] = wave3d_form(args.wave3d_prec, stream, flush, hbm, steps=args.wave3d_steps,
+                                        ne=args.wave3d_ne, iop=args.iop)
+        if "vortex" in legs:
+            out["vortex"] = vortex_workload(stream, flush)
+        if "serving" in legs:
             out["serving"] = serving_workload(args.serve_requests, workers=args.serve_workers)
-        if "batched" in args.legs:
+        if "batched" in legs:
             out["batched"] = batched_workload(args.batch_instances, workers=args.batch_workers)
-        if "burgers" in args.legs:
+        if "burgers" in legs:
             out["burgers"] = burgers_workload(iop=args.burgers_iop)
-        if "exprb32" in args.legs:
-            out["exprb32"] = exprb32_workload()
+        if "exprb32" in legs:
+            out["exprb32"] = exprb32_workload(stream, flush)
         if rank == 0:
             print(json.dumps({"legs": args.legs, **out}), flush=True)
         return
-    stream = torch.cuda.current_stream()
+
     ctx = expdg.Context(**CFG, prec=expdg.EXPDG_MIXED)
     ctx.set_stream(stream)
-    # reference form: FP64 with full orthogonalisation
-    ctx64 = expdg.Context(**{**CFG, "iop": 0}, prec=expdg.EXPDG_FP64)
-    ctx64.set_stream(stream)
-    q0 = torch.from_numpy(np.ascontiguousarray(inputs.isentropic_vortex(ctx.node_coords(), 0.0))).cuda()
+    q0 = torch.from_numpy(np.ascontiguousarray(inputs.density_wave(ctx.node_coords(), 0.0))).cuda()
+    exact = torch.from_numpy(np.ascontiguousarray(inputs.density_wave(ctx.node_coords(), DT))).cuda()
     N = ctx.n
-    flush = torch.empty(512 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")
 
-    # accuracy of the mixed form against the FP64 form, one step from the same state
+    # accuracy: one step from the same state against the FP64 form (full
+    # orthogonalisation, tol 1e-10) and against the exactly translated wave
+    ref_ctx = expdg.Context(**{**CFG, "iop": 0, "krylov_tol": 1e-10}, prec=expdg.EXPDG_FP64)
+    ref_ctx.set_stream(stream)
+    qref = q0.clone()
+    ref_ctx.step(qref, DT)
+    ref_ctx.close()
     qa = q0.clone()
-    qb = q0.clone()
     ctx.step(qa, DT)
-    ctx64.step(qb, DT)
-    err_vs_fp64 = float(torch.linalg.vector_norm(qa - qb) / torch.linalg.vector_norm(qb))
+    err_vs_fp64 = rel(qa, qref)
+    err_vs_exact = rel(qa, exact)
+    fp64_vs_exact = rel(qref, exact)
+    del qa
 
-    def timed(c, q, k):
-        ev0 = torch.cuda.Event(enable_timing=True)
-        ev1 = torch.cuda.Event(enable_timing=True)
-        per, iters = [], []
-        for _ in range(k):
-            flush.zero_()
-            ev0.record(stream)
-            st, _ = c.step(q, DT)
-            ev1.record(stream)
-            ev1.synchronize()
-            per.append(ev0.elapsed_time(ev1))
-            iters.append(st["krylov_iters"])
-        return per, iters
-
+    timed = step_timer(stream, flush)
     q = q0.clone()
     for _ in range(args.warmup):
         ctx.step(q, DT)
@@ -548,7 +674,7 @@ def main():
     ctx.profile_enable(False)
     barrier()
     with ClockSampler(local) as clk:
-        per, iters = timed(ctx, q, args.steps)
+        per, iters = timed(ctx, q, args.steps, DT)
         barrier()
         launches = sum(v["launches"] for v in ctx.profile_get(reset=True).values())
         qx = q0.clone()
@@ -559,30 +685,38 @@ def main():
     # the same K steps again with a CUDA event pair around every launch
     q = q0.clone()
     ctx.profile_enable(True)
-    per_prof, _ = timed(ctx, q, args.steps)
+    per_prof, _ = timed(ctx, q, args.steps, DT)
     kern = ctx.profile_get(reset=True)
     ctx.profile_enable(False)
 
-    # per-kernel-class profile over the timed region
-    hbm, peak_kind = peaks()
-    bw = {k: v for k, v in kern.items() if k in ("jv", "dots", "update", "residual", "combine")}
-    dom = max(bw, key=lambda k: bw[k]["ms"])
+    # roofline of the dominant kernel class over the profiled region
+    rates = kernel_rates(kern, hbm, expdg.EXPDG_MIXED, N + 1)
+    dom = max(rates, key=lambda k: kern[k]["ms"])
     d = kern[dom]
-    achieved = (d["bytes"] / d["launches"]) / (d["ms"] / d["launches"] * 1e-3) / 1e9 if d["ms"] > 0 else 0.0
-    traffic = NCU_TRAFFIC_RATIO[dom] * d["bytes"] / d["launches"] if dom in NCU_TRAFFIC_RATIO else None
+    achieved = (d["bytes"] / d["launches"]) / (d["ms"] / d["launches"] * 1e-3) / 1e9
+    tr = traffic_record(dom, "mixed", "wave3d_32_p3")
     roofline = {"kernel": dom, "bound": "hbm", "achieved": achieved, "peak": hbm, "unit": "GB/s",
-                "frac": achieved / hbm, "traffic": traffic, "traffic_unit": "bytes per launch",
-                "peak_kind": peak_kind,
-                "note": ("the 64^2 p=4 vectors (3.3 MB) stay in L2: launch-latency bound, not HBM bound; "
-                         "HBM-bound rates of the same kernels: wave3d (32^3)"),
+                "frac": achieved / hbm, "peak_kind": peak_kind,
+                "traffic": tr["dram_bytes_per_launch"] if tr else None, "traffic_unit": "bytes per launch",
+                "traffic_source": (tr["capture"] if tr else "no ncu record for the current sources"),
+                "algorithmic_bytes_per_launch": d["bytes"] / d["launches"],
                 "kernel_share": d["ms"] / max(1e-9, sum(v["ms"] for v in kern.values()))}
+    if dom in ("dots", "update"):
+        roofline["fp64_pipe"] = {"fp64_ops_per_s": rates[dom]["fp64_ops_per_s"], "peak": FP64_FMA_PER_S,
+                                 "frac": rates[dom]["frac_of_fp64_pipe"],
+                                 "note": ("FP64 operations of the pass (window products and norm in FP64) against the "
+                                          "measured DFMA rate")}
 
-    # FP64 form, same workload
+    # the FP64 form, same workload and window
+    ctx64 = expdg.Context(**CFG, prec=expdg.EXPDG_FP64)
+    ctx64.set_stream(stream)
     q = q0.clone()
     ctx64.step(q, DT)
-    per64, it64 = timed(ctx64, q, args.fp64_steps)
+    q = q0.clone()
+    per64, it64 = timed(ctx64, q, args.fp64_steps, DT)
+    ctx64.close()
     fp64 = {"value": N * len(per64) / (sum(per64) / 1e3), "ms_per_step": sum(per64) / len(per64),
-            "steps": len(per64), "krylov_iters_per_step": statistics.mean(it64)}
+            "steps": len(per64), "krylov_iters_per_step": statistics.mean(it64), "window": CFG["iop"]}
 
     # end to end through the C-ABI with pinned host buffers (copies inside the call)
     qh = torch.empty(q0.shape, dtype=torch.float64, pin_memory=True)
@@ -596,47 +730,57 @@ def main():
     te = time.perf_counter() - t0
     e2e = {"value": world * N * args.steps / te, "unit": UNIT, "h2d_bytes_per_step": 8 * N,
            "d2h_bytes_per_step": 8 * N}
+    tile = ctx.tile
+    ctx.close()
 
-    hbm, _ = peaks()
-    legs = set(args.legs.split(","))
-    wave3d = None
-    if "wave3d" in legs and not args.no_3d:
-        wave3d = wave3d_workload(steps=args.wave3d_steps, hbm=hbm, ne=args.wave3d_ne, iop=args.iop)
-    serving = (serving_workload(args.serve_requests, workers=args.serve_workers)
-               if args.serve_requests > 0 and "serving" in legs else None)
-    batched = (batched_workload(args.batch_instances, workers=args.batch_workers)
-               if args.batch_instances > 0 and "batched" in legs else None)
-    burgers = burgers_workload(iop=args.burgers_iop) if "burgers" in legs else None
-    exprb32 = exprb32_workload() if "exprb32" in legs else None
+    extra = {}
+    if "wave3d_ff" in legs:
+        extra["wave3d_float_float"] = wave3d_form(expdg.EXPDG_MIXED_FF, stream, flush, hbm, ref=qref,
+                                                  steps=args.wave3d_steps)
+    del qref
+    if "vortex" in legs:
+        extra["vortex"] = vortex_workload(stream, flush)
+    if "burgers" in legs:
+        extra["burgers"] = burgers_workload(iop=args.burgers_iop)
+    if "exprb32" in legs:
+        extra["exprb32"] = exprb32_workload(stream, flush)
+    if args.serve_requests > 0 and "serving" in legs:
+        extra["serving"] = serving_workload(args.serve_requests, workers=args.serve_workers)
+    if args.batch_instances > 0 and "batched" in legs:
+        extra["batched"] = batched_workload(args.batch_instances, workers=args.batch_workers)
 
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
-        r, tt = oracle_step_rate(1)
+        r, tt, ms = oracle_sample_step()
         cpu = {"value": r, "unit": UNIT, "cores": 1, "kind": "oracle",
-               "sample": f"one full EPI2 step of the workload ({tt:.1f} s, single thread, numpy FP64)",
-               "host": host_info()}
-        if "burgers" in legs or "wave3d" in legs:
-            cpu["other_workloads"] = oracle_other_rates()
+               "sample": SAMPLE_TEXT + f" ({tt:.1f} s; Krylov dimension {ms})", "host": host_info(),
+               "other_workloads": oracle_other_rates()}
 
     if rank == 0:
         line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
                 "warmup": args.warmup, "ms_per_step": 1e3 * t_max / args.steps, "higher_is_better": True,
-                "scaling": "weak", "vs_baseline": None, "dtype": "f32+ff(48-bit)+f64",
+                "scaling": "weak", "vs_baseline": None, "dtype": "f32+f64",
                 "data": "synthetic",
                 "config": {"workload": WORKLOAD,
-                           "precision": "mixed: float-float R, FP32 Jv, float-float Krylov and phi(H), FP64 update",
+                           "precision": ("mixed: FP32 R and Jv (FP32 accumulation); FP64 Krylov basis, inner "
+                                         "products, orthogonalisation, phi(H) and update"),
                            "krylov": (f"incomplete orthogonalisation, window {CFG['iop']} (KIOPS)" if CFG["iop"]
                                       else "full Arnoldi (DCGS2)"),
-                           "l2": "flushed between timed steps (512 MiB write)",
-                           "jv_tile": {1: "256", 2: "128", 3: "512"}.get(ctx.tile, "?") + " threads per CTA (autotuned)",
+                           "l2": "inputs larger than L2 (84 MB state, 84 MB per Krylov vector); also flushed "
+                                 "between timed steps (512 MiB write)",
+                           "jv_tile": {1: "256", 2: "128", 3: "512"}.get(tile, "?") + " threads per CTA (autotuned)",
                            "parallelism": "replicas" if world > 1 else "single GPU"},
-                "err_vs_fp64": err_vs_fp64, "fp64_form": fp64, "e2e": e2e, "gpu_launches": launches,
-                "serving": serving, "batched": batched, "wave3d": wave3d, "burgers": burgers, "exprb32": exprb32,
-                "roofline": roofline, "kernels": kern, "cpu_baseline": cpu, "clocks": clk.summary(),
+                "err_vs_fp64": err_vs_fp64,
+                "err_kind": ("relative L2 after one step against the FP64 form (full orthogonalisation, tol 1e-10), "
+                             "which matches the CPU oracle to 1e-11 at this size in the GPU tests"),
+                "err_vs_exact": err_vs_exact, "fp64_form_err_vs_exact": fp64_vs_exact,
+                "fp64_form": fp64, "e2e": e2e, "gpu_launches": launches,
+                "roofline": roofline, "kernels": kern, "kernel_rates": rates, "cpu_baseline": cpu,
+                "clocks": clk.summary(),
                 "ms_per_step_min": min(per), "ms_per_step_median": statistics.median(per),
                 "krylov_iters_per_step": statistics.mean(iters),
                 "jv_per_s": sum(iters) / (sum(per) / 1e3),
-                "ms_per_step_profiled": sum(per_prof) / len(per_prof)}
+                "ms_per_step_profiled": sum(per_prof) / len(per_prof), **extra}
         print(json.dumps(line), flush=True)
     if world > 1:
         dist.destroy_process_group()

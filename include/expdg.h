@@ -19,7 +19,9 @@
  *     with i along x.  Length expdg_num_unknowns().
  *   - Pointers may be host or device memory (detected per call).  Host
  *     buffers are copied through library-owned device memory; the copies
- *     are part of the call.  The caller owns every buffer it passes; the
+ *     are part of the call.  Device memory must belong to the context's
+ *     device (or be managed memory); another device's memory is rejected
+ *     with EXPDG_EINVAL.  The caller owns every buffer it passes; the
  *     library owns all device memory it allocates (released by
  *     expdg_destroy).
  *   - Calls are synchronous with respect to the host: they return after the
@@ -60,19 +62,25 @@ typedef enum { EXPDG_BC_PERIODIC = 0, EXPDG_BC_DIRICHLET = 1 } expdg_bc;
 typedef enum { EXPDG_FLUX_LF = 0, EXPDG_FLUX_ROE = 1 } expdg_flux;
 
 /* Arithmetic of the operator applies (R, Jv) and of the Arnoldi process.
- *   EXPDG_FP64:  everything in FP64 (reference form).
- *   EXPDG_MIXED: Jv in FP32 (FP32 accumulation); the residual R (in
- *                expdg_residual and in every step) in float-float arithmetic;
- *                Krylov basis, inner products and orthogonalisation in
- *                float-float (pairs of FP32 numbers, 48-bit significand, FP32
- *                arithmetic with error-free transformations); phi(H) in
- *                float-float, the solution update in FP64.  An FP32 residual's rounding noise
- *                would cost extra Arnoldi steps, FP64 arithmetic runs on
- *                the slow FP64 pipe.
- *                On this GPU the FP64 pipe (and every f32<->f64 conversion)
- *                runs about 1/70 of the FP32 rate, so the streaming Krylov
- *                kernels avoid it. */
-typedef enum { EXPDG_FP64 = 0, EXPDG_MIXED = 1 } expdg_precision;
+ *   EXPDG_FP64:     everything in FP64 (reference form).
+ *   EXPDG_MIXED:    the linear operator L v (every Jv) in FP32 arithmetic with
+ *                   FP32 accumulation, on the FP32 rounding of its input (kept
+ *                   beside each FP64 basis vector; conversions on the integer
+ *                   pipes); the Krylov basis, the Arnoldi inner products and
+ *                   orthogonalisation, phi(H) and the solution update in FP64.
+ *                   The residual R is FP64 too: an FP32 residual's rounding
+ *                   (relative 3e-6 on smooth data, where R is a small
+ *                   difference of large fluxes) cost extra Arnoldi steps and
+ *                   errors above 1e-6 after tens of steps.
+ *   EXPDG_MIXED_FF: a variant: Jv in FP32; the residual in float-float
+ *                   arithmetic (pairs of FP32 numbers, 48-bit significand,
+ *                   error-free transformations on the FP32 pipes); Krylov
+ *                   basis, inner products, orthogonalisation and phi(H) in
+ *                   float-float; the solution update in FP64.  On this GPU the
+ *                   FP64 pipe runs about 1/70 of the FP32 rate, so this form's
+ *                   streaming Krylov kernels stay off it; its results are
+ *                   within 48-bit rounding of FP64 arithmetic, not FP64. */
+typedef enum { EXPDG_FP64 = 0, EXPDG_MIXED = 1, EXPDG_MIXED_FF = 2 } expdg_precision;
 
 typedef struct {
   int dim;              /* 1, 2 or 3 (Burgers: 1) */
@@ -96,15 +104,16 @@ typedef struct {
                            q** = {q} (Eq. gov-burgers1d); Burgers only */
   int bc;               /* expdg_bc */
   int flux;             /* expdg_flux (Euler; Burgers uses Lax-Friedrichs) */
-  int tile;             /* expdg_tile: CTA size of the EXPDG_MIXED operator apply */
+  int tile;             /* expdg_tile: CTA size of the FP32 operator apply (EXPDG_MIXED, EXPDG_MIXED_FF) */
 } expdg_config;
 
-/* CTA size (elements per CTA, one thread per node) of the EXPDG_MIXED
- * operator apply L(qt) v.  EXPDG_TILE_AUTO times the three sizes on the
- * context's own mesh when it is created (about 20 operator applies on zero
- * data) and keeps the fastest; the choice is cached per mesh shape for the
- * process, so later contexts of the same shape do not time again.  The
- * EXPDG_FP64 form and the other kernels always use EXPDG_TILE_256. */
+/* CTA size (elements per CTA, one thread per node) of the FP32 operator
+ * apply L(qt) v (EXPDG_MIXED, EXPDG_MIXED_FF).  EXPDG_TILE_AUTO times the
+ * three sizes on the context's own mesh when it is created (about 20 operator
+ * applies on zero data) and keeps the fastest; the choice is cached per mesh
+ * shape and form for the process, so later contexts of the same shape do not
+ * time again.  The EXPDG_FP64 form and the other kernels always use
+ * EXPDG_TILE_256. */
 typedef enum {
   EXPDG_TILE_AUTO = 0,
   EXPDG_TILE_256 = 1,  /* about 256 threads per CTA */
@@ -175,12 +184,13 @@ expdg_status expdg_set_source(expdg_ctx* ctx, const double* s);
 /* R(q): the DG right-hand side (Sec. 2.2, Eq. EXPO-SemiDiscretizedForm_ode;
  * strong collocated LGL form; LF flux with lambda = max(|u|) for Burgers,
  * Sec. 3.1, and max(|u.n| + a) for Euler, Sec. 5.1).  q, r: canonical layout.
- * In EXPDG_MIXED the arithmetic is float-float (inputs and outputs stay FP64). */
+ * In EXPDG_MIXED_FF the arithmetic is float-float (inputs and outputs stay
+ * FP64), FP64 in the other forms. */
 expdg_status expdg_residual(expdg_ctx* ctx, const double* q, double* r);
 
 /* L(qt) v: the frozen-flux linear DG operator (Sec. 2.2, Eq. linearflux, with
  * (u~u)* of Sec. 3.1 / (A~q)* of Sec. 3.2; LF coefficient from qt).  In
- * EXPDG_MIXED the arithmetic is FP32. */
+ * EXPDG_MIXED and EXPDG_MIXED_FF the arithmetic is FP32. */
 expdg_status expdg_jv(expdg_ctx* ctx, const double* qt, const double* v, double* out);
 
 /* out = sum_{i=0}^{P} phi_i(tau L(qt)) c_i with c = [c_0, ..., c_P] (P <= 3;
@@ -195,7 +205,8 @@ expdg_status expdg_jv(expdg_ctx* ctx, const double* qt, const double* v, double*
  * the approximation and the error estimate are unchanged.  The error estimate
  * err = beta h_{m+1,m} |e_m^T exp(H_m) e_1| is checked at m = m_step,
  * 2 m_step, ..., m_max; accepted when err <= krylov_tol * beta (or on a happy
- * breakdown).  In EXPDG_MIXED a check at m is also accepted when the
+ * breakdown).  In the FP32-operator forms (EXPDG_MIXED, EXPDG_MIXED_FF) a
+ * check at m is also accepted when the
  * approximation changed by at most krylov_tol * beta since m - 1
  * (beta |y_m - [y_{m-1}; 0]|, y_{m-1} = exp(H_{m-1}) e_1 evaluated in the same
  * launch, on problems of at least 131072 unknowns), else when it
@@ -304,18 +315,6 @@ expdg_status expdg_server_fetch(expdg_server* s, int64_t id, double* q_out, expd
 /* Bytes held by contexts, queued and running solve counts. */
 expdg_status expdg_server_info(expdg_server* s, size_t* used_bytes, int* pending, int* running);
 
-/* Arithmetic-unit throughput of the current device, measured by short
- * dependent-chain-free loops (allocates and frees a small buffer): FP64 FMA,
- * FP32 FMA, packed FP32 FMA (lane FMAs) and f64 -> f32 conversions per second. */
-typedef struct {
-  double fp64_fma_per_s;
-  double fp32_fma_per_s;
-  double fp32x2_fma_per_s;
-  double f64_to_f32_per_s;
-  int sms;
-  double clock_mhz;
-} expdg_rates;
-expdg_status expdg_probe_rates(expdg_rates* out);
 
 /* ---- Allocation-free residual ---------------------------------------------
  * The paper has no counterpart to this call; it is a deployment convenience.
@@ -328,18 +327,22 @@ expdg_status expdg_probe_rates(expdg_rates* out);
  * account for.  expdg_residual_noalloc computes exactly what expdg_residual
  * computes for the configuration cfg, with no context and without allocating:
  *
- *   - q (input) and r (output) are caller-owned DEVICE arrays of
- *     m * Ne * (p+1)^dim doubles in the canonical layout; host pointers are
- *     rejected with EXPDG_EINVAL.  cuda_stream: the stream to run on (NULL =
- *     legacy default stream); the call returns after that stream has finished.
- *   - Scratch (the float-float state copy and output of EXPDG_MIXED, and
- *     the non-physical-state flag of both forms) is a fixed static device
+ *   - q (input) and r (output) are caller-owned DEVICE arrays of the current
+ *     device (or managed memory), m * Ne * (p+1)^dim doubles in the canonical
+ *     layout; host pointers and other devices' memory are rejected with
+ *     EXPDG_EINVAL.  cuda_stream: the stream to run on (NULL = legacy default
+ *     stream); the call returns after that stream has finished.
+ *   - Scratch (the float-float state copy and output of EXPDG_MIXED_FF, and
+ *     the non-physical-state flag of every form) is a fixed static device
  *     array of about 8 MiB that every GPU which loads the library keeps until
- *     the process exits.  EXPDG_MIXED is limited to
+ *     the process exits.  EXPDG_MIXED_FF is limited to
  *     EXPDG_NOALLOC_MAX_UNKNOWNS unknowns (larger sizes return EXPDG_EINVAL);
- *     EXPDG_FP64 has no size limit.
- *   - The first call on a device looks up the array's device address; make
- *     that first call before any stream capture.
+ *     EXPDG_FP64 and EXPDG_MIXED work in place on q and r and have no size
+ *     limit.
+ *   - The first call on a device looks up the array's device address (once
+ *     per device, safe from several host threads).  Every call copies the
+ *     status word to the host and synchronises the stream, so the call cannot
+ *     be used inside a stream capture.
  *   - All calls share the array: calls that overlap on the GPU (other streams,
  *     other host threads) race and must be serialised by the caller.
  *   - Returns EXPDG_ENONPHYSICAL for an Euler state with rho <= 0 or p <= 0,

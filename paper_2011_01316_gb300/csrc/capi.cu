@@ -4,6 +4,7 @@
 #include <cmath>
 #include <cstdio>
 #include <cstring>
+#include <initializer_list>
 #include <map>
 #include <mutex>
 #include <string>
@@ -18,7 +19,10 @@ struct expdg_ctx {
   expdg_config cfg{};
   int dev = 0;
   cudaStream_t stream = nullptr;
-  bool ff = false;  // mixed form: FP32 operators, float-float Krylov storage
+  bool ff = false;     // float-float form: float-float Krylov storage and residual
+  bool f32op = false;  // FP32 operator applies (EXPDG_MIXED, EXPDG_MIXED_FF)
+  int lin_form = 0;    // DgForm of the linear operator apply
+
   int M = 0, NP = 0;
   size_t nelem = 0, N = 0, ld = 0;
   Tab tab{};
@@ -30,9 +34,11 @@ struct expdg_ctx {
   double* d_t2 = nullptr;  // FP64 scratch (state differences)
   double* d_in = nullptr;  // API input scratch
   double* d_out = nullptr; // API output scratch
-  // FP32 buffers (mixed form)
+  // FP32 buffers (float-float and mixed forms)
   float* d_q32b = nullptr;  // FP32 operand of the operator apply (expdg_jv, the EXPRB stage correction)
-  float* d_qfx = nullptr;   // the state as interleaved float-float pairs (mixed-form residual)
+  float* d_qfx = nullptr;   // the state as interleaved float-float pairs (float-float form's residual)
+  // mixed form: FP32 copies of the augmentation vectors b_1..b_P, read by the FP32 operator apply
+  float* d_bf[EXPDG_MAX_PHI + 1] = {};
   double* d_src = nullptr;  // forcing added to R (expdg_set_source), allocated on first use
   bool has_src = false;
   // linearisation state of the linear operator (compute form: float or double)
@@ -106,14 +112,30 @@ cudaError_t alloc_vec(expdg_ctx* ctx, Vec* v, size_t n) {
   return dalloc(ctx, &v->d, n);
 }
 
-bool is_device_ptr(const void* p) {
-  if (p == nullptr) return false;
+// Where a caller's pointer points: 0 host memory (copied through library
+// buffers), 1 memory the context's device reaches directly (its own device
+// memory, or managed memory; used in place), -1 device memory of another
+// device (rejected: the kernels would dereference it without peer access).
+int ptr_kind(const expdg_ctx* ctx, const void* p) {
+  if (p == nullptr) return 0;
   cudaPointerAttributes at{};
   if (cudaPointerGetAttributes(&at, p) != cudaSuccess) {
     cudaGetLastError();
-    return false;
+    return 0;
   }
-  return at.type == cudaMemoryTypeDevice || at.type == cudaMemoryTypeManaged;
+  if (at.type == cudaMemoryTypeManaged) return 1;
+  if (at.type == cudaMemoryTypeDevice) return at.device == ctx->dev ? 1 : -1;
+  return 0;
+}
+bool is_device_ptr(const expdg_ctx* ctx, const void* p) { return ptr_kind(ctx, p) == 1; }
+// EXPDG_EINVAL if any of the caller's pointers is another device's memory.
+expdg_status check_ptrs(expdg_ctx* ctx, std::initializer_list<const void*> ps) {
+  for (const void* p : ps)
+    if (ptr_kind(ctx, p) < 0) {
+      ctx->err = "a pointer to another device's memory";
+      return EXPDG_EINVAL;
+    }
+  return EXPDG_OK;
 }
 
 Vec null_vec() { return Vec{}; }
@@ -123,28 +145,22 @@ Vec dvec(double* p) {
   return v;
 }
 
-cudaError_t launch_dg(expdg_ctx* ctx, bool linear, const DGArgs& a, bool fp32) {
-  const int p = ctx->cfg.p;
-  const int eq = ctx->cfg.eq;
+// The operator kernel of DgForm `form` on stream s.
+cudaError_t launch_dg_form(expdg_ctx* ctx, bool linear, int form, const DGArgs& a, cudaStream_t s) {
+  const int p = ctx->cfg.p, eq = ctx->cfg.eq;
   switch (ctx->cfg.dim) {
-    case 1: return launch_dg_1d(linear, fp32, eq, p, a, ctx->tab, ctx->stream);
-    case 2: return launch_dg_2d(linear, fp32, eq, p, a, ctx->tab, ctx->stream);
-    case 3: return launch_dg_3d(linear, fp32, eq, p, a, ctx->tab, ctx->stream);
+    case 1: return launch_dg_1d(linear, form, eq, p, a, ctx->tab, s);
+    case 2: return launch_dg_2d(linear, form, eq, p, a, ctx->tab, s);
+    case 3: return launch_dg_3d(linear, form, eq, p, a, ctx->tab, s);
   }
   return cudaErrorInvalidValue;
 }
 
-cudaError_t launch_dg(expdg_ctx* ctx, bool linear, const DGArgs& a) { return launch_dg(ctx, linear, a, ctx->ff); }
-
-// The operator kernel on an explicit stream (graph capture).
-cudaError_t launch_dg_on(expdg_ctx* ctx, bool linear, const DGArgs& a, cudaStream_t s) {
-  const int p = ctx->cfg.p, eq = ctx->cfg.eq;
-  switch (ctx->cfg.dim) {
-    case 1: return launch_dg_1d(linear, ctx->ff, eq, p, a, ctx->tab, s);
-    case 2: return launch_dg_2d(linear, ctx->ff, eq, p, a, ctx->tab, s);
-    case 3: return launch_dg_3d(linear, ctx->ff, eq, p, a, ctx->tab, s);
-  }
-  return cudaErrorInvalidValue;
+// The context's linear operator apply (its form) on the context's stream, or
+// on an explicit stream (graph capture).
+cudaError_t launch_lin(expdg_ctx* ctx, const DGArgs& a) { return launch_dg_form(ctx, true, ctx->lin_form, a, ctx->stream); }
+cudaError_t launch_lin_on(expdg_ctx* ctx, const DGArgs& a, cudaStream_t s) {
+  return launch_dg_form(ctx, true, ctx->lin_form, a, s);
 }
 
 long long graph_key(int j0, int j1, int P) { return ((long long)j0 * 1024 + j1) * 8 + P; }
@@ -222,13 +238,15 @@ void set_alpha(DGArgs& a, double alpha) {
   a.alpha_l = (float)(alpha - (double)a.alpha_h);
 }
 
-// R(q) -> out (Krylov storage form), times alpha.  FP64 form: FP64 throughout.
-// Mixed form: the state is split once into float-float pairs and the residual
-// is computed in float-float arithmetic on the FP32 pipes (accurate to about
-// 1e-14 of the flux scale).  R of a smooth state is a small difference of
-// large fluxes: an FP32 residual (relative error 6e-5 on the 64^2 p = 4
-// vortex) puts broadband noise into the Krylov start vector that costs about
-// five extra Arnoldi steps; FP64 arithmetic runs on GB300's slow FP64 pipe.
+// R(q) -> out (Krylov storage form), times alpha.  FP64 and mixed forms: FP64
+// throughout.  R of a smooth state is a small difference of large fluxes: an
+// FP32 residual (measured in the mixed form: relative error 3e-6 on the 32^3
+// p = 3 wave) put broadband noise into the Krylov start vector that cost extra
+// Arnoldi steps (m = 37 against 27 at tol 1e-8) and errors above 1e-6 against
+// the FP64 form after the 20 - 50 steps of the batched and served solves.
+// Float-float form: the state is split once into float-float pairs and the
+// residual is computed in float-float arithmetic on the FP32 pipes (accurate
+// to about 1e-14 of the flux scale).
 // converted: ctx->d_qfx already holds q (written by linstate_into).
 cudaError_t residual_into(expdg_ctx* ctx, const double* q, Vec out, double alpha, bool converted = false) {
   DGArgs a = ctx->mesh;
@@ -238,7 +256,8 @@ cudaError_t residual_into(expdg_ctx* ctx, const double* q, Vec out, double alpha
   if (!ctx->ff) {
     a.q = q;
     a.out = out.d;
-    return run(ctx, EXPDG_K_RESIDUAL, 16.0 * ctx->N, [&]() { return launch_dg(ctx, false, a); });
+    return run(ctx, EXPDG_K_RESIDUAL, 16.0 * ctx->N,
+               [&]() { return launch_dg_form(ctx, false, DG_F64, a, ctx->stream); });
   }
   if (!converted) {
     const cudaError_t e =
@@ -264,23 +283,33 @@ cudaError_t residual_into(expdg_ctx* ctx, const double* q, Vec out, double alpha
 // a residual at qt that follows.
 cudaError_t linstate_into(expdg_ctx* ctx, const double* qt, bool with_fx = false) {
   float* qfx = (with_fx && ctx->ff) ? ctx->d_qfx : nullptr;
-  const double bytes = (8.0 + (ctx->ff ? 4.0 : 8.0) + (qfx ? 8.0 : 0.0)) * ctx->N;
+  const bool f32 = ctx->f32op;
+  const double bytes = (8.0 + (f32 ? 4.0 : 8.0) + (qfx ? 8.0 : 0.0)) * ctx->N;
   return run(ctx, EXPDG_K_VECTOR, bytes, [&]() {
     const size_t stride = ctx->mesh.stride;
     switch (ctx->cfg.dim) {
-      case 1: return launch_linstate_1d(ctx->cfg.eq, ctx->ff, qt, ctx->d_z, stride, ctx->cfg.gamma, ctx->mesh.roe,
+      case 1: return launch_linstate_1d(ctx->cfg.eq, f32, qt, ctx->d_z, stride, ctx->cfg.gamma, ctx->mesh.roe,
                                          qfx, ctx->stream);
-      case 2: return launch_linstate_2d(ctx->cfg.eq, ctx->ff, qt, ctx->d_z, stride, ctx->cfg.gamma, ctx->mesh.roe,
+      case 2: return launch_linstate_2d(ctx->cfg.eq, f32, qt, ctx->d_z, stride, ctx->cfg.gamma, ctx->mesh.roe,
                                          qfx, ctx->stream);
-      case 3: return launch_linstate_3d(ctx->cfg.eq, ctx->ff, qt, ctx->d_z, stride, ctx->cfg.gamma, ctx->mesh.roe,
+      case 3: return launch_linstate_3d(ctx->cfg.eq, f32, qt, ctx->d_z, stride, ctx->cfg.gamma, ctx->mesh.roe,
                                          qfx, ctx->stream);
     }
     return cudaErrorInvalidValue;
   });
 }
 
+// Algorithmic bytes of one linear operator apply per unknown: read v and z,
+// write the output (FP64 form 8 + 8 + 8; FP32-operator forms v FP32, z FP32,
+// output FP64 or a float-float pair (8), or FP32 (4: the mixed form's Arnoldi
+// steps with incomplete orthogonalisation)).
+double jv_bytes_per_unknown(const expdg_ctx* ctx, bool out32 = false) {
+  return ctx->f32op ? (out32 ? 12.0 : 16.0) : 24.0;
+}
+
 // L(qt) v -> out (no augmentation).  qt_T: linearisation state of qt in compute
-// form (ctx->d_z, from linstate_into), v_T: input in compute form.
+// form (ctx->d_z, from linstate_into), v_T: input (FP32 in the FP32-operator
+// forms, FP64 otherwise); out FP64 (or float-float in the float-float form).
 cudaError_t jv_into(expdg_ctx* ctx, const void* qt_T, const void* v_T, Vec out, double alpha) {
   DGArgs a = ctx->mesh;
   set_alpha(a, alpha);
@@ -292,7 +321,7 @@ cudaError_t jv_into(expdg_ctx* ctx, const void* qt_T, const void* v_T, Vec out, 
   } else {
     a.out = out.d;
   }
-  return run(ctx, EXPDG_K_JV, (ctx->ff ? 16.0 : 24.0) * ctx->N, [&]() { return launch_dg(ctx, true, a); });
+  return run(ctx, EXPDG_K_JV, jv_bytes_per_unknown(ctx) * ctx->N, [&]() { return launch_lin(ctx, a); });
 }
 
 // while_waiting: host work done after the copy is queued and before the wait
@@ -379,6 +408,8 @@ expdg_status phi_solve(expdg_ctx* ctx, const void* qt_T, double tau, const bool*
         ++nx;
       }
       RUN(ctx, EXPDG_K_VECTOR, 8.0 * (nx + 1) * N, launch_lincomb(F, ctx->b[i], nx, xs, as, N, s));
+      // mixed form: the FP32 operator apply reads an FP32 copy of b_i
+      if (ctx->f32op && !F) RUN(ctx, EXPDG_K_VECTOR, 12.0 * N, launch_to_f32(ctx->d_bf[i], ctx->b[i].d, N, s));
     }
     {
       Vec xs[EXPDG_MAX_PHI + 1];
@@ -414,11 +445,14 @@ expdg_status phi_solve(expdg_ctx* ctx, const void* qt_T, double tau, const bool*
     const int limit = replay ? m_fix : cfg.m_max;
     // checks at m_first, m_again, m_late and m_late + 2, then at the multiples of m_step
     int m_first = cfg.m_step, m_again = 0, m_late = 0;
-    // Paired checks (the float-float form's change since m - 1, evaluated in the
-    // check's launch) on problems of at least kPairMinUnknowns: there an Arnoldi
-    // step costs more than the second exponential.  Below that, when many
-    // small solves share the GPU, the extra cluster time outweighs the saved steps.
-    const bool pairs = F && !replay && N >= kPairMinUnknowns;
+    // Paired checks (the FP32-operator forms' change since m - 1, evaluated in
+    // the check's launch) on problems of at least kPairMinUnknowns: there an
+    // Arnoldi step costs more than the second exponential.  Below that, when
+    // many small solves share the GPU, the extra cluster time outweighs the
+    // saved steps.
+    const bool f32 = ctx->f32op, mx = f32 && !F;
+    const int kf = F ? KF_FF : (mx ? KF_MX : KF_F64);
+    const bool pairs = f32 && !replay && N >= kPairMinUnknowns;
     const bool first_sub = (sv == 0.0 && rejected == 0);
     const int sid = solve_id & 1;
     bool probe = false;
@@ -438,6 +472,23 @@ expdg_status phi_solve(expdg_ctx* ctx, const void* qt_T, double tau, const bool*
     // start kernel wrote them), so a step's launches are the same for every
     // sub-step and a run of steps can be replayed as a CUDA graph.
     const double vb = 8.0 * (double)n_aug;  // one vector: FP64 or float-float pair
+    // an operator apply of an Arnoldi step: v, z and the output, plus the
+    // augmentation vectors b_i (FP64, FP32 copies in the mixed form, float-float)
+    const double jv_apply_bytes =
+        (jv_bytes_per_unknown(ctx, mx && iop) + P * (mx ? 4.0 : 8.0)) * (double)N;
+    // orthogonalisation passes: window slots read (8 bytes an entry), w' read
+    // (FP32 top part in the mixed form's incomplete orthogonalisation), the
+    // update's output written (plus its FP32 shadow in the mixed form)
+    auto dots_bytes = [&](int jj) {
+      if (!iop) return (jj + 2) * vb;
+      const int nw = std::min(iop, jj + 1);
+      return mx ? (nw + 0.5) * vb : (nw + 1) * vb;
+    };
+    auto update_bytes = [&](int jj) {
+      if (!iop) return (jj + 4) * vb + (mx ? 0.5 * vb : 0.0);
+      const int nw = std::min(iop, jj + 1);
+      return (nw + 2) * vb;  // mixed: w' 4 + slot 8 + shadow 4 bytes
+    };
     auto step_launches = [&](int j, cudaStream_t ss, bool counted) -> cudaError_t {
       DGArgs a = ctx->mesh;
       a.scal = &ctx->ks->jv;
@@ -448,6 +499,12 @@ expdg_status phi_solve(expdg_ctx* ctx, const void* qt_T, double tau, const bool*
         a.v = vj.h;
         a.out_h = vo.h;
         a.out_l = vo.l;
+      } else if (mx) {  // FP32 shadow in; FP32 out with incomplete orthogonalisation, else FP64
+        a.v = vj.h;
+        if (iop)
+          a.out_h = vo.h;
+        else
+          a.out = vo.d;
       } else {
         a.v = vj.d;
         a.out = vo.d;
@@ -467,17 +524,17 @@ expdg_status phi_solve(expdg_ctx* ctx, const void* qt_T, double tau, const bool*
           a.W_d[i] = ctx->b[i].d;
           a.W_h[i] = ctx->b[i].h;
           a.W_l[i] = ctx->b[i].l;
+          a.W_f[i] = ctx->d_bf[i];
         }
       }
-      const int nwin = iop ? std::min(iop, j + 1) : 0;
-      const double bytes[3] = {(F ? 16.0 : 24.0) * N, (iop ? nwin + 1 : j + 2) * vb, (iop ? nwin + 2 : j + 4) * vb};
-      auto l0 = [&]() { return launch_dg_on(ctx, true, a, ss); };
+      const double bytes[3] = {jv_apply_bytes, dots_bytes(j), update_bytes(j)};
+      auto l0 = [&]() { return launch_lin_on(ctx, a, ss); };
       auto l1 = [&]() {
-        return iop ? launch_iom_dots(F, iop, ctx->ks, ctx->part, ctx->U, j, n_aug, ss)
+        return iop ? launch_iom_dots(kf, iop, ctx->ks, ctx->part, ctx->U, j, N, n_aug, ss)
                    : launch_dots(F, ctx->ks, ctx->part, ctx->U, j, n_aug, ss);
       };
       auto l2 = [&]() {
-        return iop ? launch_iom_update(F, iop, ctx->ks, ctx->part, ctx->U, j, n_aug, ss)
+        return iop ? launch_iom_update(kf, iop, ctx->ks, ctx->part, ctx->U, j, N, n_aug, ss)
                    : launch_update(F, ctx->ks, ctx->part, ctx->U, j, n_aug, ss);
       };
       cudaError_t e;
@@ -510,13 +567,12 @@ expdg_status phi_solve(expdg_ctx* ctx, const void* qt_T, double tau, const bool*
         return cudaSuccess;
       }
       for (int jj = j0; jj < j1; ++jj) {  // count the replayed launches like direct ones
-        const int nwin = iop ? std::min(iop, jj + 1) : 0;
         ctx->prof[EXPDG_K_JV].launches++;
-        ctx->prof[EXPDG_K_JV].bytes += (F ? 16.0 : 24.0) * N;
+        ctx->prof[EXPDG_K_JV].bytes += jv_apply_bytes;
         ctx->prof[EXPDG_K_DOTS].launches++;
-        ctx->prof[EXPDG_K_DOTS].bytes += (iop ? nwin + 1 : jj + 2) * vb;
+        ctx->prof[EXPDG_K_DOTS].bytes += dots_bytes(jj);
         ctx->prof[EXPDG_K_UPDATE].launches++;
-        ctx->prof[EXPDG_K_UPDATE].bytes += (iop ? nwin + 2 : jj + 4) * vb;
+        ctx->prof[EXPDG_K_UPDATE].bytes += update_bytes(jj);
       }
       return cudaGraphLaunch(g, s);
     };
@@ -529,11 +585,12 @@ expdg_status phi_solve(expdg_ctx* ctx, const void* qt_T, double tau, const bool*
       st->jv_applies += m - j;
       j = m;
       if (!due(m)) continue;
-      // mixed form: the FP32 operator's rounding noise inflates Saad's estimate, so a
-      // converged change since m - 1 also accepts (the check evaluates both)
+      // FP32-operator forms: the operator's rounding noise inflates Saad's
+      // estimate, so a converged change since m - 1 also accepts (the check
+      // evaluates both).  phi(H) in FP64, float-float in the float-float form.
       RUN(ctx, EXPDG_K_PHI, 8.0 * m * m,
-          launch_phi(ctx->ks, m, beta, cfg.krylov_tol, replay ? 1 : 0, F ? 1 : 0, iop ? ctx->part : nullptr, F ? 1 : 0,
-                     iop ? iom_update_blocks(F, iop, n_aug) : 0, F, pairs, s));
+          launch_phi(ctx->ks, m, beta, cfg.krylov_tol, replay ? 1 : 0, f32 ? 1 : 0, iop ? ctx->part : nullptr, kf,
+                     iop ? iom_update_blocks(kf, iop, n_aug) : 0, F, pairs, s));
       // the combination follows the check at once and writes only if it
       // accepted, so an accepted check needs no second host round trip; its
       // bytes are counted once the decision is known
@@ -589,7 +646,7 @@ expdg_status validate(const expdg_config* c) {
   }
   if (c->eq == EXPDG_EULER && !(c->gamma > 1.0)) return EXPDG_EINVAL;
   if (c->scheme != EXPDG_EPI2 && c->scheme != EXPDG_EXPRB32 && c->scheme != EXPDG_EXPRB42) return EXPDG_EINVAL;
-  if (c->prec != EXPDG_FP64 && c->prec != EXPDG_MIXED) return EXPDG_EINVAL;
+  if (c->prec != EXPDG_FP64 && c->prec != EXPDG_MIXED && c->prec != EXPDG_MIXED_FF) return EXPDG_EINVAL;
   if (!(c->krylov_tol > 0.0)) return EXPDG_EINVAL;
   if (c->m_max < 1 || c->m_max > EXPDG_MAX_KRYLOV) return EXPDG_EINVAL;
   if (c->m_step < 1) return EXPDG_EINVAL;
@@ -608,7 +665,7 @@ expdg_status validate(const expdg_config* c) {
 // returns the device pointer to use (the caller's own if already on device).
 const double* in_dev(expdg_ctx* ctx, const double* p, double* scratch, size_t n, cudaError_t* e) {
   *e = cudaSuccess;
-  if (p == nullptr || is_device_ptr(p)) return p;
+  if (p == nullptr || is_device_ptr(ctx, p)) return p;
   *e = cudaMemcpyAsync(scratch, p, n * sizeof(double), cudaMemcpyHostToDevice, ctx->stream);
   return scratch;
 }
@@ -652,7 +709,7 @@ expdg_status step_dev(expdg_ctx* ctx, double* q, double dt, const Replay& rp, ex
     double a[2] = {1.0, -1.0};
     RUN(ctx, EXPDG_K_VECTOR, 24.0 * N, launch_lincomb(false, dvec(ctx->d_t2), 2, x, a, N, s));
   }
-  if (F) {
+  if (ctx->f32op) {  // the FP32 operator reads an FP32 input
     RUN(ctx, EXPDG_K_VECTOR, 12.0 * N, launch_to_f32(ctx->d_q32b, ctx->d_t2, N, s));
     CU(ctx, jv_into(ctx, qt_T, ctx->d_q32b, ctx->t3, 1.0));
   } else {
@@ -714,7 +771,7 @@ void expdg_default_config(expdg_config* c) {
 
 size_t expdg_context_bytes(const expdg_config* cfg) {
   if (validate(cfg) != EXPDG_OK) return 0;
-  const bool ff = cfg->prec == EXPDG_MIXED;
+  const bool ff = cfg->prec == EXPDG_MIXED_FF, f32 = cfg->prec != EXPDG_FP64;
   size_t nelem = 1, np = 1;
   for (int d = 0; d < cfg->dim; ++d) {
     nelem *= (size_t)cfg->ne[d];
@@ -726,34 +783,38 @@ size_t expdg_context_bytes(const expdg_config* cfg) {
   const size_t gran = (size_t)2 << 20;
   auto r = [&](size_t b) { return ((b + gran - 1) / gran) * gran; };
   size_t total = 5 * r(N * sizeof(double));                 // q, q2, t2, in, out
-  if (ff) total += r(N * sizeof(float)) + r(2 * N * sizeof(float));  // FP32 operand, float-float state
-  total += r(N * (ff ? sizeof(float) : sizeof(double)));     // linearisation state
+  if (f32) total += r(N * sizeof(float));                            // FP32 operand
+  if (ff) total += r(2 * N * sizeof(float));                          // float-float state
+  if (f32 && !ff) total += EXPDG_MAX_PHI * r(N * sizeof(float));     // FP32 copies of b_1..b_P
+  total += r(N * (f32 ? sizeof(float) : sizeof(double)));    // linearisation state
   const size_t nvec = 2 * (EXPDG_MAX_PHI + 1) + 4;          // c, b, w, rn, t1, t3
   total += nvec * (ff ? 2 * r(N * sizeof(float)) : r(N * sizeof(double)));
   const size_t nb = ld * (size_t)(cfg->m_max + 1);
   total += ff ? 2 * r(nb * sizeof(float)) : r(nb * sizeof(double));
+  if (f32 && !ff) total += r(nb * sizeof(float));                     // FP32 shadow planes
   total += r(sizeof(KState)) + r(reduction_scratch_entries() * sizeof(double));
   return total;
 }
 
-// Tile class of the mixed-form operator apply for this context: the one
-// asked for, or (EXPDG_TILE_AUTO) the fastest of the three on the context's
-// own mesh, timed with CUDA events over five applies each after two warm-up
-// applies, on zero data (the apply's time does not depend on the values).
-// The default class is kept unless another is 3 % faster.  Results are
-// cached per mesh shape for the process.
+// Tile class of the FP32 operator apply (mixed and float-float forms) for
+// this context: the one asked for, or (EXPDG_TILE_AUTO) the fastest of the
+// three on the context's own mesh, timed with CUDA events over five applies
+// each after two warm-up applies, on zero data (the apply's time does not
+// depend on the values).  The default class is kept unless another is 3 %
+// faster.  Results are cached per mesh shape and form for the process.
 std::mutex g_tile_mu;
 std::map<std::vector<long>, int> g_tile_cache;
 
 cudaError_t choose_tile(expdg_ctx* ctx) {
   const expdg_config& c = ctx->cfg;
   ctx->mesh.tile = 0;
-  if (!ctx->ff) return cudaSuccess;
+  if (!ctx->f32op) return cudaSuccess;
   if (c.tile != EXPDG_TILE_AUTO) {
     ctx->mesh.tile = c.tile - 1;
     return cudaSuccess;
   }
-  const std::vector<long> key = {c.dim, c.p, c.eq, c.flux, c.bc, c.kappa != 0.0 ? 1 : 0, c.ne[0], c.ne[1], c.ne[2]};
+  const std::vector<long> key = {c.dim, c.p,     c.eq,     c.flux,   c.bc,    c.kappa != 0.0 ? 1 : 0,
+                                 c.ne[0], c.ne[1], c.ne[2], ctx->lin_form};
   {
     std::lock_guard<std::mutex> lk(g_tile_mu);
     auto it = g_tile_cache.find(key);
@@ -764,13 +825,19 @@ cudaError_t choose_tile(expdg_ctx* ctx) {
   }
   const cudaStream_t s = ctx->stream;
   cudaError_t e = cudaMemsetAsync(ctx->d_z, 0, ctx->N * sizeof(float), s);
-  if (e == cudaSuccess) e = cudaMemsetAsync(ctx->U.h, 0, ctx->N * sizeof(float), s);
-  if (e != cudaSuccess) return e;
   DGArgs a = ctx->mesh;
   a.q = ctx->d_z;
-  a.v = ctx->U.h;
-  a.out_h = ctx->U.h + ctx->ld;
-  a.out_l = ctx->U.l + ctx->ld;
+  if (ctx->ff) {
+    if (e == cudaSuccess) e = cudaMemsetAsync(ctx->U.h, 0, ctx->N * sizeof(float), s);
+    a.v = ctx->U.h;
+    a.out_h = ctx->U.h + ctx->ld;
+    a.out_l = ctx->U.l + ctx->ld;
+  } else {  // mixed form: the FP32 shadow plane in and out, as in its Arnoldi steps
+    if (e == cudaSuccess) e = cudaMemsetAsync(ctx->U.h, 0, ctx->N * sizeof(float), s);
+    a.v = ctx->U.h;
+    a.out_h = ctx->U.h + ctx->ld;
+  }
+  if (e != cudaSuccess) return e;
   set_alpha(a, 1.0);
   cudaEvent_t e0 = nullptr, e1 = nullptr;
   if ((e = cudaEventCreate(&e0)) != cudaSuccess) return e;
@@ -783,9 +850,9 @@ cudaError_t choose_tile(expdg_ctx* ctx) {
   for (int tk = 0; tk < 3 && e == cudaSuccess; ++tk) {
     if (tk > 0 && tile_elems_per_block(ctx->NP, tk) == tile_elems_per_block(ctx->NP, 0)) continue;  // same kernel
     a.tile = tk;
-    for (int r = 0; r < 2 && e == cudaSuccess; ++r) e = launch_dg(ctx, true, a);
+    for (int r = 0; r < 2 && e == cudaSuccess; ++r) e = launch_lin(ctx, a);
     if (e == cudaSuccess) e = cudaEventRecord(e0, s);
-    for (int r = 0; r < 5 && e == cudaSuccess; ++r) e = launch_dg(ctx, true, a);
+    for (int r = 0; r < 5 && e == cudaSuccess; ++r) e = launch_lin(ctx, a);
     if (e == cudaSuccess) e = cudaEventRecord(e1, s);
     if (e == cudaSuccess) e = cudaEventSynchronize(e1);
     float ms = 0.0f;
@@ -820,7 +887,9 @@ expdg_status expdg_create(const expdg_config* cfg, expdg_ctx** out) {
     delete ctx;
     return EXPDG_ECUDA;
   }
-  ctx->ff = (cfg->prec == EXPDG_MIXED);
+  ctx->ff = (cfg->prec == EXPDG_MIXED_FF);
+  ctx->f32op = (cfg->prec != EXPDG_FP64);
+  ctx->lin_form = ctx->ff ? DG_F32_FF : (ctx->f32op ? DG_F32_MX : DG_F64);
   const int p = cfg->p;
   ctx->M = (cfg->eq == EXPDG_BURGERS) ? 1 : cfg->dim + 2;
   ctx->NP = 1;
@@ -864,9 +933,11 @@ expdg_status expdg_create(const expdg_config* cfg, expdg_ctx** out) {
   ALLOC(dalloc(ctx, &ctx->d_t2, N));
   ALLOC(dalloc(ctx, &ctx->d_in, N));
   ALLOC(dalloc(ctx, &ctx->d_out, N));
-  if (ctx->ff) {
-    ALLOC(dalloc(ctx, &ctx->d_q32b, N));
-    ALLOC(dalloc(ctx, &ctx->d_qfx, 2 * N));
+  if (ctx->f32op) ALLOC(dalloc(ctx, &ctx->d_q32b, N));
+  if (ctx->ff) ALLOC(dalloc(ctx, &ctx->d_qfx, 2 * N));
+  if (ctx->f32op && !ctx->ff)
+    for (int i = 1; i <= EXPDG_MAX_PHI; ++i) ALLOC(dalloc(ctx, &ctx->d_bf[i], N));
+  if (ctx->f32op) {
     float* z = nullptr;
     ALLOC(dalloc(ctx, &z, N));
     ctx->d_z = z;
@@ -890,6 +961,7 @@ expdg_status expdg_create(const expdg_config* cfg, expdg_ctx** out) {
     ALLOC(dalloc(ctx, &ctx->U.l, nb));
   } else {
     ALLOC(dalloc(ctx, &ctx->U.d, nb));
+    if (ctx->f32op) ALLOC(dalloc(ctx, &ctx->U.h, nb));  // mixed form: FP32 shadow planes
   }
   ALLOC(dalloc(ctx, &ctx->ks, 1));
   double* part = nullptr;
@@ -989,7 +1061,8 @@ expdg_status expdg_set_source(expdg_ctx* ctx, const double* s) {
       return fail(ctx, e == cudaErrorMemoryAllocation ? EXPDG_ENOMEM : EXPDG_ECUDA, "source allocation");
     }
   }
-  const cudaMemcpyKind kind = is_device_ptr(s) ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice;
+  if (check_ptrs(ctx, {s}) != EXPDG_OK) return EXPDG_EINVAL;
+  const cudaMemcpyKind kind = is_device_ptr(ctx, s) ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice;
   CU(ctx, cudaMemcpyAsync(ctx->d_src, s, ctx->N * sizeof(double), kind, ctx->stream));
   CU(ctx, cudaStreamSynchronize(ctx->stream));
   ctx->has_src = true;
@@ -998,10 +1071,11 @@ expdg_status expdg_set_source(expdg_ctx* ctx, const double* s) {
 
 expdg_status expdg_residual(expdg_ctx* ctx, const double* q, double* r) {
   if (!ctx || !q || !r) return fail(ctx, EXPDG_EINVAL, "null argument");
+  if (check_ptrs(ctx, {q, r}) != EXPDG_OK) return EXPDG_EINVAL;
   cudaError_t e;
   const double* qd = in_dev(ctx, q, ctx->d_in, ctx->N, &e);
   CU(ctx, e);
-  const bool rdev = is_device_ptr(r);
+  const bool rdev = is_device_ptr(ctx, r);
   double* rd = rdev ? r : ctx->d_out;
   CU(ctx, cudaMemsetAsync(&ctx->ks->status, 0, sizeof(int), ctx->stream));
   if (ctx->ff) {
@@ -1016,18 +1090,22 @@ expdg_status expdg_residual(expdg_ctx* ctx, const double* q, double* r) {
 
 expdg_status expdg_jv(expdg_ctx* ctx, const double* qt, const double* v, double* out) {
   if (!ctx || !qt || !v || !out) return fail(ctx, EXPDG_EINVAL, "null argument");
+  if (check_ptrs(ctx, {qt, v, out}) != EXPDG_OK) return EXPDG_EINVAL;
   cudaError_t e;
   const double* qd = in_dev(ctx, qt, ctx->d_in, ctx->N, &e);
   CU(ctx, e);
   const double* vd = in_dev(ctx, v, ctx->d_t2, ctx->N, &e);
   CU(ctx, e);
-  const bool odev = is_device_ptr(out);
+  const bool odev = is_device_ptr(ctx, out);
   double* od = odev ? out : ctx->d_out;
   CU(ctx, linstate_into(ctx, qd));
   if (ctx->ff) {
     RUN(ctx, EXPDG_K_VECTOR, 12.0 * ctx->N, launch_to_f32(ctx->d_q32b, vd, ctx->N, ctx->stream));
     CU(ctx, jv_into(ctx, ctx->d_z, ctx->d_q32b, ctx->t1, 1.0));
     RUN(ctx, EXPDG_K_VECTOR, 16.0 * ctx->N, launch_ff_to_f64(od, ctx->t1, ctx->N, ctx->stream));
+  } else if (ctx->f32op) {  // mixed form: FP32 input, FP64 output
+    RUN(ctx, EXPDG_K_VECTOR, 12.0 * ctx->N, launch_to_f32(ctx->d_q32b, vd, ctx->N, ctx->stream));
+    CU(ctx, jv_into(ctx, ctx->d_z, ctx->d_q32b, dvec(od), 1.0));
   } else {
     CU(ctx, jv_into(ctx, ctx->d_z, vd, dvec(od), 1.0));
   }
@@ -1040,6 +1118,9 @@ expdg_status expdg_phi(expdg_ctx* ctx, const double* qt, double tau, const doubl
                        expdg_stats* stats, const expdg_trace_entry* replay, int nreplay, expdg_trace_entry* trace,
                        int trace_cap, int* ntrace) {
   if (!ctx || !qt || !out || P < 0 || P > EXPDG_MAX_PHI) return fail(ctx, EXPDG_EINVAL, "bad argument");
+  if (check_ptrs(ctx, {qt, out}) != EXPDG_OK) return EXPDG_EINVAL;
+  for (int i = 0; c && i <= P; ++i)
+    if (check_ptrs(ctx, {c[i]}) != EXPDG_OK) return EXPDG_EINVAL;
   const size_t N = ctx->N;
   const cudaStream_t s = ctx->stream;
   cudaError_t e;
@@ -1059,7 +1140,7 @@ expdg_status expdg_phi(expdg_ctx* ctx, const double* qt, double tau, const doubl
   }
   CU(ctx, linstate_into(ctx, qd));
   const void* qt_T = ctx->d_z;
-  const bool odev = is_device_ptr(out);
+  const bool odev = is_device_ptr(ctx, out);
   double* od = odev ? out : ctx->d_out;
   expdg_stats st{};
   std::vector<expdg_trace_entry> tr;
@@ -1078,8 +1159,9 @@ expdg_status expdg_phi(expdg_ctx* ctx, const double* qt, double tau, const doubl
 expdg_status expdg_step(expdg_ctx* ctx, double* q, double dt, expdg_stats* stats, const expdg_trace_entry* replay,
                         int nreplay, expdg_trace_entry* trace, int trace_cap, int* ntrace) {
   if (!ctx || !q) return fail(ctx, EXPDG_EINVAL, "null argument");
+  if (check_ptrs(ctx, {q}) != EXPDG_OK) return EXPDG_EINVAL;
   const size_t N = ctx->N;
-  const bool qdev = is_device_ptr(q);
+  const bool qdev = is_device_ptr(ctx, q);
   double* qd = qdev ? q : ctx->d_q;
   if (!qdev) CU(ctx, cudaMemcpyAsync(qd, q, N * sizeof(double), cudaMemcpyHostToDevice, ctx->stream));
   expdg_stats st{};
@@ -1099,8 +1181,9 @@ expdg_status expdg_step(expdg_ctx* ctx, double* q, double dt, expdg_stats* stats
 
 expdg_status expdg_advance(expdg_ctx* ctx, double* q, double dt, int nsteps, expdg_stats* stats) {
   if (!ctx || !q || nsteps < 0) return fail(ctx, EXPDG_EINVAL, "bad argument");
+  if (check_ptrs(ctx, {q}) != EXPDG_OK) return EXPDG_EINVAL;
   const size_t N = ctx->N;
-  const bool qdev = is_device_ptr(q);
+  const bool qdev = is_device_ptr(ctx, q);
   double* qd = qdev ? q : ctx->d_q;
   if (!qdev) CU(ctx, cudaMemcpyAsync(qd, q, N * sizeof(double), cudaMemcpyHostToDevice, ctx->stream));
   expdg_stats st{};

@@ -35,7 +35,6 @@ cudaError_t pdl_launch(void (*kern)(KArgs...), dim3 grid, dim3 block, size_t sme
 
 constexpr int MAXP = EXPDG_MAX_ORDER;
 constexpr int MMAX = EXPDG_MAX_KRYLOV;
-constexpr int RED_BLOCKS = 4 * 152;   // grid of the reduction kernels (deterministic partial order)
 constexpr int RED_THREADS = 256;
 constexpr int DOT_CHUNK = 8;          // basis vectors per block row in the multi-dot kernel
 
@@ -77,8 +76,8 @@ inline void fill_tab(Tab& t, const double* D, int p, double lift) {
   t.lift = make_cst(lift);
 }
 
-// Arguments of one DG operator apply.  T is the compute and input type
-// (double: FP64 form; float: mixed form, output as float-float pairs).
+// Arguments of one DG operator apply (see DgForm below for the types of
+// q, v and the outputs).
 //   residual: out = alpha * R(q)
 //   linear:   out = alpha * L(q) v  +  aug
 //   aug (Krylov augmented matrix, only when paug > 0):
@@ -113,6 +112,7 @@ struct DGArgs {
   const double* W_d[EXPDG_MAX_PHI + 1];  // W[i] = b_i, i = 1..paug
   const float* W_h[EXPDG_MAX_PHI + 1];
   const float* W_l[EXPDG_MAX_PHI + 1];
+  const float* W_f[EXPDG_MAX_PHI + 1];   // FP32 copies of b_i (FP64 storage with FP32 arithmetic)
   double* out_tail_d;
   float* out_tail_h;
   float* out_tail_l;
@@ -142,7 +142,10 @@ struct Vec {
   float* l;
 };
 
-// Krylov basis: vector i at d + i*ld (FP64 form) or h/l + i*ld (float-float).
+// Krylov basis: vector i at d + i*ld (FP64 and mixed forms) or h/l + i*ld
+// (float-float form).  Mixed form: h + i*ld is the FP32 shadow plane of
+// vector i (its rounding, read by the FP32 operator apply; the operator's FP32
+// output lands there too).
 struct Basis {
   double* d;
   float* h;
@@ -191,15 +194,25 @@ struct KState {
 };
 
 // ---- DG operators (dg_1d.cu, dg_2d.cu, dg_3d.cu) ----
-// fp32: mixed form (float inputs, float-float output).  Returns the launch error.
-cudaError_t launch_dg_1d(bool linear, bool fp32, int eq, int p, const DGArgs& a, const Tab& t, cudaStream_t s);
-cudaError_t launch_dg_2d(bool linear, bool fp32, int eq, int p, const DGArgs& a, const Tab& t, cudaStream_t s);
-cudaError_t launch_dg_3d(bool linear, bool fp32, int eq, int p, const DGArgs& a, const Tab& t, cudaStream_t s);
+// Arithmetic and storage of one operator apply.
+enum DgForm {
+  DG_F64 = 0,     // FP64 in, FP64 arithmetic, FP64 out (the FP64 form, and every form's
+                  // residual but the float-float form's)
+  DG_F32_FF = 1,  // linear operator: FP32 input vector, FP32 arithmetic, float-float
+                  // output (the float-float form)
+  DG_F32_MX = 2   // linear operator: FP32 input vector, FP32 arithmetic, output in FP32
+                  // (a.out_h) or widened exactly to FP64 (a.out); FP64 augmentation
+                  // tail (the mixed form)
+};
+// form: a DgForm.  Returns the launch error.
+cudaError_t launch_dg_1d(bool linear, int form, int eq, int p, const DGArgs& a, const Tab& t, cudaStream_t s);
+cudaError_t launch_dg_2d(bool linear, int form, int eq, int p, const DGArgs& a, const Tab& t, cudaStream_t s);
+cudaError_t launch_dg_3d(bool linear, int form, int eq, int p, const DGArgs& a, const Tab& t, cudaStream_t s);
 // The Roe-flux kernels (Euler; dg_roe_1d.cu, dg_roe_2d.cu, dg_roe_3d.cu), reached
 // through launch_dg_Nd when a.roe is set.
-cudaError_t launch_dg_roe_1d(bool linear, bool fp32, int p, const DGArgs& a, const Tab& t, cudaStream_t s);
-cudaError_t launch_dg_roe_2d(bool linear, bool fp32, int p, const DGArgs& a, const Tab& t, cudaStream_t s);
-cudaError_t launch_dg_roe_3d(bool linear, bool fp32, int p, const DGArgs& a, const Tab& t, cudaStream_t s);
+cudaError_t launch_dg_roe_1d(bool linear, int form, int p, const DGArgs& a, const Tab& t, cudaStream_t s);
+cudaError_t launch_dg_roe_2d(bool linear, int form, int p, const DGArgs& a, const Tab& t, cudaStream_t s);
+cudaError_t launch_dg_roe_3d(bool linear, int form, int p, const DGArgs& a, const Tab& t, cudaStream_t s);
 // Residual in float-float (a.q: interleaved float-float state, out_h / out_l):
 // the mixed form's R, FP64-grade on the FP32 pipes.
 cudaError_t launch_dg_fx_1d(int eq, int p, const DGArgs& a, const Tab& t, cudaStream_t s);
@@ -217,6 +230,9 @@ cudaError_t launch_linstate_3d(int eq, bool fp32, const double* q, void* z, size
                                float* qfx, cudaStream_t s);
 
 // ---- Krylov and vector kernels (krylov.cu); ff selects the float-float form ----
+// Storage form of the incomplete-orthogonalisation kernels: FP64 basis, float-float
+// basis, or FP64 basis with FP32 shadow planes and the operator output in FP32.
+enum KForm { KF_F64 = 0, KF_FF = 1, KF_MX = 2 };
 // partial-sum buffer entries needed by the reduction kernels
 size_t reduction_scratch_entries();
 // out = sum_k a[k] x[k] (k < nx <= 5; x[k] with null pointers counts as 0), n entries
@@ -239,7 +255,8 @@ cudaError_t launch_f64_to_ff(Vec out, const double* x, size_t n, cudaStream_t s)
 cudaError_t launch_ff_to_f64(double* out, Vec x, size_t n, cudaStream_t s);
 // FP64 -> interleaved float-float pairs (out[2i], out[2i+1] = high, low part)
 cudaError_t launch_f64_to_fx(float* out, const double* x, size_t n, cudaStream_t s);
-// Arnoldi start: u_0 = [b0; e_P / eta] (b0 null: zero top); clears the Krylov scalars;
+// Arnoldi start: u_0 = [b0; e_P / eta] (b0 null: zero top; an FP64 basis with an FP32
+// shadow plane (U.h) gets u_0's rounding there too); clears the Krylov scalars;
 // vscale_0 = s0 (1 / beta for incomplete orthogonalisation, else 1), vscale_i = 1 for i > 0.
 // mode 0: eta and s0 as given; 1: eta from KState, s0 = 1 / beta (0 when beta = 0:
 // the zero start vector of incomplete orthogonalisation); 2: eta from KState, s0 = 1.
@@ -253,7 +270,8 @@ cudaError_t launch_start(bool use_ff, KState* ks, Basis U, Vec b0, size_t N, int
 //           H(k, j) = (z_k - sum_i s_i H(k, i)) / r, H(j, j) = (c - s_{j-1} r) / r,
 //           c = (gamma - s.z) / r.
 //   update: q_j = (u_j - Q s) / r -> slot j;
-//           u_{j+1} = (w - Q z - c q_j) / r -> slot j+1; H(j+1, j) = |u_{j+1}|
+//           u_{j+1} = (w - Q z - c q_j) / r -> slot j+1 (and its FP32 rounding to the
+//           shadow plane of an FP64 basis that has one); H(j+1, j) = |u_{j+1}|
 //           (provisional until the next step's correction); happy breakdown
 //           when |u_{j+1}| <= 1e-13 |A_hat q_j| (recorded in breakdown_at).
 cudaError_t launch_dots(bool use_ff, KState* ks, void* part, Basis U, int j, size_t n_aug, cudaStream_t s);
@@ -267,27 +285,29 @@ cudaError_t launch_update(bool use_ff, KState* ks, void* part, Basis U, int j, s
 //               partials): c_j, H(j, j-1) = ||slot_j||, H(i, j) = c_i c_j <slot_i, w'>;
 //               slot j+1 = c_j w' - sum_i H(i, j) v_i (in place), per-block partials of
 //               its norm; happy breakdown when ||slot_j|| <= 1e-13 ||w_{j-1}||.
-//   gd: blocks of the window-products launch (0: as launch_iom_dots picks them).
-cudaError_t launch_iom_dots(bool use_ff, int iop, KState* ks, void* part, Basis U, int j, size_t n_aug,
+// kf (KForm): KF_MX reads the top N entries of w' in FP32 from the shadow plane
+// of slot j+1 (its P tail entries in FP64) and writes slot j+1 in FP64 and its
+// FP32 rounding to the shadow plane.
+cudaError_t launch_iom_dots(int kf, int iop, KState* ks, void* part, Basis U, int j, size_t N, size_t n_aug,
                             cudaStream_t s);
-cudaError_t launch_iom_update(bool use_ff, int iop, KState* ks, void* part, Basis U, int j, size_t n_aug,
+cudaError_t launch_iom_update(int kf, int iop, KState* ks, void* part, Basis U, int j, size_t N, size_t n_aug,
                               cudaStream_t s);
 // Blocks of an incomplete-orthogonalisation update launch (0 for an invalid iop).
-int iom_update_blocks(bool use_ff, int iop, size_t n_aug);
+int iom_update_blocks(int kf, int iop, size_t n_aug);
 // FP64 phi kernel: E = exp(H_m) (Taylor-18 scaling and squaring), y = E e_1, error estimate,
 // acceptance (forced when force_accept), ycoef_i = beta y_i vscale_i.  Acceptance: Saad's
 // estimate beta h_{m+1,m} |y_m| <= tol beta; with diff_rule also when the change
 // from the previous check, beta |y - [y_prev; 0]|, is <= tol beta.
 // iom_part: the reduction scratch when the basis comes from incomplete
 // orthogonalisation (h_{m,m-1} is then finished from the last update launch's
-// partials; iom_gu = that launch's blocks, iom_ff its precision), else nullptr.
+// partials; iom_gu = that launch's blocks, iom_kf its KForm), else nullptr.
 // ff_arith: float-float arithmetic on the FP32 pipes (the mixed form), else FP64.
 // pair: also exp(H_{m-1}) e_1 in the same launch (m >= 2; on a cluster of two
 // groups of CTAs, one matrix each, where such clusters fit the GPU, else both
 // packed on one group for m <= 49), so that the change with diff_rule is the
 // one since m - 1; otherwise since the previous check (y_prev, m_prev).
 cudaError_t launch_phi(KState* ks, int m, double beta, double tol, int force_accept, int diff_rule,
-                       const void* iom_part, int iom_ff, int iom_gu, bool ff_arith, bool pair, cudaStream_t s);
+                       const void* iom_part, int iom_kf, int iom_gu, bool ff_arith, bool pair, cudaStream_t s);
 // out = base + sum_{i < m_eff} ycoef_i u_i (first N entries; base may be null).
 // out and base may each be FP64 (d) or float-float (h, l).
 // if_accepted: write nothing unless the last phi kernel accepted.

@@ -3,9 +3,9 @@
 
 namespace expdg {
 
-cudaError_t launch_dg_3d(bool linear, bool fp32, int eq, int p, const DGArgs& a, const Tab& t, cudaStream_t s) {
-  if (eq == EXPDG_EULER && a.roe) return launch_dg_roe_3d(linear, fp32, p, a, t, s);
-  if (eq == EXPDG_EULER) return launch_dg_dim<3, EXPDG_EULER>(linear, fp32, p, a, t, s);
+cudaError_t launch_dg_3d(bool linear, int form, int eq, int p, const DGArgs& a, const Tab& t, cudaStream_t s) {
+  if (eq == EXPDG_EULER && a.roe) return launch_dg_roe_3d(linear, form, p, a, t, s);
+  if (eq == EXPDG_EULER) return launch_dg_dim<3, EXPDG_EULER>(linear, form, p, a, t, s);
   return cudaErrorInvalidValue;
 }
 

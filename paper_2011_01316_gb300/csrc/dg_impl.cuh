@@ -23,6 +23,7 @@
 #include <type_traits>
 
 #include "common.cuh"
+#include "cvt.cuh"
 #include "ff.cuh"
 #include "fx.cuh"
 
@@ -280,11 +281,13 @@ __device__ __forceinline__ void build_neighbours(const DGArgs& a, int e0, int* s
 //   acc = - sum_d (2/h_d) ( [D^(d) F_d]_n + (1/w_0) (F*.n - F^-.n) at face nodes ),
 // from the fluxes of the CTA's nodes in sF.  qv: own state (residual) or
 // linearisation state z (linear); vv: own linear input; w: own primitive
-// variables (residual); nb_v(f, gi): the linear input of field f at node gi
-// (index within the field plane) of a neighbour element.  Outside a Dirichlet
-// end the neighbour's state and input are the boundary data 0.
-template <int DIM, int P, int EQ, typename T, bool LINEAR, bool ROE, int TK, class NbV>
-__device__ __forceinline__ void node_terms(const DGArgs& a, T lift, const T* __restrict__ qin, const T* sF,
+// variables (residual); nb_q(f, gi), nb_v(f, gi): the state (residual) or
+// linearisation state (linear) and the linear input of field f at node gi
+// (index within the field plane) of a neighbour element, in the compute type.
+// Outside a Dirichlet end the neighbour's state and input are the boundary
+// data 0.
+template <int DIM, int P, int EQ, typename T, bool LINEAR, bool ROE, int TK, class NbQ, class NbV>
+__device__ __forceinline__ void node_terms(const DGArgs& a, T lift, NbQ nb_q, const T* sF,
                                            const T* sD, const int* sNb, int tid, int le, int n,
                                            const T (&qv)[NFields<DIM, EQ>::value],
                                            const T (&vv)[NFields<DIM, EQ>::value],
@@ -294,7 +297,6 @@ __device__ __forceinline__ void node_terms(const DGArgs& a, T lift, const T* __r
   constexpr int SLOT = elems_per_block<DIM, P, TK>() * NP, NF = 2 * DIM;
   using PH = Phys<DIM, EQ, T>;
   const T gamma = cst<T>(a.gamma), gm1 = gamma - T(1);
-  const size_t stride = a.stride;
   int ii[DIM];
   {
     int t = n;
@@ -330,7 +332,7 @@ __device__ __forceinline__ void node_terms(const DGArgs& a, T lift, const T* __r
       T qn[M], vn[M], Fp[M], Fm[M];
 #pragma unroll
       for (int f = 0; f < M; ++f) {
-        qn[f] = outside ? T(0) : qin[f * stride + nb];
+        qn[f] = outside ? T(0) : nb_q(f, nb);
         if (LINEAR) vn[f] = outside ? T(0) : nb_v(f, nb);
         Fm[f] = sF[(d * M + f) * SLOT + tid];
       }
@@ -377,8 +379,8 @@ __device__ __forceinline__ void node_terms(const DGArgs& a, T lift, const T* __r
 // R, the input vector for L) in the compute type.  The CTA forms q on its
 // elements and one halo element on each side (sU, sQ: (EPB + 2)(P + 1) + 2
 // entries each); every thread of the CTA must call it.
-template <int P, typename T, int TK>
-__device__ T visc_term(const DGArgs& a, const T* __restrict__ uin, const T* sD, T lift, T* sU, T* sQ, int e0,
+template <int P, typename T, int TK, typename U>
+__device__ T visc_term(const DGArgs& a, const U* __restrict__ uin, const T* sD, T lift, T* sU, T* sQ, int e0,
                        int tid, int le, int n, bool active) {
   constexpr int NP1 = P + 1;
   constexpr int EPB = elems_per_block<1, P, TK>();
@@ -390,7 +392,7 @@ __device__ T visc_term(const DGArgs& a, const T* __restrict__ uin, const T* sD, 
       if (a.dirichlet) return T(0);
       ge = ((ge % ne) + ne) % ne;
     }
-    return uin[(size_t)ge * NP1 + i];
+    return (T)uin[(size_t)ge * NP1 + i];
   };
   for (int k = tid; k < NH; k += blockDim.x) sU[k] = elem_val(e0 - 1 + k / NP1, k % NP1);
   if (tid == 0) sU[NH] = elem_val(e0 - 2, P);             // right end of element e0 - 2
@@ -468,18 +470,23 @@ struct DgSmem {
 // launch writes (after loading z when a.z_early).
 // LINEAR = false: residual R(q), a.q = q.  LINEAR = true: linear operator,
 // a.q = the linearisation state z of qt (k_linstate), a.v = v.
-// T = double: FP64 form (double in, double out); T = float: mixed form (float
-// in, float-float out); T = fx: float-float in and out (the mixed form's
-// residual: FP64-grade accuracy on the FP32 pipes).
-template <int DIM, int P, int EQ, typename T, bool LINEAR, bool ROE, int TK = 0>
+// T = double: FP64 (double in, double out); T = fx: float-float in and out
+// (the float-float form's residual: FP64-grade accuracy on the FP32 pipes);
+// T = float: FP32 arithmetic on an FP32 input vector (linear operator), with
+//   MX = false: float-float output (the float-float form);
+//   MX = true:  the mixed form (FP64 Krylov basis): output in FP32 (a.out_h,
+//               the operator's exact result) or widened exactly to FP64 on
+//               the integer pipes (a.out); the augmentation tail in FP64.
+template <int DIM, int P, int EQ, typename T, bool LINEAR, bool ROE, int TK = 0, bool MX = false>
 __device__ __forceinline__ void dg_group(const DGArgs& a, const Tab& tab, int e0, const DgSmem<DIM, P, EQ, T, TK>& sm,
                                          bool trigger) {
+  static_assert(!MX || (std::is_same<T, float>::value && LINEAR), "the mixed form's FP32 linear operator");
   constexpr int NP1 = P + 1;
   constexpr int NP = ipow(NP1, DIM);
   constexpr int M = NFields<DIM, EQ>::value;
   constexpr int EPB = elems_per_block<DIM, P, TK>();
   constexpr int SLOT = EPB * NP;  // nodes held by the CTA
-  constexpr bool FF = !std::is_same<T, double>::value;
+  constexpr bool FF = !std::is_same<T, double>::value && !MX;  // float-float output
   using PH = Phys<DIM, EQ, T>;
   T* sF = sm.sF;
   const T* sD = sm.sD;
@@ -514,9 +521,19 @@ __device__ __forceinline__ void dg_group(const DGArgs& a, const Tab& tab, int e0
   const bool dev = LINEAR && a.scal != nullptr;  // sub-step scalars in device memory
   double d_scale = a.alpha, d_cf[EXPDG_MAX_PHI];
   ff f_scale{a.alpha_h, a.alpha_l}, f_cf[EXPDG_MAX_PHI];
+  float s_scale = a.alpha_h, s_cf[EXPDG_MAX_PHI];  // mixed form
   bool any = false;
   if constexpr (LINEAR) {
-    if constexpr (!FF) {
+    if constexpr (MX) {
+      // the tail entries narrowed on the integer pipes; eta is a power of two
+      const float etaf = dev ? a.scal->eta_f : a.eta_f;
+      if (dev) s_scale = a.scal->alpha_h;
+#pragma unroll
+      for (int k = 0; k < EXPDG_MAX_PHI; ++k) {
+        s_cf[k] = (aug && k < a.paug) ? f64_to_f32_rn(a.tail_d[k]) * etaf : 0.0f;
+        any |= (s_cf[k] != 0.0f);
+      }
+    } else if constexpr (!FF) {
       const double eta = dev ? a.scal->eta : a.eta;
       if (dev) d_scale = a.scal->alpha;
 #pragma unroll
@@ -568,14 +585,19 @@ __device__ __forceinline__ void dg_group(const DGArgs& a, const Tab& tab, int e0
   T visc = T(0);
   if constexpr (DIM == 1 && EQ == EXPDG_BURGERS) {
     constexpr int NH2 = visc_smem_entries<DIM, P, EQ, TK>() / 2;
-    if (a.viscous)  // uniform
-      visc = visc_term<P, T, TK>(a, LINEAR ? vin : qin, sD, cst<T>(tab.lift), sV, sV + NH2, e0, tid, le, n, active);
+    if (a.viscous) {  // uniform
+      if constexpr (LINEAR)
+        visc = visc_term<P, T, TK>(a, vin, sD, cst<T>(tab.lift), sV, sV + NH2, e0, tid, le, n, active);
+      else
+        visc = visc_term<P, T, TK>(a, qin, sD, cst<T>(tab.lift), sV, sV + NH2, e0, tid, le, n, active);
+    }
   }
   if (!active) return;  // no further synchronisation below
 
   T acc[M];
-  node_terms<DIM, P, EQ, T, LINEAR, ROE, TK>(a, cst<T>(tab.lift), qin, sF, sD, sNb, tid, le, n, qv, vv, w,
-                                    [&](int f, size_t gi) { return vin[f * stride + gi]; }, acc);
+  node_terms<DIM, P, EQ, T, LINEAR, ROE, TK>(
+      a, cst<T>(tab.lift), [&](int f, size_t gi) { return qin[f * stride + gi]; }, sF, sD, sNb, tid, le, n, qv, vv,
+      w, [&](int f, size_t gi) { return vin[f * stride + gi]; }, acc);
   acc[0] += visc;
 
   const size_t base = (size_t)e * NP + n;
@@ -590,8 +612,26 @@ __device__ __forceinline__ void dg_group(const DGArgs& a, const Tab& tab, int e0
       a.out_l[f * stride + base] = o.l;
     }
     return;
-  } else {
-  if constexpr (!FF) {
+  } else if constexpr (MX) {  // FP32 arithmetic to the end
+    const bool wide = a.out != nullptr;  // uniform
+#pragma unroll
+    for (int f = 0; f < M; ++f) {
+      const size_t gi = f * stride + base;
+      float o = acc[f] * s_scale;
+      if (any) {
+#pragma unroll
+        for (int k = 1; k <= EXPDG_MAX_PHI; ++k)
+          if (k <= a.paug && s_cf[k - 1] != 0.0f) o = fmaf(s_cf[k - 1], a.W_f[a.paug + 1 - k][gi], o);
+      }
+      if (wide)
+        a.out[gi] = f32_to_f64_exact(o);
+      else
+        a.out_h[gi] = o;
+    }
+    if (aug && e0 == 0 && tid == 0)
+      for (int k = 0; k < a.paug; ++k) a.out_tail_d[k] = (k + 1 < a.paug) ? a.tail_d[k + 1] : 0.0;
+    return;
+  } else if constexpr (!FF) {
     const double scale = d_scale;
     const double* cf = d_cf;
 #pragma unroll
@@ -638,10 +678,9 @@ __device__ __forceinline__ void dg_group(const DGArgs& a, const Tab& tab, int e0
         a.out_tail_l[k] = t.l;
       }
   }
-  }
 }
 
-template <int DIM, int P, int EQ, typename T, bool LINEAR, bool ROE, int TK>
+template <int DIM, int P, int EQ, typename T, bool LINEAR, bool ROE, int TK, bool MX>
 __global__ void __launch_bounds__(dg_threads<DIM, P, TK>())
 k_dg(const DGArgs a, const Tab tab) {
   // the tables and the neighbour lists come from the parameters: set up before
@@ -649,16 +688,16 @@ k_dg(const DGArgs a, const Tab tab) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   const DgSmem<DIM, P, EQ, T, TK> sm(smem_raw);
   for (int k = threadIdx.x; k < (P + 1) * (P + 1); k += blockDim.x) sm.sD[k] = d_entry<T>(tab, k);
-  dg_group<DIM, P, EQ, T, LINEAR, ROE, TK>(a, tab, blockIdx.x * elems_per_block<DIM, P, TK>(), sm, true);
+  dg_group<DIM, P, EQ, T, LINEAR, ROE, TK, MX>(a, tab, blockIdx.x * elems_per_block<DIM, P, TK>(), sm, true);
 }
 
-template <int DIM, int P, int EQ, typename T, bool LINEAR, bool ROE, int TK = 0>
+template <int DIM, int P, int EQ, typename T, bool LINEAR, bool ROE, int TK = 0, bool MX = false>
 cudaError_t launch_dg_t(const DGArgs& a, const Tab& t, cudaStream_t s) {
   constexpr int EPB = elems_per_block<DIM, P, TK>();
   const int threads = dg_threads<DIM, P, TK>();
   const size_t smem = DgSmem<DIM, P, EQ, T, TK>::bytes();
   const int blocks = (a.nelem + EPB - 1) / EPB;
-  auto kern = k_dg<DIM, P, EQ, T, LINEAR, ROE, TK>;
+  auto kern = k_dg<DIM, P, EQ, T, LINEAR, ROE, TK, MX>;
   // once per instantiation, thread-safe (function-local static initialisation)
   static const cudaError_t configured =
       cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
@@ -667,44 +706,46 @@ cudaError_t launch_dg_t(const DGArgs& a, const Tab& t, cudaStream_t s) {
   return pdl_launch(kern, dim3(blocks), dim3(threads), smem, s, a, t);
 }
 
-// The mixed-form operator apply in the tile class a.tile (0, 1, 2: CTAs of
-// about 256, 128, 512 threads); the other kernels use class 0.
-template <int DIM, int P, int EQ, typename T, bool LINEAR, bool ROE>
+// The FP32 operator apply in the tile class a.tile (0, 1, 2: CTAs of about
+// 256, 128, 512 threads); the other kernels use class 0.
+template <int DIM, int P, int EQ, typename T, bool LINEAR, bool ROE, bool MX>
 cudaError_t launch_dg_tile(const DGArgs& a, const Tab& t, cudaStream_t s) {
   if constexpr (LINEAR && std::is_same<T, float>::value) {
-    if (a.tile == 1) return launch_dg_t<DIM, P, EQ, T, LINEAR, ROE, 1>(a, t, s);
-    if (a.tile == 2) return launch_dg_t<DIM, P, EQ, T, LINEAR, ROE, 2>(a, t, s);
+    if (a.tile == 1) return launch_dg_t<DIM, P, EQ, T, LINEAR, ROE, 1, MX>(a, t, s);
+    if (a.tile == 2) return launch_dg_t<DIM, P, EQ, T, LINEAR, ROE, 2, MX>(a, t, s);
   }
-  return launch_dg_t<DIM, P, EQ, T, LINEAR, ROE, 0>(a, t, s);
+  return launch_dg_t<DIM, P, EQ, T, LINEAR, ROE, 0, MX>(a, t, s);
 }
 
-template <int DIM, int EQ, typename T, bool LINEAR, bool ROE>
+template <int DIM, int EQ, typename T, bool LINEAR, bool ROE, bool MX = false>
 cudaError_t launch_dg_p(int p, const DGArgs& a, const Tab& t, cudaStream_t s) {
   switch (p) {
-    case 1: return launch_dg_tile<DIM, 1, EQ, T, LINEAR, ROE>(a, t, s);
-    case 2: return launch_dg_tile<DIM, 2, EQ, T, LINEAR, ROE>(a, t, s);
-    case 3: return launch_dg_tile<DIM, 3, EQ, T, LINEAR, ROE>(a, t, s);
-    case 4: return launch_dg_tile<DIM, 4, EQ, T, LINEAR, ROE>(a, t, s);
-    case 5: return launch_dg_tile<DIM, 5, EQ, T, LINEAR, ROE>(a, t, s);
-    case 6: return launch_dg_tile<DIM, 6, EQ, T, LINEAR, ROE>(a, t, s);
-    case 7: return launch_dg_tile<DIM, 7, EQ, T, LINEAR, ROE>(a, t, s);
-    case 8: return launch_dg_tile<DIM, 8, EQ, T, LINEAR, ROE>(a, t, s);
+    case 1: return launch_dg_tile<DIM, 1, EQ, T, LINEAR, ROE, MX>(a, t, s);
+    case 2: return launch_dg_tile<DIM, 2, EQ, T, LINEAR, ROE, MX>(a, t, s);
+    case 3: return launch_dg_tile<DIM, 3, EQ, T, LINEAR, ROE, MX>(a, t, s);
+    case 4: return launch_dg_tile<DIM, 4, EQ, T, LINEAR, ROE, MX>(a, t, s);
+    case 5: return launch_dg_tile<DIM, 5, EQ, T, LINEAR, ROE, MX>(a, t, s);
+    case 6: return launch_dg_tile<DIM, 6, EQ, T, LINEAR, ROE, MX>(a, t, s);
+    case 7: return launch_dg_tile<DIM, 7, EQ, T, LINEAR, ROE, MX>(a, t, s);
+    case 8: return launch_dg_tile<DIM, 8, EQ, T, LINEAR, ROE, MX>(a, t, s);
     default: return cudaErrorInvalidValue;
   }
 }
 
-// Float-float residual (the mixed form's R).
+// Float-float residual (the float-float form's R).
 template <int DIM, int EQ, bool ROE = false>
 cudaError_t launch_dg_fx_dim(int p, const DGArgs& a, const Tab& t, cudaStream_t s) {
   return launch_dg_p<DIM, EQ, fx, false, ROE>(p, a, t, s);
 }
 
+// form: DG_F64, or (linear operator only) DG_F32_FF or DG_F32_MX.
 // ROE: the Roe-flux instantiations (Euler), built in their own translation units.
 template <int DIM, int EQ, bool ROE = false>
-cudaError_t launch_dg_dim(bool linear, bool fp32, int p, const DGArgs& a, const Tab& t, cudaStream_t s) {
-  if (fp32)
-    return linear ? launch_dg_p<DIM, EQ, float, true, ROE>(p, a, t, s)
-                  : launch_dg_p<DIM, EQ, float, false, ROE>(p, a, t, s);
+cudaError_t launch_dg_dim(bool linear, int form, int p, const DGArgs& a, const Tab& t, cudaStream_t s) {
+  if (form == DG_F32_MX)
+    return linear ? launch_dg_p<DIM, EQ, float, true, ROE, true>(p, a, t, s) : cudaErrorInvalidValue;
+  if (form == DG_F32_FF)
+    return linear ? launch_dg_p<DIM, EQ, float, true, ROE>(p, a, t, s) : cudaErrorInvalidValue;
   return linear ? launch_dg_p<DIM, EQ, double, true, ROE>(p, a, t, s)
                 : launch_dg_p<DIM, EQ, double, false, ROE>(p, a, t, s);
 }

@@ -2,20 +2,26 @@
 // augmented matrix, the dense exponential of the projected Hessenberg matrix,
 // and the vector combinations of the phi-sum (paper Sec. 2.3).
 //
-// Two storage forms share every kernel (template parameter FF):
-//   FP64 form:   vectors are double arrays, arithmetic on the FP64 pipe.
-//   mixed form:  vectors are float-float pairs (h, l); products and sums use
-//                the error-free transformations of ff.cuh on the FP32 pipe,
-//                which runs 74x faster than the FP64 pipe on this GPU.
+// Two storage forms share most kernels (template parameter FF):
+//   FP64 storage:  vectors are double arrays, arithmetic on the FP64 pipe (the
+//                  FP64 form, and the mixed form, whose basis vectors also keep
+//                  an FP32 rounding in a shadow plane for the FP32 operator
+//                  apply; its incomplete-orthogonalisation passes are the
+//                  k_iom_*_mx kernels).
+//   float-float:   vectors are float-float pairs (h, l); products and sums use
+//                  the error-free transformations of ff.cuh on the FP32 pipe,
+//                  which runs 74x faster than the FP64 pipe on this GPU.
 // Reductions are deterministic: each block writes one partial per value and
 // the partials are summed in block order, one warp per value - by the last
 // block to finish (atomic ticket) in the full-orthogonalisation and norm
 // kernels, by every block of the consuming launch in incomplete
 // orthogonalisation (see there).
 #include <algorithm>
+#include <atomic>
 #include <cooperative_groups.h>
 
 #include "common.cuh"
+#include "cvt.cuh"
 #include "ff.cuh"
 #include "fx.cuh"
 
@@ -25,7 +31,9 @@ namespace expdg {
 
 namespace {
 
-constexpr int RB = 4 * 152;     // blocks of the streaming reduction kernels
+// Blocks of the streaming reduction kernels: four per SM of the current
+// device (red_blocks()), at most RB_MAX, which sizes the partial-sum scratch.
+constexpr int RB_MAX = 1024;
 constexpr int NT = 256;         // threads per block
 constexpr int NW = NT / 32;
 constexpr int NORMS_MAX = 5;
@@ -253,7 +261,7 @@ __global__ void __launch_bounds__(NT) k_norms(KState* ks, typename Acc<FF>::T* p
 
 __global__ void k_to_f32(float* out, const double* x, size_t n) {
   for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x)
-    out[i] = __double2float_rn(x[i]);
+    out[i] = f64_to_f32_rn(x[i]);  // on the integer pipes
 }
 __global__ void k_f64_to_ff(Vec out, const double* x, size_t n) {
   for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x) {
@@ -284,6 +292,8 @@ __global__ void __launch_bounds__(NT) k_start(KState* ks, Vec u0, Vec b0, size_t
     else
       x = (i == n_aug - 1) ? from_d<FF>(1.0 / eta) : A::zero();
     store<FF>(u0, i, x);
+    if constexpr (!FF)
+      if (u0.h != nullptr) u0.h[i] = f64_to_f32_rn(x);  // FP32 shadow (mixed form)
   }
   if (blockIdx.x == 0) {
     for (int k = threadIdx.x; k < (MMAX + 1) * MMAX; k += NT) ks->H[k] = 0.0;
@@ -515,6 +525,11 @@ __global__ void __launch_bounds__(NT) k_update(KState* ks, typename Acc<FF>::T* 
     }
     stq<FF>(U, j, g, xq);
     stq<FF>(U, j + 1, g, xu);
+    if constexpr (!FF)
+      if (U.h != nullptr)  // FP32 shadow of u_{j+1}, the next operator apply's input (mixed form)
+        *reinterpret_cast<float4*>(U.h + (size_t)(j + 1) * U.ld + 4 * g) =
+            make_float4(f64_to_f32_rn(xu.v[0]), f64_to_f32_rn(xu.v[1]), f64_to_f32_rn(xu.v[2]),
+                        f64_to_f32_rn(xu.v[3]));
   }
   for (size_t i = 4 * ng + tid; i < n_aug; i += nthr) {
     typename A::T xq = ldb<FF>(U, j, i);
@@ -529,6 +544,8 @@ __global__ void __launch_bounds__(NT) k_update(KState* ks, typename Acc<FF>::T* 
     nrm[0] = fma_acc<FF>(xu, xu, nrm[0]);
     stb<FF>(U, j, i, xq);
     stb<FF>(U, j + 1, i, xu);
+    if constexpr (!FF)
+      if (U.h != nullptr) U.h[(size_t)(j + 1) * U.ld + i] = f64_to_f32_rn(xu);
   }
   __shared__ typename A::T tot[1];
   block_sum<FF, 1>(nrm, sh, tot);
@@ -805,7 +822,7 @@ __global__ void __launch_bounds__(NT, 3) k_update_ff(KState* ks, ff* part, Basis
 constexpr int IOP_MAX = EXPDG_MAX_IOP;
 // The update launches' norm partials follow the window products' partials in
 // the reduction scratch: two regions, by the parity of j.
-constexpr int IOM_UPD_OFF = (IOP_MAX + 1) * RB;
+constexpr int IOM_UPD_OFF = (IOP_MAX + 1) * RB_MAX;
 
 // Prologue of update launch j (FP64 form; the float-float form uses
 // iom_prologue_ff below), in every block: sums the window products of
@@ -830,7 +847,7 @@ __device__ bool iom_prologue(KState* ks, const typename Acc<FF>::T* part, int j,
   __shared__ int s_ok;
   // every global load first (one round trip): partials, window scales, flags
   const int nd = K * Gd, nu = (j > 0) ? Gu : 0;
-  const T* pu = part + IOM_UPD_OFF + ((j + 1) & 1) * RB;  // region of launch j - 1
+  const T* pu = part + IOM_UPD_OFF + ((j + 1) & 1) * RB_MAX;  // region of launch j - 1
   for (int i = threadIdx.x; i < nd + nu; i += blockDim.x) {
     const T* src = (i < nd) ? part + i : pu + (i - nd);
     if constexpr (FF) {
@@ -915,7 +932,7 @@ __device__ int iom_prologue_ff(KState* ks, const ff* part, int j, int lo, int nw
   __shared__ float s_wprev;
   __shared__ int s_go;
   const int nd = K * Gd, nu = (j > 0) ? Gu : 0;
-  const ff* pu = part + IOM_UPD_OFF + ((j + 1) & 1) * RB;  // region of launch j - 1
+  const ff* pu = part + IOM_UPD_OFF + ((j + 1) & 1) * RB_MAX;  // region of launch j - 1
   for (int i = threadIdx.x; i < nd + nu; i += blockDim.x) {
     const ff* src = (i < nd) ? part + i : pu + (i - nd);
     const float2 t = __ldcg(reinterpret_cast<const float2*>(src));
@@ -1140,7 +1157,7 @@ __global__ void __launch_bounds__(NT) k_iom_update_ff(KState* ks, ff* part, Basi
   }
   ff v[1] = {dot2_value(S, C)};
   block_sum<true, 1>(v, sh, tot);
-  if (threadIdx.x == 0) part[IOM_UPD_OFF + (j & 1) * RB + blockIdx.x] = tot[0];
+  if (threadIdx.x == 0) part[IOM_UPD_OFF + (j & 1) * RB_MAX + blockIdx.x] = tot[0];
   griddep_launch();
   write_iom_scalars(ks, sc, j, lo, nwin);
 }
@@ -1219,7 +1236,139 @@ __global__ void __launch_bounds__(NT) k_iom_update(KState* ks, double* part, Bas
     nrm[0] = fma(w, w, nrm[0]);
   }
   block_sum<false, 1>(nrm, sh, tot);
-  if (threadIdx.x == 0) part[IOM_UPD_OFF + (j & 1) * RB + blockIdx.x] = tot[0];
+  if (threadIdx.x == 0) part[IOM_UPD_OFF + (j & 1) * RB_MAX + blockIdx.x] = tot[0];
+  griddep_launch();
+}
+
+// ---- mixed form: FP32 operator applies on an FP64 Krylov basis ----
+// Slot i keeps its FP64 entries in U.d and their FP32 rounding in the shadow
+// plane U.h, which the FP32 operator apply reads.  The operator apply of step
+// j writes the top N entries of w' = A_hat slot_j in FP32 to the shadow plane
+// of slot j+1 (the FP32 operator's result, exact there) and the P tail
+// entries in FP64 to slot j+1.  The window-products launch widens w' exactly
+// (cvt.cuh, integer pipes) and forms the inner products in FP64; the update
+// writes slot j+1 in FP64 and its FP32 rounding to the shadow plane.  |w'|^2
+// only scales the happy-breakdown test: its top part is summed in FP32 (one
+// FP64 operation fewer per element on the narrow FP64 pipe; the true-scale
+// slots keep w' within a few orders of magnitude of the operator's norm).
+// The update scales w' by c_j in FP32 too (part of the operator apply on the
+// unit vector v_j), so its FP64 operations are the window's and the norm's.
+// Loads before griddepcontrol.wait as in the float-float kernels above.
+
+// Entry i of w' (slot j1): FP32 top part widened, FP64 tail.
+__device__ __forceinline__ double mx_w(const Basis& U, int j1, size_t i, size_t N) {
+  const size_t o = (size_t)j1 * U.ld + i;
+  return i < N ? f32_to_f64_exact(U.h[o]) : U.d[o];
+}
+
+template <int KW>
+__global__ void __launch_bounds__(NT) k_iom_dots_mx(KState* ks, double* part, Basis U, int j, size_t N,
+                                                    size_t n_aug) {
+  constexpr int K = KW + 1;
+  __shared__ double sh[NW * K];
+  __shared__ double tot[K];
+  const int lo = max(0, j - KW + 1), nwin = j - lo + 1;
+  double acc[KW];
+#pragma unroll
+  for (int c = 0; c < KW; ++c) acc[c] = 0.0;
+  float wn = 0.0f;     // |w'|^2 of the top part (FP32)
+  double wnt = 0.0;    // and of the ragged end and tail
+  const size_t ld = U.ld, ng = N / 4;
+  const size_t tid = blockIdx.x * (size_t)NT + threadIdx.x, nthr = (size_t)gridDim.x * NT;
+  // the first trip's window slots before the wait (written by the previous update)
+  Quad<false> px[KW];
+  if (tid < ng)
+#pragma unroll
+    for (int c = 0; c < KW; ++c) px[c] = ldq<false>(U, lo + (c < nwin ? c : 0), tid);
+  griddep_wait();
+  for (size_t g = tid; g < ng; g += nthr) {
+    const float4 wf = __ldg(reinterpret_cast<const float4*>(U.h + (size_t)(j + 1) * ld + 4 * g));
+    const double w[4] = {f32_to_f64_exact(wf.x), f32_to_f64_exact(wf.y), f32_to_f64_exact(wf.z),
+                         f32_to_f64_exact(wf.w)};
+#pragma unroll
+    for (int c = 0; c < KW; ++c) {
+      const Quad<false> x = (g == tid) ? px[c] : ldq<false>(U, lo + (c < nwin ? c : 0), g);
+      if (c < nwin)
+#pragma unroll
+        for (int e = 0; e < 4; ++e) acc[c] = fma(x.v[e], w[e], acc[c]);
+    }
+    wn = fmaf(wf.x, wf.x, fmaf(wf.y, wf.y, fmaf(wf.z, wf.z, fmaf(wf.w, wf.w, wn))));
+  }
+  for (size_t i = 4 * ng + tid; i < n_aug; i += nthr) {  // ragged end and the augmentation tail
+    const double wi = mx_w(U, j + 1, i, N);
+#pragma unroll
+    for (int c = 0; c < KW; ++c)
+      if (c < nwin) acc[c] = fma(ldb<false>(U, lo + c, i), wi, acc[c]);
+    wnt = fma(wi, wi, wnt);
+  }
+  double v[K];
+#pragma unroll
+  for (int c = 0; c < KW; ++c) v[c] = acc[c];
+  v[KW] = (double)wn + wnt;
+  block_sum<false, K>(v, sh, tot);
+  const int G = gridDim.x;
+  if (threadIdx.x < K) part[(size_t)threadIdx.x * G + blockIdx.x] = tot[threadIdx.x];
+  griddep_launch();
+}
+
+template <int KW>
+__global__ void __launch_bounds__(NT) k_iom_update_mx(KState* ks, double* part, Basis U, int j, size_t N,
+                                                      size_t n_aug, int Gd) {
+  __shared__ double cf[IOP_MAX];
+  __shared__ double sh[NW];
+  __shared__ double tot[1];
+  __shared__ double cj;
+  const int lo = max(0, j - KW + 1), nwin = j - lo + 1;
+  const size_t ld = U.ld, ng = N / 4;
+  const size_t tid = blockIdx.x * (size_t)NT + threadIdx.x, nthr = (size_t)gridDim.x * NT;
+  float* __restrict__ Uh = U.h;
+  // the first trip's w' and window slots before the wait (written by the
+  // operator apply and the previous update); the window products' partials after it
+  float4 pwf = make_float4(0.f, 0.f, 0.f, 0.f);
+  Quad<false> px[KW];
+  if (tid < ng) {
+    pwf = *reinterpret_cast<const float4*>(Uh + (size_t)(j + 1) * ld + 4 * tid);
+#pragma unroll
+    for (int c = 0; c < KW; ++c) px[c] = ldq<false>(U, lo + (c < nwin ? c : 0), tid);
+  }
+  griddep_wait();
+  if (!iom_prologue<false>(ks, part, j, lo, nwin, KW + 1, Gd, gridDim.x, cf, &cj)) return;
+  const double c_j = cj;
+  // c_j w' = A_hat v_j: the operator's FP32 output scaled to the unit basis
+  // vector in FP32 (one rounding, at the level of the FP32 operator's own),
+  // then widened exactly; the slots stay at true scale
+  const float c_jf = f64_to_f32_rn(c_j);
+  double nrm[1] = {0.0};
+  for (size_t g = tid; g < ng; g += nthr) {
+    const size_t o = (size_t)(j + 1) * ld + 4 * g;
+    const float4 wf = (g == tid) ? pwf : *reinterpret_cast<const float4*>(Uh + o);
+    Quad<false> w;
+    w.v[0] = f32_to_f64_exact(__fmul_rn(c_jf, wf.x));
+    w.v[1] = f32_to_f64_exact(__fmul_rn(c_jf, wf.y));
+    w.v[2] = f32_to_f64_exact(__fmul_rn(c_jf, wf.z));
+    w.v[3] = f32_to_f64_exact(__fmul_rn(c_jf, wf.w));
+#pragma unroll
+    for (int c = 0; c < KW; ++c) {
+      const Quad<false> x = (g == tid) ? px[c] : ldq<false>(U, lo + (c < nwin ? c : 0), g);
+      if (c < nwin)
+#pragma unroll
+        for (int e = 0; e < 4; ++e) w.v[e] = fma(cf[c], x.v[e], w.v[e]);
+    }
+#pragma unroll
+    for (int e = 0; e < 4; ++e) nrm[0] = fma(w.v[e], w.v[e], nrm[0]);
+    stq<false>(U, j + 1, g, w);
+    *reinterpret_cast<float4*>(Uh + o) =
+        make_float4(f64_to_f32_rn(w.v[0]), f64_to_f32_rn(w.v[1]), f64_to_f32_rn(w.v[2]), f64_to_f32_rn(w.v[3]));
+  }
+  for (size_t i = 4 * ng + tid; i < n_aug; i += nthr) {  // ragged end (FP32 scaling) and the FP64 tail
+    double w = (i < N) ? f32_to_f64_exact(__fmul_rn(c_jf, Uh[(size_t)(j + 1) * ld + i])) : c_j * U.d[(size_t)(j + 1) * ld + i];
+    for (int c = 0; c < nwin; ++c) w = fma(cf[c], ldb<false>(U, lo + c, i), w);
+    stb<false>(U, j + 1, i, w);
+    if (i < N) Uh[(size_t)(j + 1) * ld + i] = f64_to_f32_rn(w);
+    nrm[0] = fma(w, w, nrm[0]);
+  }
+  block_sum<false, 1>(nrm, sh, tot);
+  if (threadIdx.x == 0) part[IOM_UPD_OFF + (j & 1) * RB_MAX + blockIdx.x] = tot[0];
   griddep_launch();
 }
 
@@ -1346,8 +1495,9 @@ __device__ void cl_matmul(cg::cluster_group& cl, const T* A, const T* B, T* C, c
 // Launched with the cluster size as a launch attribute.
 template <typename T, int GROUPS>
 __global__ void __launch_bounds__(PHI_NT)
-k_phi(KState* ks, int m_req, double beta, double tol, int force, int diff_rule, const void* iom_part, int iom_ff,
+k_phi(KState* ks, int m_req, double beta, double tol, int force, int diff_rule, const void* iom_part, int iom_kf,
       int iom_gu, int pair, const PhiConst pc) {
+  const bool iom_ff = iom_kf == KF_FF;
   using PT = PhiT<T>;
   using SC = typename PT::S;
   cg::cluster_group cl = cg::this_cluster();
@@ -1367,7 +1517,7 @@ k_phi(KState* ks, int m_req, double beta, double tol, int force, int diff_rule, 
   // Incomplete orthogonalisation: h_{m,m-1} = ||slot_m|| from the partials of
   // the last update launch (every CTA sums them alike).
   if (iom_part != nullptr && s_m == m_req && !s_brk) {
-    const int off = IOM_UPD_OFF + (((m_req - 1) & 1) ? RB : 0);
+    const int off = IOM_UPD_OFF + (((m_req - 1) & 1) ? RB_MAX : 0);
     if (threadIdx.x < 32) {
       double x = 0.0;
       if (iom_ff) {
@@ -1630,16 +1780,40 @@ __global__ void __launch_bounds__(NT) k_combine_ff(const KState* ks, Basis U, Ve
   }
 }
 
+// SMs of the current device, cached per device ordinal (thread-safe: a
+// benign race only stores the same value twice).
+int device_sms() {
+  static std::atomic<int> cache[64];
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) {
+    cudaGetLastError();
+    return 1;
+  }
+  int v = cache[dev].load(std::memory_order_relaxed);
+  if (v == 0) {
+    if (cudaDeviceGetAttribute(&v, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || v < 1) {
+      cudaGetLastError();
+      v = 1;
+    }
+    cache[dev].store(v, std::memory_order_relaxed);
+  }
+  return v;
+}
+
+// Blocks of the streaming reduction kernels: four per SM, at most RB_MAX.
+int red_blocks() { return std::min(RB_MAX, 4 * device_sms()); }
+
 int grid_for(size_t n) {
   size_t b = (n + NT - 1) / NT;
-  if (b > (size_t)RB) b = RB;
+  const size_t cap = (size_t)red_blocks();
+  if (b > cap) b = cap;
   if (b < 1) b = 1;
   return (int)b;
 }
 
 }  // namespace
 
-size_t reduction_scratch_entries() { return (size_t)RB * (2 * MMAX + 4) + 64; }
+size_t reduction_scratch_entries() { return (size_t)RB_MAX * (2 * MMAX + 4) + 64; }
 
 cudaError_t launch_lincomb(bool use_ff, Vec out, int nx, const Vec* x, const double* a, size_t n, cudaStream_t s) {
   if (nx > NORMS_MAX) return cudaErrorInvalidValue;
@@ -1723,7 +1897,7 @@ cudaError_t launch_dots(bool use_ff, KState* ks, void* part, Basis U, int j, siz
   if (j < 0 || j + 1 > MMAX) return cudaErrorInvalidValue;
   const int ch = use_ff ? FF_CH : DOT_CHUNK;
   const int chunks = (j + 1 + ch - 1) / ch;
-  int gx = (RB + chunks - 1) / chunks;
+  int gx = (red_blocks() + chunks - 1) / chunks;
   const int need = (int)((n_aug / 4 + NT - 1) / NT);
   if (gx > need) gx = need;
   if (gx < 1) gx = 1;
@@ -1732,9 +1906,10 @@ cudaError_t launch_dots(bool use_ff, KState* ks, void* part, Basis U, int j, siz
   const dim3 grid1((unsigned)(gx * chunks));  // float-float kernel: chunk-fastest 1D grid
   // thread-safe one-time set-up (function-local static initialisation)
   static const cudaError_t configured = [] {
-    cudaError_t e = cudaFuncSetAttribute(k_dots_ff, cudaFuncAttributeMaxDynamicSharedMemorySize, 128 * 1024);
+    // (2 MMAX + 1) partials of up to RB_MAX / chunks blocks each, 8 bytes
+    cudaError_t e = cudaFuncSetAttribute(k_dots_ff, cudaFuncAttributeMaxDynamicSharedMemorySize, 160 * 1024);
     if (e == cudaSuccess)
-      e = cudaFuncSetAttribute(k_dots<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, 128 * 1024);
+      e = cudaFuncSetAttribute(k_dots<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, 160 * 1024);
     return e;
   }();
   if (configured != cudaSuccess) return configured;
@@ -1746,7 +1921,8 @@ cudaError_t launch_update(bool use_ff, KState* ks, void* part, Basis U, int j, s
   if (j < 0 || j + 1 > MMAX) return cudaErrorInvalidValue;
   if (use_ff) {
     const size_t tiles = (n_aug / 4 + UQB - 1) / UQB;
-    const int g = (int)(tiles < (size_t)(3 * 152) ? (tiles > 0 ? tiles : 1) : 3 * 152);
+    const size_t cap = (size_t)std::min(RB_MAX, 3 * device_sms());
+    const int g = (int)(tiles < cap ? (tiles > 0 ? tiles : 1) : cap);
     return pdl_launch(k_update_ff, dim3(g), dim3(NT), (size_t)g * 8, s, ks, static_cast<ff*>(part), U, j, n_aug);
   }
   const int g = grid_for(n_aug / 4 + 1);
@@ -1756,9 +1932,11 @@ cudaError_t launch_update(bool use_ff, KState* ks, void* part, Basis U, int j, s
 namespace {
 
 // One full wave of kernel Kern (its resident blocks on every SM with
-// smem_max bytes of dynamic shared memory each), capped at RB blocks (the
-// partial-sum scratch) and at `need`.  Measured once per kernel (thread-safe
-// static initialisation; smem_max is a constant of the kernel).
+// smem_max bytes of dynamic shared memory each), capped at red_blocks() (the
+// partial-sum scratch and the update's staging hold that many per row) and at
+// `need`.  Measured once per kernel (thread-safe static initialisation;
+// smem_max is a constant of the kernel, and the kernel's dynamic shared memory
+// limit must already admit it).
 template <auto Kern>
 int one_wave(size_t need, size_t smem_max) {
   static const int wave = [smem_max] {
@@ -1766,93 +1944,115 @@ int one_wave(size_t need, size_t smem_max) {
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
     cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, Kern, NT, smem_max);
-    return std::min(RB, std::max(1, nsm) * std::max(1, occ));
+    return std::min(red_blocks(), std::max(1, nsm) * std::max(1, occ));
   }();
   return (int)std::max<size_t>(std::min(need, (size_t)wave), 1);
 }
 
 template <int KW>
-int iom_dots_grid(bool use_ff, size_t n_aug) {
+int iom_dots_grid(int kf, size_t n_aug) {
   const size_t need = (n_aug / 4 + NT - 1) / NT;
-  return use_ff ? one_wave<k_iom_dots_ff<KW>>(need, 0) : one_wave<k_iom_dots<KW>>(need, 0);
+  if (kf == KF_FF) return one_wave<k_iom_dots_ff<KW>>(need, 0);
+  if (kf == KF_MX) return one_wave<k_iom_dots_mx<KW>>(need, 0);
+  return one_wave<k_iom_dots<KW>>(need, 0);
 }
-// the update's dynamic shared memory stages (KW + 1) Gd + Gu partials, Gd, Gu <= RB
+// the update's dynamic shared memory stages (KW + 1) Gd + Gu partials, Gd, Gu <= red_blocks()
 template <int KW>
-int iom_update_grid(bool use_ff, size_t n_aug) {
+size_t iom_update_smem_max() {
+  return (size_t)(KW + 2) * red_blocks() * 8;
+}
+// Raise the update kernels' dynamic shared memory limit to that (once; before
+// any occupancy query or launch).
+template <int KW>
+cudaError_t iom_update_configure() {
+  static const cudaError_t configured = [] {
+    const int mx = (int)iom_update_smem_max<KW>();
+    cudaError_t e = cudaFuncSetAttribute(k_iom_update_ff<KW>, cudaFuncAttributeMaxDynamicSharedMemorySize, mx);
+    if (e == cudaSuccess) e = cudaFuncSetAttribute(k_iom_update<KW>, cudaFuncAttributeMaxDynamicSharedMemorySize, mx);
+    if (e == cudaSuccess)
+      e = cudaFuncSetAttribute(k_iom_update_mx<KW>, cudaFuncAttributeMaxDynamicSharedMemorySize, mx);
+    return e;
+  }();
+  return configured;
+}
+template <int KW>
+int iom_update_grid(int kf, size_t n_aug) {
   const size_t need = (n_aug / 4 + NT - 1) / NT;
-  const size_t smem = (size_t)(KW + 2) * RB * 8;
-  return use_ff ? one_wave<k_iom_update_ff<KW>>(need, smem) : one_wave<k_iom_update<KW>>(need, smem);
+  if (iom_update_configure<KW>() != cudaSuccess) return 1;
+  const size_t smem = iom_update_smem_max<KW>();
+  if (kf == KF_FF) return one_wave<k_iom_update_ff<KW>>(need, smem);
+  if (kf == KF_MX) return one_wave<k_iom_update_mx<KW>>(need, smem);
+  return one_wave<k_iom_update<KW>>(need, smem);
 }
 
 template <int KW>
-cudaError_t iom_dots_kw(bool use_ff, KState* ks, void* part, Basis U, int j, size_t n_aug, cudaStream_t s) {
-  const int g = iom_dots_grid<KW>(use_ff, n_aug);
-  if (use_ff)
+cudaError_t iom_dots_kw(int kf, KState* ks, void* part, Basis U, int j, size_t N, size_t n_aug, cudaStream_t s) {
+  const int g = iom_dots_grid<KW>(kf, n_aug);
+  if (kf == KF_FF)
     return pdl_launch(k_iom_dots_ff<KW>, dim3(g), dim3(NT), 0, s, ks, static_cast<ff*>(part), U, j, n_aug);
+  if (kf == KF_MX)
+    return pdl_launch(k_iom_dots_mx<KW>, dim3(g), dim3(NT), 0, s, ks, static_cast<double*>(part), U, j, N, n_aug);
   return pdl_launch(k_iom_dots<KW>, dim3(g), dim3(NT), 0, s, ks, static_cast<double*>(part), U, j, n_aug);
 }
 
 template <int KW>
-cudaError_t iom_update_kw(bool use_ff, KState* ks, void* part, Basis U, int j, size_t n_aug, cudaStream_t s) {
-  const int gd = iom_dots_grid<KW>(use_ff, n_aug), g = iom_update_grid<KW>(use_ff, n_aug);
-  const size_t smem = (size_t)((KW + 1) * gd + g) * 8;
-  static const cudaError_t configured = [] {
-    cudaError_t e = cudaFuncSetAttribute(k_iom_update_ff<KW>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                         (int)((KW + 2) * RB * 8));
-    if (e == cudaSuccess)
-      e = cudaFuncSetAttribute(k_iom_update<KW>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)((KW + 2) * RB * 8));
-    return e;
-  }();
+cudaError_t iom_update_kw(int kf, KState* ks, void* part, Basis U, int j, size_t N, size_t n_aug, cudaStream_t s) {
+  const cudaError_t configured = iom_update_configure<KW>();
   if (configured != cudaSuccess) return configured;
-  if (use_ff)
+  const int gd = iom_dots_grid<KW>(kf, n_aug), g = iom_update_grid<KW>(kf, n_aug);
+  const size_t smem = (size_t)((KW + 1) * gd + g) * 8;
+  if (kf == KF_FF)
     return pdl_launch(k_iom_update_ff<KW>, dim3(g), dim3(NT), smem, s, ks, static_cast<ff*>(part), U, j, n_aug, gd);
+  if (kf == KF_MX)
+    return pdl_launch(k_iom_update_mx<KW>, dim3(g), dim3(NT), smem, s, ks, static_cast<double*>(part), U, j, N,
+                      n_aug, gd);
   return pdl_launch(k_iom_update<KW>, dim3(g), dim3(NT), smem, s, ks, static_cast<double*>(part), U, j, n_aug, gd);
 }
 
 }  // namespace
 
-cudaError_t launch_iom_dots(bool use_ff, int iop, KState* ks, void* part, Basis U, int j, size_t n_aug,
+cudaError_t launch_iom_dots(int kf, int iop, KState* ks, void* part, Basis U, int j, size_t N, size_t n_aug,
                             cudaStream_t s) {
   if (j < 0 || j + 1 > MMAX) return cudaErrorInvalidValue;
   switch (iop) {
-    case 1: return iom_dots_kw<1>(use_ff, ks, part, U, j, n_aug, s);
-    case 2: return iom_dots_kw<2>(use_ff, ks, part, U, j, n_aug, s);
-    case 3: return iom_dots_kw<3>(use_ff, ks, part, U, j, n_aug, s);
-    case 4: return iom_dots_kw<4>(use_ff, ks, part, U, j, n_aug, s);
-    case 5: return iom_dots_kw<5>(use_ff, ks, part, U, j, n_aug, s);
-    case 6: return iom_dots_kw<6>(use_ff, ks, part, U, j, n_aug, s);
-    case 7: return iom_dots_kw<7>(use_ff, ks, part, U, j, n_aug, s);
-    case 8: return iom_dots_kw<8>(use_ff, ks, part, U, j, n_aug, s);
+    case 1: return iom_dots_kw<1>(kf, ks, part, U, j, N, n_aug, s);
+    case 2: return iom_dots_kw<2>(kf, ks, part, U, j, N, n_aug, s);
+    case 3: return iom_dots_kw<3>(kf, ks, part, U, j, N, n_aug, s);
+    case 4: return iom_dots_kw<4>(kf, ks, part, U, j, N, n_aug, s);
+    case 5: return iom_dots_kw<5>(kf, ks, part, U, j, N, n_aug, s);
+    case 6: return iom_dots_kw<6>(kf, ks, part, U, j, N, n_aug, s);
+    case 7: return iom_dots_kw<7>(kf, ks, part, U, j, N, n_aug, s);
+    case 8: return iom_dots_kw<8>(kf, ks, part, U, j, N, n_aug, s);
     default: return cudaErrorInvalidValue;
   }
 }
 
-int iom_update_blocks(bool use_ff, int iop, size_t n_aug) {
+int iom_update_blocks(int kf, int iop, size_t n_aug) {
   switch (iop) {
-    case 1: return iom_update_grid<1>(use_ff, n_aug);
-    case 2: return iom_update_grid<2>(use_ff, n_aug);
-    case 3: return iom_update_grid<3>(use_ff, n_aug);
-    case 4: return iom_update_grid<4>(use_ff, n_aug);
-    case 5: return iom_update_grid<5>(use_ff, n_aug);
-    case 6: return iom_update_grid<6>(use_ff, n_aug);
-    case 7: return iom_update_grid<7>(use_ff, n_aug);
-    case 8: return iom_update_grid<8>(use_ff, n_aug);
+    case 1: return iom_update_grid<1>(kf, n_aug);
+    case 2: return iom_update_grid<2>(kf, n_aug);
+    case 3: return iom_update_grid<3>(kf, n_aug);
+    case 4: return iom_update_grid<4>(kf, n_aug);
+    case 5: return iom_update_grid<5>(kf, n_aug);
+    case 6: return iom_update_grid<6>(kf, n_aug);
+    case 7: return iom_update_grid<7>(kf, n_aug);
+    case 8: return iom_update_grid<8>(kf, n_aug);
     default: return 0;
   }
 }
 
-cudaError_t launch_iom_update(bool use_ff, int iop, KState* ks, void* part, Basis U, int j, size_t n_aug,
+cudaError_t launch_iom_update(int kf, int iop, KState* ks, void* part, Basis U, int j, size_t N, size_t n_aug,
                               cudaStream_t s) {
   if (j < 0 || j + 1 > MMAX) return cudaErrorInvalidValue;
   switch (iop) {
-    case 1: return iom_update_kw<1>(use_ff, ks, part, U, j, n_aug, s);
-    case 2: return iom_update_kw<2>(use_ff, ks, part, U, j, n_aug, s);
-    case 3: return iom_update_kw<3>(use_ff, ks, part, U, j, n_aug, s);
-    case 4: return iom_update_kw<4>(use_ff, ks, part, U, j, n_aug, s);
-    case 5: return iom_update_kw<5>(use_ff, ks, part, U, j, n_aug, s);
-    case 6: return iom_update_kw<6>(use_ff, ks, part, U, j, n_aug, s);
-    case 7: return iom_update_kw<7>(use_ff, ks, part, U, j, n_aug, s);
-    case 8: return iom_update_kw<8>(use_ff, ks, part, U, j, n_aug, s);
+    case 1: return iom_update_kw<1>(kf, ks, part, U, j, N, n_aug, s);
+    case 2: return iom_update_kw<2>(kf, ks, part, U, j, N, n_aug, s);
+    case 3: return iom_update_kw<3>(kf, ks, part, U, j, N, n_aug, s);
+    case 4: return iom_update_kw<4>(kf, ks, part, U, j, N, n_aug, s);
+    case 5: return iom_update_kw<5>(kf, ks, part, U, j, N, n_aug, s);
+    case 6: return iom_update_kw<6>(kf, ks, part, U, j, N, n_aug, s);
+    case 7: return iom_update_kw<7>(kf, ks, part, U, j, N, n_aug, s);
+    case 8: return iom_update_kw<8>(kf, ks, part, U, j, N, n_aug, s);
     default: return cudaErrorInvalidValue;
   }
 }
@@ -1860,7 +2060,7 @@ cudaError_t launch_iom_update(bool use_ff, int iop, KState* ks, void* part, Basi
 // One phi kernel instantiation, launched as clusters of `cl` CTAs.
 template <typename T, int GROUPS>
 cudaError_t phi_launch(int cl, size_t smem, cudaStream_t s, KState* ks, int m, double beta, double tol, int force,
-                       int diff_rule, const void* iom_part, int iom_ff, int iom_gu, int pair, const PhiConst& pc) {
+                       int diff_rule, const void* iom_part, int iom_kf, int iom_gu, int pair, const PhiConst& pc) {
   cudaLaunchConfig_t lc = {};
   lc.gridDim = dim3(cl);
   lc.blockDim = dim3(PHI_NT);
@@ -1873,7 +2073,7 @@ cudaError_t phi_launch(int cl, size_t smem, cudaStream_t s, KState* ks, int m, d
   at[0].val.clusterDim.z = 1;
   lc.attrs = at;
   lc.numAttrs = 1;
-  return cudaLaunchKernelEx(&lc, k_phi<T, GROUPS>, ks, m, beta, tol, force, diff_rule, iom_part, iom_ff, iom_gu, pair,
+  return cudaLaunchKernelEx(&lc, k_phi<T, GROUPS>, ks, m, beta, tol, force, diff_rule, iom_part, iom_kf, iom_gu, pair,
                             pc);
 }
 
@@ -1908,7 +2108,7 @@ bool phi_two_groups_fit(int smax) {
 }
 
 cudaError_t launch_phi(KState* ks, int m, double beta, double tol, int force_accept, int diff_rule,
-                       const void* iom_part, int iom_ff, int iom_gu, bool ff_arith, bool pair, cudaStream_t s) {
+                       const void* iom_part, int iom_kf, int iom_gu, bool ff_arith, bool pair, cudaStream_t s) {
   if (m < 1 || m > MMAX) return cudaErrorInvalidValue;
   static const PhiConst pc = [] {
     PhiConst c{};
@@ -1941,13 +2141,13 @@ cudaError_t launch_phi(KState* ks, int m, double beta, double tol, int force_acc
       6 * sizeof(double) * ((size_t)m * m + (pair && !two_groups ? (size_t)(m - 1) * (m - 1) : 0));
   const int cl = two_groups ? 2 * PHI_CL : PHI_CL;
   if (ff_arith)
-    return two_groups ? phi_launch<ff, 2>(cl, smem, s, ks, m, beta, tol, force_accept, diff_rule, iom_part, iom_ff,
+    return two_groups ? phi_launch<ff, 2>(cl, smem, s, ks, m, beta, tol, force_accept, diff_rule, iom_part, iom_kf,
                                           iom_gu, 1, pc)
-                      : phi_launch<ff, 1>(cl, smem, s, ks, m, beta, tol, force_accept, diff_rule, iom_part, iom_ff,
+                      : phi_launch<ff, 1>(cl, smem, s, ks, m, beta, tol, force_accept, diff_rule, iom_part, iom_kf,
                                           iom_gu, pair ? 1 : 0, pc);
-  return two_groups ? phi_launch<double, 2>(cl, smem, s, ks, m, beta, tol, force_accept, diff_rule, iom_part, iom_ff,
+  return two_groups ? phi_launch<double, 2>(cl, smem, s, ks, m, beta, tol, force_accept, diff_rule, iom_part, iom_kf,
                                             iom_gu, 1, pc)
-                    : phi_launch<double, 1>(cl, smem, s, ks, m, beta, tol, force_accept, diff_rule, iom_part, iom_ff,
+                    : phi_launch<double, 1>(cl, smem, s, ks, m, beta, tol, force_accept, diff_rule, iom_part, iom_kf,
                                             iom_gu, pair ? 1 : 0, pc);
 }
 

@@ -2,10 +2,11 @@
 // device allocation, for callers that cannot allocate device memory.
 //
 // Its scratch - the float-float copy of the state and the float-float output
-// of the mixed form, and the non-physical-state flag of both forms - lives in
-// the file-scope arrays below.  Every GPU that loads this library holds them
-// (about 8 MiB) until the process exits.
+// of the float-float form, and the non-physical-state flag of every form -
+// lives in the file-scope arrays below.  Every GPU that loads this library
+// holds them (about 8 MiB) until the process exits.
 #include <cstring>
+#include <mutex>
 
 #include "common.cuh"
 #include "tables.h"
@@ -21,38 +22,45 @@ static __device__ __align__(256) float g_scratch[4 * kMaxUnknowns];
 static __device__ __align__(256) int g_status[64];
 
 // Device addresses of the arrays, per device ordinal (the host-side names of
-// g_scratch / g_status are stand-ins, not device addresses).
+// g_scratch / g_status are stand-ins, not device addresses).  Looked up once
+// per device, with that device current, under a std::call_once per device, so
+// first calls from several host threads do not race on the cache.
 struct Addr {
   float* scratch;
   int* status;
-  bool ready;
+  cudaError_t err;
 };
 Addr g_addr[kMaxDevices];
+std::once_flag g_once[kMaxDevices];
 
 cudaError_t device_addresses(int dev, Addr** out) {
   if (dev < 0 || dev >= kMaxDevices) return cudaErrorInvalidDevice;
   Addr& a = g_addr[dev];
-  if (!a.ready) {
+  std::call_once(g_once[dev], [&a] {
     void* p = nullptr;
-    cudaError_t e = cudaGetSymbolAddress(&p, g_scratch);
-    if (e != cudaSuccess) return e;
+    a.err = cudaGetSymbolAddress(&p, g_scratch);
     a.scratch = static_cast<float*>(p);
-    e = cudaGetSymbolAddress(&p, g_status);
-    if (e != cudaSuccess) return e;
-    a.status = static_cast<int*>(p);
-    a.ready = true;
-  }
+    if (a.err == cudaSuccess) {
+      a.err = cudaGetSymbolAddress(&p, g_status);
+      a.status = static_cast<int*>(p);
+    }
+  });
+  if (a.err != cudaSuccess) return a.err;
   *out = &a;
   return cudaSuccess;
 }
 
-bool on_device(const void* p) {
+// Memory the current device reaches directly: its own device memory, or
+// managed memory.  Host memory and another device's memory are rejected (the
+// kernels would dereference them without access).
+bool on_device(const void* p, int dev) {
   cudaPointerAttributes at{};
   if (p == nullptr || cudaPointerGetAttributes(&at, p) != cudaSuccess) {
     cudaGetLastError();
     return false;
   }
-  return at.type == cudaMemoryTypeDevice || at.type == cudaMemoryTypeManaged;
+  if (at.type == cudaMemoryTypeManaged) return true;
+  return at.type == cudaMemoryTypeDevice && at.device == dev;
 }
 
 }  // namespace
@@ -66,7 +74,7 @@ extern "C" expdg_status expdg_residual_noalloc(const expdg_config* cfg, const do
   if (cfg->eq != EXPDG_BURGERS && cfg->eq != EXPDG_EULER) return EXPDG_EINVAL;
   if (cfg->eq == EXPDG_BURGERS && dim != 1) return EXPDG_EINVAL;
   if (cfg->eq == EXPDG_EULER && !(cfg->gamma > 1.0)) return EXPDG_EINVAL;
-  if (cfg->prec != EXPDG_FP64 && cfg->prec != EXPDG_MIXED) return EXPDG_EINVAL;
+  if (cfg->prec != EXPDG_FP64 && cfg->prec != EXPDG_MIXED && cfg->prec != EXPDG_MIXED_FF) return EXPDG_EINVAL;
   if (!(cfg->kappa >= 0.0) || (cfg->bc != EXPDG_BC_PERIODIC && cfg->bc != EXPDG_BC_DIRICHLET)) return EXPDG_EINVAL;
   if ((cfg->kappa > 0.0 || cfg->bc != EXPDG_BC_PERIODIC) && cfg->eq != EXPDG_BURGERS) return EXPDG_EINVAL;
   if (cfg->flux != EXPDG_FLUX_LF && (cfg->flux != EXPDG_FLUX_ROE || cfg->eq != EXPDG_EULER)) return EXPDG_EINVAL;
@@ -80,12 +88,12 @@ extern "C" expdg_status expdg_residual_noalloc(const expdg_config* cfg, const do
   const int m = (cfg->eq == EXPDG_BURGERS) ? 1 : dim + 2;
   if (nelem > (size_t)0x7fffffff / (size_t)np) return EXPDG_EINVAL;
   const size_t N = (size_t)m * nelem * np;
-  const bool mixed = cfg->prec == EXPDG_MIXED;
-  if (mixed && N > kMaxUnknowns) return EXPDG_EINVAL;  // beyond the static scratch
-  if (!on_device(q) || !on_device(r)) return EXPDG_EINVAL;
-
+  const bool ffr = cfg->prec == EXPDG_MIXED_FF;  // float-float residual: needs the scratch
+  if (ffr && N > kMaxUnknowns) return EXPDG_EINVAL;  // beyond the static scratch
   int dev = 0;
   if (cudaGetDevice(&dev) != cudaSuccess) return EXPDG_ECUDA;
+  if (!on_device(q, dev) || !on_device(r, dev)) return EXPDG_EINVAL;
+
   Addr* ad = nullptr;
   if (device_addresses(dev, &ad) != cudaSuccess) return EXPDG_ECUDA;
   const cudaStream_t s = static_cast<cudaStream_t>(cuda_stream);
@@ -119,7 +127,7 @@ extern "C" expdg_status expdg_residual_noalloc(const expdg_config* cfg, const do
   float* rh = ad->scratch + 2 * kMaxUnknowns;
   float* rl = ad->scratch + 3 * kMaxUnknowns;
   cudaError_t e = cudaSuccess;
-  if (mixed) {  // float-float residual, as expdg_residual computes it in the mixed form
+  if (ffr) {  // float-float residual, as expdg_residual computes it in the float-float form
     e = launch_f64_to_fx(qfx, q, N, s);
     a.q = qfx;
     a.out_h = rh;
@@ -132,17 +140,17 @@ extern "C" expdg_status expdg_residual_noalloc(const expdg_config* cfg, const do
       else
         e = launch_dg_fx_3d(cfg->eq, p, a, tab, s);
     }
-  } else {
+  } else {  // the FP64 residual (FP64 and mixed forms): in place, no scratch
     a.q = q;
     a.out = r;
     if (dim == 1)
-      e = launch_dg_1d(false, false, cfg->eq, p, a, tab, s);
+      e = launch_dg_1d(false, DG_F64, cfg->eq, p, a, tab, s);
     else if (dim == 2)
-      e = launch_dg_2d(false, false, cfg->eq, p, a, tab, s);
+      e = launch_dg_2d(false, DG_F64, cfg->eq, p, a, tab, s);
     else
-      e = launch_dg_3d(false, false, cfg->eq, p, a, tab, s);
+      e = launch_dg_3d(false, DG_F64, cfg->eq, p, a, tab, s);
   }
-  if (e == cudaSuccess && mixed) {
+  if (e == cudaSuccess && ffr) {
     Vec v{};
     v.h = rh;
     v.l = rl;

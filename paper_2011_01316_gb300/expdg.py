@@ -18,7 +18,7 @@ LIB_PATH = os.environ.get("EXPDG_LIB", os.path.join(HERE, "libexpdg.so"))
 EXPDG_OK, EXPDG_EINVAL, EXPDG_ENOMEM, EXPDG_EKRYLOV, EXPDG_ENONPHYSICAL, EXPDG_ETIMEOUT, EXPDG_ECUDA = range(7)
 EXPDG_BURGERS, EXPDG_EULER = 1, 2
 EXPDG_EPI2, EXPDG_EXPRB32, EXPDG_EXPRB42 = 2, 3, 4
-EXPDG_FP64, EXPDG_MIXED = 0, 1
+EXPDG_FP64, EXPDG_MIXED, EXPDG_MIXED_FF = 0, 1, 2
 EXPDG_BC_PERIODIC, EXPDG_BC_DIRICHLET = 0, 1
 EXPDG_FLUX_LF, EXPDG_FLUX_ROE = 0, 1
 EXPDG_TILE_AUTO, EXPDG_TILE_256, EXPDG_TILE_128, EXPDG_TILE_512 = 0, 1, 2, 3
@@ -59,12 +59,6 @@ class expdg_server_config(ctypes.Structure):
     _fields_ = [("hbm_budget", ctypes.c_size_t), ("workers", ctypes.c_int)]
 
 
-class expdg_rates(ctypes.Structure):
-    _fields_ = [("fp64_fma_per_s", ctypes.c_double), ("fp32_fma_per_s", ctypes.c_double),
-                ("fp32x2_fma_per_s", ctypes.c_double), ("f64_to_f32_per_s", ctypes.c_double),
-                ("sms", ctypes.c_int), ("clock_mhz", ctypes.c_double)]
-
-
 class ExpdgError(RuntimeError):
     def __init__(self, status, msg):
         super().__init__(f"{STATUS_NAMES.get(status, status)}: {msg}")
@@ -103,7 +97,6 @@ def _load():
         "expdg_profile_get": (ctypes.c_int, [P, P, ctypes.c_int]),
         "expdg_residual_noalloc": (ctypes.c_int, [vp(expdg_config), P, P, P]),
         "expdg_config_node_coords": (ctypes.c_int, [vp(expdg_config), P]),
-        "expdg_probe_rates": (ctypes.c_int, [vp(expdg_rates)]),
         "expdg_context_bytes": (ctypes.c_size_t, [vp(expdg_config)]),
         "expdg_server_create": (ctypes.c_int, [vp(expdg_server_config), vp(P)]),
         "expdg_server_destroy": (None, [P]),
@@ -167,15 +160,6 @@ def config_node_coords(cfg):
     if st != EXPDG_OK:
         raise ExpdgError(st, "expdg_config_node_coords failed")
     return out
-
-
-def probe_rates():
-    """Measured FP64 / FP32 / packed-FP32 FMA and f64->f32 conversion rates (per second)."""
-    r = expdg_rates()
-    st = _lib.expdg_probe_rates(ctypes.byref(r))
-    if st != EXPDG_OK:
-        raise ExpdgError(st, "expdg_probe_rates failed")
-    return {k: getattr(r, k) for k, _ in r._fields_}
 
 
 def context_bytes(cfg):

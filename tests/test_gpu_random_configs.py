@@ -1,8 +1,8 @@
 """Seeded random configurations across the supported space (dimension,
 order, uneven meshes, both equations, LF / Roe fluxes, viscosity, the three
 schemes, orthogonalisation window, CTA tile): one step of the FP64 form with
-the oracle's decisions replayed (1e-11) and one adaptive step of the mixed
-form against the oracle (1e-6, the mixed form's bar)."""
+the oracle's decisions replayed (1e-11) and one adaptive step of each of the
+mixed and float-float forms against the oracle (1e-6, those forms' bar)."""
 import math
 
 import numpy as np
@@ -10,7 +10,7 @@ import pytest
 
 from oracle import dg, integrators
 from paper_2011_01316_gb300 import inputs
-from tests.test_gpu_parity import TOL_MIXED, TOL_STEP64, _replay_from, rel
+from tests.test_gpu_parity import MIXED_PRECS, TOL_MIXED, TOL_STEP64, _replay_from, rel
 
 pytestmark = pytest.mark.gpu
 
@@ -72,7 +72,9 @@ def test_random_config_step(E, seed):
     ctx.step(got, dt, replay=_replay_from(st))
     assert rel(got, ref) <= TOL_STEP64, cfg
     ctx.close()
-    ctxm, _ = make(E, cfg, 1)
-    gotm = q.copy()
-    ctxm.step(gotm, dt)
-    assert rel(gotm, ref) <= TOL_MIXED, cfg
+    for prec in MIXED_PRECS:
+        ctxm, _ = make(E, cfg, prec)
+        gotm = q.copy()
+        ctxm.step(gotm, dt)
+        ctxm.close()
+        assert rel(gotm, ref) <= TOL_MIXED, (prec, rel(gotm, ref), cfg)

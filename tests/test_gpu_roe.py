@@ -1,13 +1,14 @@
 """The Roe flux (Sec. 3.2) on the CUDA path against the oracle.
 
 FP64 form: operators 1e-12, steps with the oracle's decisions replayed 1e-11;
-mixed-form operators within the forward-error bounds of tests/test_gpu_parity.py;
-mixed steps 1e-6."""
+FP32 and float-float operators within the forward-error bounds of
+tests/test_gpu_parity.py (the mixed form's residual is the FP64 one: 1e-12);
+mixed and float-float steps 1e-6."""
 import numpy as np
 import pytest
 
 from oracle import dg, integrators
-from tests.test_gpu_parity import (C_JV32, C_RFX, CASES, TOL_MIXED, TOL_OP64, TOL_STEP64, _replay_from,
+from tests.test_gpu_parity import (C_JV32, C_RFX, CASES, MIXED_PRECS, PRECS, TOL_MIXED, TOL_OP64, TOL_STEP64, _replay_from,
                                    flux_scale, rel, state)
 
 pytestmark = pytest.mark.gpu
@@ -34,7 +35,7 @@ def make(E, case, prec=0, scheme=2, iop=0, tol=1e-10):
     return ctx, mesh
 
 
-@pytest.mark.parametrize("prec", [0, 1])
+@pytest.mark.parametrize("prec", PRECS)
 @pytest.mark.parametrize("case", EULER_CASES)
 def test_roe_residual_and_jv_parity(E, case, prec):
     rng = np.random.default_rng(95)
@@ -44,12 +45,14 @@ def test_roe_residual_and_jv_parity(E, case, prec):
         R, Rref = ctx.residual(q), dg.residual(mesh, q)
         v = np.ascontiguousarray(rng.standard_normal(q.shape))
         Lv, Lref = ctx.jv(q, v), dg.jv(mesh, q, v)
-        if prec == 0:
+        amp = (mesh.p + 1) ** 2
+        if prec == 2:
+            assert np.linalg.norm(R - Rref) <= C_RFX * amp * flux_scale(mesh, q)
+        else:
             assert rel(R, Rref) <= TOL_OP64
+        if prec == 0:
             assert rel(Lv, Lref) <= TOL_OP64
         else:
-            amp = (mesh.p + 1) ** 2
-            assert np.linalg.norm(R - Rref) <= C_RFX * amp * flux_scale(mesh, q)
             assert np.linalg.norm(Lv - Lref) <= C_JV32 * amp * flux_scale(mesh, q, v)
 
 
@@ -67,11 +70,12 @@ def test_roe_step_fp64_replayed(E, case, scheme, iop):
     np.testing.assert_allclose(dg.totals(mesh, got), dg.totals(mesh, q), rtol=1e-13, atol=1e-13)
 
 
+@pytest.mark.parametrize("prec", MIXED_PRECS)
 @pytest.mark.parametrize("scheme", [2, 3])
 @pytest.mark.parametrize("case", ["euler2d_p4", "euler3d_p3"])
-def test_roe_step_mixed(E, case, scheme):
+def test_roe_step_mixed(E, case, scheme, prec):
     rng = np.random.default_rng(97)
-    ctx, mesh = make(E, case, prec=1, scheme=scheme, iop=4)
+    ctx, mesh = make(E, case, prec=prec, scheme=scheme, iop=4)
     q = np.ascontiguousarray(state(mesh, rng))
     ref, _ = integrators.step(mesh, q, 0.05, scheme=scheme, tol=1e-10)
     got = q.copy()

@@ -37,7 +37,7 @@ def _requests(expdg, inputs, serve, n, seed, prec):
     return reqs
 
 
-@pytest.mark.parametrize("prec", [0, 1])
+@pytest.mark.parametrize("prec", [0, 1, 2])
 def test_same_result_alone_and_in_the_mix(mods, prec):
     expdg, inputs, serve = mods
     reqs = _requests(expdg, inputs, serve, 12, 3 + prec, prec)
@@ -108,17 +108,18 @@ def test_server_matches_context_advance(mods):
     np.testing.assert_array_equal(res[0][0], q)
 
 
-def test_served_sample_against_oracle(mods):
+@pytest.mark.parametrize("prec", [1, 2])
+def test_served_sample_against_oracle(mods, prec):
     """The serving workload's CPU-oracle check: a seeded 5 % sample (3 of the
     48 requests of the bench's stream, seed 1: sides 112, 23 and 57 at p = 4,
-    3, 3) served in the mixed form through the server, against the oracle's
-    FP64 solve of the same request (tol 1e-10, full Arnoldi).  Two of each
-    request's 50 EPI2 steps (the oracle's time)."""
+    3, 3) served in the mixed (or float-float) form through the server,
+    against the oracle's FP64 solve of the same request (tol 1e-10, full
+    Arnoldi).  Two of each request's 50 EPI2 steps (the oracle's time)."""
     from oracle import dg, integrators
     from tests.test_gpu_parity import TOL_MIXED, rel
     expdg, inputs, serve = mods
     rng = np.random.default_rng(1)
-    reqs = [serve.vortex_request(rng, 1, iop=4) for _ in range(48)]
+    reqs = [serve.vortex_request(rng, prec, iop=4) for _ in range(48)]
     pick = np.random.default_rng(7).choice(48, size=3, replace=False)
     sub = [(reqs[i][0], reqs[i][1], reqs[i][2], 2) for i in pick]
     srv = serve.Server(workers=3)

@@ -2,7 +2,7 @@
 ends, manufactured forcing) on the CUDA path against the oracle.
 
 FP64 form: operators 1e-12, steps with the oracle's decisions replayed 1e-11.
-Mixed form: 1e-6 per step (its bar).  The manufactured-solution run of
+Mixed and float-float forms: 1e-6 per step (their bar).  The manufactured-solution run of
 Sec. 5.1 (EXPRB32, dt = 5e-5 to t = 0.01) reproduces the oracle's error."""
 import math
 
@@ -10,7 +10,7 @@ import numpy as np
 import pytest
 
 from oracle import dg, integrators
-from tests.test_gpu_parity import TOL_MIXED, TOL_OP64, TOL_STEP64, _replay_from, rel
+from tests.test_gpu_parity import MIXED_PRECS, TOL_MIXED, TOL_OP64, TOL_STEP64, _replay_from, rel
 from tests.test_oracle_viscous import manufactured
 
 pytestmark = pytest.mark.gpu
@@ -56,10 +56,13 @@ def test_viscous_residual_and_jv_fp64(E, case):
     assert rel(ctx.jv(q, v), dg.jv(mesh, q, v)) <= TOL_OP64
 
 
+@pytest.mark.parametrize("prec", MIXED_PRECS)
 @pytest.mark.parametrize("case", list(CASES))
-def test_viscous_residual_mixed(E, case):
-    """Float-float residual (relative to the size of the terms it sums)."""
-    ctx, mesh, q = make(E, case, prec=1)
+def test_viscous_residual_mixed(E, case, prec):
+    """The mixed form's residual (the FP64 kernel) and the float-float one,
+    relative to the size of the terms they sum: 1e-13 (a few hundred units of
+    2^-48)."""
+    ctx, mesh, q = make(E, case, prec=prec)
     ref = dg.residual(mesh, q)
     scale = np.max(np.abs(ref)) + mesh.kappa * (2.0 / mesh.h[0]) ** 2 * (mesh.p + 1) ** 4 * np.max(np.abs(q))
     assert np.max(np.abs(ctx.residual(q) - ref)) <= 1e-13 * scale
@@ -77,10 +80,11 @@ def test_viscous_step_fp64_replayed(E, case, scheme, iop):
     assert rel(got, ref) <= TOL_STEP64
 
 
+@pytest.mark.parametrize("prec", MIXED_PRECS)
 @pytest.mark.parametrize("scheme", [2, 3])
 @pytest.mark.parametrize("case", ["dirichlet_p2", "periodic_p3"])
-def test_viscous_step_mixed(E, case, scheme):
-    ctx, mesh, q = make(E, case, prec=1, scheme=scheme, iop=4)
+def test_viscous_step_mixed(E, case, scheme, prec):
+    ctx, mesh, q = make(E, case, prec=prec, scheme=scheme, iop=4)
     dt = 2e-3
     ref, _ = integrators.step(mesh, q, dt, scheme=scheme, tol=1e-10)
     got = q.copy()

@@ -6,7 +6,10 @@ implicit synchronisation is not acceptable on their path).  Its scratch is a
 fixed static device array shared by all calls, so each check makes two calls
 in a row and compares both with the context-based expdg_residual, at the
 tolerance the operator parity tests use for the FP64 form (relative 1e-12;
-both paths run the same kernels, so the results should agree exactly).
+both paths run the same kernels, so the results should agree exactly), and
+with the CPU oracle's residual at the operator parity tests' bars (the FP64
+residual of the FP64 and mixed forms 1e-12; the float-float one within its
+forward-error bound).
 
 This file is named to be collected last: it must pass alone in a fresh
 process and after every other test.
@@ -16,6 +19,9 @@ import math
 
 import numpy as np
 import pytest
+
+from oracle import dg
+from tests.test_gpu_parity import C_RFX, TOL_OP64, flux_scale
 
 pytestmark = pytest.mark.gpu
 
@@ -47,15 +53,24 @@ CASES = [
 ]
 
 
-@pytest.mark.parametrize("prec", [0, 1])
+def _mesh(cfg):
+    d = cfg.dim
+    return dg.Mesh(dim=d, p=cfg.p, ne=tuple(cfg.ne[:d]), lo=tuple(cfg.lo[:d]), hi=tuple(cfg.hi[:d]),
+                   eq="burgers" if cfg.eq == 1 else "euler")
+
+
+@pytest.mark.parametrize("prec", [0, 1, 2])
 @pytest.mark.parametrize("kind,kw", CASES)
 def test_noalloc_residual_matches_context_residual(env, kind, kw, prec):
     torch, expdg, inputs = env
     cfg = expdg.default_config(**kw, prec=prec)
     ctx = expdg.Context(cfg)
-    q = torch.from_numpy(np.ascontiguousarray(_state(expdg, inputs, ctx, kind))).cuda()
+    qh = np.ascontiguousarray(_state(expdg, inputs, ctx, kind))
+    q = torch.from_numpy(qh).cuda()
     ref = torch.empty_like(q)
     ctx.residual(q, ref)
+    mesh = _mesh(cfg)
+    oracle = dg.residual(mesh, qh)
     for _ in range(2):
         out = torch.full_like(q, float("nan"))
         st = expdg.lib.expdg_residual_noalloc(ctypes.byref(cfg), ctypes.c_void_p(q.data_ptr()),
@@ -63,12 +78,17 @@ def test_noalloc_residual_matches_context_residual(env, kind, kw, prec):
         assert st == expdg.EXPDG_OK
         err = float(torch.linalg.vector_norm(out - ref) / torch.linalg.vector_norm(ref))
         assert err <= TOL, err
+        got = out.cpu().numpy()
+        if prec == 2:
+            assert np.linalg.norm(got - oracle) <= C_RFX * (mesh.p + 1) ** 2 * flux_scale(mesh, qh)
+        else:
+            assert np.linalg.norm(got - oracle) <= TOL_OP64 * np.linalg.norm(oracle)
     ctx.close()
 
 
 def test_noalloc_rejects_oversize_and_host_pointers(env):
     torch, expdg, inputs = env
-    big = expdg.default_config(dim=3, p=3, ne=[32, 32, 32], lo=[0, 0, 0], hi=[1, 1, 1], eq=2, prec=1)
+    big = expdg.default_config(dim=3, p=3, ne=[32, 32, 32], lo=[0, 0, 0], hi=[1, 1, 1], eq=2, prec=2)
     small = torch.zeros(8, dtype=torch.float64, device="cuda")
     st = expdg.lib.expdg_residual_noalloc(ctypes.byref(big), ctypes.c_void_p(small.data_ptr()),
                                           ctypes.c_void_p(small.data_ptr()), None)
