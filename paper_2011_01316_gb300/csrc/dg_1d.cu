@@ -1,5 +1,5 @@
 // DG operator kernels instantiated for dimension 1.
-#include "dg_impl.cuh"
+#include "jv32.cuh"
 
 namespace expdg {
 

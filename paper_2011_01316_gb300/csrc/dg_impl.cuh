@@ -738,16 +738,4 @@ cudaError_t launch_dg_fx_dim(int p, const DGArgs& a, const Tab& t, cudaStream_t 
   return launch_dg_p<DIM, EQ, fx, false, ROE>(p, a, t, s);
 }
 
-// form: DG_F64, or (linear operator only) DG_F32_FF or DG_F32_MX.
-// ROE: the Roe-flux instantiations (Euler), built in their own translation units.
-template <int DIM, int EQ, bool ROE = false>
-cudaError_t launch_dg_dim(bool linear, int form, int p, const DGArgs& a, const Tab& t, cudaStream_t s) {
-  if (form == DG_F32_MX)
-    return linear ? launch_dg_p<DIM, EQ, float, true, ROE, true>(p, a, t, s) : cudaErrorInvalidValue;
-  if (form == DG_F32_FF)
-    return linear ? launch_dg_p<DIM, EQ, float, true, ROE>(p, a, t, s) : cudaErrorInvalidValue;
-  return linear ? launch_dg_p<DIM, EQ, double, true, ROE>(p, a, t, s)
-                : launch_dg_p<DIM, EQ, double, false, ROE>(p, a, t, s);
-}
-
 }  // namespace expdg

@@ -1,5 +1,5 @@
 // DG operator kernels with the Roe flux (Euler), instantiated for dimension 2.
-#include "dg_impl.cuh"
+#include "jv32.cuh"
 
 namespace expdg {
 

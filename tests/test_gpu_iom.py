@@ -228,4 +228,7 @@ def test_mixed_large_krylov_dimension(E, dt, prec):
     got = q.copy()
     gst, gtr = ctx.step(got, dt)
     assert rel(got, ref) <= TOL_MIXED
-    assert max(m for (_, m, _, _) in gtr) > 49
+    if dt == 0.2:
+        assert max(m for (_, m, _, _) in gtr) > 49
+    else:
+        assert gst["rejected"] >= 1 and len(gtr) >= 2
