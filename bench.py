@@ -50,10 +50,16 @@ METRIC = "DOF-steps/s"
 UNIT = "DOF-steps/s"
 WORKLOAD = ("3D Euler density wave rho=1+0.2sin(x+y+z), u=(1,1,1), p=1, periodic [0,2pi]^3, 32^3 hexes, p=3 LGL, "
             "10,485,760 unknowns, LF flux, EPI2, dt=0.1, Krylov tol 1e-8")
+# incomplete orthogonalisation over the last 2 basis vectors: on this workload
+# the mixed form's FP64 orthogonalisation passes are FP64-pipe bound, and a
+# shorter window (37 Krylov steps instead of 31) is faster overall
 CFG = dict(dim=3, p=3, ne=[32, 32, 32], lo=[0.0] * 3, hi=[2 * math.pi] * 3, eq=2, gamma=1.4, scheme=2,
-           krylov_tol=1e-8, m_max=64, m_step=5, max_substeps=32, iop=4)
+           krylov_tol=1e-8, m_max=64, m_step=5, max_substeps=32, iop=2)
 DT = 0.1
-# The 2D workload of the paper's vortex experiments (second configuration).
+# The 2D workload of the paper's vortex experiments (second configuration);
+# its vectors stay in L2 and its Arnoldi steps are launch-latency bound, so
+# the longer window's smaller Krylov dimension wins there (also for the served
+# and batched solves).
 VORTEX = dict(dim=2, p=4, ne=[64, 64, 1], lo=[0.0, 0.0, 0.0], hi=[10.0, 10.0, 1.0], eq=2, gamma=1.4, scheme=2,
               krylov_tol=1e-8, m_max=64, m_step=5, max_substeps=32, iop=4)
 VORTEX_DT = 0.05
@@ -263,6 +269,39 @@ def oracle_other_rates():
     return out
 
 
+def _oracle_solve(job):
+    """One bounded oracle solve in a worker process: (unknowns x steps, seconds)."""
+    dim, p, ne, hi, eq, q0, dt, steps, iop = job
+    from oracle import dg, integrators
+    mesh = dg.Mesh(dim=dim, p=p, ne=tuple(ne), lo=(0.0,) * dim, hi=tuple(hi), eq=eq)
+    q = np.asarray(q0, np.float64).reshape(-1)
+    t0 = time.perf_counter()
+    for _ in range(steps):
+        q, _ = integrators.step(mesh, q, dt, tol=1e-8, iop=iop)
+    return mesh.n_unknowns * steps, time.perf_counter() - t0
+
+
+def oracle_concurrent(jobs, nproc=None):
+    """The oracle on every host core at once: one worker process per core
+    (spawned: the parent holds a CUDA context), each taking whole solves from
+    `jobs`.  Returns the aggregate DOF-steps/s over the wall time of the pool
+    and the worker count."""
+    import multiprocessing as mp
+    nproc = nproc or os.cpu_count() or 1
+    with mp.get_context("spawn").Pool(nproc) as pool:
+        pool.map(_oracle_solve, [(1, 1, [4], [1.0], "burgers", np.ones(8), 0.01, 1, 4)] * nproc)  # start-up
+        t0 = time.perf_counter()
+        out = pool.map(_oracle_solve, jobs, chunksize=1)
+        wall = time.perf_counter() - t0
+    return sum(u for u, _ in out) / wall, nproc, wall
+
+
+def _job_of(cfg, q0, dt, steps):
+    d = cfg.dim
+    return (d, cfg.p, [cfg.ne[k] for k in range(d)], [cfg.hi[k] for k in range(d)],
+            "burgers" if cfg.eq == 1 else "euler", q0, dt, steps, cfg.iop or None)
+
+
 # -------------------------------------------------------------- GPU legs ---
 
 def step_timer(stream, flush):
@@ -314,13 +353,13 @@ def kernel_rates(kern, hbm, prec=1, n_aug=None):
     return rates
 
 
-def wave3d_form(prec, stream, flush, hbm, steps=3, ne=32, iop=4, ref=None):
+def wave3d_form(prec, stream, flush, hbm, steps=3, ne=32, iop=4, ref=None, p=3, tile=0):
     """The workload in one precision form: ms per step (K steps from the same
     state after one warm step), Krylov dimension, per-kernel rates (a second,
     profiled step) and the error of one step against `ref` (a device array)."""
     from paper_2011_01316_gb300 import expdg, inputs
-    cfg = {**CFG, "ne": [ne] * 3, "iop": iop}
-    ctx = expdg.Context(**cfg, prec=prec)
+    cfg = {**CFG, "ne": [ne] * 3, "iop": iop, "p": p}
+    ctx = expdg.Context(**cfg, prec=prec, tile=tile)
     ctx.set_stream(stream)
     import torch
     q0 = torch.from_numpy(np.ascontiguousarray(inputs.density_wave(ctx.node_coords(), 0.0))).cuda()
@@ -339,7 +378,7 @@ def wave3d_form(prec, stream, flush, hbm, steps=3, ne=32, iop=4, ref=None):
     ctx.close()
     ms = float(np.mean(per))
     return {"ms_per_step": ms, "dof_steps_per_s": n / (ms * 1e-3), "krylov_iters_per_step": statistics.mean(iters),
-            "jv_tile": {1: "256", 2: "128", 3: "512"}.get(tile, "?") + " threads per CTA",
+            "jv_tile": {1: "256", 2: "128", 3: "512", 4: "tensor cores 3xTF32", 5: "tensor cores TF32"}.get(tile, "?"),
             "kernels": kernel_rates(kern, hbm, prec, n + 1), "err_vs_fp64_form": err}
 
 
@@ -443,7 +482,7 @@ def exprb32_workload(stream, flush, steps=5):
             "err_vs_fp64_form": err}
 
 
-def serving_workload(n, seed=1, rate=200.0, workers=8):
+def serving_workload(n, seed=1, rate=200.0, workers=8, cpu=False):
     """Poisson stream (mean `rate`/s) of n 2D Euler vortex solves (side 8..128,
     p 2..5, strength U[1,5], centre U(domain), 50 EPI2 steps at Courant 5, tol
     1e-8).  Served: the mixed form, `workers` solves in flight.  Plain: the
@@ -456,9 +495,9 @@ def serving_workload(n, seed=1, rate=200.0, workers=8):
     reqs = {"mixed": [], "fp64": [], "fp64_full": []}
     for _ in range(n):
         state = rng.bit_generator.state
-        reqs["mixed"].append(serve.vortex_request(rng, 1, iop=CFG["iop"]))
+        reqs["mixed"].append(serve.vortex_request(rng, 1, iop=VORTEX["iop"]))
         rng.bit_generator.state = state
-        reqs["fp64"].append(serve.vortex_request(rng, 0, iop=CFG["iop"]))
+        reqs["fp64"].append(serve.vortex_request(rng, 0, iop=VORTEX["iop"]))
         rng.bit_generator.state = state
         reqs["fp64_full"].append(serve.vortex_request(rng, 0))
     # warm the kernels of every order once (outside the measured streams)
@@ -493,6 +532,18 @@ def serving_workload(n, seed=1, rate=200.0, workers=8):
         out["plain_fp64_full_orthogonalisation"] = dict(serve.latency_summary(res["fp64_full"], wall["fp64_full"]),
                                                         workers=1)
     out["speedup_solves_per_s"] = out["served_mixed"]["solves_per_s"] / out["plain_fp64_same_window"]["solves_per_s"]
+    if cpu:
+        # the oracle on every host core: a seeded sample of 32 of the stream's
+        # requests (every request when fewer), 2 of each request's 50 steps
+        pick = np.random.default_rng(seed + 7).choice(n, size=min(n, 32), replace=False)
+        jobs = [_job_of(reqs["fp64"][i][0], reqs["fp64"][i][1], reqs["fp64"][i][2], 2) for i in pick]
+        rate, nproc, wall = oracle_concurrent(jobs)
+        per_solve = float(np.mean([reqs["fp64"][i][1].size * 50 for i in range(n)]))
+        out["cpu_oracle_all_cores"] = {"dof_steps_per_s": rate, "solves_per_s_equiv": rate / per_solve,
+                                       "processes": nproc, "wall_s": wall,
+                                       "sample": f"{len(jobs)} seeded requests x 2 of their 50 EPI2 steps, FP64 "
+                                                 "oracle (window 4, tol 1e-8), one process per core at once; "
+                                                 "solves/s = DOF-steps/s / mean DOF-steps of a 50-step request"}
     return out
 
 
@@ -505,7 +556,7 @@ def batched_requests(n, seed, steps, prec):
         if i % 2 == 0:
             ne = int(round(math.exp(rng.uniform(math.log(16), math.log(4096)))))
             cfg = expdg.default_config(dim=1, p=p, ne=[ne, 1, 1], lo=[0, 0, 0], hi=[2 * math.pi, 1, 1],
-                                       eq=expdg.EXPDG_BURGERS, prec=prec, krylov_tol=1e-8, iop=CFG["iop"])
+                                       eq=expdg.EXPDG_BURGERS, prec=prec, krylov_tol=1e-8, iop=VORTEX["iop"])
             X = expdg.config_node_coords(cfg)
             u0, (amp, _) = inputs.fourier_modes(X[0], rng)
             u0 = u0[None]
@@ -518,7 +569,7 @@ def batched_requests(n, seed, steps, prec):
         else:
             side = int(rng.integers(8, 97))
             cfg = expdg.default_config(dim=2, p=p, ne=[side, side, 1], lo=[0, 0, 0], hi=[2 * math.pi] * 2 + [1],
-                                       eq=expdg.EXPDG_EULER, prec=prec, krylov_tol=1e-8, iop=CFG["iop"])
+                                       eq=expdg.EXPDG_EULER, prec=prec, krylov_tol=1e-8, iop=VORTEX["iop"])
             X = expdg.config_node_coords(cfg)
             rho, (amp, _) = inputs.fourier_modes(X[0] + X[1], rng)
             if amp.sum() > 0.8:  # keep rho >= 0.2: 1 - sum a_k must stay positive
@@ -528,7 +579,7 @@ def batched_requests(n, seed, steps, prec):
     return reqs
 
 
-def batched_workload(n, seed=0, workers=16, steps=20):
+def batched_workload(n, seed=0, workers=16, steps=20, cpu=False):
     """n independent periodic instances (half 1D Burgers with Ne log-uniform in
     [16, 4096], half 2D Euler density waves with side in {8..96}; p uniform in
     {1..5}; initial data 1 + 4 seeded Fourier modes, a_k ~ U[0, 0.3]; dt from
@@ -550,13 +601,69 @@ def batched_workload(n, seed=0, workers=16, steps=20):
     res64, _ = serve.run_stream(srv, batched_requests(n, seed, steps, 0), 0.0, rng, check=False)
     srv.close()
     errs = [rel(a[0], b[0]) for a, b in zip(resn, res64) if a[3] == 0 and b[3] == 0]
+    cpu_all = None
+    if cpu:
+        # the oracle on every host core: a seeded sample of 32 instances (half
+        # 1D Burgers, half 2D Euler, as the workload), 2 of each one's steps
+        r64 = batched_requests(n, seed, steps, 0)
+        pick = np.random.default_rng(seed + 7).choice(n, size=min(n, 32), replace=False)
+        jobs = [_job_of(r64[i][0], r64[i][1], r64[i][2], 2) for i in pick]
+        rate, nproc, wall = oracle_concurrent(jobs)
+        cpu_all = {"dof_steps_per_s": rate, "processes": nproc, "wall_s": wall,
+                   "sample": f"{len(jobs)} seeded instances x 2 of their {steps} EPI2 steps, FP64 "
+                             "oracle (window 4, tol 1e-8), one process per core at once"}
     return {"workload": f"{n} instances (1D Burgers / 2D Euler, p 1..5, uneven sizes), {steps} EPI2 steps each",
+            "cpu_oracle_all_cores": cpu_all,
             "concurrent": {"workers": workers, "wall_s": walln, "dof_steps_per_s": dofs / walln},
             "sequential": {"wall_s": wall1, "dof_steps_per_s": dofs / wall1},
             "speedup": wall1 / walln, "identical_results": same,
             "failed": sum(1 for a in resn if a[3] != 0),
             "max_rel_err_vs_fp64": max(errs) if errs else None,
             "err_kind": "each instance's mixed result against the FP64 form of the same instance"}
+
+
+def k7_workload(stream, flush, hbm, orders=(4, 5, 6, 7, 8), unknowns=5.0e6):
+    """The tensor-core trial: the 3D density wave at each order p (about
+    `unknowns` unknowns: (unknowns / (5 (p+1)^3))^(1/3) elements per
+    direction, dt at the 32^3 p = 3 workload's Courant number), one mixed-form
+    EPI2 step (window 2) with the operator's derivative on the FP32 FMA pipes
+    (256-thread tile) and on the tensor cores (3xTF32, TF32): microseconds per
+    operator apply, Krylov steps and the error against the FP64 form (full
+    orthogonalisation, tol 1e-10) after one step from the same state."""
+    import torch
+    from paper_2011_01316_gb300 import expdg, inputs
+    out = []
+    for p in orders:
+        ne = max(2, int(round((unknowns / (5 * (p + 1) ** 3)) ** (1.0 / 3.0))))
+        dt = 0.1 * (32 / ne) * 16.0 / (p + 1) ** 2  # the same dt (p+1)^2 / h as 32^3 p = 3
+        cfg = {**CFG, "ne": [ne] * 3, "p": p}
+        ref = expdg.Context(**{**cfg, "iop": 0, "krylov_tol": 1e-10}, prec=expdg.EXPDG_FP64)
+        ref.set_stream(stream)
+        q0 = torch.from_numpy(np.ascontiguousarray(inputs.density_wave(ref.node_coords(), 0.0))).cuda()
+        qr = q0.clone()
+        ref.step(qr, dt)
+        ref.close()
+        row = {"p": p, "ne": ne, "unknowns": int(q0.numel()), "dt": dt}
+        for name, tile in (("fma", expdg.EXPDG_TILE_256), ("tc_3xtf32", expdg.EXPDG_TILE_TC3),
+                           ("tc_tf32", expdg.EXPDG_TILE_TC1)):
+            ctx = expdg.Context(**cfg, prec=expdg.EXPDG_MIXED, tile=tile)
+            ctx.set_stream(stream)
+            q = q0.clone()
+            ctx.step(q, dt)
+            err = rel(q, qr)
+            q = q0.clone()
+            ctx.profile_enable(True)
+            st, _ = ctx.step(q, dt)
+            kern = ctx.profile_get(reset=True)
+            ctx.profile_enable(False)
+            ctx.close()
+            jv = kern["jv"]
+            row[name] = {"us_per_jv": 1e3 * jv["ms"] / max(1, jv["launches"]), "krylov_iters": st["krylov_iters"],
+                         "err_vs_fp64_form": err, "jv_frac_of_measured_hbm":
+                             (jv["bytes"] / max(1, jv["launches"])) / (jv["ms"] / max(1, jv["launches"]) * 1e-3) / 1e9 / hbm}
+        out.append(row)
+    return {"workload": "3D Euler density wave at p = 4..8, about 5 M unknowns each, mixed form, window 2",
+            "orders": out}
 
 
 def run_reference(args, rank, world):
@@ -598,6 +705,8 @@ def main():
     ap.add_argument("--wave3d-ne", type=int, default=32, help="elements per direction of the wave3d legs")
     ap.add_argument("--wave3d-steps", type=int, default=3)
     ap.add_argument("--wave3d-prec", type=int, default=1, help="precision form of a wave3d-only run (1 or 2)")
+    ap.add_argument("--wave3d-p", type=int, default=3, help="polynomial order of a wave3d-only run")
+    ap.add_argument("--tile", type=int, default=0, help="operator tile class of a wave3d-only run (0: autotuned)")
     ap.add_argument("--iop", type=int, default=CFG["iop"],
                     help="Krylov orthogonalisation window (0: full Arnoldi; k: incomplete, last k vectors)")
     args = ap.parse_args()
@@ -630,17 +739,21 @@ def main():
         out = {}
         if "wave3d" in legs:
             out["wave3d"] = wave3d_form(args.wave3d_prec, stream, flush, hbm, steps=args.wave3d_steps,
-                                        ne=args.wave3d_ne, iop=args.iop)
+                                        ne=args.wave3d_ne, iop=args.iop, p=args.wave3d_p, tile=args.tile)
         if "vortex" in legs:
             out["vortex"] = vortex_workload(stream, flush)
         if "serving" in legs:
-            out["serving"] = serving_workload(args.serve_requests, workers=args.serve_workers)
+            out["serving"] = serving_workload(args.serve_requests, workers=args.serve_workers,
+                                              cpu=not args.no_cpu_baseline)
         if "batched" in legs:
-            out["batched"] = batched_workload(args.batch_instances, workers=args.batch_workers)
+            out["batched"] = batched_workload(args.batch_instances, workers=args.batch_workers,
+                                              cpu=not args.no_cpu_baseline)
         if "burgers" in legs:
             out["burgers"] = burgers_workload(iop=args.burgers_iop)
         if "exprb32" in legs:
             out["exprb32"] = exprb32_workload(stream, flush)
+        if "k7" in legs:
+            out["k7"] = k7_workload(stream, flush, hbm)
         if rank == 0:
             print(json.dumps({"legs": args.legs, **out}), flush=True)
         return
@@ -744,10 +857,11 @@ def main():
         extra["burgers"] = burgers_workload(iop=args.burgers_iop)
     if "exprb32" in legs:
         extra["exprb32"] = exprb32_workload(stream, flush)
+    cpu_legs = rank == 0 and world == 1 and not args.no_cpu_baseline
     if args.serve_requests > 0 and "serving" in legs:
-        extra["serving"] = serving_workload(args.serve_requests, workers=args.serve_workers)
+        extra["serving"] = serving_workload(args.serve_requests, workers=args.serve_workers, cpu=cpu_legs)
     if args.batch_instances > 0 and "batched" in legs:
-        extra["batched"] = batched_workload(args.batch_instances, workers=args.batch_workers)
+        extra["batched"] = batched_workload(args.batch_instances, workers=args.batch_workers, cpu=cpu_legs)
 
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:

@@ -118,7 +118,14 @@ typedef enum {
   EXPDG_TILE_AUTO = 0,
   EXPDG_TILE_256 = 1,  /* about 256 threads per CTA */
   EXPDG_TILE_128 = 2,
-  EXPDG_TILE_512 = 3
+  EXPDG_TILE_512 = 3,
+  /* Tensor-core trial (2D / 3D Euler, LF flux, EXPDG_MIXED; elsewhere these
+   * act as EXPDG_TILE_256): the operator's derivative contractions
+   * sum_j D_ij F_j as warp-level m16n8k8 TF32 matrix products (lines of 16
+   * along each direction against D^T), FP32 accumulation.  Never chosen by
+   * EXPDG_TILE_AUTO: measured slower than the FP32 FMA form at p = 4..8. */
+  EXPDG_TILE_TC3 = 4,  /* operands split hi + lo, three products: about FP32 accuracy */
+  EXPDG_TILE_TC1 = 5   /* one TF32 product (10-bit significands): far above the 1e-6 bar */
 } expdg_tile;
 
 #define EXPDG_MAX_ORDER 8

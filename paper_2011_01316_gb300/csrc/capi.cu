@@ -657,7 +657,7 @@ expdg_status validate(const expdg_config* c) {
   if ((c->kappa > 0.0 || c->bc != EXPDG_BC_PERIODIC) && c->eq != EXPDG_BURGERS) return EXPDG_EINVAL;
   if (c->flux != EXPDG_FLUX_LF && c->flux != EXPDG_FLUX_ROE) return EXPDG_EINVAL;
   if (c->flux == EXPDG_FLUX_ROE && c->eq != EXPDG_EULER) return EXPDG_EINVAL;
-  if (c->tile < EXPDG_TILE_AUTO || c->tile > EXPDG_TILE_512) return EXPDG_EINVAL;
+  if (c->tile < EXPDG_TILE_AUTO || c->tile > EXPDG_TILE_TC1) return EXPDG_EINVAL;
   return EXPDG_OK;
 }
 

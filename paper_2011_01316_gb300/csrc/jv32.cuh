@@ -75,14 +75,15 @@ __device__ __forceinline__ NodeV<DIM + 2> lin_flux(const NodeV<DIM + 2>& z, cons
   return out;
 }
 
-template <int DIM, int P, int TK>
+template <int DIM, int P, int TK, int TC = 0>
 struct Smem {
   static constexpr int NP1 = P + 1, NP = ipow(NP1, DIM), EPB = elems_per_block<DIM, P, TK>(), SLOT = EPB * NP;
   static constexpr bool F5 = DIM == 3;  // a fifth field
   __host__ __device__ static constexpr size_t bytes() {
     return sizeof(float4) * ((size_t)DIM * SLOT + 2 * SLOT) +  // fluxes, z, v (fields 0..3)
            (F5 ? sizeof(float) * (size_t)DIM * SLOT + sizeof(float2) * SLOT : 0) +  // field 4
-           sizeof(float) * NP1 * NP1 + sizeof(int) * EPB * 2 * DIM;
+           sizeof(float) * NP1 * NP1 + sizeof(int) * EPB * 2 * DIM +
+           (TC ? sizeof(float) * (size_t)DIM * (DIM + 2) * SLOT : 0);  // tensor-core derivatives
   }
   float4* F4;  // [DIM][SLOT]
   float4* Z4;  // [SLOT]
@@ -91,6 +92,7 @@ struct Smem {
   float2* ZV1; // [SLOT] (z_4, v_4) (3D)
   float* D;    // [NP1][NP1]
   int* Nb;     // [EPB][2 DIM]
+  float* Der;  // [DIM][M][SLOT] derivatives formed on the tensor cores (TC)
   __device__ explicit Smem(unsigned char* raw) {
     F4 = reinterpret_cast<float4*>(raw);
     Z4 = F4 + DIM * SLOT;
@@ -106,22 +108,128 @@ struct Smem {
     }
     D = reinterpret_cast<float*>(p);
     Nb = reinterpret_cast<int*>(D + NP1 * NP1);
+    Der = reinterpret_cast<float*>(Nb + EPB * 2 * DIM);
   }
 };
+
+// ---- the derivative contraction on the tensor cores (experiment K7) ----
+// TF32 bits of x, rounded to nearest (ties away).
+__device__ __forceinline__ uint32_t tf32_of(float x) {
+  uint32_t r;
+  asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(r) : "f"(x));
+  return r;
+}
+// c += a b for one m16n8k8 TF32 tile (warp-wide; FP32 accumulation).
+__device__ __forceinline__ void mma_tf32(float (&c)[4], const uint32_t (&a)[4], const uint32_t (&b)[2]) {
+  asm volatile("mma.sync.aligned.m16n8k8.row.col.f32.tf32.tf32.f32 {%0,%1,%2,%3}, {%4,%5,%6,%7}, {%8,%9}, "
+               "{%0,%1,%2,%3};"
+               : "+f"(c[0]), "+f"(c[1]), "+f"(c[2]), "+f"(c[3])
+               : "r"(a[0]), "r"(a[1]), "r"(a[2]), "r"(a[3]), "r"(b[0]), "r"(b[1]));
+}
+
+// All derivatives sum_j D(i, j) F_d(line node j) of the CTA's fluxes as
+// matrix products on the tensor cores, into Der: for each direction d and
+// field f, the lines along x_d are the rows of A (16 lines per tile, their
+// P+1 nodes the K dimension, padded to multiples of 8 with zeros) and
+// B = D^T (K x N, N = P+1 output nodes, padded likewise); warp-level
+// m16n8k8 TF32 MMAs with FP32 accumulation.  TC = 1: one TF32 product
+// (operands rounded to 10-bit significands); TC = 3: the split x = hi + lo
+// of both operands and three products (lo hi + hi lo + hi hi, about FP32
+// accuracy).  Every thread of the CTA calls it; it ends with a barrier.
+template <int DIM, int P, int TK, int TC>
+__device__ __forceinline__ void tc_derivative(const Smem<DIM, P, TK, TC>& sm, int tid) {
+  constexpr int M = DIM + 2, NP1 = P + 1, NP = ipow(NP1, DIM), EPB = elems_per_block<DIM, P, TK>(),
+                SLOT = EPB * NP;
+  constexpr int LPE = ipow(NP1, DIM - 1), L = EPB * LPE, NG = (L + 15) / 16, KS = (NP1 + 7) / 8;
+  const int lane = tid & 31, warp = tid >> 5, nwarp = blockDim.x >> 5;
+  const int g = lane >> 2, t4 = lane & 3;
+  uint32_t bh[KS][KS][2], bl[KS][KS][2];  // [k step][n tile][2]: B(k, n) = D(n, k)
+#pragma unroll
+  for (int ks = 0; ks < KS; ++ks)
+#pragma unroll
+    for (int nt = 0; nt < KS; ++nt)
+#pragma unroll
+      for (int h = 0; h < 2; ++h) {
+        const int k = t4 + 4 * h + 8 * ks, nn = g + 8 * nt;
+        const float x = (k < NP1 && nn < NP1) ? sm.D[nn * NP1 + k] : 0.0f;
+        bh[ks][nt][h] = tf32_of(x);
+        bl[ks][nt][h] = tf32_of(__fsub_rn(x, __uint_as_float(bh[ks][nt][h])));
+      }
+  for (int task = warp; task < DIM * M * NG; task += nwarp) {  // warp-uniform
+    const int d = task / (M * NG), f = (task / NG) % M, grp = task % NG;
+    const int sd = (d == 0) ? 1 : (d == 1 ? NP1 : NP1 * NP1);
+    // this thread's two rows (lines) g and g + 8 of the tile: their first slots
+    int st[2];
+    bool ok[2];
+#pragma unroll
+    for (int h = 0; h < 2; ++h) {
+      const int r = grp * 16 + g + 8 * h;
+      ok[h] = r < L;
+      const int le = ok[h] ? r / LPE : 0, l = ok[h] ? r - (r / LPE) * LPE : 0;
+      int o;
+      if (d == 0)
+        o = NP1 * l;
+      else if (d == 1)
+        o = (l % NP1) + NP1 * NP1 * (l / NP1);
+      else
+        o = l;
+      st[h] = le * NP + o;
+    }
+    const float* Fd = (f < 4) ? reinterpret_cast<const float*>(sm.F4 + d * SLOT) + f : sm.F1 + d * SLOT;
+    const int fs = (f < 4) ? 4 : 1;
+    float c[KS][4];
+#pragma unroll
+    for (int nt = 0; nt < KS; ++nt) c[nt][0] = c[nt][1] = c[nt][2] = c[nt][3] = 0.0f;
+#pragma unroll
+    for (int ks = 0; ks < KS; ++ks) {
+      float av[4];
+#pragma unroll
+      for (int q = 0; q < 4; ++q) {  // a0: (g, t4), a1: (g + 8, t4), a2: (g, t4 + 4), a3: (g + 8, t4 + 4)
+        const int h = q & 1, k = t4 + 4 * (q >> 1) + 8 * ks;
+        av[q] = (ok[h] && k < NP1) ? Fd[(st[h] + k * sd) * fs] : 0.0f;
+      }
+      uint32_t ah[4], al[4];
+#pragma unroll
+      for (int q = 0; q < 4; ++q) {
+        ah[q] = tf32_of(av[q]);
+        al[q] = tf32_of(__fsub_rn(av[q], __uint_as_float(ah[q])));
+      }
+#pragma unroll
+      for (int nt = 0; nt < KS; ++nt) {
+        if (TC == 3) {
+          mma_tf32(c[nt], al, bh[ks][nt]);
+          mma_tf32(c[nt], ah, bl[ks][nt]);
+        }
+        mma_tf32(c[nt], ah, bh[ks][nt]);
+      }
+    }
+    float* out = sm.Der + (d * M + f) * SLOT;
+#pragma unroll
+    for (int nt = 0; nt < KS; ++nt)
+#pragma unroll
+      for (int q = 0; q < 4; ++q) {  // c0: (g, 2 t4), c1: (g, 2 t4 + 1), c2: (g + 8, 2 t4), c3: (g + 8, 2 t4 + 1)
+        const int h = q >> 1, nn = 2 * t4 + (q & 1) + 8 * nt;
+        if (ok[h] && nn < NP1) out[st[h] + nn * sd] = c[nt][q];
+      }
+  }
+  __syncthreads();
+}
 
 }  // namespace jv32
 
 // MX = true: the mixed form's output (FP32 to a.out_h, or widened to FP64 in
 // a.out; FP64 augmentation tail); false: the float-float form's (float-float
 // output and tail).
-template <int DIM, int P, bool ROE, int TK, bool MX>
-// LF: at most 32 registers (a full SM of resident threads: the kernel is
-// latency bound); Roe keeps more state live
-__global__ void __launch_bounds__(dg_threads<DIM, P, TK>(), ROE ? 1 : 2048 / dg_threads<DIM, P, TK>()) k_jv32(const DGArgs a, const Tab tab) {
+// TC (experiment K7): 0 the derivative in FP32 on the FMA pipes; 1 or 3 on the
+// tensor cores (tc_derivative).  LF: at most 32 registers (a full SM of
+// resident threads: the kernel is latency bound); Roe keeps more state live.
+template <int DIM, int P, bool ROE, int TK, bool MX, int TC = 0>
+__global__ void __launch_bounds__(dg_threads<DIM, P, TK>(), (ROE || TC) ? 1 : 2048 / dg_threads<DIM, P, TK>())
+    k_jv32(const DGArgs a, const Tab tab) {
   using namespace jv32;
   constexpr int M = DIM + 2, NP1 = P + 1, NP = ipow(NP1, DIM), NF = 2 * DIM;
   constexpr int EPB = elems_per_block<DIM, P, TK>(), SLOT = EPB * NP;
-  using SM = Smem<DIM, P, TK>;
+  using SM = Smem<DIM, P, TK, TC>;
   using NV = NodeV<M>;
   extern __shared__ __align__(16) unsigned char smem_raw[];
   const SM sm(smem_raw);
@@ -192,6 +300,7 @@ __global__ void __launch_bounds__(dg_threads<DIM, P, TK>(), ROE ? 1 : 2048 / dg_
   }
   __syncthreads();
   griddep_launch();
+  if constexpr (TC != 0) tc_derivative<DIM, P, TK, TC>(sm, tid);
   if (!active) return;
 
   int ii[DIM];
@@ -214,14 +323,21 @@ __global__ void __launch_bounds__(dg_threads<DIM, P, TK>(), ROE ? 1 : 2048 / dg_
     // derivative along x_d: sum_j D(i_d, j) F_d(line node j), two fields per packed FMA
     float2 s01 = make_float2(0.f, 0.f), s23 = make_float2(0.f, 0.f);
     float s4 = 0.0f;
+    if constexpr (TC != 0) {
+      const float* Dd = sm.Der + d * M * SLOT + tid;
+      s01 = make_float2(Dd[0], Dd[SLOT]);
+      s23 = make_float2(Dd[2 * SLOT], Dd[3 * SLOT]);
+      if (DIM == 3) s4 = Dd[4 * SLOT];
+    } else {
 #pragma unroll
-    for (int j = 0; j < NP1; ++j) {
-      const float dj = sm.D[ii[d] * NP1 + j];
-      const float2 dd = make_float2(dj, dj);
-      const float4 F = sm.F4[d * SLOT + lbase + j * sd];
-      s01 = __ffma2_rn(dd, lo(F), s01);
-      s23 = __ffma2_rn(dd, hi(F), s23);
-      if (DIM == 3) s4 = __fmaf_rn(dj, sm.F1[d * SLOT + lbase + j * sd], s4);
+      for (int j = 0; j < NP1; ++j) {
+        const float dj = sm.D[ii[d] * NP1 + j];
+        const float2 dd = make_float2(dj, dj);
+        const float4 F = sm.F4[d * SLOT + lbase + j * sd];
+        s01 = __ffma2_rn(dd, lo(F), s01);
+        s23 = __ffma2_rn(dd, hi(F), s23);
+        if (DIM == 3) s4 = __fmaf_rn(dj, sm.F1[d * SLOT + lbase + j * sd], s4);
+      }
     }
     const float2 mc = make_float2(-c2h, -c2h);
     acc01 = __ffma2_rn(mc, s01, acc01);
@@ -343,13 +459,13 @@ __global__ void __launch_bounds__(dg_threads<DIM, P, TK>(), ROE ? 1 : 2048 / dg_
   }
 }
 
-template <int DIM, int P, bool ROE, int TK, bool MX>
+template <int DIM, int P, bool ROE, int TK, bool MX, int TC = 0>
 cudaError_t launch_jv32_t(const DGArgs& a, const Tab& t, cudaStream_t s) {
   constexpr int EPB = elems_per_block<DIM, P, TK>();
   const int threads = dg_threads<DIM, P, TK>();
-  const size_t smem = jv32::Smem<DIM, P, TK>::bytes();
+  const size_t smem = jv32::Smem<DIM, P, TK, TC>::bytes();
   const int blocks = (a.nelem + EPB - 1) / EPB;
-  auto kern = k_jv32<DIM, P, ROE, TK, MX>;
+  auto kern = k_jv32<DIM, P, ROE, TK, MX, TC>;
   static const cudaError_t configured =
       cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (configured != cudaSuccess) return configured;
@@ -357,10 +473,16 @@ cudaError_t launch_jv32_t(const DGArgs& a, const Tab& t, cudaStream_t s) {
   return pdl_launch(kern, dim3(blocks), dim3(threads), smem, s, a, t);
 }
 
+// tile classes 0..2: CTA sizes; 3 and 4 (the LF mixed form): the 256-thread
+// CTA with the derivative on the tensor cores, 3xTF32 and TF32 (experiment K7)
 template <int DIM, int P, bool ROE, bool MX>
 cudaError_t launch_jv32_tile(const DGArgs& a, const Tab& t, cudaStream_t s) {
   if (a.tile == 1) return launch_jv32_t<DIM, P, ROE, 1, MX>(a, t, s);
   if (a.tile == 2) return launch_jv32_t<DIM, P, ROE, 2, MX>(a, t, s);
+  if constexpr (MX && !ROE) {
+    if (a.tile == 3) return launch_jv32_t<DIM, P, ROE, 0, MX, 3>(a, t, s);
+    if (a.tile == 4) return launch_jv32_t<DIM, P, ROE, 0, MX, 1>(a, t, s);
+  }
   return launch_jv32_t<DIM, P, ROE, 0, MX>(a, t, s);
 }
 

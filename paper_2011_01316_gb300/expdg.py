@@ -21,7 +21,7 @@ EXPDG_EPI2, EXPDG_EXPRB32, EXPDG_EXPRB42 = 2, 3, 4
 EXPDG_FP64, EXPDG_MIXED, EXPDG_MIXED_FF = 0, 1, 2
 EXPDG_BC_PERIODIC, EXPDG_BC_DIRICHLET = 0, 1
 EXPDG_FLUX_LF, EXPDG_FLUX_ROE = 0, 1
-EXPDG_TILE_AUTO, EXPDG_TILE_256, EXPDG_TILE_128, EXPDG_TILE_512 = 0, 1, 2, 3
+EXPDG_TILE_AUTO, EXPDG_TILE_256, EXPDG_TILE_128, EXPDG_TILE_512, EXPDG_TILE_TC3, EXPDG_TILE_TC1 = 0, 1, 2, 3, 4, 5
 EXPDG_MAX_ORDER, EXPDG_MAX_KRYLOV, EXPDG_MAX_PHI, EXPDG_MAX_IOP = 8, 64, 3, 8
 STATUS_NAMES = {0: "EXPDG_OK", 1: "EXPDG_EINVAL", 2: "EXPDG_ENOMEM", 3: "EXPDG_EKRYLOV",
                 4: "EXPDG_ENONPHYSICAL", 5: "EXPDG_ETIMEOUT", 6: "EXPDG_ECUDA"}

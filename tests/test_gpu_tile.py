@@ -77,7 +77,7 @@ def test_autotuned_tile_is_valid_and_cached(E, prec):
 
 
 def test_invalid_tile_rejected(E):
-    for bad in (-1, 4):
+    for bad in (-1, 6):
         with pytest.raises(E.ExpdgError) as ei:
             E.Context(tile=bad)
         assert ei.value.status == E.EXPDG_EINVAL
