@@ -876,8 +876,9 @@ def main():
                 "scaling": "weak", "vs_baseline": None, "dtype": "f32+f64",
                 "data": "synthetic",
                 "config": {"workload": WORKLOAD,
-                           "precision": ("mixed: FP32 R and Jv (FP32 accumulation); FP64 Krylov basis, inner "
-                                         "products, orthogonalisation, phi(H) and update"),
+                           "precision": ("mixed: Jv in FP32 (FP32 accumulation); R in float-float (48-bit "
+                                         "significand) delivered in FP64; FP64 Krylov basis, inner products, "
+                                         "orthogonalisation, phi(H) and update"),
                            "krylov": (f"incomplete orthogonalisation, window {CFG['iop']} (KIOPS)" if CFG["iop"]
                                       else "full Arnoldi (DCGS2)"),
                            "l2": "inputs larger than L2 (84 MB state, 84 MB per Krylov vector); also flushed "

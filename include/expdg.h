@@ -68,10 +68,12 @@ typedef enum { EXPDG_FLUX_LF = 0, EXPDG_FLUX_ROE = 1 } expdg_flux;
  *                   beside each FP64 basis vector; conversions on the integer
  *                   pipes); the Krylov basis, the Arnoldi inner products and
  *                   orthogonalisation, phi(H) and the solution update in FP64.
- *                   The residual R is FP64 too: an FP32 residual's rounding
- *                   (relative 3e-6 on smooth data, where R is a small
- *                   difference of large fluxes) cost extra Arnoldi steps and
- *                   errors above 1e-6 after tens of steps.
+ *                   The residual R in float-float arithmetic (pairs of FP32
+ *                   numbers, 48-bit significand, below), delivered in FP64:
+ *                   an FP32 residual's rounding (relative 3e-6 on smooth
+ *                   data, where R is a small difference of large fluxes) cost
+ *                   extra Arnoldi steps and errors above 1e-6 after tens of
+ *                   steps; an FP64 one runs 3.7x slower on this GPU.
  *   EXPDG_MIXED_FF: a variant: Jv in FP32; the residual in float-float
  *                   arithmetic (pairs of FP32 numbers, 48-bit significand,
  *                   error-free transformations on the FP32 pipes); Krylov
@@ -339,13 +341,13 @@ expdg_status expdg_server_info(expdg_server* s, size_t* used_bytes, int* pending
  *     layout; host pointers and other devices' memory are rejected with
  *     EXPDG_EINVAL.  cuda_stream: the stream to run on (NULL = legacy default
  *     stream); the call returns after that stream has finished.
- *   - Scratch (the float-float state copy and output of EXPDG_MIXED_FF, and
- *     the non-physical-state flag of every form) is a fixed static device
- *     array of about 8 MiB that every GPU which loads the library keeps until
- *     the process exits.  EXPDG_MIXED_FF is limited to
+ *   - Scratch (the float-float state copy of EXPDG_MIXED and
+ *     EXPDG_MIXED_FF, the float-float output of EXPDG_MIXED_FF, and the
+ *     non-physical-state flag of every form) is a fixed static device array
+ *     of about 8 MiB that every GPU which loads the library keeps until the
+ *     process exits.  EXPDG_MIXED and EXPDG_MIXED_FF are limited to
  *     EXPDG_NOALLOC_MAX_UNKNOWNS unknowns (larger sizes return EXPDG_EINVAL);
- *     EXPDG_FP64 and EXPDG_MIXED work in place on q and r and have no size
- *     limit.
+ *     EXPDG_FP64 works in place on q and r and has no size limit.
  *   - The first call on a device looks up the array's device address (once
  *     per device, safe from several host threads).  Every call copies the
  *     status word to the host and synchronises the stream, so the call cannot

@@ -36,7 +36,7 @@ struct expdg_ctx {
   double* d_out = nullptr; // API output scratch
   // FP32 buffers (float-float and mixed forms)
   float* d_q32b = nullptr;  // FP32 operand of the operator apply (expdg_jv, the EXPRB stage correction)
-  float* d_qfx = nullptr;   // the state as interleaved float-float pairs (float-float form's residual)
+  float* d_qfx = nullptr;   // the state as interleaved float-float pairs (residual of the FP32-operator forms)
   // mixed form: FP32 copies of the augmentation vectors b_1..b_P, read by the FP32 operator apply
   float* d_bf[EXPDG_MAX_PHI + 1] = {};
   double* d_src = nullptr;  // forcing added to R (expdg_set_source), allocated on first use
@@ -238,22 +238,25 @@ void set_alpha(DGArgs& a, double alpha) {
   a.alpha_l = (float)(alpha - (double)a.alpha_h);
 }
 
-// R(q) -> out (Krylov storage form), times alpha.  FP64 and mixed forms: FP64
+// R(q) -> out (Krylov storage form), times alpha.  FP64 form: FP64
 // throughout.  R of a smooth state is a small difference of large fluxes: an
 // FP32 residual (measured in the mixed form: relative error 3e-6 on the 32^3
 // p = 3 wave) put broadband noise into the Krylov start vector that cost extra
 // Arnoldi steps (m = 37 against 27 at tol 1e-8) and errors above 1e-6 against
 // the FP64 form after the 20 - 50 steps of the batched and served solves.
-// Float-float form: the state is split once into float-float pairs and the
-// residual is computed in float-float arithmetic on the FP32 pipes (accurate
-// to about 1e-14 of the flux scale).
+// The FP32-operator forms (mixed and float-float): the state is split once
+// into float-float pairs and the residual is computed in float-float
+// arithmetic on the FP32 pipes (accurate to about 1e-14 of the flux scale;
+// 3.7x faster than the FP64 kernel on the 32^3 p = 3 wave, whose FP64 flux
+// and derivative arithmetic is bound by GB300's FP64 pipe); the mixed form
+// takes the result as h + l in FP64 (exact).
 // converted: ctx->d_qfx already holds q (written by linstate_into).
 cudaError_t residual_into(expdg_ctx* ctx, const double* q, Vec out, double alpha, bool converted = false) {
   DGArgs a = ctx->mesh;
   set_alpha(a, alpha);
   a.src = ctx->has_src ? ctx->d_src : nullptr;
   a.status = &ctx->ks->status;
-  if (!ctx->ff) {
+  if (!ctx->f32op) {
     a.q = q;
     a.out = out.d;
     return run(ctx, EXPDG_K_RESIDUAL, 16.0 * ctx->N,
@@ -265,8 +268,12 @@ cudaError_t residual_into(expdg_ctx* ctx, const double* q, Vec out, double alpha
     if (e != cudaSuccess) return e;
   }
   a.q = ctx->d_qfx;
-  a.out_h = out.h;
-  a.out_l = out.l;
+  if (ctx->ff) {
+    a.out_h = out.h;
+    a.out_l = out.l;
+  } else {
+    a.out = out.d;
+  }
   return run(ctx, EXPDG_K_RESIDUAL, 16.0 * ctx->N, [&]() {
     const int p = ctx->cfg.p, eq = ctx->cfg.eq;
     switch (ctx->cfg.dim) {
@@ -279,10 +286,10 @@ cudaError_t residual_into(expdg_ctx* ctx, const double* q, Vec out, double alpha
 }
 
 // Linearisation state of qt (FP64, device) -> ctx->d_z, in compute form;
-// with_fx (mixed form): qt as float-float pairs into ctx->d_qfx as well, for
-// a residual at qt that follows.
+// with_fx (FP32-operator forms): qt as float-float pairs into ctx->d_qfx as
+// well, for a residual at qt that follows.
 cudaError_t linstate_into(expdg_ctx* ctx, const double* qt, bool with_fx = false) {
-  float* qfx = (with_fx && ctx->ff) ? ctx->d_qfx : nullptr;
+  float* qfx = (with_fx && ctx->f32op) ? ctx->d_qfx : nullptr;
   const bool f32 = ctx->f32op;
   const double bytes = (8.0 + (f32 ? 4.0 : 8.0) + (qfx ? 8.0 : 0.0)) * ctx->N;
   return run(ctx, EXPDG_K_VECTOR, bytes, [&]() {
@@ -683,13 +690,13 @@ expdg_status step_dev(expdg_ctx* ctx, double* q, double dt, const Replay& rp, ex
   bool has[EXPDG_MAX_PHI + 1] = {false, false, false, false};
   const int scheme = ctx->cfg.scheme;
   if (scheme == EXPDG_EPI2) {
-    CU(ctx, residual_into(ctx, q, ctx->c[1], dt, ctx->ff));
+    CU(ctx, residual_into(ctx, q, ctx->c[1], dt, ctx->f32op));
     st->residual_applies++;
     has[1] = true;
     return phi_solve(ctx, qt_T, dt, has, 1, dvec(q), dvec(q), 0, rp, st, trace, true);
   }
   // EXPRB32 / EXPRB42 share: R^n, stage 1, D_{n,2} = R(q2) - R^n - L (q2 - q)
-  CU(ctx, residual_into(ctx, q, ctx->rn, 1.0, ctx->ff));
+  CU(ctx, residual_into(ctx, q, ctx->rn, 1.0, ctx->f32op));
   st->residual_applies++;
   const double a1 = (scheme == EXPDG_EXPRB32) ? dt : 0.75 * dt;
   {
@@ -784,7 +791,7 @@ size_t expdg_context_bytes(const expdg_config* cfg) {
   auto r = [&](size_t b) { return ((b + gran - 1) / gran) * gran; };
   size_t total = 5 * r(N * sizeof(double));                 // q, q2, t2, in, out
   if (f32) total += r(N * sizeof(float));                            // FP32 operand
-  if (ff) total += r(2 * N * sizeof(float));                          // float-float state
+  if (f32) total += r(2 * N * sizeof(float));                         // float-float state
   if (f32 && !ff) total += EXPDG_MAX_PHI * r(N * sizeof(float));     // FP32 copies of b_1..b_P
   total += r(N * (f32 ? sizeof(float) : sizeof(double)));    // linearisation state
   const size_t nvec = 2 * (EXPDG_MAX_PHI + 1) + 4;          // c, b, w, rn, t1, t3
@@ -934,7 +941,7 @@ expdg_status expdg_create(const expdg_config* cfg, expdg_ctx** out) {
   ALLOC(dalloc(ctx, &ctx->d_in, N));
   ALLOC(dalloc(ctx, &ctx->d_out, N));
   if (ctx->f32op) ALLOC(dalloc(ctx, &ctx->d_q32b, N));
-  if (ctx->ff) ALLOC(dalloc(ctx, &ctx->d_qfx, 2 * N));
+  if (ctx->f32op) ALLOC(dalloc(ctx, &ctx->d_qfx, 2 * N));
   if (ctx->f32op && !ctx->ff)
     for (int i = 1; i <= EXPDG_MAX_PHI; ++i) ALLOC(dalloc(ctx, &ctx->d_bf[i], N));
   if (ctx->f32op) {

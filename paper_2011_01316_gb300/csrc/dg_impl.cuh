@@ -470,8 +470,9 @@ struct DgSmem {
 // launch writes (after loading z when a.z_early).
 // LINEAR = false: residual R(q), a.q = q.  LINEAR = true: linear operator,
 // a.q = the linearisation state z of qt (k_linstate), a.v = v.
-// T = double: FP64 (double in, double out); T = fx: float-float in and out
-// (the float-float form's residual: FP64-grade accuracy on the FP32 pipes);
+// T = double: FP64 (double in, double out); T = fx: float-float in, out
+// float-float (a.out_h / a.out_l) or h + l in FP64 (a.out) (the residual of
+// the FP32-operator forms: FP64-grade accuracy on the FP32 pipes);
 // T = float: FP32 arithmetic on an FP32 input vector (linear operator), with
 //   MX = false: float-float output (the float-float form);
 //   MX = true:  the mixed form (FP64 Krylov basis): output in FP32 (a.out_h,
@@ -604,12 +605,17 @@ __device__ __forceinline__ void dg_group(const DGArgs& a, const Tab& tab, int e0
   if constexpr (std::is_same<T, fx>::value) {  // residual in float-float: out = alpha (R + s)
     static_assert(!LINEAR, "the float-float kernels compute the residual");
     const fx al(a.alpha_h, a.alpha_l);
+    const bool wide = a.out != nullptr;  // uniform: FP64 output (mixed form)
 #pragma unroll
     for (int f = 0; f < M; ++f) {
       fx o = al * acc[f];
       if (a.src != nullptr) o = o + fx(a.alpha * a.src[f * stride + base]);
-      a.out_h[f * stride + base] = o.h;
-      a.out_l[f * stride + base] = o.l;
+      if (wide) {  // h + l: at most 48 significant bits, exact in binary64
+        a.out[f * stride + base] = f32_to_f64_exact(o.h) + f32_to_f64_exact(o.l);
+      } else {
+        a.out_h[f * stride + base] = o.h;
+        a.out_l[f * stride + base] = o.l;
+      }
     }
     return;
   } else if constexpr (MX) {  // FP32 arithmetic to the end

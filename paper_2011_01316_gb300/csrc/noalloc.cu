@@ -1,8 +1,9 @@
 // expdg_residual_noalloc: the residual R(q) without a context and without any
 // device allocation, for callers that cannot allocate device memory.
 //
-// Its scratch - the float-float copy of the state and the float-float output
-// of the float-float form, and the non-physical-state flag of every form -
+// Its scratch - the float-float copy of the state (mixed and float-float
+// forms), the float-float output of the float-float form, and the
+// non-physical-state flag of every form -
 // lives in the file-scope arrays below.  Every GPU that loads this library
 // holds them (about 8 MiB) until the process exits.
 #include <cstring>
@@ -88,7 +89,8 @@ extern "C" expdg_status expdg_residual_noalloc(const expdg_config* cfg, const do
   const int m = (cfg->eq == EXPDG_BURGERS) ? 1 : dim + 2;
   if (nelem > (size_t)0x7fffffff / (size_t)np) return EXPDG_EINVAL;
   const size_t N = (size_t)m * nelem * np;
-  const bool ffr = cfg->prec == EXPDG_MIXED_FF;  // float-float residual: needs the scratch
+  const bool ffr = cfg->prec != EXPDG_FP64;  // float-float residual: needs the scratch
+  const bool ffo = cfg->prec == EXPDG_MIXED_FF;  // its float-float output (else FP64, into r)
   if (ffr && N > kMaxUnknowns) return EXPDG_EINVAL;  // beyond the static scratch
   int dev = 0;
   if (cudaGetDevice(&dev) != cudaSuccess) return EXPDG_ECUDA;
@@ -127,11 +129,15 @@ extern "C" expdg_status expdg_residual_noalloc(const expdg_config* cfg, const do
   float* rh = ad->scratch + 2 * kMaxUnknowns;
   float* rl = ad->scratch + 3 * kMaxUnknowns;
   cudaError_t e = cudaSuccess;
-  if (ffr) {  // float-float residual, as expdg_residual computes it in the float-float form
+  if (ffr) {  // float-float residual, as expdg_residual computes it in the FP32-operator forms
     e = launch_f64_to_fx(qfx, q, N, s);
     a.q = qfx;
-    a.out_h = rh;
-    a.out_l = rl;
+    if (ffo) {
+      a.out_h = rh;
+      a.out_l = rl;
+    } else {
+      a.out = r;
+    }
     if (e == cudaSuccess) {
       if (dim == 1)
         e = launch_dg_fx_1d(cfg->eq, p, a, tab, s);
@@ -140,7 +146,7 @@ extern "C" expdg_status expdg_residual_noalloc(const expdg_config* cfg, const do
       else
         e = launch_dg_fx_3d(cfg->eq, p, a, tab, s);
     }
-  } else {  // the FP64 residual (FP64 and mixed forms): in place, no scratch
+  } else {  // the FP64 residual (FP64 form): in place, no scratch
     a.q = q;
     a.out = r;
     if (dim == 1)
@@ -150,7 +156,7 @@ extern "C" expdg_status expdg_residual_noalloc(const expdg_config* cfg, const do
     else
       e = launch_dg_3d(false, DG_F64, cfg->eq, p, a, tab, s);
   }
-  if (e == cudaSuccess && ffr) {
+  if (e == cudaSuccess && ffo) {
     Vec v{};
     v.h = rh;
     v.l = rl;

@@ -46,7 +46,7 @@ def test_roe_residual_and_jv_parity(E, case, prec):
         v = np.ascontiguousarray(rng.standard_normal(q.shape))
         Lv, Lref = ctx.jv(q, v), dg.jv(mesh, q, v)
         amp = (mesh.p + 1) ** 2
-        if prec == 2:
+        if prec in MIXED_PRECS:
             assert np.linalg.norm(R - Rref) <= C_RFX * amp * flux_scale(mesh, q)
         else:
             assert rel(R, Rref) <= TOL_OP64

@@ -79,7 +79,7 @@ def test_noalloc_residual_matches_context_residual(env, kind, kw, prec):
         err = float(torch.linalg.vector_norm(out - ref) / torch.linalg.vector_norm(ref))
         assert err <= TOL, err
         got = out.cpu().numpy()
-        if prec == 2:
+        if prec != 0:
             assert np.linalg.norm(got - oracle) <= C_RFX * (mesh.p + 1) ** 2 * flux_scale(mesh, qh)
         else:
             assert np.linalg.norm(got - oracle) <= TOL_OP64 * np.linalg.norm(oracle)
@@ -88,11 +88,12 @@ def test_noalloc_residual_matches_context_residual(env, kind, kw, prec):
 
 def test_noalloc_rejects_oversize_and_host_pointers(env):
     torch, expdg, inputs = env
-    big = expdg.default_config(dim=3, p=3, ne=[32, 32, 32], lo=[0, 0, 0], hi=[1, 1, 1], eq=2, prec=2)
     small = torch.zeros(8, dtype=torch.float64, device="cuda")
-    st = expdg.lib.expdg_residual_noalloc(ctypes.byref(big), ctypes.c_void_p(small.data_ptr()),
-                                          ctypes.c_void_p(small.data_ptr()), None)
-    assert st == expdg.EXPDG_EINVAL
+    for prec in (1, 2):   # the forms that use the static float-float scratch
+        big = expdg.default_config(dim=3, p=3, ne=[32, 32, 32], lo=[0, 0, 0], hi=[1, 1, 1], eq=2, prec=prec)
+        st = expdg.lib.expdg_residual_noalloc(ctypes.byref(big), ctypes.c_void_p(small.data_ptr()),
+                                              ctypes.c_void_p(small.data_ptr()), None)
+        assert st == expdg.EXPDG_EINVAL
     cfg = expdg.default_config(dim=1, p=2, ne=[4, 1, 1], lo=[0, 0, 0], hi=[1, 1, 1], eq=1)
     h = np.zeros(12)
     st = expdg.lib.expdg_residual_noalloc(ctypes.byref(cfg), ctypes.c_void_p(h.ctypes.data),
