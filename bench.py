@@ -327,13 +327,14 @@ def fp64_ops(kclass, prec, bytes_, launches, n_aug):
     """FP64 operations of the incomplete-orthogonalisation passes from their
     algorithmic bytes (per element: FP64 form, window products nwin + 1 for
     (nwin + 1) x 8 bytes, update nwin + 2 for (nwin + 2) x 8; mixed form, window
-    products nwin for (nwin + 1/2) x 8 (|w'|^2 in FP32), update nwin + 1 for
-    (nwin + 2) x 8 (the scale by c_j in FP32)); None for the float-float form."""
+    products nwin for (nwin + 1/2) x 8 (|w'|^2 in FP32), update nwin for
+    (nwin + 2) x 8 (the scale by c_j and the norm in FP32)); None for the
+    float-float form."""
     if prec == 2:
         return None
     if prec == 0:
         return bytes_ / 8
-    return bytes_ / 8 - launches * n_aug * (0.5 if kclass == "dots" else 1.0)
+    return bytes_ / 8 - launches * n_aug * (0.5 if kclass == "dots" else 2.0)
 
 
 def kernel_rates(kern, hbm, prec=1, n_aug=None):

@@ -1251,6 +1251,12 @@ __global__ void __launch_bounds__(NT) k_iom_update(KState* ks, double* part, Bas
 // only scales the happy-breakdown test: its top part is summed in FP32 (one
 // FP64 operation fewer per element on the narrow FP64 pipe; the true-scale
 // slots keep w' within a few orders of magnitude of the operator's norm).
+// ||slot_{j+1}||^2 likewise, from the FP32 rounding the update writes
+// (compensated FP32 sums per thread, FP64 across threads): it sets
+// c_{j+1} = 1 / ||slot_{j+1}|| and H(j+1, j) = ||slot_{j+1}|| together, so
+// H(j+1, j) v_{j+1} = slot_{j+1} and the Arnoldi relation hold whatever its
+// rounding; only the unit length of v_{j+1} depends on it (to about 1e-7),
+// and the update's FP64 operations are the window's alone.
 // The update scales w' by c_j in FP32 too (part of the operator apply on the
 // unit vector v_j), so its FP64 operations are the window's and the norm's.
 // Loads before griddepcontrol.wait as in the float-float kernels above.
@@ -1339,6 +1345,7 @@ __global__ void __launch_bounds__(NT) k_iom_update_mx(KState* ks, double* part, 
   // then widened exactly; the slots stay at true scale
   const float c_jf = f64_to_f32_rn(c_j);
   double nrm[1] = {0.0};
+  float ns = 0.0f, nc = 0.0f;  // |slot_{j+1}|^2 of the top part from its FP32 rounding (compensated sum)
   for (size_t g = tid; g < ng; g += nthr) {
     const size_t o = (size_t)(j + 1) * ld + 4 * g;
     const float4 wf = (g == tid) ? pwf : *reinterpret_cast<const float4*>(Uh + o);
@@ -1354,12 +1361,16 @@ __global__ void __launch_bounds__(NT) k_iom_update_mx(KState* ks, double* part, 
 #pragma unroll
         for (int e = 0; e < 4; ++e) w.v[e] = fma(cf[c], x.v[e], w.v[e]);
     }
-#pragma unroll
-    for (int e = 0; e < 4; ++e) nrm[0] = fma(w.v[e], w.v[e], nrm[0]);
     stq<false>(U, j + 1, g, w);
-    *reinterpret_cast<float4*>(Uh + o) =
+    const float4 sh =
         make_float4(f64_to_f32_rn(w.v[0]), f64_to_f32_rn(w.v[1]), f64_to_f32_rn(w.v[2]), f64_to_f32_rn(w.v[3]));
+    *reinterpret_cast<float4*>(Uh + o) = sh;
+    const float sq = __fmaf_rn(sh.x, sh.x, __fmaf_rn(sh.y, sh.y, __fmaf_rn(sh.z, sh.z, __fmul_rn(sh.w, sh.w))));
+    const float y = __fsub_rn(sq, nc), t = __fadd_rn(ns, y);  // Kahan's compensated summation
+    nc = __fsub_rn(__fsub_rn(t, ns), y);
+    ns = t;
   }
+  nrm[0] = f32_to_f64_exact(ns) - f32_to_f64_exact(nc);
   for (size_t i = 4 * ng + tid; i < n_aug; i += nthr) {  // ragged end (FP32 scaling) and the FP64 tail
     double w = (i < N) ? f32_to_f64_exact(__fmul_rn(c_jf, Uh[(size_t)(j + 1) * ld + i])) : c_j * U.d[(size_t)(j + 1) * ld + i];
     for (int c = 0; c < nwin; ++c) w = fma(cf[c], ldb<false>(U, lo + c, i), w);
