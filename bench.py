@@ -65,7 +65,8 @@ VORTEX = dict(dim=2, p=4, ne=[64, 64, 1], lo=[0.0, 0.0, 0.0], hi=[10.0, 10.0, 1.
 VORTEX_DT = 0.05
 CLASSES = ["residual", "jv", "dots", "update", "phi", "combine", "vector"]
 # DFMA throughput of this GPU (FP64 FMA per second over all SMs; 1.6 per SM per
-# clock at 2070 MHz), measured by an independent-chain throughput probe.
+# clock at 2070 MHz), measured by the independent-chain throughput probe
+# tests/native/alu_rates.cu (tests/test_gpu_alu_rates.py checks it stays so).
 FP64_FMA_PER_S = 0.5015e12
 # ncu DRAM-traffic records of the dominant kernels, with the hash of the sources
 # they were taken from (a record whose sources have changed since is not used)
@@ -444,11 +445,34 @@ def burgers_workload(steps=50, iop=4):
     ms = ev0.elapsed_time(ev1)
     mesh = dg.Mesh(dim=1, p=2, ne=(64,), lo=(0.0,), hi=(2 * math.pi,), eq="burgers")
     ref, _ = integrators.advance(mesh, u0.reshape(-1), 1e-2, steps, tol=1e-10, iop=iop or None)
+    # the same solve as one resident launch (one CTA, every step inside it;
+    # Krylov limit 40, which this solve never reaches: m = 10)
+    cfg = expdg.default_config(dim=1, p=2, ne=[64, 1, 1], lo=[0.0, 0.0, 0.0], hi=[2 * math.pi, 1.0, 1.0],
+                               eq=expdg.EXPDG_BURGERS, scheme=expdg.EXPDG_EPI2, prec=expdg.EXPDG_FP64,
+                               krylov_tol=1e-10, m_max=40, m_step=5, max_substeps=32, iop=iop)
+    b = expdg.Batch([cfg])
+    qr = q0.clone()
+    b.advance([qr], [1e-2], 3)
+    qr = q0.clone()
+    torch.cuda.synchronize()
+    ev0.record(stream)
+    st_b = b.advance([qr], [1e-2], steps)
+    ev1.record(stream)
+    ev1.synchronize()
+    ms_r = ev0.elapsed_time(ev1)
+    _, rst, _ = b.result(0)
+    launches = b.launches()
+    b.close()
+    ref40, _ = integrators.advance(mesh, u0.reshape(-1), 1e-2, steps, tol=1e-10, m_max=40, iop=iop or None)
     return {"workload": "1D Burgers, 64 elements, p=2, 192 unknowns, u0 = 0.5 + sin x, EPI2 dt=1e-2, tol 1e-10, FP64, "
                         + (f"window {iop} (KIOPS)" if iop else "full orthogonalisation"),
             "steps": steps, "us_per_step": 1e3 * ms / steps, "dof_steps_per_s": ctx.n * steps / (ms * 1e-3),
             "krylov_iters_per_step": st["krylov_iters"] / steps,
-            "err_vs_oracle": rel(q.cpu().numpy(), ref), "err_kind": f"oracle, {steps} adaptive steps, same window"}
+            "err_vs_oracle": rel(q.cpu().numpy(), ref), "err_kind": f"oracle, {steps} adaptive steps, same window",
+            "resident": {"us_per_step": 1e3 * ms_r / steps, "dof_steps_per_s": ctx.n * steps / (ms_r * 1e-3),
+                         "launches": launches, "status": st_b, "krylov_iters_per_step": rst["krylov_iters"] / steps,
+                         "err_vs_oracle": rel(qr.cpu().numpy(), ref40),
+                         "what": f"expdg_batch_advance: all {steps} steps in one launch of one CTA (FP64)"}}
 
 
 def exprb32_workload(stream, flush, steps=5):
@@ -580,7 +604,60 @@ def batched_requests(n, seed, steps, prec):
     return reqs
 
 
-def batched_workload(n, seed=0, workers=16, steps=20, cpu=False):
+def resident_and_streams(reqs, workers, resident_max):
+    """The requests with at most `resident_max` unknowns as one resident batch
+    (one launch per class of equal eq, dim, p; Krylov limit 40), the rest
+    through the solve server at the same time; returns (results in request
+    order as (q, status), wall seconds, resident count, launches)."""
+    import threading
+    import torch
+    from paper_2011_01316_gb300 import expdg, serve
+    small = [i for i, r in enumerate(reqs) if r[1].size <= resident_max]
+    large = [i for i in range(len(reqs)) if i not in set(small)]
+    cfgs = []
+    for i in small:
+        c = expdg.expdg_config()
+        ctypes_copy(c, reqs[i][0])
+        c.m_max = min(c.m_max, expdg.BATCH_MAX_KRYLOV)
+        cfgs.append(c)
+    b = expdg.Batch(cfgs) if small else None
+    qs = [torch.from_numpy(reqs[i][1].copy()).cuda() for i in small]
+    dts = [reqs[i][2] for i in small]
+    if b is not None:  # warm-up (module load), then fresh states
+        b.advance([q.clone() for q in qs], dts, 1)
+        torch.cuda.synchronize()
+    out = [None] * len(reqs)
+    box = {}
+
+    def run_small():
+        if b is not None:
+            box["status"] = b.advance(qs, dts, reqs[small[0]][3])
+
+    srv = serve.Server(workers=workers)
+    rng = np.random.default_rng(5)
+    t0 = time.perf_counter()
+    th = threading.Thread(target=run_small)
+    th.start()
+    res, _ = serve.run_stream(srv, [reqs[i] for i in large], 0.0, rng, check=False) if large else ([], 0.0)
+    th.join()
+    wall = time.perf_counter() - t0
+    srv.close()
+    for k, i in enumerate(large):
+        out[i] = (res[k][0], res[k][3])
+    for k, i in enumerate(small):
+        out[i] = (qs[k].cpu().numpy(), b.result(k)[0])
+    launches = b.launches() if b is not None else 0
+    if b is not None:
+        b.close()
+    return out, wall, len(small), launches
+
+
+def ctypes_copy(dst, src):
+    import ctypes
+    ctypes.memmove(ctypes.addressof(dst), ctypes.addressof(src), ctypes.sizeof(src))
+
+
+def batched_workload(n, seed=0, workers=16, steps=20, cpu=False, resident_max=8192):
     """n independent periodic instances (half 1D Burgers with Ne log-uniform in
     [16, 4096], half 2D Euler density waves with side in {8..96}; p uniform in
     {1..5}; initial data 1 + 4 seeded Fourier modes, a_k ~ U[0, 0.3]; dt from
@@ -602,6 +679,8 @@ def batched_workload(n, seed=0, workers=16, steps=20, cpu=False):
     res64, _ = serve.run_stream(srv, batched_requests(n, seed, steps, 0), 0.0, rng, check=False)
     srv.close()
     errs = [rel(a[0], b[0]) for a, b in zip(resn, res64) if a[3] == 0 and b[3] == 0]
+    resr, wallr, nres, launches = resident_and_streams(reqs, workers, resident_max)
+    errs_r = [rel(a[0], b[0]) for a, b in zip(resr, res64) if a[1] == 0 and b[3] == 0]
     cpu_all = None
     if cpu:
         # the oracle on every host core: a seeded sample of 32 instances (half
@@ -616,6 +695,13 @@ def batched_workload(n, seed=0, workers=16, steps=20, cpu=False):
     return {"workload": f"{n} instances (1D Burgers / 2D Euler, p 1..5, uneven sizes), {steps} EPI2 steps each",
             "cpu_oracle_all_cores": cpu_all,
             "concurrent": {"workers": workers, "wall_s": walln, "dof_steps_per_s": dofs / walln},
+            "resident_plus_streams": {"wall_s": wallr, "dof_steps_per_s": dofs / wallr, "resident_instances": nres,
+                                      "resident_launches": launches, "streamed_instances": n - nres,
+                                      "resident_max_unknowns": resident_max, "failed": sum(1 for a in resr if a[1] != 0),
+                                      "max_rel_err_vs_fp64": max(errs_r) if errs_r else None,
+                                      "what": "instances with at most resident_max unknowns as one resident batch "
+                                              "(one launch per class, one CTA per instance, all steps inside), the "
+                                              "rest through the solve server at the same time"},
             "sequential": {"wall_s": wall1, "dof_steps_per_s": dofs / wall1},
             "speedup": wall1 / walln, "identical_results": same,
             "failed": sum(1 for a in resn if a[3] != 0),
@@ -701,6 +787,8 @@ def main():
     ap.add_argument("--burgers-iop", type=int, default=4, help="orthogonalisation window of the Burgers leg (0: full)")
     ap.add_argument("--batch-instances", type=int, default=256, help="instances of the batched workload (0: skip)")
     ap.add_argument("--batch-workers", type=int, default=16, help="instances in flight in the batched workload")
+    ap.add_argument("--resident-max", type=int, default=8192,
+                    help="batched workload: instances up to this many unknowns run as one resident batch")
     ap.add_argument("--legs", default="main,wave3d_ff,vortex,burgers,exprb32,serving,batched",
                     help="comma list of legs to run (main = the timed workload; profiling runs pick one)")
     ap.add_argument("--wave3d-ne", type=int, default=32, help="elements per direction of the wave3d legs")
@@ -748,7 +836,7 @@ def main():
                                               cpu=not args.no_cpu_baseline)
         if "batched" in legs:
             out["batched"] = batched_workload(args.batch_instances, workers=args.batch_workers,
-                                              cpu=not args.no_cpu_baseline)
+                                              cpu=not args.no_cpu_baseline, resident_max=args.resident_max)
         if "burgers" in legs:
             out["burgers"] = burgers_workload(iop=args.burgers_iop)
         if "exprb32" in legs:
@@ -862,7 +950,8 @@ def main():
     if args.serve_requests > 0 and "serving" in legs:
         extra["serving"] = serving_workload(args.serve_requests, workers=args.serve_workers, cpu=cpu_legs)
     if args.batch_instances > 0 and "batched" in legs:
-        extra["batched"] = batched_workload(args.batch_instances, workers=args.batch_workers, cpu=cpu_legs)
+        extra["batched"] = batched_workload(args.batch_instances, workers=args.batch_workers, cpu=cpu_legs,
+                                            resident_max=args.resident_max)
 
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:

@@ -324,6 +324,45 @@ expdg_status expdg_server_fetch(expdg_server* s, int64_t id, double* q_out, expd
 /* Bytes held by contexts, queued and running solve counts. */
 expdg_status expdg_server_info(expdg_server* s, size_t* used_bytes, int* pending, int* running);
 
+/* ---- Resident batch: many small solves, one launch per class ---------------
+ * Batching pattern (not in the paper): n independent EPI2 solves (Sec. 5.1
+ * footnote; the phi_1 sum by the augmented Krylov method of Sec. 2.3, with the
+ * decisions of expdg_phi: checks at multiples of m_step and at m_max, Saad's
+ * estimate <= krylov_tol beta, happy breakdown, sub-steps halving at m_max and
+ * doubling after an accepted sub-step with m <= m_max / 2) run as ONE kernel
+ * launch per class of equal (eq, dim, p, prec), one CTA per instance; every
+ * step of every instance runs inside that launch (Krylov basis in device
+ * memory, H and exp(H_m) in shared memory, decisions on the device), and the
+ * classes' launches run side by side.  For instances too small to fill the
+ * GPU, where a solve through a context is a chain of short launches.
+ *   - Each configuration: scheme EXPDG_EPI2; 1D Burgers (periodic or
+ *     Dirichlet, kappa >= 0) or 2D Euler; p = 1..5; LF flux; prec EXPDG_FP64
+ *     or EXPDG_MIXED (FP32 operator applies on the FP32 rounding of each basis
+ *     vector, float-float residual, FP64 Krylov basis, inner products,
+ *     orthogonalisation (modified Gram-Schmidt), exp(H_m) and update); m_max
+ *     <= EXPDG_BATCH_MAX_KRYLOV; iop = 0 (full orthogonalisation) or the
+ *     window.  Other configurations: EXPDG_EINVAL.
+ *   - expdg_batch_create allocates every instance's scratch (basis of
+ *     m_max + 1 vectors, the operator's state, four vectors).
+ *   - expdg_batch_advance: nsteps steps of size dt[i] of instance i from its
+ *     state q[i] (a DEVICE array of the current device, canonical layout),
+ *     in place, on `stream` (NULL: legacy default stream); returns after the
+ *     stream has finished.  Returns EXPDG_OK, or the status of the first
+ *     instance (in the given order) that failed (EXPDG_ENONPHYSICAL,
+ *     EXPDG_EKRYLOV); that instance stopped at the start of the failing
+ *     step, the others ran all steps.  EXPDG_EINVAL for a bad pointer or dt.
+ *   - expdg_batch_result: instance i's status, its statistics over the last
+ *     advance, and the steps it completed.
+ *   - Results do not depend on the other instances of the batch. */
+#define EXPDG_BATCH_MAX_KRYLOV 40
+typedef struct expdg_batch expdg_batch;
+expdg_status expdg_batch_create(const expdg_config* cfgs, int n, expdg_batch** out);
+expdg_status expdg_batch_advance(expdg_batch* b, double* const* q, const double* dt, int nsteps, void* stream);
+expdg_status expdg_batch_result(const expdg_batch* b, int i, expdg_stats* stats, int* steps_done);
+/* Kernel launches one advance makes (the number of classes). */
+int expdg_batch_launches(const expdg_batch* b);
+void expdg_batch_destroy(expdg_batch* b);
+
 
 /* ---- Allocation-free residual ---------------------------------------------
  * The paper has no counterpart to this call; it is a deployment convenience.

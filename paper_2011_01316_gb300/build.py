@@ -12,7 +12,7 @@ CSRC = os.path.join(HERE, "csrc")
 BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(HERE, "libexpdg.so")
 SOURCES = ["capi.cu", "krylov.cu", "dg_1d.cu", "dg_2d.cu", "dg_3d.cu", "dg_roe_1d.cu", "dg_roe_2d.cu", "dg_roe_3d.cu",
-           "tables.cpp", "noalloc.cu", "server.cu"]
+           "tables.cpp", "noalloc.cu", "server.cu", "resident.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-std=c++17", "-lineinfo", "-Xcompiler", "-fPIC", "-Xcompiler", "-O2"]
 

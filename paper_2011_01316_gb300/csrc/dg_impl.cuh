@@ -202,28 +202,50 @@ struct Phys {
   }
 };
 
-// Linearisation state z of q (FP64 in, T out), node by node; stride =
+// Linearisation state z of q (FP64 in, T out) at node i; stride =
 // unknowns per field.  Computed in FP64 and rounded once.  Euler: (u, H, a),
 // or (u, H, sqrt(rho)) for the Roe flux (its average weights).  qfx (may be
 // null): q as float-float pairs as well (the mixed form's residual operand).
 template <int DIM, int EQ, typename T>
-__global__ void __launch_bounds__(256) k_linstate(const double* __restrict__ q, T* __restrict__ z, size_t stride,
-                                                  double gamma, int roe, float2* __restrict__ qfx) {
+__device__ __forceinline__ void linstate_node(const double* __restrict__ q, T* __restrict__ z, size_t stride,
+                                              double gamma, int roe, float2* __restrict__ qfx, size_t i) {
   constexpr int M = NFields<DIM, EQ>::value;
-  griddep_wait();
-  const size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (i < stride) {
+  {
     double qv[M];
 #pragma unroll
     for (int f = 0; f < M; ++f) qv[f] = q[f * stride + i];
-    if (qfx != nullptr)
+    if (qfx != nullptr)  // the float-float split, conversions on the integer pipes
 #pragma unroll
       for (int f = 0; f < M; ++f) {
-        const ff x = ff_from_double(qv[f]);
-        qfx[f * stride + i] = make_float2(x.h, x.l);
+        const float h = f64_to_f32_rn(qv[f]);
+        qfx[f * stride + i] = make_float2(h, f64_to_f32_rn(qv[f] - f32_to_f64_exact(h)));
       }
     if (EQ != EXPDG_EULER) {
-      z[i] = (T)qv[0];
+      if constexpr (std::is_same<T, float>::value)
+        z[i] = f64_to_f32_rn(qv[0]);
+      else
+        z[i] = (T)qv[0];
+    } else if constexpr (std::is_same<T, float>::value) {
+      // FP32 state (mixed and float-float forms), few FP64 operations (on
+      // GB300 the FP64 pipe runs about 1.6 lane operations per SM per clock):
+      // 1/rho from the FP32 reciprocal and one Newton step in FP64 (relative
+      // error about 2^-46), the pressure (where E and the kinetic energy may
+      // cancel) in FP64, the sound speed's square root in FP32, conversions on
+      // the integer pipes.  Each z entry is within about one FP32 rounding of
+      // the FP64 value.
+      const double r0 = f32_to_f64_exact(__frcp_rn(f64_to_f32_rn(qv[0])));
+      const double inv = r0 * fma(-qv[0], r0, 2.0);
+      double ke = 0.0;
+#pragma unroll
+      for (int k = 0; k < DIM; ++k) {
+        const double u = qv[1 + k] * inv;
+        z[k * stride + i] = f64_to_f32_rn(u);
+        ke = fma(qv[1 + k], u, ke);
+      }
+      const double p = (gamma - 1.0) * fma(-0.5, ke, qv[DIM + 1]);
+      z[DIM * stride + i] = f64_to_f32_rn((qv[DIM + 1] + p) * inv);
+      z[(DIM + 1) * stride + i] =
+          __fsqrt_rn(f64_to_f32_rn(roe ? qv[0] : gamma * p * inv));
     } else {
       const double inv = 1.0 / qv[0];
       double ke = 0.0;
@@ -238,6 +260,14 @@ __global__ void __launch_bounds__(256) k_linstate(const double* __restrict__ q, 
       z[(DIM + 1) * stride + i] = (T)(roe ? sqrt(qv[0]) : sqrt(gamma * p * inv));
     }
   }
+}
+
+template <int DIM, int EQ, typename T>
+__global__ void __launch_bounds__(256) k_linstate(const double* __restrict__ q, T* __restrict__ z, size_t stride,
+                                                  double gamma, int roe, float2* __restrict__ qfx) {
+  griddep_wait();
+  const size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < stride) linstate_node<DIM, EQ, T>(q, z, stride, gamma, roe, qfx, i);
   griddep_launch();
 }
 

@@ -1274,9 +1274,9 @@ __global__ void __launch_bounds__(NT) k_iom_dots_mx(KState* ks, double* part, Ba
   __shared__ double sh[NW * K];
   __shared__ double tot[K];
   const int lo = max(0, j - KW + 1), nwin = j - lo + 1;
-  double acc[KW];
+  double acc[KW], acc2[KW];  // two chains a slot (more FP64 operations in flight)
 #pragma unroll
-  for (int c = 0; c < KW; ++c) acc[c] = 0.0;
+  for (int c = 0; c < KW; ++c) acc[c] = acc2[c] = 0.0;
   float wn = 0.0f;     // |w'|^2 of the top part (FP32)
   double wnt = 0.0;    // and of the ragged end and tail
   const size_t ld = U.ld, ng = N / 4;
@@ -1294,12 +1294,15 @@ __global__ void __launch_bounds__(NT) k_iom_dots_mx(KState* ks, double* part, Ba
 #pragma unroll
     for (int c = 0; c < KW; ++c) {
       const Quad<false> x = (g == tid) ? px[c] : ldq<false>(U, lo + (c < nwin ? c : 0), g);
-      if (c < nwin)
-#pragma unroll
-        for (int e = 0; e < 4; ++e) acc[c] = fma(x.v[e], w[e], acc[c]);
+      if (c < nwin) {
+        acc[c] = fma(x.v[1], w[1], fma(x.v[0], w[0], acc[c]));
+        acc2[c] = fma(x.v[3], w[3], fma(x.v[2], w[2], acc2[c]));
+      }
     }
     wn = fmaf(wf.x, wf.x, fmaf(wf.y, wf.y, fmaf(wf.z, wf.z, fmaf(wf.w, wf.w, wn))));
   }
+#pragma unroll
+  for (int c = 0; c < KW; ++c) acc[c] += acc2[c];
   for (size_t i = 4 * ng + tid; i < n_aug; i += nthr) {  // ragged end and the augmentation tail
     const double wi = mx_w(U, j + 1, i, N);
 #pragma unroll
@@ -1346,29 +1349,50 @@ __global__ void __launch_bounds__(NT) k_iom_update_mx(KState* ks, double* part, 
   const float c_jf = f64_to_f32_rn(c_j);
   double nrm[1] = {0.0};
   float ns = 0.0f, nc = 0.0f;  // |slot_{j+1}|^2 of the top part from its FP32 rounding (compensated sum)
-  for (size_t g = tid; g < ng; g += nthr) {
-    const size_t o = (size_t)(j + 1) * ld + 4 * g;
-    const float4 wf = (g == tid) ? pwf : *reinterpret_cast<const float4*>(Uh + o);
+  // quad g from its loaded inputs: the update, both stores, the norm term
+  auto finish = [&](size_t g, const float4 wf, const Quad<false>* x) {
     Quad<false> w;
     w.v[0] = f32_to_f64_exact(__fmul_rn(c_jf, wf.x));
     w.v[1] = f32_to_f64_exact(__fmul_rn(c_jf, wf.y));
     w.v[2] = f32_to_f64_exact(__fmul_rn(c_jf, wf.z));
     w.v[3] = f32_to_f64_exact(__fmul_rn(c_jf, wf.w));
 #pragma unroll
-    for (int c = 0; c < KW; ++c) {
-      const Quad<false> x = (g == tid) ? px[c] : ldq<false>(U, lo + (c < nwin ? c : 0), g);
+    for (int c = 0; c < KW; ++c)
       if (c < nwin)
 #pragma unroll
-        for (int e = 0; e < 4; ++e) w.v[e] = fma(cf[c], x.v[e], w.v[e]);
-    }
+        for (int e = 0; e < 4; ++e) w.v[e] = fma(cf[c], x[c].v[e], w.v[e]);
     stq<false>(U, j + 1, g, w);
     const float4 sh =
         make_float4(f64_to_f32_rn(w.v[0]), f64_to_f32_rn(w.v[1]), f64_to_f32_rn(w.v[2]), f64_to_f32_rn(w.v[3]));
-    *reinterpret_cast<float4*>(Uh + o) = sh;
+    *reinterpret_cast<float4*>(Uh + (size_t)(j + 1) * ld + 4 * g) = sh;
     const float sq = __fmaf_rn(sh.x, sh.x, __fmaf_rn(sh.y, sh.y, __fmaf_rn(sh.z, sh.z, __fmul_rn(sh.w, sh.w))));
     const float y = __fsub_rn(sq, nc), t = __fadd_rn(ns, y);  // Kahan's compensated summation
     nc = __fsub_rn(__fsub_rn(t, ns), y);
     ns = t;
+  };
+  auto load = [&](size_t g, float4& wf, Quad<false>* x) {
+    wf = *reinterpret_cast<const float4*>(Uh + (size_t)(j + 1) * ld + 4 * g);
+#pragma unroll
+    for (int c = 0; c < KW; ++c) x[c] = ldq<false>(U, lo + (c < nwin ? c : 0), g);
+  };
+  size_t g = tid;
+  if (g < ng) {  // the first trip, loaded before the wait
+    finish(g, pwf, px);
+    g += nthr;
+  }
+  for (; g + nthr < ng; g += 2 * nthr) {  // two trips' loads in flight at once
+    float4 wa, wb;
+    Quad<false> xa[KW], xb[KW];
+    load(g, wa, xa);
+    load(g + nthr, wb, xb);
+    finish(g, wa, xa);
+    finish(g + nthr, wb, xb);
+  }
+  if (g < ng) {
+    float4 wa;
+    Quad<false> xa[KW];
+    load(g, wa, xa);
+    finish(g, wa, xa);
   }
   nrm[0] = f32_to_f64_exact(ns) - f32_to_f64_exact(nc);
   for (size_t i = 4 * ng + tid; i < n_aug; i += nthr) {  // ragged end (FP32 scaling) and the FP64 tail

@@ -105,6 +105,11 @@ def _load():
         "expdg_server_poll": (ctypes.c_int, [P, vp(ctypes.c_int64), ctypes.c_int, vp(ctypes.c_int)]),
         "expdg_server_fetch": (ctypes.c_int, [P, ctypes.c_int64, P, vp(expdg_stats), vp(ctypes.c_double)]),
         "expdg_server_info": (ctypes.c_int, [P, vp(ctypes.c_size_t), vp(ctypes.c_int), vp(ctypes.c_int)]),
+        "expdg_batch_create": (ctypes.c_int, [P, ctypes.c_int, vp(P)]),
+        "expdg_batch_advance": (ctypes.c_int, [P, P, P, ctypes.c_int, P]),
+        "expdg_batch_result": (ctypes.c_int, [P, ctypes.c_int, vp(expdg_stats), vp(ctypes.c_int)]),
+        "expdg_batch_launches": (ctypes.c_int, [P]),
+        "expdg_batch_destroy": (None, [P]),
     }
     for name, (res, args) in sig.items():
         f = getattr(lib, name)
@@ -277,3 +282,51 @@ class Context:
         st = expdg_stats()
         self._check(_lib.expdg_advance(self.h, _ptr(q), float(dt), int(nsteps), ctypes.byref(st)))
         return st.as_dict()
+
+
+BATCH_MAX_KRYLOV = 40   # EXPDG_BATCH_MAX_KRYLOV
+
+
+class Batch:
+    """One expdg_batch: n small EPI2 solves, one kernel launch per class of
+    equal (eq, dim, p, prec).  Methods mirror the C-ABI calls."""
+
+    def __init__(self, cfgs):
+        self.n = len(cfgs)
+        self._cfgs = (expdg_config * self.n)(*cfgs)
+        h = ctypes.c_void_p()
+        st = _lib.expdg_batch_create(self._cfgs, self.n, ctypes.byref(h))
+        if st != EXPDG_OK:
+            raise ExpdgError(st, "expdg_batch_create failed")
+        self.h = h
+
+    def launches(self):
+        return int(_lib.expdg_batch_launches(self.h))
+
+    def advance(self, qs, dts, nsteps, stream=None):
+        """nsteps steps of instance i from device tensor qs[i] (float64,
+        contiguous) with step dts[i], in place.  Returns the call's status
+        (EXPDG_OK or the first failing instance's)."""
+        if len(qs) != self.n or len(dts) != self.n:
+            raise ValueError("one state and one dt per instance")
+        ptrs = (ctypes.c_void_p * self.n)(*[_ptr(q) for q in qs])
+        dt = (ctypes.c_double * self.n)(*[float(x) for x in dts])
+        return _lib.expdg_batch_advance(self.h, ptrs, dt, int(nsteps), stream)
+
+    def result(self, i):
+        """(status, stats dict, steps done) of instance i after the last advance."""
+        st = expdg_stats()
+        done = ctypes.c_int(0)
+        status = _lib.expdg_batch_result(self.h, int(i), ctypes.byref(st), ctypes.byref(done))
+        return status, st.as_dict(), done.value
+
+    def close(self):
+        if self.h:
+            _lib.expdg_batch_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

@@ -116,3 +116,23 @@ def test_noalloc_reports_nonphysical_state(env):
                                           ctypes.c_void_p(out.data_ptr()), None)
     assert st == expdg.EXPDG_OK   # the flag of the previous call was cleared
     ctx.close()
+
+
+def test_noalloc_and_context_reject_another_devices_memory(env):
+    """Memory of a GPU other than the current one is refused (EXPDG_EINVAL), not
+    dereferenced: the kernels would fault without peer access.  Needs two GPUs."""
+    torch, expdg, inputs = env
+    if torch.cuda.device_count() < 2:
+        pytest.skip("needs a second GPU")
+    cfg = expdg.default_config(dim=1, p=2, ne=[8, 1, 1], lo=[0, 0, 0], hi=[1, 1, 1], eq=1)
+    other = torch.zeros(24, dtype=torch.float64, device="cuda:1")
+    mine = torch.zeros(24, dtype=torch.float64, device="cuda:0")
+    with torch.cuda.device(0):
+        st = expdg.lib.expdg_residual_noalloc(ctypes.byref(cfg), ctypes.c_void_p(other.data_ptr()),
+                                              ctypes.c_void_p(mine.data_ptr()), None)
+        assert st == expdg.EXPDG_EINVAL
+        ctx = expdg.Context(cfg)
+        with pytest.raises(expdg.ExpdgError) as ei:
+            ctx.residual(other, mine)
+        assert ei.value.status == expdg.EXPDG_EINVAL
+        ctx.close()
