@@ -50,11 +50,14 @@ METRIC = "DOF-steps/s"
 UNIT = "DOF-steps/s"
 WORKLOAD = ("3D Euler density wave rho=1+0.2sin(x+y+z), u=(1,1,1), p=1, periodic [0,2pi]^3, 32^3 hexes, p=3 LGL, "
             "10,485,760 unknowns, LF flux, EPI2, dt=0.1, Krylov tol 1e-8")
-# incomplete orthogonalisation over the last 2 basis vectors: on this workload
-# the mixed form's FP64 orthogonalisation passes are FP64-pipe bound, and a
-# shorter window (37 Krylov steps instead of 31) is faster overall
+# incomplete orthogonalisation against the latest basis vector only (window 1):
+# on this workload the mixed form's FP64 orthogonalisation passes are bound by
+# GB300's FP64 pipe, and with window 1 the Krylov dimension hardly grows (37
+# steps against 36 with window 2 and 30 with 4) while each step's two passes
+# read and multiply one slot instead of two or four: 6.5 ms per step against
+# 8.2 (window 2) and 8.8 (window 4), the same error against the FP64 form
 CFG = dict(dim=3, p=3, ne=[32, 32, 32], lo=[0.0] * 3, hi=[2 * math.pi] * 3, eq=2, gamma=1.4, scheme=2,
-           krylov_tol=1e-8, m_max=64, m_step=5, max_substeps=32, iop=2)
+           krylov_tol=1e-8, m_max=64, m_step=5, max_substeps=32, iop=1)
 DT = 0.1
 # The 2D workload of the paper's vortex experiments (second configuration);
 # its vectors stay in L2 and its Arnoldi steps are launch-latency bound, so

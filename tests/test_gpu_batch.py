@@ -184,3 +184,22 @@ def test_bad_configurations_and_pointers_rejected(env):
     dev = torch.from_numpy(q.copy()).cuda()
     assert b.advance([dev], [0.0], 1) == E.EXPDG_EINVAL     # dt must be positive
     b.close()
+
+
+@pytest.mark.parametrize("bc,kappa,prec", [("dirichlet", 0.03, 0), ("periodic", 0.05, 0), ("dirichlet", 0.03, 1)])
+def test_viscous_burgers_resident(env, bc, kappa, prec):
+    """Viscous Burgers (central fluxes for the diffusion, zero Dirichlet ends or
+    periodic; no forcing) through the resident solve against the oracle."""
+    torch, E = env
+    ne, p = 24, 3
+    cfg = E.default_config(eq=1, dim=1, p=p, ne=[ne, 1, 1], lo=[0.0, 0, 0], hi=[1.0, 1, 1], prec=prec, scheme=2,
+                           krylov_tol=1e-10, m_max=40, m_step=5, max_substeps=32, iop=4, kappa=kappa,
+                           bc=E.EXPDG_BC_DIRICHLET if bc == "dirichlet" else E.EXPDG_BC_PERIODIC)
+    mesh = dg.Mesh(dim=1, p=p, ne=(ne,), lo=(0.0,), hi=(1.0,), eq="burgers", kappa=kappa, bc=bc)
+    x = dg.node_coords(mesh)[0]
+    q = np.ascontiguousarray((np.sin(2 * math.pi * x) * (0.5 + x * (1 - x)))[None])
+    got, b, st = run(torch, E, [(cfg, mesh, q)], [2e-3], 3)
+    assert st == E.EXPDG_OK
+    ref, _ = integrators.advance(mesh, q, 2e-3, 3, tol=1e-10, m_max=40, m_step=5, iop=4)
+    assert rel(got[0], ref) <= (TOL_STEP64 if prec == 0 else TOL_MIXED)
+    b.close()

@@ -120,7 +120,7 @@ def test_step_iom_fp64_replayed(E, case, scheme):
 
 
 @pytest.mark.parametrize("prec", MIXED_PRECS)
-@pytest.mark.parametrize("iop", [2, 4])
+@pytest.mark.parametrize("iop", [1, 2, 4])
 @pytest.mark.parametrize("scheme", [2, 3])
 @pytest.mark.parametrize("case", ["burgers1d_p2", "euler2d_p4", "euler3d_p3"])
 def test_step_iom_mixed_within_1e6(E, case, scheme, iop, prec):

@@ -270,9 +270,9 @@ def test_wave3d_full_size_step(E):
     unknowns; the configuration the bench's headline times) against the
     oracle: one EPI2 step of the density wave (dt = 0.1, Krylov tol 1e-8;
     about two minutes of host time for the oracle).  The FP64 form with the
-    oracle's decisions replayed matches it to 1e-11; the mixed and float-float
-    forms (incomplete orthogonalisation over 4 vectors, decisions their own,
-    as timed) to 1e-6.  Every result conserves the cell totals to rounding
+    oracle's decisions replayed matches it to 1e-11; the mixed form
+    (incomplete orthogonalisation over 1, 2 or 4 vectors, decisions its own,
+    as timed) and the float-float form (4 vectors) to 1e-6.  Every result conserves the cell totals to rounding
     (1e-10 relative: sums over 10.5 M unknowns and up to 40 Krylov vectors;
     measured 4e-12) and lies within 5e-6 of the exactly translated wave (the
     spatial error: 2.6e-5 at 8^3 for the oracle, falling 11x per halving of h)."""
@@ -284,7 +284,7 @@ def test_wave3d_full_size_step(E):
     exact = inputs.density_wave(X, 0.1)
     ref, st = integrators.step(mesh, q, 0.1, tol=1e-8)
     assert rel(ref, exact) <= 5e-6
-    for prec, iop in ((0, 0), (1, 4), (2, 4)):
+    for prec, iop in ((0, 0), (1, 1), (1, 2), (1, 4), (2, 4)):
         ctx = E.Context(**c, prec=prec, iop=iop)
         got = q.copy()
         ctx.step(got, 0.1, replay=_replay_from(st) if prec == 0 else None)
