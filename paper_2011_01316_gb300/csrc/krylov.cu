@@ -1287,19 +1287,44 @@ __global__ void __launch_bounds__(NT) k_iom_dots_mx(KState* ks, double* part, Ba
 #pragma unroll
     for (int c = 0; c < KW; ++c) px[c] = ldq<false>(U, lo + (c < nwin ? c : 0), tid);
   griddep_wait();
-  for (size_t g = tid; g < ng; g += nthr) {
-    const float4 wf = __ldg(reinterpret_cast<const float4*>(U.h + (size_t)(j + 1) * ld + 4 * g));
+  const float* __restrict__ wtop = U.h + (size_t)(j + 1) * ld;
+  // quad g's products from its loaded inputs
+  auto body = [&](const float4 wf, const Quad<false>* x) {
     const double w[4] = {f32_to_f64_exact(wf.x), f32_to_f64_exact(wf.y), f32_to_f64_exact(wf.z),
                          f32_to_f64_exact(wf.w)};
 #pragma unroll
-    for (int c = 0; c < KW; ++c) {
-      const Quad<false> x = (g == tid) ? px[c] : ldq<false>(U, lo + (c < nwin ? c : 0), g);
+    for (int c = 0; c < KW; ++c)
       if (c < nwin) {
-        acc[c] = fma(x.v[1], w[1], fma(x.v[0], w[0], acc[c]));
-        acc2[c] = fma(x.v[3], w[3], fma(x.v[2], w[2], acc2[c]));
+        acc[c] = fma(x[c].v[1], w[1], fma(x[c].v[0], w[0], acc[c]));
+        acc2[c] = fma(x[c].v[3], w[3], fma(x[c].v[2], w[2], acc2[c]));
       }
-    }
     wn = fmaf(wf.x, wf.x, fmaf(wf.y, wf.y, fmaf(wf.z, wf.z, fmaf(wf.w, wf.w, wn))));
+  };
+  auto load = [&](size_t g, float4& wf, Quad<false>* x) {
+    wf = __ldg(reinterpret_cast<const float4*>(wtop + 4 * g));
+#pragma unroll
+    for (int c = 0; c < KW; ++c) x[c] = ldq<false>(U, lo + (c < nwin ? c : 0), g);
+  };
+  size_t g = tid;
+  if (g < ng) {  // the first trip (its slots loaded before the wait)
+    body(__ldg(reinterpret_cast<const float4*>(wtop + 4 * g)), px);
+    g += nthr;
+  }
+  if constexpr (KW <= 2) {  // short windows: two trips' loads in flight at once
+    for (; g + nthr < ng; g += 2 * nthr) {
+      float4 wa, wb;
+      Quad<false> xa[KW], xb[KW];
+      load(g, wa, xa);
+      load(g + nthr, wb, xb);
+      body(wa, xa);
+      body(wb, xb);
+    }
+  }
+  for (; g < ng; g += nthr) {
+    float4 wa;
+    Quad<false> xa[KW];
+    load(g, wa, xa);
+    body(wa, xa);
   }
 #pragma unroll
   for (int c = 0; c < KW; ++c) acc[c] += acc2[c];
