@@ -790,6 +790,8 @@ def main():
     ap.add_argument("--burgers-iop", type=int, default=4, help="orthogonalisation window of the Burgers leg (0: full)")
     ap.add_argument("--batch-instances", type=int, default=256, help="instances of the batched workload (0: skip)")
     ap.add_argument("--batch-workers", type=int, default=16, help="instances in flight in the batched workload")
+    ap.add_argument("--vortex-iop", type=int, default=VORTEX["iop"],
+                    help="orthogonalisation window of the 2D vortex, batched and served workloads")
     ap.add_argument("--resident-max", type=int, default=8192,
                     help="batched workload: instances up to this many unknowns run as one resident batch")
     ap.add_argument("--legs", default="main,wave3d_ff,vortex,burgers,exprb32,serving,batched",
@@ -811,6 +813,7 @@ def main():
         return
 
     CFG["iop"] = args.iop
+    VORTEX["iop"] = args.vortex_iop
     import torch
     import torch.distributed as dist
     if world > 1:
