@@ -60,11 +60,12 @@ CFG = dict(dim=3, p=3, ne=[32, 32, 32], lo=[0.0] * 3, hi=[2 * math.pi] * 3, eq=2
            krylov_tol=1e-8, m_max=64, m_step=5, max_substeps=32, iop=1)
 DT = 0.1
 # The 2D workload of the paper's vortex experiments (second configuration);
-# its vectors stay in L2 and its Arnoldi steps are launch-latency bound, so
-# the longer window's smaller Krylov dimension wins there (also for the served
-# and batched solves).
+# its vectors stay in L2 and its Arnoldi steps are latency bound.  Window 1
+# here too: 29 Krylov steps against 27 with window 4, but 0.78 against 0.90 ms
+# per step at the same 1.2e-9 from the FP64 form; the batched and served
+# solves use the same window (batched: 0.77 against 0.87-0.95 s).
 VORTEX = dict(dim=2, p=4, ne=[64, 64, 1], lo=[0.0, 0.0, 0.0], hi=[10.0, 10.0, 1.0], eq=2, gamma=1.4, scheme=2,
-              krylov_tol=1e-8, m_max=64, m_step=5, max_substeps=32, iop=4)
+              krylov_tol=1e-8, m_max=64, m_step=5, max_substeps=32, iop=1)
 VORTEX_DT = 0.05
 CLASSES = ["residual", "jv", "dots", "update", "phi", "combine", "vector"]
 # DFMA throughput of this GPU (FP64 FMA per second over all SMs; 1.6 per SM per
@@ -245,7 +246,7 @@ def oracle_sample_step():
 
 SAMPLE_TEXT = (f"one full oracle EPI2 step per sample of the same density wave on a {SAMPLE_NE}^3 mesh "
                f"(1,310,720 unknowns) with dt={SAMPLE_DT} (the workload's Courant number; the oracle's Krylov "
-               "dimension is 20 there as on the 32^3 workload), tol 1e-8, window 4, numpy FP64, single thread")
+               "dimension is 20 there as on the 32^3 workload), tol 1e-8, window {window}, numpy FP64, single thread")
 
 
 def oracle_other_rates():
@@ -266,10 +267,10 @@ def oracle_other_rates():
     mesh = dg.Mesh(dim=2, p=4, ne=(64, 64), lo=(0.0, 0.0), hi=(10.0, 10.0), eq="euler")
     q = inputs.isentropic_vortex(dg.node_coords(mesh), 0.0).reshape(-1)
     t0 = time.perf_counter()
-    q, _ = integrators.step(mesh, q, VORTEX_DT, tol=1e-8, iop=4)
+    q, _ = integrators.step(mesh, q, VORTEX_DT, tol=1e-8, iop=VORTEX["iop"] or None)
     t = time.perf_counter() - t0
     out["vortex2d_64_p4"] = {"ms_per_step": 1e3 * t, "dof_steps_per_s": mesh.n_unknowns / t,
-                             "sample": "one full EPI2 step (dt 0.05, tol 1e-8, window 4)"}
+                             "sample": f"one full EPI2 step (dt 0.05, tol 1e-8, window {VORTEX['iop']})"}
     return out
 
 
@@ -401,7 +402,8 @@ def vortex_workload(stream, flush, steps=5):
     ref_ctx.step(ref, VORTEX_DT)
     ref_ctx.close()
     timed = step_timer(stream, flush)
-    out = {"workload": "2D Euler isentropic vortex 64x64, p=4 (409,600 unknowns), EPI2 dt=0.05, tol 1e-8, window 4"}
+    out = {"workload": "2D Euler isentropic vortex 64x64, p=4 (409,600 unknowns), EPI2 dt=0.05, tol 1e-8, "
+                       f"window {VORTEX['iop']}"}
     for name, prec in (("mixed", expdg.EXPDG_MIXED), ("float_float", expdg.EXPDG_MIXED_FF)):
         ctx = expdg.Context(**VORTEX, prec=prec)
         ctx.set_stream(stream)
@@ -505,7 +507,7 @@ def exprb32_workload(stream, flush, steps=5):
     ctx.close()
     ctx64.close()
     return {"workload": "2D Euler isentropic vortex 64x64, p=4 (409,600 unknowns), EXPRB32, dt=0.05, tol 1e-8, "
-                        "mixed, window 4",
+                        f"mixed, window {VORTEX['iop']}",
             "ms_per_step": ms, "dof_steps_per_s": n / (ms * 1e-3), "krylov_iters_per_step": statistics.mean(iters),
             "err_vs_fp64_form": err}
 
@@ -570,7 +572,7 @@ def serving_workload(n, seed=1, rate=200.0, workers=8, cpu=False):
         out["cpu_oracle_all_cores"] = {"dof_steps_per_s": rate, "solves_per_s_equiv": rate / per_solve,
                                        "processes": nproc, "wall_s": wall,
                                        "sample": f"{len(jobs)} seeded requests x 2 of their 50 EPI2 steps, FP64 "
-                                                 "oracle (window 4, tol 1e-8), one process per core at once; "
+                                                 f"oracle (window {VORTEX['iop']}, tol 1e-8), one process per core at once; "
                                                  "solves/s = DOF-steps/s / mean DOF-steps of a 50-step request"}
     return out
 
@@ -694,7 +696,7 @@ def batched_workload(n, seed=0, workers=16, steps=20, cpu=False, resident_max=81
         rate, nproc, wall = oracle_concurrent(jobs)
         cpu_all = {"dof_steps_per_s": rate, "processes": nproc, "wall_s": wall,
                    "sample": f"{len(jobs)} seeded instances x 2 of their {steps} EPI2 steps, FP64 "
-                             "oracle (window 4, tol 1e-8), one process per core at once"}
+                             f"oracle (window {VORTEX['iop']}, tol 1e-8), one process per core at once"}
     return {"workload": f"{n} instances (1D Burgers / 2D Euler, p 1..5, uneven sizes), {steps} EPI2 steps each",
             "cpu_oracle_all_cores": cpu_all,
             "concurrent": {"workers": workers, "wall_s": walln, "dof_steps_per_s": dofs / walln},
@@ -772,7 +774,7 @@ def run_reference(args, rank, world):
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
             "data": "synthetic", "config": {"workload": WORKLOAD, "impl": "FP64 CPU oracle (numpy)"},
             "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle",
-                             "sample": SAMPLE_TEXT + f"; Krylov dimensions {sorted(set(ms_used))}"},
+                             "sample": SAMPLE_TEXT.format(window=CFG["iop"]) + f"; Krylov dimensions {sorted(set(ms_used))}"},
             "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
 
@@ -963,7 +965,7 @@ def main():
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         r, tt, ms = oracle_sample_step()
         cpu = {"value": r, "unit": UNIT, "cores": 1, "kind": "oracle",
-               "sample": SAMPLE_TEXT + f" ({tt:.1f} s; Krylov dimension {ms})", "host": host_info(),
+               "sample": SAMPLE_TEXT.format(window=CFG["iop"]) + f" ({tt:.1f} s; Krylov dimension {ms})", "host": host_info(),
                "other_workloads": oracle_other_rates()}
 
     if rank == 0:
