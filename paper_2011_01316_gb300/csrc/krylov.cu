@@ -2009,9 +2009,17 @@ int one_wave(size_t need, size_t smem_max) {
   return (int)std::max<size_t>(std::min(need, (size_t)wave), 1);
 }
 
+// Blocks of the incomplete-orthogonalisation passes: at least IOM_QUADS
+// quads (4 entries) per thread.  Every block of the update sums all the
+// products pass's per-block partials (FP64 additions on GB300's narrow FP64
+// pipe), so on a small problem fewer, fuller blocks halve that work; a large
+// problem fills the wave (red_blocks()) either way.
+constexpr size_t IOM_QUADS = 4;
+inline size_t iom_need(size_t n_aug) { return (n_aug / 4 + NT * IOM_QUADS - 1) / (NT * IOM_QUADS); }
+
 template <int KW>
 int iom_dots_grid(int kf, size_t n_aug) {
-  const size_t need = (n_aug / 4 + NT - 1) / NT;
+  const size_t need = iom_need(n_aug);
   if (kf == KF_FF) return one_wave<k_iom_dots_ff<KW>>(need, 0);
   if (kf == KF_MX) return one_wave<k_iom_dots_mx<KW>>(need, 0);
   return one_wave<k_iom_dots<KW>>(need, 0);
@@ -2037,7 +2045,7 @@ cudaError_t iom_update_configure() {
 }
 template <int KW>
 int iom_update_grid(int kf, size_t n_aug) {
-  const size_t need = (n_aug / 4 + NT - 1) / NT;
+  const size_t need = iom_need(n_aug);
   if (iom_update_configure<KW>() != cudaSuccess) return 1;
   const size_t smem = iom_update_smem_max<KW>();
   if (kf == KF_FF) return one_wave<k_iom_update_ff<KW>>(need, smem);
