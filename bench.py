@@ -80,9 +80,10 @@ FP64_FMA_PER_S = 0.5015e12
 # they were taken from (a record whose sources have changed since is not used)
 TRAFFIC_FILE = os.path.join(ROOT, "profiles", "dram_traffic.json")
 # The CPU oracle's bounded sample of the workload: the same density wave on a
-# 16^3 mesh with dt = 0.2 (the same Courant number and element resolution per
-# wavelength halved; the oracle's Krylov dimension is 20 there as on 32^3 with
-# dt = 0.1), one full EPI2 step of 1,310,720 unknowns per sample.
+# 16^3 mesh with dt = 0.2 (the same Courant number, the element resolution per
+# wavelength halved; with window 1 the oracle's Krylov dimension there is 35,
+# the 32^3 workload's 36 on the GPU), one full EPI2 step of 1,310,720 unknowns
+# per sample.
 SAMPLE_NE, SAMPLE_DT = 16, 0.2
 SAMPLE_N = 5 * 64 * SAMPLE_NE ** 3
 
@@ -249,8 +250,8 @@ def oracle_sample_step():
 
 
 SAMPLE_TEXT = (f"one full oracle EPI2 step per sample of the same density wave on a {SAMPLE_NE}^3 mesh "
-               f"(1,310,720 unknowns) with dt={SAMPLE_DT} (the workload's Courant number; the oracle's Krylov "
-               "dimension is 20 there as on the 32^3 workload), tol 1e-8, window {window}, numpy FP64, single thread")
+               f"(1,310,720 unknowns) with dt={SAMPLE_DT} (the workload's Courant number, so about the 32^3 "
+               "workload's Krylov dimension), tol 1e-8, window {window}, numpy FP64, single thread")
 
 
 def oracle_other_rates():
