@@ -229,7 +229,7 @@ expdg_status expdg_jv(expdg_ctx* ctx, const double* qt, const double* v, double*
  * check's).  If replay != NULL, the nreplay
  * records (all with solve == 0) are followed instead of deciding; otherwise,
  * if trace != NULL, up to trace_cap accepted sub-steps are written there and
- * *ntrace is set. */
+ * *ntrace is set.  EXPDG_EINVAL for a tau that is not finite. */
 expdg_status expdg_phi(expdg_ctx* ctx, const double* qt, double tau, const double* const* c, int P,
                        double* out, expdg_stats* stats,
                        const expdg_trace_entry* replay, int nreplay,
@@ -245,14 +245,16 @@ expdg_status expdg_phi(expdg_ctx* ctx, const double* qt, double tau, const doubl
  * else max(m_step, m_prev - m_step)) so that a falling m is found
  * (steps in a row need similar m; starting later can only give a more
  * accurate result).  Then m_prev itself, with paired checks (above) m_prev + 2
- * and m_prev + 4, and the multiples of m_step. */
+ * and m_prev + 4, and the multiples of m_step.  EXPDG_EINVAL (q untouched)
+ * unless dt is finite and > 0. */
 expdg_status expdg_step(expdg_ctx* ctx, double* q, double dt, expdg_stats* stats,
                         const expdg_trace_entry* replay, int nreplay,
                         expdg_trace_entry* trace, int trace_cap, int* ntrace);
 
 /* nsteps steps of size dt (in place); stats accumulate over the steps.  The
  * check-start memory of expdg_step is cleared first, so the result depends only
- * on the arguments (not on earlier calls on the context). */
+ * on the arguments (not on earlier calls on the context).  EXPDG_EINVAL (q
+ * untouched) unless dt is finite and > 0 and nsteps >= 0. */
 expdg_status expdg_advance(expdg_ctx* ctx, double* q, double dt, int nsteps, expdg_stats* stats);
 
 /* Kernel classes of the hot path, for profiling. */
@@ -312,7 +314,8 @@ expdg_status expdg_server_create(const expdg_server_config* cfg, expdg_server** 
 void expdg_server_destroy(expdg_server* s);
 /* Queue nsteps steps of size dt of configuration cfg from host state q0 (copied
  * before returning).  Non-blocking.  EXPDG_ENOMEM if the context can never fit
- * the budget, EXPDG_EINVAL for a bad configuration. */
+ * the budget, EXPDG_EINVAL for a bad configuration or a dt that is not finite
+ * and > 0. */
 expdg_status expdg_server_submit(expdg_server* s, const expdg_config* cfg, const double* q0, double dt, int nsteps,
                                  int64_t* id);
 /* Non-blocking: ids (up to cap) of solves finished since the last poll. */

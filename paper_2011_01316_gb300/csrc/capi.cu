@@ -1125,6 +1125,7 @@ expdg_status expdg_phi(expdg_ctx* ctx, const double* qt, double tau, const doubl
                        expdg_stats* stats, const expdg_trace_entry* replay, int nreplay, expdg_trace_entry* trace,
                        int trace_cap, int* ntrace) {
   if (!ctx || !qt || !out || P < 0 || P > EXPDG_MAX_PHI) return fail(ctx, EXPDG_EINVAL, "bad argument");
+  if (!std::isfinite(tau)) return fail(ctx, EXPDG_EINVAL, "tau must be finite");
   if (check_ptrs(ctx, {qt, out}) != EXPDG_OK) return EXPDG_EINVAL;
   for (int i = 0; c && i <= P; ++i)
     if (check_ptrs(ctx, {c[i]}) != EXPDG_OK) return EXPDG_EINVAL;
@@ -1166,6 +1167,7 @@ expdg_status expdg_phi(expdg_ctx* ctx, const double* qt, double tau, const doubl
 expdg_status expdg_step(expdg_ctx* ctx, double* q, double dt, expdg_stats* stats, const expdg_trace_entry* replay,
                         int nreplay, expdg_trace_entry* trace, int trace_cap, int* ntrace) {
   if (!ctx || !q) return fail(ctx, EXPDG_EINVAL, "null argument");
+  if (!(dt > 0.0) || !std::isfinite(dt)) return fail(ctx, EXPDG_EINVAL, "the step size must be finite and > 0");
   if (check_ptrs(ctx, {q}) != EXPDG_OK) return EXPDG_EINVAL;
   const size_t N = ctx->N;
   const bool qdev = is_device_ptr(ctx, q);
@@ -1188,6 +1190,7 @@ expdg_status expdg_step(expdg_ctx* ctx, double* q, double dt, expdg_stats* stats
 
 expdg_status expdg_advance(expdg_ctx* ctx, double* q, double dt, int nsteps, expdg_stats* stats) {
   if (!ctx || !q || nsteps < 0) return fail(ctx, EXPDG_EINVAL, "bad argument");
+  if (!(dt > 0.0) || !std::isfinite(dt)) return fail(ctx, EXPDG_EINVAL, "the step size must be finite and > 0");
   if (check_ptrs(ctx, {q}) != EXPDG_OK) return EXPDG_EINVAL;
   const size_t N = ctx->N;
   const bool qdev = is_device_ptr(ctx, q);

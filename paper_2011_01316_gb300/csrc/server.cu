@@ -11,6 +11,7 @@
 // allocation; idle contexts are released when the budget needs room.
 #include <algorithm>
 #include <chrono>
+#include <cmath>
 #include <condition_variable>
 #include <cstring>
 #include <deque>
@@ -204,6 +205,7 @@ void expdg_server_destroy(expdg_server* s) {
 expdg_status expdg_server_submit(expdg_server* s, const expdg_config* cfg, const double* q0, double dt, int nsteps,
                                  int64_t* id) {
   if (!s || !cfg || !q0 || !id || nsteps < 0) return EXPDG_EINVAL;
+  if (!(dt > 0.0) || !std::isfinite(dt)) return EXPDG_EINVAL;
   const size_t bytes = expdg_context_bytes(cfg);
   if (bytes == 0) return EXPDG_EINVAL;
   if (bytes > s->budget) return EXPDG_ENOMEM;

@@ -309,6 +309,44 @@ def test_nonphysical_state_reported(E):
     assert ei.value.status == E.EXPDG_ENONPHYSICAL
 
 
+def test_invalid_step_sizes_rejected(E):
+    """The step size must be finite and > 0 (expdg_step, expdg_advance) and
+    tau finite (expdg_phi): EXPDG_EINVAL, the state untouched."""
+    ctx, mesh = make(E, "euler2d_p1")
+    q = np.ascontiguousarray(state(mesh, np.random.default_rng(16)))
+    for dt in (0.0, -0.05, float("nan"), float("inf")):
+        for advance in (False, True):
+            x = q.copy()
+            with pytest.raises(E.ExpdgError) as ei:
+                ctx.advance(x, dt, 2) if advance else ctx.step(x, dt)
+            assert ei.value.status == E.EXPDG_EINVAL
+            np.testing.assert_array_equal(x, q)
+    with pytest.raises(E.ExpdgError) as ei:
+        ctx.phi(q, float("nan"), [q])
+    assert ei.value.status == E.EXPDG_EINVAL
+
+
+@pytest.mark.parametrize("prec", PRECS)
+@pytest.mark.parametrize("case", ["burgers1d_p2", "euler2d_p4", "euler3d_p3"])
+def test_free_stream_step(E, case, prec):
+    """A constant state is a steady solution of the periodic problem: every
+    face jump vanishes and the rows of the LGL derivative matrix sum to zero,
+    so R(q) is rounding only and one step changes q by rounding only."""
+    ctx, mesh = make(E, case, prec=prec)
+    q = np.ascontiguousarray(state(mesh, np.random.default_rng(17)))
+    if mesh.eq == "burgers":
+        q[0] = 0.7
+    else:
+        rho, u, p = 1.2, (0.3, -0.2, 0.1)[:mesh.dim], 0.9
+        q[0] = rho
+        for k in range(mesh.dim):
+            q[1 + k] = rho * u[k]
+        q[mesh.dim + 1] = p / 0.4 + 0.5 * rho * sum(x * x for x in u)
+    got = q.copy()
+    ctx.step(got, 0.05)
+    assert np.max(np.abs(got - q)) <= 1e-12 * np.max(np.abs(q))
+
+
 def test_invalid_configs_rejected(E):
     for bad in (dict(p=0), dict(p=99), dict(dim=4), dict(eq=1, dim=2), dict(m_max=65), dict(krylov_tol=0.0)):
         with pytest.raises(E.ExpdgError) as ei:
