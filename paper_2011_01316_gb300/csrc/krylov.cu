@@ -126,6 +126,31 @@ __device__ void block_sum(const typename Acc<FF>::T (&v)[K], typename Acc<FF>::T
   __syncthreads();
 }
 
+// FP64 block sums for kernels whose main loop is bound by GB300's narrow FP64
+// pipe, where an FP64 warp instruction costs the same whatever its active
+// lanes: every thread's values go to shared memory and one warp adds them
+// (NW - 1 additions a lane, then a five-step shuffle tree a value), instead of
+// a shuffle tree in every warp (5 K FP64 warp instructions a warp).
+template <int K>
+__device__ void block_sum_1w(const double (&v)[K], double* sh /* [K][NT] */, double* tot /* [K] */) {
+#pragma unroll
+  for (int k = 0; k < K; ++k) sh[k * NT + threadIdx.x] = v[k];
+  __syncthreads();
+  if (threadIdx.x < 32) {
+    const int lane = threadIdx.x;
+#pragma unroll
+    for (int k = 0; k < K; ++k) {
+      double x = sh[k * NT + lane];
+#pragma unroll
+      for (int w = 1; w < NW; ++w) x += sh[k * NT + w * 32 + lane];
+#pragma unroll
+      for (int off = 16; off > 0; off >>= 1) x += __shfl_down_sync(0xffffffffu, x, off);
+      if (lane == 0) tot[k] = x;
+    }
+  }
+  __syncthreads();
+}
+
 // Element i of basis vector k.
 template <bool FF>
 __device__ __forceinline__ typename Acc<FF>::T ldb(const Basis& U, int k, size_t i) {
@@ -1271,7 +1296,7 @@ template <int KW>
 __global__ void __launch_bounds__(NT) k_iom_dots_mx(KState* ks, double* part, Basis U, int j, size_t N,
                                                     size_t n_aug) {
   constexpr int K = KW + 1;
-  __shared__ double sh[NW * K];
+  __shared__ double sh[K * NT];
   __shared__ double tot[K];
   const int lo = max(0, j - KW + 1), nwin = j - lo + 1;
   double acc[KW], acc2[KW];  // two chains a slot (more FP64 operations in flight)
@@ -1339,7 +1364,7 @@ __global__ void __launch_bounds__(NT) k_iom_dots_mx(KState* ks, double* part, Ba
 #pragma unroll
   for (int c = 0; c < KW; ++c) v[c] = acc[c];
   v[KW] = (double)wn + wnt;
-  block_sum<false, K>(v, sh, tot);
+  block_sum_1w<K>(v, sh, tot);
   const int G = gridDim.x;
   if (threadIdx.x < K) part[(size_t)threadIdx.x * G + blockIdx.x] = tot[threadIdx.x];
   griddep_launch();
@@ -1349,7 +1374,7 @@ template <int KW>
 __global__ void __launch_bounds__(NT) k_iom_update_mx(KState* ks, double* part, Basis U, int j, size_t N,
                                                       size_t n_aug, int Gd) {
   __shared__ double cf[IOP_MAX];
-  __shared__ double sh[NW];
+  __shared__ double sh[NT];
   __shared__ double tot[1];
   __shared__ double cj;
   const int lo = max(0, j - KW + 1), nwin = j - lo + 1;
@@ -1427,7 +1452,7 @@ __global__ void __launch_bounds__(NT) k_iom_update_mx(KState* ks, double* part, 
     if (i < N) Uh[(size_t)(j + 1) * ld + i] = f64_to_f32_rn(w);
     nrm[0] = fma(w, w, nrm[0]);
   }
-  block_sum<false, 1>(nrm, sh, tot);
+  block_sum_1w<1>(nrm, sh, tot);
   if (threadIdx.x == 0) part[IOM_UPD_OFF + (j & 1) * RB_MAX + blockIdx.x] = tot[0];
   griddep_launch();
 }
